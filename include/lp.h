@@ -1,0 +1,184 @@
+/*
+ * lp.h -- C ABI of liblp: the fixpoint of the immediate-consequence operator of a logic
+ * program in sparse-matrix form, v_{k+1} = theta(M_P v_k), on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Nguyen, Inoue, Sakama, "Enhancing Linear Algebraic Computation of Logic Programs
+ * Using Sparse Representation" (ICLP 2020). Section, definition and algorithm numbers below
+ * refer to that paper.
+ *
+ * Conventions shared by every call
+ *  - Bit vectors are arrays of uint64_t words, little-endian bit order: item i is bit (i % 64)
+ *    of word (i / 64). Bits past the last item of the last word are written as 0 and ignored
+ *    on input.
+ *  - Pointers named *_dev or documented as "device or host" may be device memory (cudaMalloc,
+ *    torch tensors) or host memory (pageable or pinned); liblp asks the CUDA runtime which one
+ *    and stages host buffers through device memory it owns. Host buffers make the call
+ *    synchronous.
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream). Device work of a call is
+ *    ordered on that stream.
+ *  - Ownership: the caller owns every buffer it passes; liblp owns the lp_program handle and all
+ *    device memory behind it (the program matrix and solver scratch), released by lp_free.
+ *  - Errors: every call returns an lp_status; nothing is thrown across the ABI. The message of
+ *    the last error of the calling thread is returned by lp_last_error().
+ *  - A program handle must not be used by two calls at the same time (its scratch is shared).
+ */
+#ifndef LP_H
+#define LP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lp_program lp_program;
+
+typedef enum {
+  LP_OK = 0,
+  LP_ERR_INVALID = 1,           /* malformed input or unsupported argument           */
+  LP_ERR_OOM = 2,               /* device or host allocation failed                   */
+  LP_ERR_CUDA = 3,              /* a CUDA runtime call failed                         */
+  LP_ERR_NO_FIXPOINT = 4,       /* max_iters theta applications without u == v        */
+  LP_ERR_TOO_MANY_GUESSES = 5,  /* guess count or k beyond what the call supports     */
+  LP_ERR_TIMEOUT = 6            /* a bounded device-side wait gave up (kernel aborted) */
+} lp_status;
+
+/* lp_compile flags */
+#define LP_COMPILE_HOST_ONLY 1u /* build M_P on the host only (no GPU needed): the handle then
+                                   serves lp_program_info and lp_export_matrix only          */
+
+/* lp_least_model flags */
+#define LP_ROWS 1u   /* init/out are over all n' rows of M_P in canonical order (see below)   */
+#define LP_TIMING 2u /* record CUDA events around the fixpoint kernel (lp_last_solve_stats)   */
+
+typedef struct {
+  int64_t n_atoms;      /* n = |B_P|, original atoms                                        */
+  int64_t n_rules;      /* rules given to lp_compile                                        */
+  int64_t n_prime;      /* n' = rows (and columns) of M_P                                    */
+  int64_t nnz;          /* stored entries of M_P                                             */
+  int64_t n_barred;     /* distinct negated atoms q (one barred atom q-bar each, Eq. 4)      */
+  int64_t n_aux;        /* new atoms introduced by standardization (Sec. 2.1)               */
+  int64_t k;            /* guessed barred atoms: negated atoms that are not facts (Def. 8)   */
+  int64_t n_fact_rows;  /* rows a_ii = 1 of Def. 2 item 3                                    */
+  int64_t n_and_rows;   /* rows of single rules (Def. 2 item 1)                              */
+  int64_t n_or_rows;    /* rows of OR-rules (Def. 2 item 2)                                  */
+  int64_t device_bytes; /* device memory held by the handle right now                         */
+  int64_t upload_bytes; /* bytes lp_compile copied host -> device                            */
+  double compile_ms;    /* host time of lp_compile (standardize, order, CSR, upload)         */
+} lp_info;
+
+typedef struct {
+  int32_t iters;         /* theta applications of the last solve (the last shows no change)  */
+  int32_t status;        /* lp_status of the last solve as written by the device             */
+  float kernel_ms;       /* duration of the fixpoint kernel (LP_TIMING), else -1            */
+  int64_t launches;      /* kernels launched by the last call                                 */
+  int64_t tiles;         /* stable models: column tiles processed                            */
+  int64_t tile_words;    /* stable models: 64-bit guess words per tile                       */
+  int64_t max_tile_iters;/* stable models: largest per-tile iteration count                  */
+  int64_t sum_tile_iters;/* stable models: sum of per-tile iteration counts                  */
+} lp_solve_stats;
+
+/*
+ * lp_compile -- build the program matrix M_P of a (normal) logic program.
+ *
+ * Sec. 2.1 and Sec. 2.2: the literal "not q" becomes the new atom q-bar (positive form, Eq. 4);
+ * each body is taken as a set (the paper assumes distinct body atoms); a head with k >= 2 rules
+ * is standardized into the OR-rule h <- b_1 | ... | b_k plus one new atom b_i <- body(r_i) per
+ * rule, and a head with one rule keeps it (the result is singly-defined, Def. 1). M_P follows
+ * Def. 2 (a_ij = 1/m for a rule with m body atoms, 1 for an OR-rule, a_ii = 1 for a fact) and
+ * Def. 7 (a_ii = 1 and nothing else on a barred row); it is stored as CSR (Sec. 3.2) with the
+ * values implicit: a row's threshold is its body size for a rule and 1 for an OR-rule or a
+ * self-loop, which is theta(sum_j a_ij v_j) of Def. 5 evaluated exactly in integers.
+ *
+ * Canonical atom order (used by LP_ROWS and lp_export_matrix): the n original atoms, then one
+ * barred atom per negated atom by ascending atom id, then the new atoms in rule order. The
+ * device copy is stored in an internal order of liblp's choosing; results come back in the
+ * original (or canonical) order.
+ *
+ * Arguments (host arrays, read only, copied): n_atoms >= 0; rules r in [0, n_rules) have
+ * head[r] in [0, n_atoms) and body literals body_atom[body_off[r] .. body_off[r+1]) with
+ * body_off[0] = 0 and body_off non-decreasing; body_neg (nullable) marks negated literals with
+ * a non-zero byte. An empty body is a fact. n_prime and nnz must stay below 2^31.
+ * flags: 0, or LP_COMPILE_HOST_ONLY (no device memory is touched; solves on such a handle return
+ * LP_ERR_INVALID). cuda_stream: stream of the uploads. On success *out receives a new
+ * handle (free it with lp_free). Errors: LP_ERR_INVALID (malformed program), LP_ERR_OOM,
+ * LP_ERR_CUDA; *out is then NULL.
+ */
+lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, const int64_t* body_off,
+                     const int32_t* body_atom, const uint8_t* body_neg, uint32_t flags, void* cuda_stream,
+                     lp_program** out);
+
+/* Sizes and statistics of a compiled program (host struct, written on success). */
+lp_status lp_program_info(const lp_program* prog, lp_info* out);
+
+/*
+ * lp_least_model -- Algorithm 1: v = v0; u = theta(M_P v); while u != v: v = u; u = theta(M_P v).
+ *
+ * Default mode: init (device or host, ceil(n/64) words, nullable) selects original atoms whose
+ * facts enter the initial vector of Def. 4; NULL selects every fact. init must be a subset of
+ * the atoms that have a fact rule, else LP_ERR_INVALID (checked on the device). Because every
+ * fact row and barred row is a self-loop, the iterates grow monotonically and reach the least
+ * model of the program restricted to the selected facts (negated literals count as false: the
+ * barred atoms start at 0). out (device or host, ceil(n/64) words) receives the fixpoint over
+ * the n original atoms in their original order.
+ * LP_ROWS: init (required) and out are ceil(n'/64) words over all n' rows in canonical order;
+ * any initial vector is accepted and Algorithm 1 is run literally, so the loop may not
+ * converge.
+ * max_iters >= 1 bounds the theta applications; reaching it with u != v returns
+ * LP_ERR_NO_FIXPOINT (out then holds the last iterate). iters_out (host, nullable) receives
+ * the number of theta applications, the last of which showed no change; a non-NULL iters_out
+ * or a host buffer makes the call wait for the device and report device-side errors
+ * (LP_ERR_INVALID for a bad init, LP_ERR_NO_FIXPOINT, LP_ERR_TIMEOUT). Otherwise the call
+ * returns after enqueueing the work and lp_last_solve_stats reports the device status later.
+ */
+lp_status lp_least_model(lp_program* prog, const uint64_t* init, uint64_t* out, int32_t max_iters,
+                         uint32_t flags, int32_t* iters_out, void* cuda_stream);
+
+/*
+ * lp_stable_models -- Algorithms 2 and 3 over a batch of guesses (Def. 8 initial matrix).
+ *
+ * A guess is a k-bit word (k from lp_info): bit j is the initial value of the j-th guessed
+ * barred atom (the negated atoms that are not facts, by ascending atom id); 1 means "q is
+ * assumed false". Barred atoms of facts start at 0 (Def. 8 item 3) and fact rows at 1.
+ * guesses (device or host, n_guesses words) lists the guesses; NULL means all 2^k guesses in
+ * order g = 0 .. 2^k - 1 (then n_guesses must equal 2^k, k <= 40). Every column is iterated
+ * M_{k+1} = theta(M_P M_k) to its fixpoint and kept iff a_q + a_q-bar = 1 for every negated
+ * atom q (Algorithm 3; each rejected column is skipped, the others are all returned).
+ * stable_mask (device or host, ceil(n_guesses/64) words): bit g set iff guess g gives a stable
+ * model. models (device or host, nullable): max_models rows of ceil(n/64) words; row s gets the
+ * s-th stable model in guess order over the n original atoms. n_stable_out (host, nullable):
+ * number of stable guesses (may exceed max_models); a non-NULL n_stable_out makes the call wait.
+ * max_iters bounds each column tile's theta applications (LP_ERR_NO_FIXPOINT otherwise).
+ */
+lp_status lp_stable_models(lp_program* prog, const uint64_t* guesses, int64_t n_guesses,
+                           uint64_t* stable_mask, uint64_t* models, int64_t max_models,
+                           int64_t* n_stable_out, int32_t max_iters, void* cuda_stream);
+
+/* Statistics and device status of the last solve on this handle; waits for cuda_stream. */
+lp_status lp_last_solve_stats(lp_program* prog, lp_solve_stats* out, void* cuda_stream);
+
+/*
+ * lp_export_matrix -- the compiled M_P in canonical order, as the CSR of Sec. 3.2, for
+ * checking lp_compile. Host arrays: row_ptr (n'+1), col (nnz), threshold (n'): the number of
+ * body atoms of a rule row (its entries are 1/threshold), 1 for an OR-rule or a self-loop,
+ * 0 for an empty row. kind (n', nullable): 0 empty, 1 rule, 2 OR-rule, 3 fact, 4 barred.
+ * Within a row the columns are ascending.
+ */
+lp_status lp_export_matrix(const lp_program* prog, int64_t* row_ptr, int64_t* col, int32_t* threshold,
+                           int8_t* kind, void* cuda_stream);
+
+/* Release a handle and its device memory (NULL is a no-op). Waits for no stream: the caller
+ * must make sure no enqueued work still uses it. */
+void lp_free(lp_program* prog);
+
+/* Message of the last failed call on this thread ("" if none). Valid until the next call. */
+const char* lp_last_error(void);
+
+/* Number of kernels liblp has launched in this process (all handles). */
+int64_t lp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP_H */

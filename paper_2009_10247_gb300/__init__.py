@@ -1,0 +1,12 @@
+"""GB300-native sparse-matrix fixpoint of logic programs (liblp + Python binding).
+
+The compute path is liblp.so (CUDA for sm_103a, C ABI in include/lp.h); this package only
+loads it and marshals arguments. Nothing here falls back to a CPU implementation.
+"""
+from .lp import (EXPORTS, LP_ROWS, LP_TIMING, LPError, Program, launch_count, library_path,  # noqa: F401
+                 load, words)
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)

@@ -1,0 +1,522 @@
+// api.cu -- the extern "C" entry points of liblp (declared and documented in include/lp.h).
+//
+// Owns the program handle: the device copy of M_P in the internal layout built by
+// compile_host, the per-handle solver scratch (iterate vectors, tile buffers, control block),
+// and the staging buffers used when a caller passes host memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+#include "kernels.h"
+
+namespace lp {
+
+static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+}  // namespace lp
+
+using namespace lp;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct lp_program {
+  HostMatrix hm;  // metadata (row_ptr/col host copies are dropped after upload)
+  int device = 0;
+  int sm_count = 0;
+  // device copy of the matrix and its tables
+  int32_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  uint32_t* any_mask = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* inv = nullptr;  // internal -> canonical, uploaded on first LP_ROWS call
+  int32_t* fact_row = nullptr;
+  int32_t* fact_owner = nullptr;
+  uint64_t* fact_mask = nullptr;
+  int32_t* neg_row = nullptr;
+  int32_t* bar_row = nullptr;
+  int32_t* row_tag = nullptr;
+  // scratch
+  uint32_t* x[2] = {nullptr, nullptr};
+  DeviceCtl* ctl = nullptr;
+  DeviceCtl* h_ctl = nullptr;  // pinned mirror of ctl
+  DevBuf tiles;                // stable-model iterate buffers
+  DevBuf stage_in, stage_out, stage_out2;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  int64_t last_launches = 0;
+  int64_t tile_words = 0;
+  int64_t device_bytes = 0;
+  int64_t upload_bytes = 0;
+  double compile_ms = 0.0;
+  bool host_only = false;  // LP_COMPILE_HOST_ONLY: host arrays kept, nothing on the device
+};
+
+namespace {
+
+lp_status fail(lp_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+lp_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(LP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LP_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <typename T>
+lp_status dalloc(lp_program* p, T** ptr, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  p->device_bytes += (int64_t)bytes;
+  return LP_OK;
+}
+
+template <typename T>
+lp_status upload(lp_program* p, T** ptr, const std::vector<T>& v, cudaStream_t s) {
+  lp_status st = dalloc(p, ptr, v.size());
+  if (st != LP_OK) return st;
+  if (!v.empty()) {
+    LP_CUDA(cudaMemcpyAsync(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    p->upload_bytes += (int64_t)(v.size() * sizeof(T));
+  }
+  return LP_OK;
+}
+
+lp_status ensure(lp_program* p, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return LP_OK;
+  if (b.p) {
+    cudaFree(b.p);
+    p->device_bytes -= (int64_t)b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  b.bytes = std::max<size_t>(bytes, 16);
+  p->device_bytes += (int64_t)b.bytes;
+  return LP_OK;
+}
+
+// true if ptr is device-accessible memory (device or managed), false for host memory.
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+lp_status ensure_scratch(lp_program* p) {
+  if (!p->ctl) {
+    lp_status st = dalloc(p, &p->ctl, 1);
+    if (st != LP_OK) return st;
+    LP_CUDA(cudaMallocHost((void**)&p->h_ctl, sizeof(DeviceCtl)));
+    std::memset(p->h_ctl, 0, sizeof(DeviceCtl));
+  }
+  if (!p->ev0) {
+    LP_CUDA(cudaEventCreate(&p->ev0));
+    LP_CUDA(cudaEventCreate(&p->ev1));
+  }
+  return LP_OK;
+}
+
+void release(lp_program* p) {
+  void* ptrs[] = {p->row_ptr, p->col, p->any_mask, p->perm, p->inv, p->fact_row, p->fact_owner, p->fact_mask,
+                  p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
+                  p->stage_out.p, p->stage_out2.p};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->h_ctl) cudaFreeHost(p->h_ctl);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+}
+
+lp_status launch_count_and_check(cudaError_t e, const char* what, lp_program* p) {
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  g_launches.fetch_add(1);
+  p->last_launches++;
+  return LP_OK;
+}
+
+// Waits for the stream and turns the device status into the call's status.
+lp_status finish_sync(lp_program* p, cudaStream_t s) {
+  LP_CUDA(cudaStreamSynchronize(s));
+  const int st = p->h_ctl->status;
+  if (st == LP_ERR_INVALID) return fail(LP_ERR_INVALID, "initial vector selects an atom without a fact rule");
+  if (st == LP_ERR_NO_FIXPOINT) return fail(LP_ERR_NO_FIXPOINT, "no fixpoint within max_iters");
+  if (st == LP_ERR_TIMEOUT) return fail(LP_ERR_TIMEOUT, "a grid barrier wait timed out; kernel aborted");
+  if (st != 0) return fail(LP_ERR_CUDA, "device reported status " + std::to_string(st));
+  return LP_OK;
+}
+
+int max_coresident(lp_program* p, int per_sm) { return std::max(1, per_sm) * p->sm_count; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lp_last_error(void) { return g_err.c_str(); }
+
+int64_t lp_launch_count(void) { return g_launches.load(); }
+
+lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, const int64_t* body_off,
+                     const int32_t* body_atom, const uint8_t* body_neg, uint32_t flags, void* cuda_stream,
+                     lp_program** out) {
+  if (!out) return fail(LP_ERR_INVALID, "out must not be NULL");
+  *out = nullptr;
+  if (flags & ~LP_COMPILE_HOST_ONLY) return fail(LP_ERR_INVALID, "unknown flags");
+  auto t0 = std::chrono::steady_clock::now();
+  lp_program* p = new (std::nothrow) lp_program();
+  if (!p) return fail(LP_ERR_OOM, "host allocation failed");
+  std::string err;
+  lp_status st = compile_host(n_atoms, n_rules, head, body_off, body_atom, body_neg, p->hm, err);
+  if (st != LP_OK) {
+    delete p;
+    return fail(st, err);
+  }
+  if (flags & LP_COMPILE_HOST_ONLY) {
+    p->host_only = true;
+    p->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return LP_OK;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  auto cleanup = [&](lp_status code) {
+    release(p);
+    delete p;
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaGetDevice/attribute"));
+  HostMatrix& hm = p->hm;
+  if ((st = upload(p, &p->row_ptr, hm.row_ptr, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->col, hm.col, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->any_mask, hm.any_mask, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->perm, hm.perm, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->fact_row, hm.fact_row, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->fact_owner, hm.fact_owner, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->fact_mask, hm.fact_mask, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->neg_row, hm.neg_row, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->bar_row, hm.bar_row, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->row_tag, hm.row_tag, s)) != LP_OK) return cleanup(st);
+  if ((st = dalloc(p, &p->x[0], (size_t)hm.n_pad / 32)) != LP_OK) return cleanup(st);
+  if ((st = dalloc(p, &p->x[1], (size_t)hm.n_pad / 32)) != LP_OK) return cleanup(st);
+  if ((st = ensure_scratch(p)) != LP_OK) return cleanup(st);
+  e = cudaStreamSynchronize(s);  // host vectors are pageable and about to be released
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "upload"));
+  std::vector<int32_t>().swap(hm.row_ptr);
+  std::vector<int32_t>().swap(hm.col);
+  std::vector<int32_t>().swap(hm.row_tag);
+  p->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return LP_OK;
+}
+
+lp_status lp_program_info(const lp_program* p, lp_info* out) {
+  if (!p || !out) return fail(LP_ERR_INVALID, "NULL argument");
+  const HostMatrix& hm = p->hm;
+  out->n_atoms = hm.n;
+  out->n_rules = hm.n_rules;
+  out->n_prime = hm.n_prime;
+  out->nnz = hm.nnz;
+  out->n_barred = hm.n_barred;
+  out->n_aux = hm.n_aux;
+  out->k = hm.k;
+  out->n_fact_rows = hm.n_fact_rows;
+  out->n_and_rows = hm.n_rule_rows;
+  out->n_or_rows = hm.n_or_rows;
+  out->device_bytes = p->device_bytes;
+  out->upload_bytes = p->upload_bytes;
+  out->compile_ms = p->compile_ms;
+  return LP_OK;
+}
+
+lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int32_t max_iters, uint32_t flags,
+                         int32_t* iters_out, void* cuda_stream) {
+  if (!p || !out) return fail(LP_ERR_INVALID, "program and out must not be NULL");
+  if (p->host_only) return fail(LP_ERR_INVALID, "program was compiled with LP_COMPILE_HOST_ONLY");
+  if (max_iters < 1) return fail(LP_ERR_INVALID, "max_iters must be >= 1");
+  if (flags & ~(LP_ROWS | LP_TIMING)) return fail(LP_ERR_INVALID, "unknown flags");
+  const bool rows = flags & LP_ROWS;
+  if (rows && !init) return fail(LP_ERR_INVALID, "LP_ROWS needs an initial vector");
+  const HostMatrix& hm = p->hm;
+  // From a vector of facts the iterates only grow, so n' + 1 applications always suffice.
+  if (!rows) max_iters = (int32_t)std::min<int64_t>(max_iters, (int64_t)hm.n_prime + 2);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  p->last_launches = 0;
+  p->timed = flags & LP_TIMING;
+  lp_status st = ensure_scratch(p);
+  if (st != LP_OK) return st;
+  const int32_t n_in = rows ? hm.n_prime : hm.n;
+  const size_t in_words = ((size_t)n_in + 63) / 64;
+  const size_t out_words = in_words;
+
+  if (rows && !p->inv) {
+    std::vector<int32_t> inv(std::max(hm.n_pad, 1), 0);
+    for (int32_t c = 0; c < hm.n_prime; c++) inv[hm.perm[c]] = c;
+    if ((st = upload(p, &p->inv, inv, s)) != LP_OK) return st;
+    LP_CUDA(cudaStreamSynchronize(s));
+  }
+  const bool host_in = init && !is_device_ptr(init);
+  const bool host_out = !is_device_ptr(out);
+  const uint64_t* d_init = init;
+  uint64_t* d_out = out;
+  if (host_in) {
+    if ((st = ensure(p, p->stage_in, in_words * 8)) != LP_OK) return st;
+    LP_CUDA(cudaMemcpyAsync(p->stage_in.p, init, in_words * 8, cudaMemcpyHostToDevice, s));
+    d_init = (const uint64_t*)p->stage_in.p;
+  }
+  if (host_out) {
+    if ((st = ensure(p, p->stage_out, out_words * 8)) != LP_OK) return st;
+    d_out = (uint64_t*)p->stage_out.p;
+  }
+
+  LP_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(DeviceCtl), s));
+  if (!rows) LP_CUDA(cudaMemsetAsync(p->x[0], 0, (size_t)hm.n_pad / 8, s));
+
+  FixArgs a{};
+  a.row_ptr = p->row_ptr;
+  a.col = p->col;
+  a.any_mask = p->any_mask;
+  a.x0 = p->x[0];
+  a.x1 = p->x[1];
+  a.n_words = hm.n_pad / 32;
+  a.max_iters = max_iters;
+  a.ctl = p->ctl;
+  a.init = rows ? nullptr : d_init;
+  a.fact_row = p->fact_row;
+  a.fact_owner = p->fact_owner;
+  a.n_facts = hm.n_fact_rows;
+  a.fact_mask = p->fact_mask;
+  a.n_atom_words = (hm.n + 63) / 64;
+  a.rows_init = rows ? d_init : nullptr;
+  a.inv = p->inv;
+  a.n_prime = hm.n_prime;
+  a.out = d_out;
+  a.perm = p->perm;
+  a.n_out = n_in;
+
+  static int per_sm = -1;
+  if (per_sm < 0) per_sm = fixpoint_blocks_per_sm();
+  if (per_sm <= 0) return fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident");
+  const int warps_per_block = kFixBlock / 32;
+  int grid = std::min(max_coresident(p, per_sm), std::max(1, (a.n_words + warps_per_block - 1) / warps_per_block));
+  if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
+  if ((st = launch_count_and_check(launch_fixpoint(a, grid, s), "launch fixpoint kernel", p)) != LP_OK) return st;
+  if (p->timed) LP_CUDA(cudaEventRecord(p->ev1, s));
+  LP_CUDA(cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s));
+  if (host_out) LP_CUDA(cudaMemcpyAsync(out, d_out, out_words * 8, cudaMemcpyDeviceToHost, s));
+  if (iters_out || host_out || host_in) {
+    st = finish_sync(p, s);
+    if (iters_out) *iters_out = p->h_ctl->iters;
+    return st;
+  }
+  return LP_OK;
+}
+
+lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_guesses, uint64_t* stable_mask,
+                           uint64_t* models, int64_t max_models, int64_t* n_stable_out, int32_t max_iters,
+                           void* cuda_stream) {
+  if (!p) return fail(LP_ERR_INVALID, "program must not be NULL");
+  if (p->host_only) return fail(LP_ERR_INVALID, "program was compiled with LP_COMPILE_HOST_ONLY");
+  if (max_iters < 1) return fail(LP_ERR_INVALID, "max_iters must be >= 1");
+  if (n_guesses < 0 || max_models < 0) return fail(LP_ERR_INVALID, "negative count");
+  const HostMatrix& hm = p->hm;
+  if (guesses) {
+    if (hm.k > 64) return fail(LP_ERR_TOO_MANY_GUESSES, "k > 64 guessed atoms do not fit a guess word");
+  } else {
+    if (hm.k > 40) return fail(LP_ERR_TOO_MANY_GUESSES, "enumerating all 2^k guesses needs k <= 40");
+    if (n_guesses != (int64_t(1) << hm.k)) return fail(LP_ERR_INVALID, "n_guesses must be 2^k when guesses is NULL");
+  }
+  if (n_guesses > 0 && !stable_mask) return fail(LP_ERR_INVALID, "stable_mask must not be NULL");
+  if (max_models > 0 && !models) return fail(LP_ERR_INVALID, "models must not be NULL when max_models > 0");
+  // M_0 holds only self-loop rows (facts, barred atoms), so every column's iterates grow.
+  max_iters = (int32_t)std::min<int64_t>(max_iters, (int64_t)hm.n_prime + 2);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  p->last_launches = 0;
+  p->timed = false;
+  lp_status st = ensure_scratch(p);
+  if (st != LP_OK) return st;
+  if (n_guesses == 0) {
+    LP_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(DeviceCtl), s));
+    LP_CUDA(cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s));
+    if (n_stable_out) {
+      LP_CUDA(cudaStreamSynchronize(s));
+      *n_stable_out = 0;
+    }
+    return LP_OK;
+  }
+  const int64_t n_gwords = (n_guesses + 63) / 64;
+  const int32_t atom_words = (hm.n + 63) / 64;
+  // tile width: largest power of two <= 32 words whose two iterate buffers fit the budget
+  int64_t budget = 64ll << 20;
+  if (const char* env = std::getenv("LP_TILE_BYTES")) budget = std::max<int64_t>(1, std::atoll(env));
+  int log2W = 0;
+  while (log2W < 5 && (int64_t(1) << (log2W + 1)) <= n_gwords &&
+         2ll * hm.n_pad * 8 * (int64_t(1) << (log2W + 1)) <= budget)
+    log2W++;
+  const int W = 1 << log2W;
+  const int64_t n_tiles = (n_gwords + W - 1) / W;
+  if ((st = ensure(p, p->tiles, (size_t)2 * hm.n_pad * W * 8)) != LP_OK) return st;
+  p->tile_words = W;
+
+  const bool host_g = guesses && !is_device_ptr(guesses);
+  const bool host_mask = !is_device_ptr(stable_mask);
+  const bool host_models = models && max_models > 0 && !is_device_ptr(models);
+  const uint64_t* d_g = guesses;
+  uint64_t* d_mask = stable_mask;
+  uint64_t* d_models = max_models > 0 ? models : nullptr;
+  if (host_g) {
+    if ((st = ensure(p, p->stage_in, (size_t)n_guesses * 8)) != LP_OK) return st;
+    LP_CUDA(cudaMemcpyAsync(p->stage_in.p, guesses, (size_t)n_guesses * 8, cudaMemcpyHostToDevice, s));
+    d_g = (const uint64_t*)p->stage_in.p;
+  }
+  if (host_mask) {
+    if ((st = ensure(p, p->stage_out, (size_t)n_gwords * 8)) != LP_OK) return st;
+    d_mask = (uint64_t*)p->stage_out.p;
+  }
+  if (host_models) {
+    if ((st = ensure(p, p->stage_out2, (size_t)max_models * atom_words * 8)) != LP_OK) return st;
+    d_models = (uint64_t*)p->stage_out2.p;
+  }
+  LP_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(DeviceCtl), s));
+
+  StableArgs a{};
+  a.row_ptr = p->row_ptr;
+  a.col = p->col;
+  a.any_mask = p->any_mask;
+  a.row_tag = p->row_tag;
+  a.n_pad = hm.n_pad;
+  a.X0 = (uint64_t*)p->tiles.p;
+  a.X1 = (uint64_t*)p->tiles.p + (size_t)hm.n_pad * W;
+  a.W = W;
+  a.log2W = log2W;
+  a.n_guesses = n_guesses;
+  a.n_gwords = n_gwords;
+  a.n_tiles = n_tiles;
+  a.guesses = d_g;
+  a.k = hm.k;
+  a.neg_row = p->neg_row;
+  a.bar_row = p->bar_row;
+  a.n_barred = hm.n_barred;
+  a.perm = p->perm;
+  a.n = hm.n;
+  a.stable_mask = d_mask;
+  a.models = d_models;
+  a.max_models = max_models;
+  a.n_atom_words = atom_words;
+  a.max_iters = max_iters;
+  a.ctl = p->ctl;
+  static int per_sm = -1;
+  if (per_sm < 0) per_sm = stable_blocks_per_sm();
+  if (per_sm <= 0) return fail(LP_ERR_CUDA, "stable kernel cannot be resident");
+  const int64_t rows_per_block = (int64_t)(kStableBlock / 32) * (32 / W);
+  int grid = (int)std::min<int64_t>(max_coresident(p, per_sm), std::max<int64_t>(1, hm.n_pad / rows_per_block));
+  if ((st = launch_count_and_check(launch_stable(a, grid, s), "launch stable kernel", p)) != LP_OK) return st;
+  LP_CUDA(cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s));
+  if (host_mask) LP_CUDA(cudaMemcpyAsync(stable_mask, d_mask, (size_t)n_gwords * 8, cudaMemcpyDeviceToHost, s));
+  if (host_models) LP_CUDA(cudaMemcpyAsync(models, d_models, (size_t)max_models * atom_words * 8, cudaMemcpyDeviceToHost, s));
+  if (n_stable_out || host_g || host_mask || host_models) {
+    st = finish_sync(p, s);
+    if (n_stable_out) *n_stable_out = p->h_ctl->n_stable;
+    return st;
+  }
+  return LP_OK;
+}
+
+lp_status lp_last_solve_stats(lp_program* p, lp_solve_stats* out, void* cuda_stream) {
+  if (!p || !out) return fail(LP_ERR_INVALID, "NULL argument");
+  if (p->host_only) return fail(LP_ERR_INVALID, "program was compiled with LP_COMPILE_HOST_ONLY");
+  lp_status st = ensure_scratch(p);
+  if (st != LP_OK) return st;
+  LP_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+  out->iters = p->h_ctl->iters;
+  out->status = p->h_ctl->status;
+  out->kernel_ms = -1.0f;
+  if (p->timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev0, p->ev1) == cudaSuccess) out->kernel_ms = ms;
+    else cudaGetLastError();
+  }
+  out->launches = p->last_launches;
+  out->tiles = p->h_ctl->tiles;
+  out->tile_words = p->tile_words;
+  out->max_tile_iters = p->h_ctl->max_tile_iters;
+  out->sum_tile_iters = p->h_ctl->sum_tile_iters;
+  return LP_OK;
+}
+
+lp_status lp_export_matrix(const lp_program* p, int64_t* row_ptr, int64_t* col, int32_t* threshold, int8_t* kind,
+                           void* cuda_stream) {
+  if (!p || !row_ptr || !col || !threshold) return fail(LP_ERR_INVALID, "NULL argument");
+  const HostMatrix& hm = p->hm;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<int32_t> rp, cl;
+  if (p->host_only) {
+    rp = hm.row_ptr;
+    cl = hm.col;
+    cl.resize(std::max<int64_t>(hm.nnz, 1));
+  } else {
+    rp.resize((size_t)hm.n_pad + 1);
+    cl.resize(std::max<int64_t>(hm.nnz, 1));
+    LP_CUDA(cudaMemcpyAsync(rp.data(), p->row_ptr, rp.size() * 4, cudaMemcpyDeviceToHost, s));
+    if (hm.nnz) LP_CUDA(cudaMemcpyAsync(cl.data(), p->col, (size_t)hm.nnz * 4, cudaMemcpyDeviceToHost, s));
+    LP_CUDA(cudaStreamSynchronize(s));
+  }
+  std::vector<int32_t> inv(std::max(hm.n_prime, 1));
+  for (int32_t c = 0; c < hm.n_prime; c++) inv[hm.perm[c]] = c;
+  row_ptr[0] = 0;
+  for (int32_t c = 0; c < hm.n_prime; c++) {
+    const int32_t r = hm.perm[c];
+    const int64_t b = row_ptr[c];
+    int64_t m = 0;
+    for (int32_t e = rp[r]; e < rp[r + 1]; e++) col[b + m++] = inv[cl[e]];
+    std::sort(col + b, col + b + m);
+    row_ptr[c + 1] = b + m;
+    const int8_t kd = hm.canon_kind[c];
+    threshold[c] = kd == K_RULE ? (int32_t)m : (kd == K_EMPTY ? 0 : 1);
+    if (kind) kind[c] = kd;
+  }
+  return LP_OK;
+}
+
+void lp_free(lp_program* p) {
+  if (!p) return;
+  release(p);
+  delete p;
+}
+
+}  // extern "C"

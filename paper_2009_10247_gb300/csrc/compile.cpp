@@ -1,0 +1,297 @@
+// compile.cpp -- host compiler of liblp: rules -> program matrix M_P in the internal layout.
+//
+// Sec. 2.1 / 2.2 of the paper (Nguyen, Inoue, Sakama, ICLP 2020): the literal "not q" becomes
+// a new atom q-bar (Eq. 4), bodies are sets (footnote of Eq. 2), heads with several rules are
+// standardized into an OR-rule over one new atom per rule, and M_P follows Def. 2 and Def. 7.
+// The values 1/m are never stored: a rule row fires when all its body atoms hold, an OR row
+// when one does, which is theta(M_P v) of Def. 5 evaluated exactly.
+//
+// Internal order (what the kernels see; outputs are mapped back):
+//   section A: original and barred atoms, by descending number of rows that reference them,
+//              so that the most gathered bits share a few cache lines;
+//   section B: the new atoms, grouped by the OR row that references them (in section-A order
+//              of that row, then rule order), so that an OR row gathers one contiguous range;
+//   padding:   empty rows up to a multiple of 64.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace lp {
+
+namespace {
+
+inline void sort_small(int32_t* a, int64_t m) {
+  if (m > 24) {
+    std::sort(a, a + m);
+    return;
+  }
+  for (int64_t i = 1; i < m; i++) {
+    int32_t x = a[i];
+    int64_t j = i - 1;
+    while (j >= 0 && a[j] > x) {
+      a[j + 1] = a[j];
+      j--;
+    }
+    a[j + 1] = x;
+  }
+}
+
+}  // namespace
+
+lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const int64_t* body_off,
+                       const int32_t* body_atom, const uint8_t* body_neg, HostMatrix& hm, std::string& err) {
+  // ---- validation
+  if (n < 0 || n_rules < 0) {
+    err = "negative atom or rule count";
+    return LP_ERR_INVALID;
+  }
+  if (n_rules > 0 && (!head || !body_off)) {
+    err = "head/body_off must not be NULL when n_rules > 0";
+    return LP_ERR_INVALID;
+  }
+  if (n_rules > 0 && body_off[0] != 0) {
+    err = "body_off[0] must be 0";
+    return LP_ERR_INVALID;
+  }
+  for (int64_t r = 0; r < n_rules; r++) {
+    if (head[r] < 0 || head[r] >= n) {
+      err = "head atom out of range at rule " + std::to_string(r);
+      return LP_ERR_INVALID;
+    }
+    if (body_off[r + 1] < body_off[r]) {
+      err = "body_off decreases at rule " + std::to_string(r);
+      return LP_ERR_INVALID;
+    }
+  }
+  const int64_t total = n_rules > 0 ? body_off[n_rules] : 0;
+  if (total > 0 && !body_atom) {
+    err = "body_atom must not be NULL when there are body literals";
+    return LP_ERR_INVALID;
+  }
+  if (total >= (int64_t(1) << 31)) {
+    err = "too many body literals (must be < 2^31)";
+    return LP_ERR_INVALID;
+  }
+  int bad = 0;
+#pragma omp parallel for reduction(| : bad) schedule(static)
+  for (int64_t e = 0; e < total; e++) bad |= (body_atom[e] < 0 || body_atom[e] >= n);
+  if (bad) {
+    err = "body atom out of range";
+    return LP_ERR_INVALID;
+  }
+
+  try {
+    // ---- rules per head, negated atoms, barred ids (canonical: n + rank of q)
+    std::vector<int32_t> cnt(n, 0);
+    std::vector<int32_t> bar_id(n, -1);
+    for (int64_t r = 0; r < n_rules; r++) cnt[head[r]]++;
+    if (body_neg)
+      for (int64_t e = 0; e < total; e++)
+        if (body_neg[e]) bar_id[body_atom[e]] = 0;
+    int32_t nb = 0;
+    for (int32_t a = 0; a < n; a++)
+      if (bar_id[a] == 0) bar_id[a] = n + nb++;
+    // new atoms for the rules of multi-rule heads, in rule order
+    std::vector<int32_t> aux(n_rules, -1);
+    int64_t naux = 0;
+    for (int64_t r = 0; r < n_rules; r++)
+      if (cnt[head[r]] >= 2) aux[r] = (int32_t)std::min<int64_t>(INT32_MAX, (int64_t)n + nb + naux++);
+    const int64_t n_prime64 = (int64_t)n + nb + naux;
+    if (n_prime64 >= (int64_t(1) << 31) - 128) {
+      err = "standardized program too large (n' must be < 2^31 - 128)";
+      return LP_ERR_INVALID;
+    }
+    const int32_t np = (int32_t)n_prime64;
+
+    // ---- body sets in canonical columns (sorted, duplicates removed), in place per rule
+    std::vector<int32_t> rb(total);
+    std::vector<int32_t> setlen(n_rules);
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t r = 0; r < n_rules; r++) {
+      int64_t b = body_off[r], m = body_off[r + 1] - b;
+      int32_t* s = rb.data() + b;
+      for (int64_t i = 0; i < m; i++) {
+        int32_t a = body_atom[b + i];
+        s[i] = (body_neg && body_neg[b + i]) ? bar_id[a] : a;
+      }
+      sort_small(s, m);
+      int64_t u = 0;
+      for (int64_t i = 0; i < m; i++)
+        if (u == 0 || s[u - 1] != s[i]) s[u++] = s[i];
+      setlen[r] = (int32_t)u;
+    }
+
+    // ---- canonical rows: kind, defining rule, rules of each OR head
+    std::vector<int8_t> kind(np, K_EMPTY);
+    std::vector<int64_t> row_rule(np, -1);  // rule defining a RULE/FACT row
+    std::vector<int64_t> hr_off((size_t)n + 1, 0);
+    for (int64_t r = 0; r < n_rules; r++)
+      if (cnt[head[r]] >= 2) hr_off[head[r] + 1]++;
+    for (int32_t a = 0; a < n; a++) hr_off[a + 1] += hr_off[a];
+    std::vector<int64_t> hr_rule(hr_off[n]);
+    {
+      std::vector<int64_t> cur(hr_off.begin(), hr_off.end() - 1);
+      for (int64_t r = 0; r < n_rules; r++) {
+        int32_t h = head[r];
+        if (cnt[h] >= 2) {
+          kind[h] = K_OR;
+          hr_rule[cur[h]++] = r;
+          kind[aux[r]] = setlen[r] == 0 ? K_FACT : K_RULE;
+          row_rule[aux[r]] = r;
+        } else {
+          kind[h] = setlen[r] == 0 ? K_FACT : K_RULE;
+          row_rule[h] = r;
+        }
+      }
+    }
+    for (int32_t a = 0; a < n; a++)
+      if (bar_id[a] >= 0) kind[bar_id[a]] = K_BARRED;
+
+    auto row_len = [&](int32_t c) -> int64_t {
+      switch (kind[c]) {
+        case K_RULE: return setlen[row_rule[c]];
+        case K_OR: return hr_off[c + 1] - hr_off[c];
+        case K_FACT:
+        case K_BARRED: return 1;
+        default: return 0;
+      }
+    };
+
+    // ---- references per canonical column (for the internal order)
+    std::vector<int64_t> deg(np, 0);
+    int64_t nnz = 0;
+    for (int32_t c = 0; c < np; c++) nnz += row_len(c);
+    if (nnz >= (int64_t(1) << 31)) {
+      err = "too many matrix entries (nnz must be < 2^31)";
+      return LP_ERR_INVALID;
+    }
+    for (int32_t c = 0; c < np; c++) {
+      if (kind[c] == K_RULE) {
+        int64_t r = row_rule[c];
+        const int32_t* s = rb.data() + body_off[r];
+        for (int32_t i = 0; i < setlen[r]; i++) deg[s[i]]++;
+      } else if (kind[c] == K_FACT || kind[c] == K_BARRED) {
+        deg[c]++;
+      }  // OR entries point at new atoms, which are placed by their OR row
+    }
+
+    // ---- internal order
+    const int32_t nA = n + nb;
+    std::vector<int32_t> inv(np);  // internal -> canonical
+    std::iota(inv.begin(), inv.begin() + nA, 0);
+    std::stable_sort(inv.begin(), inv.begin() + nA, [&](int32_t x, int32_t y) { return deg[x] > deg[y]; });
+    {
+      int64_t pos = nA;
+      for (int32_t i = 0; i < nA; i++) {
+        int32_t c = inv[i];
+        if (kind[c] == K_OR)
+          for (int64_t t = hr_off[c]; t < hr_off[c + 1]; t++) inv[pos++] = aux[hr_rule[t]];
+      }
+      if (pos != np) {
+        err = "internal error: new atoms not covered by OR rows";
+        return LP_ERR_INVALID;
+      }
+    }
+    hm.perm.assign(np, 0);
+    for (int32_t i = 0; i < np; i++) hm.perm[inv[i]] = i;
+    const int32_t npad = (int32_t)(((int64_t)np + 63) / 64 * 64);
+
+    // ---- internal CSR
+    hm.row_ptr.assign((size_t)npad + 1, 0);
+    for (int32_t i = 0; i < np; i++) hm.row_ptr[i + 1] = (int32_t)row_len(inv[i]);
+    for (int32_t i = 0; i < npad; i++) hm.row_ptr[i + 1] += hm.row_ptr[i];
+    hm.col.assign((size_t)nnz, 0);
+#pragma omp parallel for schedule(dynamic, 2048)
+    for (int32_t i = 0; i < np; i++) {
+      int32_t c = inv[i];
+      int32_t* d = hm.col.data() + hm.row_ptr[i];
+      int64_t m = 0;
+      switch (kind[c]) {
+        case K_RULE: {
+          int64_t r = row_rule[c];
+          const int32_t* s = rb.data() + body_off[r];
+          for (int32_t t = 0; t < setlen[r]; t++) d[m++] = hm.perm[s[t]];
+          break;
+        }
+        case K_OR:
+          for (int64_t t = hr_off[c]; t < hr_off[c + 1]; t++) d[m++] = hm.perm[aux[hr_rule[t]]];
+          break;
+        case K_FACT:
+        case K_BARRED:
+          d[m++] = i;
+          break;
+        default:
+          break;
+      }
+      sort_small(d, m);
+    }
+    hm.any_mask.assign((size_t)npad / 32, 0u);
+    for (int32_t i = 0; i < np; i++)
+      if (kind[inv[i]] == K_OR) hm.any_mask[i >> 5] |= 1u << (i & 31);
+
+    // ---- facts, negated atoms, guesses (Def. 4 and Def. 8)
+    std::vector<int32_t> owner_of_row(np);
+    for (int32_t c = 0; c < np; c++) owner_of_row[c] = c < n ? c : -1;
+    for (int32_t a = 0; a < n; a++)
+      if (bar_id[a] >= 0) owner_of_row[bar_id[a]] = a;
+    for (int64_t r = 0; r < n_rules; r++)
+      if (aux[r] >= 0) owner_of_row[aux[r]] = head[r];
+    hm.fact_row.clear();
+    hm.fact_owner.clear();
+    hm.fact_mask.assign(((size_t)n + 63) / 64, 0ull);
+    int32_t n_rule_rows = 0, n_or_rows = 0;
+    for (int32_t c = 0; c < np; c++) {
+      if (kind[c] == K_FACT) {
+        hm.fact_row.push_back(hm.perm[c]);
+        hm.fact_owner.push_back(owner_of_row[c]);
+        hm.fact_mask[owner_of_row[c] >> 6] |= 1ull << (owner_of_row[c] & 63);
+      } else if (kind[c] == K_RULE) {
+        n_rule_rows++;
+      } else if (kind[c] == K_OR) {
+        n_or_rows++;
+      }
+    }
+    hm.row_tag.assign(npad, -1);
+    for (int32_t f : hm.fact_row) hm.row_tag[f] = -2;
+    hm.neg_row.clear();
+    hm.bar_row.clear();
+    hm.guess_row.clear();
+    for (int32_t a = 0; a < n; a++) {
+      if (bar_id[a] < 0) continue;
+      hm.neg_row.push_back(hm.perm[a]);
+      hm.bar_row.push_back(hm.perm[bar_id[a]]);
+      bool is_fact = (hm.fact_mask[a >> 6] >> (a & 63)) & 1ull;
+      if (is_fact) {
+        hm.row_tag[hm.perm[bar_id[a]]] = -3;
+      } else {
+        hm.row_tag[hm.perm[bar_id[a]]] = (int32_t)hm.guess_row.size();
+        hm.guess_row.push_back(hm.perm[bar_id[a]]);
+      }
+    }
+
+    hm.n = n;
+    hm.n_rules = n_rules;
+    hm.n_prime = np;
+    hm.n_pad = npad;
+    hm.nnz = nnz;
+    hm.n_barred = nb;
+    hm.n_aux = (int32_t)naux;
+    hm.k = (int32_t)hm.guess_row.size();
+    hm.n_fact_rows = (int32_t)hm.fact_row.size();
+    hm.n_rule_rows = n_rule_rows;
+    hm.n_or_rows = n_or_rows;
+    hm.canon_kind.swap(kind);
+  } catch (const std::bad_alloc&) {
+    err = "host allocation failed in lp_compile";
+    return LP_ERR_OOM;
+  }
+  return LP_OK;
+}
+
+}  // namespace lp

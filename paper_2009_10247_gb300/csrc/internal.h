@@ -1,0 +1,48 @@
+// internal.h -- liblp's private types, shared by its host compiler, kernels and C ABI glue.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lp.h"
+
+namespace lp {
+
+// Canonical row kinds (the values lp_export_matrix reports).
+enum RowKind : int8_t { K_EMPTY = 0, K_RULE = 1, K_OR = 2, K_FACT = 3, K_BARRED = 4 };
+
+// Result of the host compile (Sec. 2.1/2.2 standardization + Def. 2/7 matrix), already in the
+// internal row order the kernels use. Every "row" is also a column (M_P is square).
+struct HostMatrix {
+  int32_t n = 0;          // original atoms
+  int64_t n_rules = 0;
+  int32_t n_prime = 0;    // rows of M_P
+  int32_t n_pad = 0;      // rows padded to a multiple of 64 (padding rows are empty)
+  int64_t nnz = 0;
+  int32_t n_barred = 0, n_aux = 0, k = 0;
+  int32_t n_fact_rows = 0, n_rule_rows = 0, n_or_rows = 0;
+
+  std::vector<int32_t> row_ptr;    // internal CSR, n_pad + 1
+  std::vector<int32_t> col;        // internal column ids, nnz
+  std::vector<uint32_t> any_mask;  // n_pad / 32 words: bit set = OR-rule row (threshold 1)
+  std::vector<int32_t> perm;       // canonical row -> internal row (n_prime)
+  std::vector<int8_t> canon_kind;  // canonical row kinds (n_prime)
+  std::vector<int32_t> fact_row;   // internal rows with a_ii = 1 from a fact (Def. 2 item 3)
+  std::vector<int32_t> fact_owner; // original atom of each fact row
+  std::vector<uint64_t> fact_mask; // ceil(n/64) words: atoms with at least one fact rule
+  std::vector<int32_t> neg_row;    // per negated atom q (ascending id): internal row of q
+  std::vector<int32_t> bar_row;    // ... and internal row of q-bar
+  std::vector<int32_t> guess_row;  // internal rows of the k guessed barred atoms, bit order
+  std::vector<int32_t> row_tag;    // n_pad: -1 zero, -2 fact, j >= 0 guessed barred atom j,
+                                   //        -3 barred atom of a fact (initial column of Def. 8)
+};
+
+// Builds the matrix; returns LP_OK or LP_ERR_INVALID / LP_ERR_OOM with a message in err.
+lp_status compile_host(int32_t n_atoms, int64_t n_rules, const int32_t* head, const int64_t* body_off,
+                       const int32_t* body_atom, const uint8_t* body_neg, HostMatrix& hm, std::string& err);
+
+// Thread-local error message used by the C ABI.
+void set_error(const std::string& msg);
+
+}  // namespace lp

@@ -1,0 +1,75 @@
+// kernels.h -- launch interfaces of liblp's kernels (host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lp {
+
+struct DeviceCtl;
+
+// Algorithm 1 on one bit-packed vector (persistent cooperative kernel).
+struct FixArgs {
+  const int32_t* row_ptr;   // n_pad + 1, internal order
+  const int32_t* col;       // nnz, internal column ids
+  const uint32_t* any_mask; // n_pad / 32: OR-rule rows
+  uint32_t* x0;             // n_pad / 32 words: initial vector / even iterates
+  uint32_t* x1;             // n_pad / 32 words: odd iterates
+  int32_t n_words;          // n_pad / 32
+  int32_t max_iters;
+  DeviceCtl* ctl;
+  // initial vector, default mode (x0 zeroed by the caller): facts of the selected atoms
+  const uint64_t* init;        // ceil(n/64) words or NULL (= every fact)
+  const int32_t* fact_row;     // internal rows of the fact rows
+  const int32_t* fact_owner;   // their original atoms
+  int32_t n_facts;
+  const uint64_t* fact_mask;   // ceil(n/64): atoms that have a fact rule
+  int32_t n_atom_words;        // ceil(n/64)
+  // initial vector, LP_ROWS mode: canonical rows
+  const uint64_t* rows_init;   // ceil(n'/64) words or NULL (default mode)
+  const int32_t* inv;          // internal row -> canonical row (LP_ROWS only)
+  int32_t n_prime;
+  // output: bit a of out = final bit of internal row perm[a], a < n_out
+  uint64_t* out;
+  const int32_t* perm;         // canonical -> internal
+  int32_t n_out;
+};
+
+constexpr int kFixBlock = 256;
+cudaError_t launch_fixpoint(const FixArgs& a, int grid, cudaStream_t s);
+int fixpoint_blocks_per_sm();
+
+// Algorithms 2 + 3 over tiles of 64-bit guess words (persistent cooperative kernel).
+struct StableArgs {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const uint32_t* any_mask;
+  const int32_t* row_tag;   // n_pad: -1 zero, -2 fact, -3 barred atom of a fact, j >= 0 guess bit j
+  int32_t n_pad;
+  uint64_t* X0;             // n_pad * W words: iterate buffers of one tile
+  uint64_t* X1;
+  int32_t W;                // guess words per tile (1, 2, 4, 8, 16 or 32)
+  int32_t log2W;
+  int64_t n_guesses;
+  int64_t n_gwords;         // ceil(n_guesses / 64)
+  int64_t n_tiles;
+  const uint64_t* guesses;  // n_guesses k-bit words, or NULL = all 2^k in order
+  int32_t k;
+  const int32_t* neg_row;   // per negated atom: internal row of q
+  const int32_t* bar_row;   // ... and of q-bar
+  int32_t n_barred;
+  const int32_t* perm;      // canonical -> internal (first n entries: original atoms)
+  int32_t n;
+  uint64_t* stable_mask;    // n_gwords words
+  uint64_t* models;         // max_models x ceil(n/64) words or NULL
+  int64_t max_models;
+  int32_t n_atom_words;
+  int32_t max_iters;
+  DeviceCtl* ctl;
+};
+
+constexpr int kStableBlock = 256;
+cudaError_t launch_stable(const StableArgs& a, int grid, cudaStream_t s);
+int stable_blocks_per_sm();
+
+}  // namespace lp

@@ -1,0 +1,195 @@
+// stable.cu -- Algorithms 2 and 3 (stable models of a normal program) over batches of guesses.
+//
+// The initial matrix M_0 of Def. 8 has one column per guess. Columns are packed 64 to a
+// 64-bit word, so a row of the iterate holds the row's truth value under 64 guesses, and a
+// tile of W words (64W guesses) is iterated as one bit-packed sparse matrix x multi-vector
+// product: for a rule row the new word is the AND of the words of its body atoms (all m
+// entries 1/m true), for an OR-rule row or a self-loop the OR (one entry true) -- theta of
+// Def. 5 applied to M_P M_k exactly, for 64 columns per instruction.
+//
+// One persistent cooperative launch walks the tiles. Per tile:
+//   1. M_0 words (Def. 8): fact rows all ones; guessed barred rows carry bit j of each guess
+//      (for the full enumeration, a fixed pattern for j < 6 and the guess-word index bits
+//      above); every other row zero;
+//   2. M_{k+1} = theta(M_P M_k) until no word changes (per-tile early exit);
+//   3. Algorithm 3: a column is stable iff a_q XOR a_q-bar = 1 for every negated atom q, so the
+//      stable bits of a word are the AND over q of (word of q) XOR (word of q-bar);
+//   4. the stable columns of the tile are numbered in guess order and their models (the
+//      column over the original atoms) are written out.
+// The iterate buffers of a tile are sized by the host to stay L2 resident.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace lp {
+
+__device__ __forceinline__ uint64_t m0_word(int tag, long long gw, const StableArgs& a) {
+  if (tag == -2) return ~0ull;  // fact row (Def. 8 item 2)
+  if (tag < 0) return 0ull;     // other original rows, barred atoms of facts (item 3)
+  if (a.guesses == nullptr) {
+    // guess g = 64*gw + b, bit tag of g
+    switch (tag) {  // bit b of the word is bit tag of b
+      case 0: return 0xAAAAAAAAAAAAAAAAull;
+      case 1: return 0xCCCCCCCCCCCCCCCCull;
+      case 2: return 0xF0F0F0F0F0F0F0F0ull;
+      case 3: return 0xFF00FF00FF00FF00ull;
+      case 4: return 0xFFFF0000FFFF0000ull;
+      case 5: return 0xFFFFFFFF00000000ull;
+      default: break;
+    }
+    return ((gw >> (tag - 6)) & 1ll) ? ~0ull : 0ull;
+  }
+  uint64_t w = 0;
+  const long long g0 = gw * 64;
+  for (int b = 0; b < 64; b++) {
+    const long long g = g0 + b;
+    if (g < a.n_guesses) w |= ((a.guesses[g] >> tag) & 1ull) << b;
+  }
+  return w;
+}
+
+__global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
+  __shared__ int s_flag;
+  __shared__ long long s_base;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  DeviceCtl* ctl = a.ctl;
+  unsigned long long round = 0;
+  const int W = a.W;
+  const int rows_per_warp = 32 >> a.log2W;  // W <= 32 lanes per row
+  const int sub = lane >> a.log2W;          // row within the warp's group
+  const int wl = lane & (W - 1);            // word within the tile
+  const int n_groups = a.n_pad / rows_per_warp;
+  const long long tile_words = (long long)a.n_pad * W;
+
+  for (long long t = 0; t < a.n_tiles; ++t) {
+    const long long gw0 = t * W;  // first guess word of the tile
+    // The previous tile's readers of the change flags are all past its last barrier.
+    if (gtid == 0) ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0u;
+    // ---- 1. M_0
+    for (long long e = gtid; e < tile_words; e += nthreads) {
+      const int row = (int)(e >> a.log2W);
+      const int w = (int)(e & (W - 1));
+      a.X0[e] = m0_word(__ldg(a.row_tag + row), gw0 + w, a);
+    }
+    if (!grid_barrier(ctl, ++round, 6)) return;
+
+    // ---- 2. M_{k+1} = theta(M_P M_k) until unchanged
+    const uint64_t* fin = a.X0;
+    int it = 0;
+    bool converged = false;
+    for (; it < a.max_iters; ++it) {
+      const uint64_t* src = (it & 1) ? a.X1 : a.X0;
+      uint64_t* dst = (it & 1) ? a.X0 : a.X1;
+      bool changed = false;
+      for (int g = gwarp; g < n_groups; g += nwarps) {
+        const int row = g * rows_per_warp + sub;
+        const int beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
+        const bool any = (__ldg(a.any_mask + (row >> 5)) >> (row & 31)) & 1u;
+        uint64_t acc = (end > beg) ? (any ? 0ull : ~0ull) : 0ull;
+        for (int e = beg; e < end; ++e) {
+          const uint64_t v = src[((long long)__ldg(a.col + e) << a.log2W) + wl];
+          acc = any ? (acc | v) : (acc & v);
+        }
+        const long long o = ((long long)row << a.log2W) + wl;
+        changed |= (acc != src[o]);
+        dst[o] = acc;
+      }
+      const int any_changed = __syncthreads_or(changed);
+      if (threadIdx.x == 0) {
+        if (any_changed) atomicOr(&ctl->flag[it % 3], 1u);
+        if (blockIdx.x == 0) ctl->flag[(it + 1) % 3] = 0u;
+      }
+      if (!grid_barrier(ctl, ++round, 6)) return;
+      if (threadIdx.x == 0) s_flag = (int)ld_volatile(&ctl->flag[it % 3]);
+      __syncthreads();
+      fin = dst;
+      if (!s_flag) {
+        converged = true;
+        ++it;
+        break;
+      }
+    }
+    if (!converged) {
+      if (gtid == 0) {
+        ctl->iters = it;
+        atomicCAS(&ctl->status, 0, 4 /* LP_ERR_NO_FIXPOINT */);
+      }
+      return;  // every block takes this branch: the flag it read is the same for all
+    }
+
+    // ---- 3. Algorithm 3 on the W words of the tile
+    if (gtid < W) {
+      const long long gw = gw0 + gtid;
+      if (gw < a.n_gwords) {
+        const long long rem = a.n_guesses - gw * 64;
+        uint64_t st = rem >= 64 ? ~0ull : ((1ull << rem) - 1ull);
+        for (int j = 0; j < a.n_barred; j++)
+          st &= fin[((long long)a.neg_row[j] << a.log2W) + gtid] ^ fin[((long long)a.bar_row[j] << a.log2W) + gtid];
+        a.stable_mask[gw] = st;
+      }
+    }
+    if (gtid == 0) {
+      ctl->iters = it;
+      ctl->max_tile_iters = max(ctl->max_tile_iters, it);
+      ctl->sum_tile_iters += it;
+      ctl->tiles = t + 1;
+    }
+    if (!grid_barrier(ctl, ++round, 6)) return;
+
+    // ---- 4. models of the stable columns, numbered in guess order
+    if (threadIdx.x == 0) s_base = *reinterpret_cast<volatile long long*>(&ctl->n_stable);
+    __syncthreads();
+    const long long base = s_base;
+    // words of this tile: lane w holds popc(stable word w) (W <= 32)
+    const long long gwl = gw0 + lane;
+    const uint64_t myword = (lane < W && gwl < a.n_gwords) ? a.stable_mask[gwl] : 0ull;
+    const int mycnt = __popcll(myword);
+    int incl = mycnt;  // inclusive prefix over lanes
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const int tile_count = __shfl_sync(FULL, incl, 31);
+    if (a.models) {
+      for (int m = gwarp; m < tile_count && base + m < a.max_models; m += nwarps) {
+        // word holding the m-th stable column, and its bit
+        const unsigned ballot = __ballot_sync(FULL, incl > m);
+        const int wsel = __ffs(ballot) - 1;
+        const int before = __shfl_sync(FULL, incl - mycnt, wsel);
+        uint64_t word = __shfl_sync(FULL, myword, wsel);
+        for (int q = 0; q < m - before; q++) word &= word - 1;  // drop lower set bits
+        const int b = __ffsll((long long)word) - 1;
+        uint32_t* dst = reinterpret_cast<uint32_t*>(a.models + (base + m) * a.n_atom_words);
+        const int n32 = 2 * a.n_atom_words;
+        for (int u = 0; u < n32; u++) {
+          const int atom = (u << 5) + lane;
+          uint32_t bit = 0;
+          if (atom < a.n) bit = (uint32_t)(fin[((long long)a.perm[atom] << a.log2W) + wsel] >> b) & 1u;
+          const uint32_t word32 = __ballot_sync(FULL, bit);
+          if (lane == 0) dst[u] = word32;
+        }
+      }
+    }
+    if (!grid_barrier(ctl, ++round, 6)) return;
+    if (gtid == 0) ctl->n_stable = base + tile_count;  // everyone read base before the barrier
+  }
+}
+
+cudaError_t launch_stable(const StableArgs& a, int grid, cudaStream_t s) {
+  StableArgs copy = a;
+  void* params[] = {&copy};
+  return cudaLaunchCooperativeKernel((const void*)stable_kernel, dim3(grid), dim3(kStableBlock), params, 0, s);
+}
+
+int stable_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stable_kernel, kStableBlock, 0) != cudaSuccess) return 0;
+  return nb;
+}
+
+}  // namespace lp

@@ -1,0 +1,200 @@
+"""Thin ctypes binding of liblp (include/lp.h): argument marshalling only.
+
+Every step of the fixpoint runs in liblp's CUDA kernels; this module never computes a model.
+Buffers may be torch tensors (CUDA or CPU), numpy arrays, or anything exposing ``data_ptr()``;
+bit vectors are 64-bit words (torch.int64 / numpy uint64) in the layout of lp.h.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NO_FIXPOINT, ERR_TOO_MANY_GUESSES, ERR_TIMEOUT = range(7)
+STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_OOM", "LP_ERR_CUDA", "LP_ERR_NO_FIXPOINT",
+                "LP_ERR_TOO_MANY_GUESSES", "LP_ERR_TIMEOUT"]
+LP_ROWS, LP_TIMING = 1, 2
+LP_COMPILE_HOST_ONLY = 1
+
+
+class LPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_atoms", "n_rules", "n_prime", "nnz", "n_barred", "n_aux", "k", "n_fact_rows", "n_and_rows",
+        "n_or_rows", "device_bytes", "upload_bytes")] + [("compile_ms", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
+                ("launches", ctypes.c_int64), ("tiles", ctypes.c_int64), ("tile_words", ctypes.c_int64),
+                ("max_tile_iters", ctypes.c_int64), ("sum_tile_iters", ctypes.c_int64)]
+
+
+EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models", "lp_last_solve_stats",
+           "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load liblp.so (fails loudly if it was not built; there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"liblp is not built ({path} missing): run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    L.lp_compile.argtypes = [i32, i64, P, P, P, P, u32, P, ctypes.POINTER(P)]
+    L.lp_program_info.argtypes = [P, ctypes.POINTER(_Info)]
+    L.lp_least_model.argtypes = [P, P, P, i32, u32, ctypes.POINTER(i32), P]
+    L.lp_stable_models.argtypes = [P, P, i64, P, P, i64, ctypes.POINTER(i64), i32, P]
+    L.lp_last_solve_stats.argtypes = [P, ctypes.POINTER(_Stats), P]
+    L.lp_export_matrix.argtypes = [P, P, P, P, P, P]
+    L.lp_free.argtypes = [P]
+    L.lp_free.restype = None
+    L.lp_last_error.restype = ctypes.c_char_p
+    L.lp_launch_count.restype = ctypes.c_int64
+    for name in ("lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models", "lp_last_solve_stats",
+                 "lp_export_matrix"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != OK:
+        raise LPError(status, load().lp_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def launch_count() -> int:
+    return int(load().lp_launch_count())
+
+
+def words(n_bits: int) -> int:
+    return max(1, (n_bits + 63) // 64)
+
+
+class Program:
+    """A compiled program (owns the liblp handle)."""
+
+    def __init__(self, n_atoms, head, body_off, body_atom, body_neg=None, stream=None, host_only=False):
+        L = load()
+        self._keep = [np.ascontiguousarray(head, dtype=np.int32), np.ascontiguousarray(body_off, dtype=np.int64),
+                      np.ascontiguousarray(body_atom, dtype=np.int32),
+                      None if body_neg is None else np.ascontiguousarray(body_neg, dtype=np.uint8)]
+        h, off, atom, neg = self._keep
+        self._h = ctypes.c_void_p()
+        _check(L.lp_compile(int(n_atoms), len(h), _ptr(h), _ptr(off), _ptr(atom), _ptr(neg), LP_COMPILE_HOST_ONLY if host_only else 0,
+                            None if host_only else _stream(stream),
+                            ctypes.byref(self._h)))
+        self._keep = None
+        self.info = self._info()
+
+    @classmethod
+    def from_program(cls, prog, stream=None, host_only=False):
+        return cls(prog.n_atoms, prog.head, prog.body_off, prog.body_atom, getattr(prog, "body_neg", None), stream,
+                   host_only)
+
+    def _info(self):
+        i = _Info()
+        _check(load().lp_program_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def refresh_info(self):
+        self.info = self._info()
+        return self.info
+
+    def least_model(self, out, init=None, max_iters=1 << 30, rows=False, timing=False, sync=True, stream=None):
+        """Algorithm 1. ``out``: ceil(n/64) words (ceil(n'/64) with rows=True). Returns the
+        iteration count when sync, else None (status then via last_stats)."""
+        flags = (LP_ROWS if rows else 0) | (LP_TIMING if timing else 0)
+        it = ctypes.c_int32(-1)
+        _check(load().lp_least_model(self._h, _ptr(init), _ptr(out), int(max_iters), flags,
+                                     ctypes.byref(it) if sync else None, _stream(stream)))
+        return it.value if sync else None
+
+    def stable_models(self, stable_mask, guesses=None, n_guesses=None, models=None, max_models=0,
+                      max_iters=1 << 30, sync=True, stream=None):
+        """Algorithms 2 + 3. Returns the number of stable guesses when sync."""
+        if guesses is None and n_guesses is None:
+            n_guesses = 1 << self.info["k"]
+        if n_guesses is None:
+            n_guesses = len(guesses)
+        ns = ctypes.c_int64(-1)
+        _check(load().lp_stable_models(self._h, _ptr(guesses), int(n_guesses), _ptr(stable_mask), _ptr(models),
+                                       int(max_models), ctypes.byref(ns) if sync else None, int(max_iters),
+                                       _stream(stream)))
+        return ns.value if sync else None
+
+    def last_stats(self, stream=None):
+        s = _Stats()
+        _check(load().lp_last_solve_stats(self._h, ctypes.byref(s), _stream(stream)))
+        return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+    def export_matrix(self, stream=None):
+        n, nnz = self.info["n_prime"], self.info["nnz"]
+        row_ptr = np.zeros(n + 1, dtype=np.int64)
+        col = np.zeros(max(nnz, 1), dtype=np.int64)
+        thr = np.zeros(max(n, 1), dtype=np.int32)
+        kind = np.zeros(max(n, 1), dtype=np.int8)
+        _check(load().lp_export_matrix(self._h, _ptr(row_ptr), _ptr(col), _ptr(thr), _ptr(kind), _stream(stream)))
+        return {"row_ptr": row_ptr, "col": col[:nnz], "threshold": thr[:n], "kind": kind[:n]}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lp_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,116 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point that
+include/lp.h declares, validates its inputs, and its host compiler (lp_compile with
+LP_COMPILE_HOST_ONLY) builds exactly the standardized matrix the oracle builds."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2009_10247_gb300 as lp
+from tests.helpers import golden
+from workloads import normal_program, parse, small_definite, tiny_random, transitive_closure
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return lp.load(build_if_missing=True)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lp_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "lp_compile" in names and "lp_least_model" in names and "lp_stable_models" in names
+    raw = ctypes.CDLL(lp.library_path())
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, f"declared but not exported: {missing}"
+    assert sorted(lp.EXPORTS) == sorted(n for n in names if n in lp.EXPORTS)
+
+
+def _compare_with_oracle(prog):
+    s = oracle.standardize(prog)
+    with lp.Program.from_program(prog, host_only=True) as P:
+        info = P.info
+        m = P.export_matrix()
+    assert info["n_prime"] == s.n_prime and info["nnz"] == s.nnz
+    assert info["n_barred"] == s.n_barred and info["n_aux"] == s.n_aux
+    assert info["k"] == len(s.guess_rows())
+    assert np.array_equal(m["row_ptr"], s.row_ptr)
+    assert np.array_equal(m["col"], s.col)
+    assert np.array_equal(m["kind"], s.kind)
+    # threshold t_i with a_ij = 1/t_i (rule rows) or 1 (OR rows, self-loops): the oracle's
+    # exact values num/den must be 1/threshold on every entry, den = 1 for the rest
+    rows = np.repeat(np.arange(s.n_prime), np.diff(s.row_ptr))
+    vals = s.num / s.den[rows]
+    assert np.allclose(vals, 1.0 / np.maximum(m["threshold"][rows], 1))
+    empty = np.diff(s.row_ptr) == 0
+    assert np.all(m["threshold"][empty] == 0) and np.all(m["threshold"][~empty] >= 1)
+
+
+def test_example1_csr_arrays(lib):
+    g = golden("example1.json")
+    p = parse(g["program"], atoms=g["atoms"])
+    with lp.Program.from_program(p, host_only=True) as P:
+        m = P.export_matrix()
+    assert m["row_ptr"].tolist() == g["csr_row_index"]
+    assert m["col"].tolist() == g["csr_col_index"]
+    rows = np.repeat(np.arange(7), np.diff(m["row_ptr"]))
+    assert (1.0 / m["threshold"][rows]).tolist() == g["csr_value"]
+
+
+def test_example2_matrix(lib):
+    g = golden("example2.json")
+    _compare_with_oracle(parse(g["program"], atoms=g["atoms"]))
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_compile_tiny_random(lib, seed):
+    rng = np.random.default_rng(seed)
+    _compare_with_oracle(tiny_random(seed, n_atoms=int(rng.integers(1, 14)), n_rules=int(rng.integers(0, 30)),
+                                     max_body=5, p_fact=0.25, p_neg=0.2 if seed % 2 else 0.0))
+
+
+def test_compile_generators(lib):
+    _compare_with_oracle(small_definite(2))
+    _compare_with_oracle(transitive_closure(40, 3.0, seed=2))
+    _compare_with_oracle(normal_program(seed=4, n=3000, n_rules=9000, k=8, per_atom=3))
+
+
+def test_compile_rejects_malformed(lib):
+    def compile_raw(n, head, off, atom, neg=None):
+        return lp.Program(n, np.array(head), np.array(off), np.array(atom), neg, host_only=True)
+
+    with pytest.raises(lp.LPError) as e:
+        compile_raw(2, [0, 5], [0, 0, 1], [1])  # head out of range
+    assert e.value.status == 1
+    with pytest.raises(lp.LPError):
+        compile_raw(2, [0], [0, 1], [7])  # body atom out of range
+    with pytest.raises(lp.LPError):
+        compile_raw(2, [0, 1], [0, 2, 1], [1, 1])  # decreasing offsets
+    with pytest.raises(lp.LPError):
+        compile_raw(2, [0], [1, 2], [1, 1])  # body_off[0] != 0
+    with pytest.raises(lp.LPError):
+        compile_raw(-1, [], [0], [])
+
+
+def test_empty_program(lib):
+    with lp.Program(0, np.zeros(0, np.int32), np.zeros(1, np.int64), np.zeros(0, np.int32), host_only=True) as P:
+        assert P.info["n_prime"] == 0 and P.info["nnz"] == 0
+
+
+def test_host_only_handle_refuses_solves(lib):
+    p = parse("a. b :- a.")
+    with lp.Program.from_program(p, host_only=True) as P:
+        out = np.zeros(1, np.uint64)
+        with pytest.raises(lp.LPError) as e:
+            P.least_model(out)
+        assert e.value.status == 1

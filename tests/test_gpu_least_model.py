@@ -1,0 +1,164 @@
+"""GPU parity of the least-model path (Algorithm 1 in liblp) against the CPU oracle.
+
+Bit-exact comparison of every model bit and of the iteration count (theta applications),
+on the paper's example, tiny random programs with ragged sizes, every workload generator at
+test sizes, and the full-size large definite program in the launch configuration the
+benchmark times."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2009_10247_gb300 as lp
+from tests.helpers import golden, is_model
+from workloads import (large_definite, parse, small_definite, tiny_random, transitive_closure)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_util import gpu_least_model  # noqa: E402
+
+
+def _parity(prog, init=None):
+    want, want_it = oracle.least_model(prog, init=init)
+    with lp.Program.from_program(prog) as P:
+        got, it = gpu_least_model(P, init=init)
+    assert np.array_equal(got, want), f"{np.count_nonzero(got != want)} atoms differ"
+    assert it == want_it
+    return got, it
+
+
+def test_example1():
+    g = golden("example1.json")
+    got, it = _parity(parse(g["program"], atoms=g["atoms"]))
+    assert got.all() and it == 3
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_tiny_random(seed):
+    rng = np.random.default_rng(seed)
+    _parity(tiny_random(seed, n_atoms=int(rng.integers(1, 90)), n_rules=int(rng.integers(0, 200)),
+                        max_body=6, p_fact=0.2))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fact_subsets(seed):
+    p = small_definite(10 + seed)
+    keep = p.fact_atoms() & (np.random.default_rng(seed).random(p.n_atoms) < 0.5)
+    _parity(p, init=keep)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_small_definite(seed):
+    got, it = _parity(small_definite(seed))
+    assert it > 40
+
+
+def test_transitive_closure_bfs_30():
+    p = transitive_closure(30, 2.0, seed=7)
+    got, _ = _parity(p)
+    N, E = p.meta["n_nodes"], len(p.meta["edges"])
+    adj = {x: [] for x in range(N)}
+    for x, y in p.meta["edges"]:
+        adj[int(x)].append(int(y))
+    for x in range(N):
+        seen, stack = set(), list(adj[x])
+        while stack:
+            y = stack.pop()
+            if y not in seen:
+                seen.add(y)
+                stack.extend(adj[y])
+        row = got[E + x * N:E + (x + 1) * N]
+        assert set(np.nonzero(row)[0].tolist()) == seen
+
+
+def test_transitive_closure_500():
+    _parity(transitive_closure(500, 4.0, seed=1))
+
+
+def test_large_definite_scaled():
+    _parity(large_definite(seed=2, n=100_000, n_rules=500_000, chain_levels=100, chain_width=20))
+
+
+def test_large_definite_full_size():
+    # the benchmark workload itself: 1e6 atoms, 5e6 rules, ~1000 iterations
+    p = large_definite(seed=1)
+    got, it = _parity(p)
+    assert it > 1000
+    assert is_model(p, got)
+
+
+def test_rows_mode_matches_literal_algorithm1():
+    p = small_definite(4)
+    s = oracle.standardize(p)
+    rng = np.random.default_rng(0)
+    with lp.Program.from_program(p) as P:
+        for trial in range(4):
+            v0 = rng.random(s.n_prime) < 0.3
+            want, want_it, ok = oracle.alg1(s, v0.astype(np.uint8), max_iters=500)
+            if ok:
+                got, it = gpu_least_model(P, init=v0, rows=True, max_iters=500)
+                assert np.array_equal(got, want.astype(bool)) and it == want_it
+            else:
+                with pytest.raises(lp.LPError) as e:
+                    gpu_least_model(P, init=v0, rows=True, max_iters=500)
+                assert e.value.status == 4
+
+
+def test_oscillation_reports_no_fixpoint():
+    p = parse("p :- q. q :- p.")
+    with lp.Program.from_program(p) as P:
+        with pytest.raises(lp.LPError) as e:
+            gpu_least_model(P, init=np.array([1, 0], bool), rows=True, max_iters=51)
+        assert e.value.status == 4
+
+
+def test_max_iters_too_small():
+    p = small_definite(1)
+    with lp.Program.from_program(p) as P:
+        with pytest.raises(lp.LPError) as e:
+            gpu_least_model(P, max_iters=5)
+        assert e.value.status == 4
+
+
+def test_init_must_be_subset_of_facts():
+    p = parse("a. b :- a. c.")
+    with lp.Program.from_program(p) as P:
+        with pytest.raises(lp.LPError) as e:
+            gpu_least_model(P, init=np.array([1, 1, 0], bool))
+        assert e.value.status == 1
+        got, it = gpu_least_model(P, init=np.array([0, 0, 1], bool))
+        assert got.tolist() == [False, False, True]
+
+
+def test_host_buffers_and_async_stats():
+    p = small_definite(5)
+    want, want_it = oracle.least_model(p)
+    with lp.Program.from_program(p) as P:
+        out = np.zeros(lp.words(p.n_atoms), np.uint64)
+        it = P.least_model(out)  # host output: staged through device memory
+        from tests.helpers import bits_to_bool
+        assert np.array_equal(bits_to_bool(out, p.n_atoms), want) and it == want_it
+        dev_out = torch.zeros(lp.words(p.n_atoms), dtype=torch.int64, device="cuda:0")
+        assert P.least_model(dev_out, sync=False, timing=True) is None
+        st = P.last_stats()
+        assert st["status"] == 0 and st["iters"] == want_it and st["kernel_ms"] > 0 and st["launches"] == 1
+
+
+def test_degenerate_programs():
+    for text in ["a.", "a :- b.", "a :- a.", "a. a. a :- a.", "a :- b, c. b :- c. c :- a."]:
+        _parity(parse(text))
+    empty = type("E", (), dict(n_atoms=0, head=np.zeros(0, np.int32), body_off=np.zeros(1, np.int64),
+                               body_atom=np.zeros(0, np.int32), body_neg=None))
+    with lp.Program.from_program(empty) as P:
+        out = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+        assert P.least_model(out) == 1
+
+
+def test_ragged_word_boundaries():
+    # n' just around multiples of 32 / 64 rows
+    for n in (31, 32, 33, 63, 64, 65, 127, 129):
+        rules = [(i, [i - 1]) for i in range(1, n)] + [(0, [])]
+        from workloads import from_rules
+        p = from_rules(n, rules)
+        got, it = _parity(p)
+        assert got.all() and it == n

@@ -1,0 +1,117 @@
+"""GPU parity of the stable-model path (Algorithms 2 and 3 in liblp) against the oracle.
+
+The stable bit of every guess and every returned model are compared bit for bit with the
+oracle's per-guess Algorithm 2/3 (and its Gelfond-Lifschitz check), on the paper's example,
+textbook programs, tiny random normal programs, multi-tile runs, explicit guess lists, and
+the full-size 2^16-guess workload in the configuration the benchmark times (sampled guesses
+plus a reduct check of every model found)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2009_10247_gb300 as lp
+from tests.helpers import golden
+from workloads import normal_program, parse, small_definite, tiny_random
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_util import gpu_stable  # noqa: E402
+
+
+def _parity(prog, guesses=None, max_models=64):
+    st4, m4, _ = oracle.stable_models_alg23(prog, guesses=guesses)
+    with lp.Program.from_program(prog) as P:
+        st, models, ns = gpu_stable(P, guesses=guesses, max_models=max_models)
+    assert np.array_equal(st, st4)
+    assert ns == int(st4.sum())
+    want_models = m4[st4]
+    assert np.array_equal(models, want_models[:max_models])
+    return st, models
+
+
+def test_example2():
+    g = golden("example2.json")
+    st, models = _parity(parse(g["program"], atoms=g["atoms"]))
+    assert st.tolist() == [True]
+    assert models[0].tolist() == [a == "t" for a in g["atoms"]]
+
+
+@pytest.mark.parametrize("text,n_models", [
+    ("p :- not q. q :- not p.", 2), ("p :- not p.", 0), ("p :- not q.", 1),
+    ("a :- not b. b :- not a. c :- a. c :- b.", 2), ("p :- not q. q :- not r. r :- not p.", 0),
+])
+def test_textbook(text, n_models):
+    st, models = _parity(parse(text))
+    assert st.sum() == n_models
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_tiny_random_normal(seed):
+    rng = np.random.default_rng(2000 + seed)
+    _parity(tiny_random(2000 + seed, n_atoms=int(rng.integers(2, 60)), n_rules=int(rng.integers(1, 120)),
+                        max_body=4, p_fact=0.15, p_neg=0.1))
+
+
+def test_definite_program_single_column():
+    p = small_definite(2)
+    st, models = _parity(p)
+    assert st.tolist() == [True] and np.array_equal(models[0], oracle.least_model(p)[0])
+
+
+@pytest.mark.parametrize("tile_bytes", [None, "1"])
+def test_normal_program_all_guesses(tile_bytes, monkeypatch):
+    # 1 byte of budget forces one 64-guess word per tile: many tiles, one launch
+    if tile_bytes:
+        monkeypatch.setenv("LP_TILE_BYTES", tile_bytes)
+    p = normal_program(seed=5, n=3000, n_rules=9000, k=10, per_atom=3)
+    _parity(p, max_models=8)
+
+
+def test_choice_program_many_models():
+    # k independent even loops a_i <- not b_i, b_i <- not a_i: 2^k stable models out of 4^k guesses
+    k = 5
+    text = " ".join(f"a{i} :- not b{i}. b{i} :- not a{i}. c :- a{i}." for i in range(k))
+    st, models = _parity(parse(text), max_models=64)
+    assert st.sum() == 2 ** k
+
+
+def test_explicit_guesses():
+    p = normal_program(seed=6, n=2000, n_rules=6000, k=12, per_atom=3)
+    rng = np.random.default_rng(1)
+    g = rng.integers(0, 1 << 12, 777).astype(np.uint64)
+    g[:5] = g[0]  # duplicates are evaluated independently
+    _parity(p, guesses=g, max_models=16)
+
+
+def test_zero_guesses_and_host_buffers():
+    p = parse("p :- not q. q :- not p.")
+    with lp.Program.from_program(p) as P:
+        mask = np.zeros(1, np.uint64)
+        assert P.stable_models(mask, guesses=np.zeros(0, np.uint64), n_guesses=0) == 0
+        models = np.zeros((4, 1), np.uint64)
+        ns = P.stable_models(mask, models=models, max_models=4)
+        assert ns == 2 and int(mask[0]) == 0b0110
+        assert sorted(int(x) for x in models[:2, 0]) == [0b01, 0b10]
+
+
+def test_full_size_2_16_guesses_sampled():
+    # 1e5 atoms, 3e5 rules, k = 16: all 65,536 guesses on the GPU; the oracle checks a sample
+    # of guesses with Algorithms 2/3 and every stable model found with the reduct.
+    p = normal_program(seed=1)
+    s = oracle.standardize(p)
+    with lp.Program.from_program(p) as P:
+        assert P.info["k"] == 16
+        st, models, ns = gpu_stable(P, max_models=256)
+    rng = np.random.default_rng(0)
+    sample = np.unique(np.concatenate([rng.integers(0, 1 << 16, 96), np.nonzero(st)[0][:32], [0, 65535]]))
+    st4, m4, _ = oracle.stable_models_alg23(p, guesses=sample.astype(np.uint64), std=s)
+    assert np.array_equal(st[sample], st4)
+    idx = np.nonzero(st)[0]
+    assert ns == len(idx)
+    if len(idx):
+        st5, m5 = oracle.stable_models_gl(p, guesses=idx[:32].astype(np.uint64), std=s)
+        assert st5.all()
+        assert np.array_equal(models[:min(32, len(idx))], m5)

@@ -1,0 +1,326 @@
+"""Benchmark: fixpoint rule-evaluations per second of the least-model solve on the large
+definite program (1e6 atoms, 5e6 rules, ~1000 iterations), plus batched stable-model
+guesses per second on the 2^16-guess normal program, on one GB300 per rank.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one full least-model solve (initial vector, theta iterations to the fixpoint,
+output projection) with the program matrix resident in HBM; L2 is flushed (256 MiB write)
+before every step. value = nnz x iterations x steps x ranks / (max over ranks of the summed
+device time). e2e runs the public C ABI from host arrays: lp_compile (standardize, order,
+CSR, upload), lp_least_model with a host initial vector and host output, lp_free.
+The reference arm (--impl reference) times the CPU oracle's Algorithm 1 on the same matrix.
+Under torchrun every rank runs its own replica (the single-vector solve does not shard).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import large_definite, normal_program  # noqa: E402
+
+METRIC = "fixpoint rule-evals/sec (nnz x iters / s)"
+UNIT = "rule-evals/s"
+WORKLOAD = "large definite program: 1e6 atoms, 5e6 rules, Geom(mean 3, cap 8) bodies, Zipf(1.1) atoms, 1% facts, chain 1000x50 (seed 1)"
+WORKLOAD_STABLE = "normal program: 1e5 atoms, 3e5 rules, bodies U{1..6}, 1% facts, k=16 negated atoms x 4 (seed 1), all 65536 guesses"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def alg_bytes_per_iter(n_prime, nnz):
+    # row_ptr + col read once, x read once, y written once (bits)
+    return 4 * (n_prime + 1) + 4 * nnz + 2 * ((n_prime + 7) // 8)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+                self.lines = [ln for ln in out.splitlines() if ln.strip()]
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(prog, iters, std=None):
+    """The CPU oracle (Algorithm 1, exact integer theta, OpenMP over rows) for `iters`
+    theta applications from the fact vector of the full matrix."""
+    import oracle
+    std = std or oracle.standardize(prog)
+    v0 = oracle.initial_vector(std)
+    t = time.perf_counter()
+    _, done, _ = oracle.alg1(std, v0, max_iters=iters)
+    dt = time.perf_counter() - t
+    return std, done, dt, oracle.num_threads()
+
+
+def run_reference(args, prog):
+    """Reference arm: the oracle as it stands, on the host cores, bounded samples."""
+    import oracle
+    t0 = time.perf_counter()
+    std = oracle.standardize(prog)
+    std_s = time.perf_counter() - t0
+    per_step = args.ref_iters
+    for _ in range(args.warmup):
+        cpu_oracle_sample(prog, per_step, std)
+    total_evals, total_t, cores = 0, 0.0, 1
+    for _ in range(args.steps):
+        _, done, dt, cores = cpu_oracle_sample(prog, per_step, std)
+        total_evals += std.nnz * done
+        total_t += dt
+    value = total_evals / total_t
+    sample = (f"Algorithm 1 (oracle O2) on the full standardized matrix (n'={std.n_prime}, nnz={std.nnz}), "
+              f"{per_step} theta applications per step from the fact vector; standardize took {std_s:.2f} s (untimed)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_prime": std.n_prime, "nnz": std.nnz},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-iters", type=int, default=400, help="oracle theta applications in cpu_baseline")
+    ap.add_argument("--ref-iters", type=int, default=25, help="oracle theta applications per reference step")
+    ap.add_argument("--no-stable", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, large_definite(seed=1))
+        return
+
+    import torch
+    import paper_2009_10247_gb300 as lp
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    lp.load()
+
+    prog = large_definite(seed=1)
+    P = lp.Program.from_program(prog)
+    info = P.info
+    n, n_prime, nnz = info["n_atoms"], info["n_prime"], info["nnz"]
+    out = torch.zeros(lp.words(n), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    iters = P.least_model(out)  # checks status once, synchronously
+    for _ in range(args.warmup):
+        flush.zero_()
+        P.least_model(out, sync=False, timing=True)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    launches0 = lp.launch_count()
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            P.least_model(out, sync=False, timing=True)
+            ends[i].record(stream)
+            st = P.last_stats()  # waits; reads the kernel's own CUDA events
+            if st["status"] != 0 or st["iters"] != iters:
+                raise RuntimeError(f"solve failed: {st}")
+            kernel_ms.append(st["kernel_ms"])
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - wall0
+    launches = lp.launch_count() - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * nnz * iters * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the persistent fixpoint kernel)
+    peak, peak_kind = peaks()
+    per_launch_bytes = alg_bytes_per_iter(n_prime, nnz) * iters
+    k_ms = sum(kernel_ms) / len(kernel_ms)
+    achieved = per_launch_bytes / (k_ms / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers
+    facts_host = np.zeros(lp.words(n), dtype=np.uint64)
+    fa = prog.fact_atoms()
+    facts_host[:] = np.packbits(np.pad(fa, (0, lp.words(n) * 64 - n)).astype(np.uint8), bitorder="little").view(np.uint64)
+    out_host = np.zeros(lp.words(n), dtype=np.uint64)
+    e2e_t, h2d = [], 0
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Q = lp.Program.from_program(prog)
+        it2 = Q.least_model(out_host, init=facts_host)
+        h2d = Q.info["upload_bytes"] + facts_host.nbytes
+        Q.close()
+        dt = time.perf_counter() - t0
+        if i > 0:  # first one warms the allocator
+            e2e_t.append(dt)
+        assert it2 == iters
+    e2e = None
+    if e2e_t:
+        if not np.array_equal(out_host, out.cpu().numpy().view(np.uint64)):
+            raise RuntimeError("e2e output differs from the device-timed output")
+        e2e = {"value": world * nnz * iters / (sum(e2e_t) / len(e2e_t)), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_host.nbytes),
+               "ms_per_step": 1e3 * sum(e2e_t) / len(e2e_t)}
+
+    secondary = None
+    if not args.no_stable and rank == 0:
+        secondary = bench_stable(lp, torch, dev, flush)
+
+    cpu = None
+    if rank == 0 and args.cpu_iters > 0:
+        std, done, dt, cores = cpu_oracle_sample(prog, args.cpu_iters)
+        cpu = {"value": std.nnz * done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"Algorithm 1 (oracle O2, OpenMP over rows) on the same full matrix, first {done} of "
+                         f"{iters} theta applications from the fact vector ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_atoms": n, "n_rules": int(prog.n_rules), "n_prime": n_prime,
+                       "nnz": nnz, "iters": iters, "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every step (256 MiB write)", "wall_s": round(wall, 3)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "fixpoint_kernel", "kernel_ms": k_ms, "bytes_per_launch": per_launch_bytes,
+                         "bytes_per_iter": alg_bytes_per_iter(n_prime, nnz)},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "stable_models": secondary,
+        }
+        print(json.dumps(line), flush=True)
+    P.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def bench_stable(lp, torch, dev, flush, steps=5):
+    """Batched stable models (Algorithms 2 + 3): all 2^16 guesses of the normal program."""
+    prog = normal_program(seed=1)
+    P = lp.Program.from_program(prog)
+    k = P.info["k"]
+    ng = 1 << k
+    mask = torch.zeros(lp.words(ng), dtype=torch.int64, device=dev)
+    ns = P.stable_models(mask)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        flush.zero_()
+        P.stable_models(mask, sync=False)
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.stable_models(mask, sync=False)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    st = P.last_stats()
+    ms = sum(ts) / len(ts)
+    info = P.info
+    W = st["tile_words"]
+    bytes_tile_iter = 4 * (info["n_prime"] + 1) + 4 * info["nnz"] + 16 * info["n_prime"] * W
+    achieved = bytes_tile_iter * st["sum_tile_iters"] / (ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    out = {"metric": "stable-model guesses/sec", "value": ng / (ms / 1e3), "unit": "guesses/s",
+           "ms_per_step": ms, "workload": WORKLOAD_STABLE, "n_prime": info["n_prime"], "nnz": info["nnz"], "k": k,
+           "n_stable": ns, "tiles": st["tiles"], "tile_words": W, "tile_iters_max": st["max_tile_iters"],
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "peak_kind": peak_kind, "kernel": "stable_kernel",
+                        "note": "tiles are sized to stay L2 resident, so this fraction can exceed 1"}}
+    P.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

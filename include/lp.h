@@ -167,6 +167,37 @@ lp_status lp_last_solve_stats(lp_program* prog, lp_solve_stats* out, void* cuda_
 lp_status lp_export_matrix(const lp_program* prog, int64_t* row_ptr, int64_t* col, int32_t* threshold,
                            int8_t* kind, void* cuda_stream);
 
+/*
+ * lp_least_model_static -- Algorithm 1 on a matrix the caller already holds in device memory,
+ * without allocating anything. The paper has no counterpart: this is a deployment variant of
+ * lp_least_model for callers that may not call cudaMalloc or cudaFree, such as code that runs
+ * under another framework's fixed device-memory pool or budget, or a latency-critical loop that
+ * cannot afford the synchronisation an allocation can cause.
+ *
+ * Its only scratch (a second iterate vector and a control block) is one fixed array of
+ * 256 B + 2 MiB compiled into liblp; every GPU that loads the library holds it until the process
+ * exits. Hence n_rows <= 2^24 (16,777,216); larger matrices return LP_ERR_INVALID with a message.
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress) and queries the
+ * kernel's occupancy; make that first call before any stream capture. Every call on a device
+ * shares the array and it keeps the previous call's contents (the control block is cleared
+ * at the start of each call): calls that overlap on the GPU -- on different streams or threads
+ * -- race and must not be issued.
+ *
+ * Matrix (device, read only): row_ptr (n_rows + 1 int32, non-decreasing, row_ptr[0] = 0), col
+ * (row_ptr[n_rows] int32 column ids in [0, n_rows); an id outside is reported as
+ * LP_ERR_INVALID and counts as false), threshold (n_rows int32): row i becomes true when at
+ * least threshold[i] of its entries are true -- the body size for a rule (entries 1/m), 1 for an
+ * OR-rule or a self-loop; values below 1 count as 1. lp_export_matrix returns this form.
+ * v0 (device, ceil(n_rows/64) words): initial vector over the rows; out (device, same size,
+ * may be v0 itself): receives the fixpoint (or the last iterate when max_iters is reached).
+ * Host pointers are rejected (LP_ERR_INVALID): nothing is staged. iters_out (host, nullable):
+ * when given, the call waits for the device and reports the theta applications and the device
+ * status (LP_ERR_NO_FIXPOINT, LP_ERR_INVALID, LP_ERR_TIMEOUT); when NULL it only enqueues.
+ */
+lp_status lp_least_model_static(int32_t n_rows, const int32_t* row_ptr, const int32_t* col, const int32_t* threshold,
+                                const uint64_t* v0, uint64_t* out, int32_t max_iters, int32_t* iters_out,
+                                void* cuda_stream);
+
 /* Release a handle and its device memory (NULL is a no-op). Waits for no stream: the caller
  * must make sure no enqueued work still uses it. */
 void lp_free(lp_program* prog);

@@ -37,7 +37,7 @@ class _Stats(ctypes.Structure):
 
 
 EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models", "lp_last_solve_stats",
-           "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count"]
+           "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static"]
 
 _lib = None
 
@@ -64,6 +64,8 @@ def load(build_if_missing: bool = False):
     L.lp_stable_models.argtypes = [P, P, i64, P, P, i64, ctypes.POINTER(i64), i32, P]
     L.lp_last_solve_stats.argtypes = [P, ctypes.POINTER(_Stats), P]
     L.lp_export_matrix.argtypes = [P, P, P, P, P, P]
+    L.lp_least_model_static.argtypes = [i32, P, P, P, P, P, i32, ctypes.POINTER(i32), P]
+    L.lp_least_model_static.restype = ctypes.c_int
     L.lp_free.argtypes = [P]
     L.lp_free.restype = None
     L.lp_last_error.restype = ctypes.c_char_p
@@ -106,6 +108,15 @@ def _stream(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def least_model_static(n_rows, row_ptr, col, threshold, v0, out, max_iters=1 << 30, sync=True, stream=None):
+    """lp_least_model_static: Algorithm 1 on caller-held device buffers, no allocation.
+    Returns the iteration count when sync."""
+    it = ctypes.c_int32(-1)
+    _check(load().lp_least_model_static(int(n_rows), _ptr(row_ptr), _ptr(col), _ptr(threshold), _ptr(v0), _ptr(out),
+                                        int(max_iters), ctypes.byref(it) if sync else None, _stream(stream)))
+    return it.value if sync else None
 
 
 def launch_count() -> int:

@@ -50,6 +50,11 @@ struct lp_program {
   int32_t* neg_row = nullptr;
   int32_t* bar_row = nullptr;
   int32_t* row_tag = nullptr;
+  // streamed layout of the least-model kernel
+  uint32_t* desc = nullptr;
+  int32_t* word_hdr = nullptr;
+  int32_t* and_col = nullptr;
+  int32_t* groups = nullptr;
   // scratch
   uint32_t* x[2] = {nullptr, nullptr};
   DeviceCtl* ctl = nullptr;
@@ -155,7 +160,7 @@ lp_status ensure_scratch(lp_program* p) {
 void release(lp_program* p) {
   void* ptrs[] = {p->row_ptr, p->col, p->any_mask, p->perm, p->inv, p->fact_row, p->fact_owner, p->fact_mask,
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
-                  p->stage_out.p, p->stage_out2.p};
+                  p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_ctl) cudaFreeHost(p->h_ctl);
@@ -232,6 +237,10 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   if ((st = upload(p, &p->neg_row, hm.neg_row, s)) != LP_OK) return cleanup(st);
   if ((st = upload(p, &p->bar_row, hm.bar_row, s)) != LP_OK) return cleanup(st);
   if ((st = upload(p, &p->row_tag, hm.row_tag, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->desc, hm.desc, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->word_hdr, hm.word_hdr, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->and_col, hm.and_col, s)) != LP_OK) return cleanup(st);
+  if ((st = upload(p, &p->groups, hm.groups, s)) != LP_OK) return cleanup(st);
   if ((st = dalloc(p, &p->x[0], (size_t)hm.n_pad / 32)) != LP_OK) return cleanup(st);
   if ((st = dalloc(p, &p->x[1], (size_t)hm.n_pad / 32)) != LP_OK) return cleanup(st);
   if ((st = ensure_scratch(p)) != LP_OK) return cleanup(st);
@@ -240,6 +249,10 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   std::vector<int32_t>().swap(hm.row_ptr);
   std::vector<int32_t>().swap(hm.col);
   std::vector<int32_t>().swap(hm.row_tag);
+  std::vector<uint32_t>().swap(hm.desc);
+  std::vector<int32_t>().swap(hm.word_hdr);
+  std::vector<int32_t>().swap(hm.and_col);
+  std::vector<int32_t>().swap(hm.groups);
   p->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
   return LP_OK;
@@ -329,13 +342,32 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
   a.perm = p->perm;
   a.n_out = n_in;
 
-  static int per_sm = -1;
-  if (per_sm < 0) per_sm = fixpoint_blocks_per_sm();
-  if (per_sm <= 0) return fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident");
-  const int warps_per_block = kFixBlock / 32;
-  int grid = std::min(max_coresident(p, per_sm), std::max(1, (a.n_words + warps_per_block - 1) / warps_per_block));
-  if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
-  if ((st = launch_count_and_check(launch_fixpoint(a, grid, s), "launch fixpoint kernel", p)) != LP_OK) return st;
+  // Kernel choice: the one-warp-per-word kernel (default) or the streamed kernel
+  // (LP_FIXPOINT=stream), both exact; the environment variable exists for A/B measurement.
+  static int variant = -1;
+  if (variant < 0) {
+    const char* env = std::getenv("LP_FIXPOINT");
+    variant = (env && std::strcmp(env, "stream") == 0) ? 1 : 0;
+  }
+  cudaError_t le;
+  if (variant == 1) {
+    static int per_sm_s = -1;
+    if (per_sm_s < 0) per_sm_s = fixpoint_stream_blocks_per_sm();
+    if (per_sm_s <= 0) return fail(LP_ERR_CUDA, "streamed fixpoint kernel cannot be resident");
+    StreamLayout L{p->desc, p->word_hdr, p->and_col, p->groups, hm.n_groups};
+    int grid = std::max(1, std::min(max_coresident(p, per_sm_s), hm.n_groups));
+    if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
+    le = launch_fixpoint_stream(a, L, grid, s);
+  } else {
+    static int per_sm = -1;
+    if (per_sm < 0) per_sm = fixpoint_blocks_per_sm();
+    if (per_sm <= 0) return fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident");
+    const int warps_per_block = kFixBlock / 32;
+    int grid = std::min(max_coresident(p, per_sm), std::max(1, (a.n_words + warps_per_block - 1) / warps_per_block));
+    if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
+    le = launch_fixpoint(a, grid, s);
+  }
+  if ((st = launch_count_and_check(le, "launch fixpoint kernel", p)) != LP_OK) return st;
   if (p->timed) LP_CUDA(cudaEventRecord(p->ev1, s));
   LP_CUDA(cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s));
   if (host_out) LP_CUDA(cudaMemcpyAsync(out, d_out, out_words * 8, cudaMemcpyDeviceToHost, s));

@@ -275,6 +275,76 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       }
     }
 
+    // ---- streamed layout (row descriptors, word headers, rule-row entries, stage groups)
+    {
+      const int32_t nw = npad / 32;
+      hm.desc.assign(npad, 0u);
+      hm.word_hdr.assign(2 * ((size_t)nw + 1), 0);
+      int64_t n_and = 0;
+      for (int32_t i = 0; i < np; i++) {
+        const int8_t kd = kind[inv[i]];
+        const int64_t len = hm.row_ptr[i + 1] - hm.row_ptr[i];
+        if (len >= (int64_t(1) << 30)) {
+          err = "row too long for the streamed layout";
+          return LP_ERR_INVALID;
+        }
+        uint32_t sk = (kd == K_OR) ? SK_OR : (kd == K_FACT || kd == K_BARRED) ? SK_SELF : SK_RULE;
+        hm.desc[i] = (sk << 30) | (uint32_t)len;
+        if (sk == SK_RULE) n_and += len;
+      }
+      hm.and_col.assign((size_t)n_and + 8, 0);
+      int64_t ca = 0, oa = nA;  // OR rows' new atoms are section B in OR-row order
+      for (int32_t i = 0; i < npad; i++) {
+        if ((i & 31) == 0) {
+          hm.word_hdr[2 * (i >> 5)] = (int32_t)ca;
+          hm.word_hdr[2 * (i >> 5) + 1] = (int32_t)oa;
+        }
+        if (i >= np) continue;
+        const uint32_t sk = hm.desc[i] >> 30;
+        const int32_t b = hm.row_ptr[i], e = hm.row_ptr[i + 1];
+        if (sk == SK_RULE) {
+          for (int32_t t = b; t < e; t++) hm.and_col[ca++] = hm.col[t];
+        } else if (sk == SK_OR) {
+          for (int32_t t = b; t < e; t++)
+            if (hm.col[t] != oa + (t - b)) {
+              err = "internal error: OR row entries are not the next new atoms";
+              return LP_ERR_INVALID;
+            }
+          oa += e - b;
+        } else if (e - b != 1 || hm.col[b] != i) {
+          err = "internal error: self-loop row expected";
+          return LP_ERR_INVALID;
+        }
+      }
+      hm.word_hdr[2 * nw] = (int32_t)ca;
+      hm.word_hdr[2 * nw + 1] = (int32_t)oa;
+      // groups of an even number of words whose entries fit a stage (with alignment slack)
+      hm.groups.clear();
+      const int32_t cap = kStageColInts - 8;
+      int32_t w = 0;
+      while (w < nw) {
+        int32_t w1 = w;
+        auto words_cols = [&](int32_t a, int32_t b2) { return hm.word_hdr[2 * b2] - hm.word_hdr[2 * a]; };
+        while (w1 < nw && w1 - w < kGroupWordsMax && words_cols(w, std::min(w1 + 2, nw)) <= cap)
+          w1 = std::min(w1 + 2, nw);
+        int32_t ncol;
+        const int32_t c0 = hm.word_hdr[2 * w] & ~3;
+        if (w1 == w) {  // one pair of words alone exceeds a stage: its entries stay in global memory
+          w1 = std::min(w + 2, nw);
+          ncol = -1;
+        } else {
+          const int32_t c1 = (hm.word_hdr[2 * w1] + 3) & ~3;
+          ncol = c1 - c0;
+        }
+        hm.groups.push_back(w);
+        hm.groups.push_back(w1);
+        hm.groups.push_back(c0);
+        hm.groups.push_back(ncol);
+        w = w1;
+      }
+      hm.n_groups = (int32_t)(hm.groups.size() / 4);
+    }
+
     hm.n = n;
     hm.n_rules = n_rules;
     hm.n_prime = np;

@@ -39,6 +39,17 @@ constexpr int kFixBlock = 256;
 cudaError_t launch_fixpoint(const FixArgs& a, int grid, cudaStream_t s);
 int fixpoint_blocks_per_sm();
 
+// The same loop with the matrix streamed through shared memory (fixpoint_stream.cu).
+struct StreamLayout {
+  const uint32_t* desc;     // n_pad row descriptors
+  const int32_t* word_hdr;  // 2 * (n_pad / 32 + 1)
+  const int32_t* and_col;   // rule-row entries (+ padding)
+  const int32_t* groups;    // 4 per group
+  int32_t n_groups;
+};
+cudaError_t launch_fixpoint_stream(const FixArgs& a, const StreamLayout& layout, int grid, cudaStream_t s);
+int fixpoint_stream_blocks_per_sm();
+
 // Algorithms 2 + 3 over tiles of 64-bit guess words (persistent cooperative kernel).
 struct StableArgs {
   const int32_t* row_ptr;

@@ -162,3 +162,15 @@ def test_ragged_word_boundaries():
         p = from_rules(n, rules)
         got, it = _parity(p)
         assert got.all() and it == n
+
+
+def test_rows_longer_than_a_stage():
+    # a rule with 7000 body atoms: its word's entries do not fit a shared-memory stage and
+    # are read from global memory; a word with more than 1024 entries takes the long path
+    from workloads import from_rules
+    rules = [(0, list(range(1, 7001)))] + [(a, []) for a in range(1, 7001)] + [(7001, [0]), (7002, [0]), (7002, [7001])]
+    got, it = _parity(from_rules(7003, rules))
+    assert got.all()
+    rules = [(0, list(range(1, 7001)))] + [(a, []) for a in range(1, 7000)] + [(7001, [0])]
+    got, it = _parity(from_rules(7002, rules))
+    assert not got[0] and not got[7001]

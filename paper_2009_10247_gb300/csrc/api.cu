@@ -241,8 +241,9 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   if ((st = upload(p, &p->word_hdr, hm.word_hdr, s)) != LP_OK) return cleanup(st);
   if ((st = upload(p, &p->and_col, hm.and_col, s)) != LP_OK) return cleanup(st);
   if ((st = upload(p, &p->groups, hm.groups, s)) != LP_OK) return cleanup(st);
-  if ((st = dalloc(p, &p->x[0], (size_t)hm.n_pad / 32)) != LP_OK) return cleanup(st);
-  if ((st = dalloc(p, &p->x[1], (size_t)hm.n_pad / 32)) != LP_OK) return cleanup(st);
+  // iterate vectors, padded so 16-byte vector loads of a staged prefix stay inside
+  if ((st = dalloc(p, &p->x[0], (size_t)hm.n_pad / 32 + 4)) != LP_OK) return cleanup(st);
+  if ((st = dalloc(p, &p->x[1], (size_t)hm.n_pad / 32 + 4)) != LP_OK) return cleanup(st);
   if ((st = ensure_scratch(p)) != LP_OK) return cleanup(st);
   e = cudaStreamSynchronize(s);  // host vectors are pageable and about to be released
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "upload"));
@@ -354,7 +355,7 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
     static int per_sm_s = -1;
     if (per_sm_s < 0) per_sm_s = fixpoint_stream_blocks_per_sm();
     if (per_sm_s <= 0) return fail(LP_ERR_CUDA, "streamed fixpoint kernel cannot be resident");
-    StreamLayout L{p->desc, p->word_hdr, p->and_col, p->groups, hm.n_groups};
+    StreamLayout L{p->desc, p->word_hdr, p->and_col, p->groups, hm.n_groups, hm.n_sec_a};
     int grid = std::max(1, std::min(max_coresident(p, per_sm_s), hm.n_groups));
     if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
     le = launch_fixpoint_stream(a, L, grid, s);

@@ -318,6 +318,24 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       }
       hm.word_hdr[2 * nw] = (int32_t)ca;
       hm.word_hdr[2 * nw + 1] = (int32_t)oa;
+      // words whose rows all have <= 32 entries carry each row's offset in its descriptor
+      for (int32_t wd = 0; wd < nw; wd++) {
+        bool small = true;
+        for (int l = 0; l < 32; l++) small &= (hm.desc[32 * wd + l] & 0x3fffffffu) <= 32u;
+        if (!small) {
+          hm.word_hdr[2 * wd + 1] = (int32_t)((uint32_t)hm.word_hdr[2 * wd + 1] | kLongWord);
+          continue;
+        }
+        uint32_t ao = 0, oo = 0;
+        for (int l = 0; l < 32; l++) {
+          uint32_t& d = hm.desc[32 * wd + l];
+          const uint32_t sk = d >> 30, len = d & 0x3fffffffu;
+          const uint32_t off = sk == SK_RULE ? ao : (sk == SK_OR ? oo : 0u);
+          if (sk == SK_RULE) ao += len;
+          if (sk == SK_OR) oo += len;
+          d = (sk << 30) | (off << 6) | len;
+        }
+      }
       // groups of an even number of words whose entries fit a stage (with alignment slack)
       hm.groups.clear();
       const int32_t cap = kStageColInts - 8;
@@ -343,6 +361,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         w = w1;
       }
       hm.n_groups = (int32_t)(hm.groups.size() / 4);
+      hm.n_sec_a = nA;
     }
 
     hm.n = n;

@@ -20,6 +20,8 @@ struct DeviceCtl {
   long long n_stable;    // stable guesses found so far
   long long tiles;
   unsigned long long timeout_site;  // where a wait gave up (diagnostics)
+  unsigned long long count[3];      // true rows per iteration, rotating (monotone runs)
+  unsigned long long init_count;    // true rows of the initial vector
 };
 
 // Upper bound of one barrier wait. A healthy wait takes microseconds; after this the waiting
@@ -36,6 +38,10 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {

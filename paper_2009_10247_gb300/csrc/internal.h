@@ -37,18 +37,22 @@ struct HostMatrix {
   std::vector<int32_t> row_tag;    // n_pad: -1 zero, -2 fact, j >= 0 guessed barred atom j,
                                    //        -3 barred atom of a fact (initial column of Def. 8)
 
-  // Streamed layout of the least-model kernel (see fixpoint.cu). Per row one descriptor
-  // kind << 30 | length: kind 0 = rule row (entries listed in and_col), 1 = OR-rule row (its
-  // entries are the next `length` new atoms after those of the OR rows before it, so they are
-  // not stored), 2 = self-loop (fact or barred atom: its own bit). Per 32-row word a header
-  // {first and_col index of the word, first new atom of the word's OR rows}. Groups are
-  // consecutive word ranges whose headers, descriptors and and_col entries fit one
-  // shared-memory stage.
+  // Streamed layout of the least-model kernel (see fixpoint_stream.cu). Row kinds: 0 = rule
+  // row (entries listed in and_col), 1 = OR-rule row (its entries are the next `length` new
+  // atoms after those of the OR rows before it, so they are not stored), 2 = self-loop (fact
+  // or barred atom: its own bit). Per 32-row word a header {first and_col index of the word,
+  // first new atom of the word's OR rows | kLongWord}. In a word whose rows all have at most
+  // 32 entries a row's descriptor is kind << 30 | offset << 6 | length, the offset counted
+  // from the word's first rule entry (rule rows) or first new atom (OR rows); in a "long"
+  // word (header bit kLongWord) it is kind << 30 | length and offsets come from prefix sums.
+  // Groups are consecutive word ranges whose headers, descriptors and and_col entries fit
+  // one shared-memory stage.
   std::vector<uint32_t> desc;      // n_pad
   std::vector<int32_t> word_hdr;   // 2 * (n_pad / 32 + 1)
   std::vector<int32_t> and_col;    // entries of rule rows, in row order (+ padding)
   std::vector<int32_t> groups;     // 4 per group: w0, w1, col0 (multiple of 4), ncol (-1: read from global)
   int32_t n_groups = 0;
+  int32_t n_sec_a = 0;  // rows of section A (original + barred atoms): every rule-row entry is one
 };
 
 // Stage geometry of the streamed least-model kernel (shared by compile_host and the kernel).
@@ -60,6 +64,7 @@ constexpr int kStageBytes = kStageHdrBytes + kStageDescBytes + kStageColInts * 4
 static_assert(kStageBytes == 32768, "stage layout");
 
 enum StreamKind : uint32_t { SK_RULE = 0, SK_OR = 1, SK_SELF = 2 };
+constexpr uint32_t kLongWord = 0x80000000u;  // header flag: descriptors hold lengths only
 
 // Builds the matrix; returns LP_OK or LP_ERR_INVALID / LP_ERR_OOM with a message in err.
 lp_status compile_host(int32_t n_atoms, int64_t n_rules, const int32_t* head, const int64_t* body_off,

@@ -46,9 +46,11 @@ struct StreamLayout {
   const int32_t* and_col;   // rule-row entries (+ padding)
   const int32_t* groups;    // 4 per group
   int32_t n_groups;
+  int32_t n_sec_a;          // leading rows that rule rows refer to (staged in shared memory)
 };
 cudaError_t launch_fixpoint_stream(const FixArgs& a, const StreamLayout& layout, int grid, cudaStream_t s);
 int fixpoint_stream_blocks_per_sm();
+int fixpoint_stream_xs_words(int n_sec_a);  // words of the vector the kernel stages
 
 // Algorithms 2 + 3 over tiles of 64-bit guess words (persistent cooperative kernel).
 struct StableArgs {

@@ -253,7 +253,6 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   std::vector<uint32_t>().swap(hm.desc);
   std::vector<int32_t>().swap(hm.word_hdr);
   std::vector<int32_t>().swap(hm.and_col);
-  std::vector<int32_t>().swap(hm.groups);
   p->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
   return LP_OK;
@@ -342,6 +341,7 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
   a.out = d_out;
   a.perm = p->perm;
   a.n_out = n_in;
+  a.n_sec_a = hm.n_sec_a;
 
   // Kernel choice: the one-warp-per-word kernel (default) or the streamed kernel
   // (LP_FIXPOINT=stream), both exact; the environment variable exists for A/B measurement.
@@ -355,7 +355,7 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
     static int per_sm_s = -1;
     if (per_sm_s < 0) per_sm_s = fixpoint_stream_blocks_per_sm();
     if (per_sm_s <= 0) return fail(LP_ERR_CUDA, "streamed fixpoint kernel cannot be resident");
-    StreamLayout L{p->desc, p->word_hdr, p->and_col, p->groups, hm.n_groups, hm.n_sec_a};
+    StreamLayout L{p->desc, p->word_hdr, p->and_col, p->groups, hm.n_groups, hm.n_sec_a, hm.groups.data()};
     int grid = std::max(1, std::min(max_coresident(p, per_sm_s), hm.n_groups));
     if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
     le = launch_fixpoint_stream(a, L, grid, s);

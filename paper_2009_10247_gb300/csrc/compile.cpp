@@ -176,10 +176,8 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         int64_t r = row_rule[c];
         const int32_t* s = rb.data() + body_off[r];
         for (int32_t i = 0; i < setlen[r]; i++) deg[s[i]]++;
-      } else if (kind[c] == K_FACT || kind[c] == K_BARRED) {
-        deg[c]++;
-      }  // OR entries point at new atoms, which are placed by their OR row
-    }
+      }  // OR entries point at new atoms, which are placed by their OR row; self-loops read
+    }    // their own bit: only rule-row entries count as references (gathers)
 
     // ---- internal order
     const int32_t nA = n + nb;
@@ -318,6 +316,20 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       }
       hm.word_hdr[2 * nw] = (int32_t)ca;
       hm.word_hdr[2 * nw + 1] = (int32_t)oa;
+      if (ca >= (int64_t(1) << 30)) {
+        err = "too many rule entries for the streamed layout (must be < 2^30)";
+        return LP_ERR_INVALID;
+      }
+      // which row kinds a word holds (header bits kHasOr / kHasSelf)
+      for (int32_t wd = 0; wd < nw; wd++) {
+        uint32_t fl = 0;
+        for (int l = 0; l < 32; l++) {
+          const uint32_t sk = hm.desc[32 * wd + l] >> 30;
+          if (sk == SK_OR) fl |= kHasOr;
+          if (sk == SK_SELF) fl |= kHasSelf;
+        }
+        hm.word_hdr[2 * wd] = (int32_t)((uint32_t)hm.word_hdr[2 * wd] | fl);
+      }
       // words whose rows all have <= 32 entries carry each row's offset in its descriptor
       for (int32_t wd = 0; wd < nw; wd++) {
         bool small = true;
@@ -342,26 +354,37 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       int32_t w = 0;
       while (w < nw) {
         int32_t w1 = w;
-        auto words_cols = [&](int32_t a, int32_t b2) { return hm.word_hdr[2 * b2] - hm.word_hdr[2 * a]; };
+        auto hdr_col = [&](int32_t wd) { return (int32_t)((uint32_t)hm.word_hdr[2 * wd] & ~(kHasOr | kHasSelf)); };
+        auto words_cols = [&](int32_t a, int32_t b2) { return hdr_col(b2) - hdr_col(a); };
         while (w1 < nw && w1 - w < kGroupWordsMax && words_cols(w, std::min(w1 + 2, nw)) <= cap)
           w1 = std::min(w1 + 2, nw);
         int32_t ncol;
-        const int32_t c0 = hm.word_hdr[2 * w] & ~3;
+        const int32_t c0 = hdr_col(w) & ~3;
         if (w1 == w) {  // one pair of words alone exceeds a stage: its entries stay in global memory
           w1 = std::min(w + 2, nw);
           ncol = -1;
         } else {
-          const int32_t c1 = (hm.word_hdr[2 * w1] + 3) & ~3;
+          const int32_t c1 = (hdr_col(w1) + 3) & ~3;
           ncol = c1 - c0;
         }
-        hm.groups.push_back(w);
-        hm.groups.push_back(w1);
-        hm.groups.push_back(c0);
-        hm.groups.push_back(ncol);
+        // the slice of the vector holding the group's OR rows' new atoms (whole 4-word units)
+        const int64_t ob0 = (uint32_t)hm.word_hdr[2 * w + 1] & ~kLongWord;
+        const int64_t ob1 = (uint32_t)hm.word_hdr[2 * w1 + 1] & ~kLongWord;
+        int32_t xw0 = 0, nxw = 0;
+        if (ob1 > ob0) {
+          xw0 = (int32_t)((ob0 >> 5) & ~int64_t(3));
+          const int32_t xw1 = (int32_t)((((ob1 + 31) >> 5) + 3) & ~int64_t(3));
+          nxw = xw1 - xw0 <= kStageXWords ? xw1 - xw0 : -1;  // -1: read from global memory
+        }
+        const int32_t rec[kGroupInts] = {w, w1, c0, ncol, xw0, nxw, 0, 0};
+        hm.groups.insert(hm.groups.end(), rec, rec + kGroupInts);
         w = w1;
       }
-      hm.n_groups = (int32_t)(hm.groups.size() / 4);
-      hm.n_sec_a = nA;
+      hm.n_groups = (int32_t)(hm.groups.size() / kGroupInts);
+      // rule rows refer only to the leading section-A rows that have references
+      int32_t ng_atoms = 0;
+      while (ng_atoms < nA && deg[inv[ng_atoms]] > 0) ng_atoms++;
+      hm.n_sec_a = ng_atoms;
     }
 
     hm.n = n;

@@ -1,16 +1,20 @@
 // fixpoint_stream.cu -- Algorithm 1 as a persistent kernel fed by bulk asynchronous copies.
 //
 // Same loop as fixpoint.cu (v0 of Def. 4, u = theta(M_P v) until u = v, projection), laid out
-// for GB300:
-//  * one 1024-thread CTA per SM owns a contiguous range of "groups" (<= 64 words of 32 rows
-//    whose headers, row descriptors and rule entries fit a 32 KiB stage); a producer thread
-//    copies them with cp.async.bulk into a ring of stages guarded by mbarriers and 31 consumer
-//    warps evaluate the words. The matrix never changes, so the producer prefetches the next
-//    iteration's first groups while the grid meets at its barrier.
+// for GB300 so that evaluating a 32-row word touches shared memory only:
+//  * one 1024-thread CTA per SM owns a contiguous range of "groups" (<= 64 words of 32 rows).
+//    A producer thread copies each group's word headers, row descriptors and rule entries
+//    with cp.async.bulk into a ring of 32 KiB stages guarded by mbarriers; 31 consumer warps
+//    evaluate the words. That part of a stage never changes, so the producer prefetches the
+//    next iteration's first groups while the grid meets at its barrier. Each stage also gets
+//    the slice of the current vector that holds the group's OR rows' new atoms, copied by the
+//    producer after the barrier (a second arrival on the stage's mbarrier).
 //  * every rule-row entry is an original or barred atom, and those atoms form the first rows
 //    of the internal order, most referenced first. After each grid barrier every CTA copies
-//    that prefix of the current vector into shared memory (as much as fits), so the random
-//    bit gathers of rule rows are shared-memory reads.
+//    that prefix of the vector into shared memory (as much as fits), so rule rows' bit
+//    gathers are shared-memory reads.
+//  * each CTA keeps the words it writes in shared memory too; a self-loop reads its own bit
+//    from there.
 //  * in the default mode the iterates only grow (the initial vector holds self-loop rows only,
 //    and theta is monotone), so u = v exactly when both have the same number of true rows:
 //    the kernel counts true rows instead of comparing words. With an arbitrary initial vector
@@ -25,6 +29,8 @@
 // That is theta(M_P v) of Def. 5 row by row, exactly.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.h"
 #include "kernels.h"
@@ -35,6 +41,8 @@ constexpr int kStreamThreads = 1024;
 constexpr int kConsumerWarps = kStreamThreads / 32 - 1;
 constexpr int kStages = 3;
 constexpr int kStageRegion = kStages * kStageBytes;
+constexpr int kStageXOff = kStageHdrBytes + kStageDescBytes;
+constexpr int kStageColOff = kStageXOff + kStageXBytes;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -50,14 +58,23 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Test the phase; a thread whose phase is not complete is suspended (not spinning, so it
+// takes no issue slots) until the phase completes or the hint of kSuspendNs expires.
+constexpr unsigned kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
+}
+
+__device__ __forceinline__ uint32_t lds32(unsigned addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
 }
 
 // Bounded wait on an mbarrier phase; false when the grid is aborting or the wait timed out
@@ -67,8 +84,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, Device
   unsigned long long t0 = 0;
   while (!mbar_try_wait(bar, parity)) {
     ++polls;
-    if (polls == 16) t0 = global_ns();
-    if (polls > 16 && (polls & 31) == 0) {
+    if (polls == 1) t0 = global_ns();
+    if (polls > 1) {
       if (ld_volatile(&ctl->abort)) return false;
       if (global_ns() - t0 > kWaitLimitNs) {
         atomicExch(&ctl->abort, 1u);
@@ -91,10 +108,11 @@ struct StreamArgs {
   const uint32_t* desc;
   const int32_t* word_hdr;  // 2 per word
   const int32_t* and_col;
-  const int32_t* groups;    // 4 per group
+  const int32_t* groups;    // kGroupInts per group
   int32_t n_groups;
   int32_t xs_words;         // words of the vector staged in shared memory (multiple of 4)
   int32_t sec_a_words;      // words holding the rows rule rows refer to: ceil(n_sec_a / 32)
+  int32_t own_words;        // shared-memory words for the CTA's own output words (multiple of 4)
   int32_t monotone;         // 1: convergence by true-row counts (default mode)
   uint32_t* x0;
   uint32_t* x1;
@@ -123,6 +141,14 @@ struct XView {
   __device__ __forceinline__ uint32_t operator[](int i) const { return i < xs_words ? xs[i] : src[i]; }
 };
 
+// Where a word finds what it reads besides the rule entries.
+struct WordCtx {
+  const uint32_t* or_src;  // vector words holding the OR rows' new atoms (stage slice or global)
+  int or_shift;            // bit index of or_src[0] in the vector
+  uint32_t self_word;      // the word's own previous value
+  int zero_j;              // a gather index whose bit is always 0 (kAllSmem)
+};
+
 // theta of the 32 rows of a word whose rows all have <= 32 entries; each descriptor carries
 // its row's offset. col points at the word's first rule entry, or_base is the word's first
 // new atom. Rule entries are gathered 32 per ballot (lanes past the word's last entry read a
@@ -131,54 +157,104 @@ struct XView {
 // range of new atoms with one funnel shift, a self-loop reads its own bit.
 // kAllSmem: every gathered atom lies in the shared-memory copy of the vector.
 template <bool kAllSmem>
-__device__ __forceinline__ uint32_t stream_word_fast(int w, int lane, uint32_t d, int or_base, const int32_t* col,
-                                                     const XView& x, int zero_j) {
+__device__ __noinline__ uint32_t stream_word_fast(int lane, uint32_t d, uint32_t hflags, int or_base,
+                                                  const int32_t* col, const XView& x, const WordCtx& ctx) {
   const uint32_t kind = d >> 30;
   const int off = (int)((d >> 6) & 0xffffffu);
   const int len = (int)(d & 63u);
   const bool rule = kind == SK_RULE;
   const int a_total = (int)__reduce_max_sync(FULL, rule ? (unsigned)(off + len) : 0u);
   const uint32_t want = __funnelshift_rc(FULL, 0u, 32 - len);  // len low bits set (len <= 32)
-  uint32_t mymask = 0;
-  const int nch = (a_total + 31) >> 5;
-  for (int c = 0; c < nch; c++) {
-    const int e = (c << 5) + lane;
-    uint32_t bit;
-    if (kAllSmem) {
-      const int j = e < a_total ? col[e] : zero_j;
-      const uint32_t wd = x.xs[j >> 5];
-      bit = __funnelshift_r(wd, wd, j) & 1u;
-    } else {
-      bit = 0u;
-      if (e < a_total) {
-        const int j = col[e];
-        const uint32_t wd = x[j >> 5];
-        bit = __funnelshift_r(wd, wd, j) & 1u;
-      }
-    }
-    const uint32_t m = __ballot_sync(FULL, bit);
-    if (lane == c) mymask = m;
-  }
   bool val = false;
-  if (a_total > 0) {  // warp-uniform: the shuffles need every lane
-    const uint32_t m0 = __shfl_sync(FULL, mymask, (off >> 5) & 31);
-    const uint32_t m1 = __shfl_sync(FULL, mymask, ((off >> 5) + 1) & 31);
-    val = rule && len > 0 && (__funnelshift_r(m0, m1, off) & want) == want;
+  if (a_total > 0) {  // warp-uniform
+    uint32_t mymask = 0;
+    const int nch = (a_total + 31) >> 5;
+    for (int c = 0; c < nch; c += 2) {
+      const int e0 = (c << 5) + lane, e1 = e0 + 32;
+      uint32_t b0, b1;
+      if (kAllSmem) {
+        const int j0 = e0 < a_total ? col[e0] : ctx.zero_j;
+        const int j1 = e1 < a_total ? col[e1] : ctx.zero_j;
+        const uint32_t w0 = x.xs[j0 >> 5], w1 = x.xs[j1 >> 5];
+        b0 = __funnelshift_r(w0, w0, j0) & 1u;
+        b1 = __funnelshift_r(w1, w1, j1) & 1u;
+      } else {
+        b0 = b1 = 0u;
+        if (e0 < a_total) {
+          const int j0 = col[e0];
+          const uint32_t w0 = x[j0 >> 5];
+          b0 = __funnelshift_r(w0, w0, j0) & 1u;
+        }
+        if (e1 < a_total) {
+          const int j1 = col[e1];
+          const uint32_t w1 = x[j1 >> 5];
+          b1 = __funnelshift_r(w1, w1, j1) & 1u;
+        }
+      }
+      const uint32_t m0 = __ballot_sync(FULL, b0);
+      const uint32_t m1 = __ballot_sync(FULL, b1);
+      if (lane == c) mymask = m0;
+      if (lane == c + 1) mymask = m1;
+    }
+    const uint32_t lo = __shfl_sync(FULL, mymask, (off >> 5) & 31);
+    const uint32_t hi = __shfl_sync(FULL, mymask, ((off >> 5) + 1) & 31);
+    val = rule && len > 0 && (__funnelshift_r(lo, hi, off) & want) == want;
   }
-  if (kind == SK_OR) {  // new atoms lie past the shared copy: global reads
-    const int p = or_base + off;
-    const uint32_t lo = x.src[p >> 5], hi = x.src[(p + len - 1) >> 5];
+  if ((hflags & kHasOr) && kind == SK_OR) {
+    const int p = or_base + off - ctx.or_shift;
+    const uint32_t lo = ctx.or_src[p >> 5], hi = ctx.or_src[(p + len - 1) >> 5];
     val = (__funnelshift_r(lo, hi, p) & want) != 0u;
-  } else if (kind == SK_SELF) {
-    val = (x[w] >> lane) & 1u;
   }
+  if ((hflags & kHasSelf) && kind == SK_SELF) val = (ctx.self_word >> lane) & 1u;
+  return __ballot_sync(FULL, val);
+}
+
+// The same evaluation when everything the word reads is in shared memory (the common case):
+// 32-bit shared addresses and explicit shared loads. col_a: the word's first rule entry in the
+// stage; xs_a: the staged vector prefix; or_a: the group's vector slice, whose first bit is
+// bit or_shift of the vector.
+__device__ __forceinline__ uint32_t stream_word_smem(int lane, uint32_t d, uint32_t hflags, int or_base,
+                                                     unsigned col_a, unsigned xs_a, unsigned or_a, int or_shift,
+                                                     uint32_t self_word, int zero_j) {
+  const uint32_t kind = d >> 30;
+  const int off = (int)((d >> 6) & 0xffffffu);
+  const int len = (int)(d & 63u);
+  const bool rule = kind == SK_RULE;
+  const int a_total = (int)__reduce_max_sync(FULL, rule ? (unsigned)(off + len) : 0u);
+  const uint32_t want = __funnelshift_rc(FULL, 0u, 32 - len);  // len low bits set (len <= 32)
+  bool val = false;
+  if (a_total > 0) {  // warp-uniform
+    uint32_t mymask = 0;
+    const int nch = (a_total + 31) >> 5;
+    for (int c = 0; c < nch; c += 2) {
+      const int e0 = (c << 5) + lane, e1 = e0 + 32;
+      const unsigned j0 = e0 < a_total ? lds32(col_a + 4u * (unsigned)e0) : (unsigned)zero_j;
+      const unsigned j1 = e1 < a_total ? lds32(col_a + 4u * (unsigned)e1) : (unsigned)zero_j;
+      const uint32_t w0 = lds32(xs_a + ((j0 >> 3) & ~3u));
+      const uint32_t w1 = lds32(xs_a + ((j1 >> 3) & ~3u));
+      const uint32_t m0 = __ballot_sync(FULL, __funnelshift_r(w0, w0, j0) & 1u);
+      const uint32_t m1 = __ballot_sync(FULL, __funnelshift_r(w1, w1, j1) & 1u);
+      mymask = lane == c ? m0 : mymask;
+      mymask = lane == c + 1 ? m1 : mymask;
+    }
+    const uint32_t lo = __shfl_sync(FULL, mymask, (off >> 5) & 31);
+    const uint32_t hi = __shfl_sync(FULL, mymask, ((off >> 5) + 1) & 31);
+    val = rule && len > 0 && (__funnelshift_r(lo, hi, off) & want) == want;
+  }
+  if ((hflags & kHasOr) && kind == SK_OR) {
+    const unsigned p = (unsigned)(or_base + off - or_shift);
+    const uint32_t lo = lds32(or_a + ((p >> 3) & ~3u));
+    const uint32_t hi = lds32(or_a + (((p + (unsigned)len - 1u) >> 3) & ~3u));
+    val = (__funnelshift_r(lo, hi, p) & want) != 0u;
+  }
+  if ((hflags & kHasSelf) && kind == SK_SELF) val = (self_word >> lane) & 1u;
   return __ballot_sync(FULL, val);
 }
 
 // theta of the 32 rows of a long word (some row has more than 32 entries): offsets come from
 // prefix sums of the row lengths. col points at the word's first rule entry.
-__device__ __noinline__ uint32_t stream_word_long(int w, int lane, uint32_t d, int or_base, const int32_t* col,
-                                                  const XView& x) {
+__device__ __noinline__ uint32_t stream_word_long(int lane, uint32_t d, int or_base, const int32_t* col,
+                                                  const XView& x, uint32_t self_word) {
   const uint32_t kind = d >> 30;
   const int len = (int)(d & 0x3fffffffu);
   const int and_len = kind == SK_RULE ? len : 0;
@@ -209,20 +285,20 @@ __device__ __noinline__ uint32_t stream_word_long(int w, int lane, uint32_t d, i
     if (hi > lo) cnt += __popc(m & ((hi - lo == 32) ? FULL : (((1u << (hi - lo)) - 1u) << lo)));
   }
   bool val = kind == SK_RULE && len > 0 && cnt == len;
-  if (kind == SK_OR) {  // one of the row's new atoms, a contiguous bit range
+  if (kind == SK_OR) {  // one of the row's new atoms, a contiguous bit range (global reads)
     bool any = false;
     int p = or_base + o_off, rem = len;
     while (rem > 0 && !any) {
       const int bpos = p & 31;
       const int take = min(32 - bpos, rem);
       const uint32_t want = take == 32 ? FULL : ((1u << take) - 1u);
-      any = ((x[p >> 5] >> bpos) & want) != 0u;
+      any = ((x.src[p >> 5] >> bpos) & want) != 0u;
       p += take;
       rem -= take;
     }
     val = any;
   } else if (kind == SK_SELF) {
-    val = (x[w] >> lane) & 1u;
+    val = (self_word >> lane) & 1u;
   }
   return __ballot_sync(FULL, val);
 }
@@ -244,15 +320,18 @@ __global__ void __launch_bounds__(kStreamThreads, 1) fixpoint_stream_kernel(Stre
   DeviceCtl* ctl = a.ctl;
   unsigned long long round = 0;
   uint32_t* xs = reinterpret_cast<uint32_t*>(smem + kStageRegion);
+  uint32_t* own = xs + a.xs_words;
 
-  // this CTA's groups
+  // this CTA's groups and the words they cover
   const int g_beg = (int)((long long)a.n_groups * blockIdx.x / gridDim.x);
   const int g_end = (int)((long long)a.n_groups * (blockIdx.x + 1) / gridDim.x);
   const int ng = g_end - g_beg;
+  const int own0 = ng > 0 ? __ldg(a.groups + kGroupInts * g_beg) : 0;
+  const int own1 = ng > 0 ? __ldg(a.groups + kGroupInts * (g_end - 1) + 1) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; s++) {
-      mbar_init(&full_bar[s], 1);
+      mbar_init(&full_bar[s], 2);  // static part + vector slice
       mbar_init(&empty_bar[s], kConsumerWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -276,8 +355,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1) fixpoint_stream_kernel(Stre
   } else {
     unsigned long long mine = 0;
     for (int i = gtid; i < a.n_facts; i += nthreads) {
-      const int own = a.fact_owner[i];
-      const bool sel = a.init ? ((a.init[own >> 6] >> (own & 63)) & 1ull) : true;
+      const int own_atom = a.fact_owner[i];
+      const bool sel = a.init ? ((a.init[own_atom >> 6] >> (own_atom & 63)) & 1ull) : true;
       if (sel) {
         const uint32_t bit = 1u << (a.fact_row[i] & 31);
         if (!(atomicOr(a.x0 + (a.fact_row[i] >> 5), bit) & bit)) mine++;
@@ -293,26 +372,32 @@ __global__ void __launch_bounds__(kStreamThreads, 1) fixpoint_stream_kernel(Stre
   __syncthreads();
   if (s_flag != 0) ok = false;  // bad initial vector: nothing to iterate
   unsigned long long prev_count = ld_volatile64(&ctl->init_count);
+  for (int i = threadIdx.x; i < own1 - own0; i += blockDim.x) own[i] = __ldcg(a.x0 + own0 + i);
 
-  // producer state (thread 0 only): next sequence number to issue
-  long long q_issue = 0;
-  auto issue_upto = [&](long long q_target) -> bool {
-    for (; q_issue < q_target; ++q_issue) {
-      const int s = (int)(q_issue % kStages);
-      if (q_issue >= kStages && !mbar_wait(&empty_bar[s], (unsigned)(((q_issue / kStages) + 1) & 1), ctl))
-        return false;
-      const int g = g_beg + (int)(q_issue % ng);
-      const int w0 = __ldg(a.groups + 4 * g), w1 = __ldg(a.groups + 4 * g + 1);
-      const int col0 = __ldg(a.groups + 4 * g + 2), ncol = __ldg(a.groups + 4 * g + 3);
-      unsigned char* st = smem + (size_t)s * kStageBytes;
-      const unsigned hb = 8u * (unsigned)(w1 - w0), db = 128u * (unsigned)(w1 - w0);
-      const unsigned cb = ncol > 0 ? 4u * (unsigned)ncol : 0u;
-      mbar_arrive_expect_tx(&full_bar[s], hb + db + cb);
-      bulk_copy_g2s(st, a.word_hdr + 2 * w0, hb, &full_bar[s]);
-      bulk_copy_g2s(st + kStageHdrBytes, a.desc + 32 * w0, db, &full_bar[s]);
-      if (cb) bulk_copy_g2s(st + kStageHdrBytes + kStageDescBytes, a.and_col + col0, cb, &full_bar[s]);
-    }
+  // ---- producer (thread 0): static stage parts run ahead; vector slices follow the barrier
+  long long q_static = 0, q_dyn = 0;
+  auto group_of = [&](long long q) { return a.groups + kGroupInts * (g_beg + (int)(q % ng)); };
+  auto issue_static = [&](long long q) -> bool {
+    const int s = (int)(q % kStages);
+    if (q >= kStages && !mbar_wait(&empty_bar[s], (unsigned)(((q / kStages) + 1) & 1), ctl)) return false;
+    const int32_t* gr = group_of(q);
+    const int w0 = __ldg(gr), w1 = __ldg(gr + 1), col0 = __ldg(gr + 2), ncol = __ldg(gr + 3);
+    unsigned char* st = smem + (size_t)s * kStageBytes;
+    const unsigned hb = 8u * (unsigned)(w1 - w0), db = 128u * (unsigned)(w1 - w0);
+    const unsigned cb = ncol > 0 ? 4u * (unsigned)ncol : 0u;
+    mbar_arrive_expect_tx(&full_bar[s], hb + db + cb);
+    bulk_copy_g2s(st, a.word_hdr + 2 * w0, hb, &full_bar[s]);
+    bulk_copy_g2s(st + kStageHdrBytes, a.desc + 32 * w0, db, &full_bar[s]);
+    if (cb) bulk_copy_g2s(st + kStageColOff, a.and_col + col0, cb, &full_bar[s]);
     return true;
+  };
+  auto issue_dyn = [&](long long q, const uint32_t* src) {
+    const int s = (int)(q % kStages);
+    const int32_t* gr = group_of(q);
+    const int xw0 = __ldg(gr + 4), nxw = __ldg(gr + 5);
+    const unsigned xb = nxw > 0 ? 4u * (unsigned)nxw : 0u;
+    mbar_arrive_expect_tx(&full_bar[s], xb);
+    if (xb) bulk_copy_g2s(smem + (size_t)s * kStageBytes + kStageXOff, src + xw0, xb, &full_bar[s]);
   };
 
   const uint32_t* fin = a.x0;
@@ -321,38 +406,67 @@ __global__ void __launch_bounds__(kStreamThreads, 1) fixpoint_stream_kernel(Stre
   for (; ok && it < a.max_iters; ++it) {
     const uint32_t* src = (it & 1) ? a.x1 : a.x0;
     uint32_t* dst = (it & 1) ? a.x0 : a.x1;
-    // stage the vector's prefix (the atoms rule rows refer to) in shared memory
+    // the vector slices of the stages prefetched during the last iteration can go now
+    if (threadIdx.x == 0 && ng > 0) {
+      // order the last iteration's writes (seen through the grid barrier) before the bulk
+      // copies that read the vector
+      asm volatile("fence.proxy.async;" ::: "memory");
+      const long long hi = (long long)(it + 1) * ng;
+      while (q_dyn < q_static && q_dyn < hi) issue_dyn(q_dyn++, src);
+    }
+    // stage the vector's prefix (the atoms rule rows refer to) in shared memory; the word after
+    // it is kept at zero (the gather target of lanes without an entry). Four loads in flight
+    // per thread.
     {
-      // words [0, sec_a_words) from the vector; the word after them is kept at zero (the
-      // gather target of lanes without an entry)
       const uint4* s4 = reinterpret_cast<const uint4*>(src);
       uint4* d4 = reinterpret_cast<uint4*>(xs);
       const int n4 = a.xs_words >> 2;
       const int copy_words = min(a.sec_a_words, a.xs_words);
-      for (int i = threadIdx.x; i < n4; i += blockDim.x) {
-        uint4 v = __ldcg(s4 + i);
-        const int w0 = 4 * i;
-        if (w0 + 0 >= copy_words) v.x = 0u;
-        if (w0 + 1 >= copy_words) v.y = 0u;
-        if (w0 + 2 >= copy_words) v.z = 0u;
-        if (w0 + 3 >= copy_words) v.w = 0u;
-        d4[i] = v;
+      for (int base = threadIdx.x; base < n4; base += 4 * (int)blockDim.x) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int i = base + u * (int)blockDim.x;
+          if (i < n4) v[u] = __ldcg(s4 + i);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int i = base + u * (int)blockDim.x;
+          if (i < n4) {
+            const int w0 = 4 * i;
+            if (w0 + 0 >= copy_words) v[u].x = 0u;
+            if (w0 + 1 >= copy_words) v[u].y = 0u;
+            if (w0 + 2 >= copy_words) v[u].z = 0u;
+            if (w0 + 3 >= copy_words) v[u].w = 0u;
+            d4[i] = v[u];
+          }
+        }
       }
     }
     __syncthreads();
     // only the copied words are the vector's; the staged words after them read as zero
     const XView x{xs, src, min(a.sec_a_words, a.xs_words)};
-    const bool all_smem = a.xs_words > a.sec_a_words;  // the gathered atoms and a zero word
-    const int zero_j = a.sec_a_words * 32;              // a bit of that always-zero word
+    const bool all_smem = a.xs_words > a.sec_a_words;
     bool changed = false;
     unsigned long long ones = 0;
     if (ng > 0) {
       if (warp == 0) {
         if (lane == 0) {
-          // this iteration's groups, then the next iteration's first stages
-          const long long next = (long long)(it + 1) * ng;
-          const long long target = (it + 1 < a.max_iters) ? next + min(ng, kStages) : next;
-          if (!issue_upto(target)) s_fail = 1;
+          const long long hi = (long long)(it + 1) * ng;
+          bool good = true;
+          while (good && q_static < hi) {
+            good = issue_static(q_static);
+            if (!good) break;
+            issue_dyn(q_static, src);
+            q_dyn = ++q_static;
+          }
+          // the next iteration's first stages (static part only)
+          const long long target = (it + 1 < a.max_iters) ? hi + min(ng, kStages) : hi;
+          while (good && q_static < target) {
+            good = issue_static(q_static);
+            if (good) ++q_static;
+          }
+          if (!good) s_fail = 1;
         }
       } else {
         const int cw = warp - 1;
@@ -363,28 +477,42 @@ __global__ void __launch_bounds__(kStreamThreads, 1) fixpoint_stream_kernel(Stre
             if (lane == 0) s_fail = 1;
             break;
           }
-          const int g = g_beg + k;
-          const int w0 = __ldg(a.groups + 4 * g), w1 = __ldg(a.groups + 4 * g + 1);
-          const int col0 = __ldg(a.groups + 4 * g + 2), ncol = __ldg(a.groups + 4 * g + 3);
+          const int32_t* gr = a.groups + kGroupInts * (g_beg + k);
+          const int w0 = __ldg(gr), w1 = __ldg(gr + 1), col0 = __ldg(gr + 2), ncol = __ldg(gr + 3);
+          const int xw0 = __ldg(gr + 4), nxw = __ldg(gr + 5);
           const unsigned char* st = smem + (size_t)s * kStageBytes;
           const int2* hdr = reinterpret_cast<const int2*>(st);
           const uint32_t* dsc = reinterpret_cast<const uint32_t*>(st + kStageHdrBytes);
-          const int32_t* scol = reinterpret_cast<const int32_t*>(st + kStageHdrBytes + kStageDescBytes);
+          const uint32_t* sx = reinterpret_cast<const uint32_t*>(st + kStageXOff);
+          const int32_t* scol = reinterpret_cast<const int32_t*>(st + kStageColOff);
+          WordCtx ctx;
+          ctx.or_src = nxw >= 0 ? sx : src;
+          ctx.or_shift = nxw >= 0 ? xw0 * 32 : 0;
+          ctx.zero_j = a.sec_a_words * 32;
+          const bool smem_path = all_smem && ncol >= 0 && nxw >= 0;
+          const unsigned st_a = smem_u32(st), xs_a = smem_u32(xs);
           for (int w = w0 + cw; w < w1; w += kConsumerWarps) {
             const int2 h = hdr[w - w0];
             const uint32_t d = dsc[(w - w0) * 32 + lane];
-            const int32_t* colp = ncol >= 0 ? scol + (h.x - col0) : a.and_col + h.x;
+            const uint32_t hflags = (uint32_t)h.x & (kHasOr | kHasSelf);
+            const int hcol = (int)((uint32_t)h.x & ~(kHasOr | kHasSelf));
+            const int32_t* colp = ncol >= 0 ? scol + (hcol - col0) : a.and_col + hcol;
+            ctx.self_word = own[w - own0];
             uint32_t u;
-            if ((uint32_t)h.y & kLongWord)
-              u = stream_word_long(w, lane, d, (int)((uint32_t)h.y & ~kLongWord), colp, x);
+            if (smem_path && !((uint32_t)h.y & kLongWord))
+              u = stream_word_smem(lane, d, hflags, h.y, st_a + kStageColOff + 4u * (unsigned)(hcol - col0), xs_a,
+                                   st_a + kStageXOff, xw0 * 32, ctx.self_word, ctx.zero_j);
+            else if ((uint32_t)h.y & kLongWord)
+              u = stream_word_long(lane, d, (int)((uint32_t)h.y & ~kLongWord), colp, x, ctx.self_word);
             else if (all_smem)
-              u = stream_word_fast<true>(w, lane, d, h.y, colp, x, zero_j);
+              u = stream_word_fast<true>(lane, d, hflags, h.y, colp, x, ctx);
             else
-              u = stream_word_fast<false>(w, lane, d, h.y, colp, x, zero_j);
+              u = stream_word_fast<false>(lane, d, hflags, h.y, colp, x, ctx);
             if (lane == 0) {
               dst[w] = u;
               if (a.monotone) ones += __popc(u);
-              else changed |= (u != x[w]);
+              else changed |= (u != ctx.self_word);
+              own[w - own0] = u;
             }
           }
           __syncwarp();
@@ -429,10 +557,13 @@ __global__ void __launch_bounds__(kStreamThreads, 1) fixpoint_stream_kernel(Stre
       break;
     }
   }
-  // copies still in flight (prefetched stages nobody will consume) must land before exit
+  // Stages prefetched for an iteration that did not run still have bulk copies in flight.
+  // Give them their missing vector-slice arrival (zero bytes) so their phase can complete,
+  // then wait (bounded) until every copy this CTA issued has landed.
   if (threadIdx.x == 0 && ng > 0) {
+    for (long long q = q_dyn; q < q_static; ++q) mbar_arrive_expect_tx(&full_bar[(int)(q % kStages)], 0u);
     const long long consumed = (long long)it * ng;  // groups of iterations 0 .. it-1
-    for (long long q = consumed; q < q_issue; ++q)
+    for (long long q = consumed; q < q_static; ++q)
       if (!mbar_wait(&full_bar[(int)(q % kStages)], (unsigned)((q / kStages) & 1), ctl)) break;
   }
   __syncthreads();
@@ -466,20 +597,23 @@ static int max_dyn_smem() {
   return g_max_dyn_smem;
 }
 
-// Words of the vector staged in shared memory (a multiple of 4) for a program whose first
-// n_sec_a rows are the atoms rule rows gather: those words and one word kept at zero.
-static int stream_xs_words(int n_sec_a) {
-  const int budget_bytes = max_dyn_smem() - kStageRegion - 1024;  // room for static shared data
-  const int want = ((n_sec_a + 31) / 32 + 1 + 3) & ~3;
-  const int fit = budget_bytes > 0 ? (budget_bytes / 16) * 4 : 0;
-  return want < fit ? want : fit;
+// Shared-memory words for the CTA's own output words: the most words a CTA's groups cover.
+static int own_words_for(const StreamLayout& L, int grid) {
+  int most = 0;
+  for (int c = 0; c < grid; c++) {
+    const int gb = (int)((long long)L.n_groups * c / grid), ge = (int)((long long)L.n_groups * (c + 1) / grid);
+    if (ge > gb) most = std::max(most, L.host_groups[kGroupInts * (ge - 1) + 1] - L.host_groups[kGroupInts * gb]);
+  }
+  return (most + 3) & ~3;
 }
 
-int fixpoint_stream_xs_words(int n_sec_a) { return stream_xs_words(n_sec_a); }
-
 cudaError_t launch_fixpoint_stream(const FixArgs& f, const StreamLayout& L, int grid, cudaStream_t s) {
-  const int xs_words = stream_xs_words(L.n_sec_a);
-  const size_t dyn = (size_t)kStageRegion + 4 * (size_t)xs_words;
+  const int own_words = own_words_for(L, grid);
+  const int budget = max_dyn_smem() - kStageRegion - 1024 - 4 * own_words;  // 1 KiB for static shared data
+  if (budget < 16) return cudaErrorInvalidConfiguration;
+  const int want = ((L.n_sec_a + 31) / 32 + 1 + 3) & ~3;  // the referenced words and a zero word
+  const int xs_words = std::min(want, (budget / 16) * 4);
+  const size_t dyn = (size_t)kStageRegion + 4 * (size_t)(xs_words + own_words);
   cudaError_t e = cudaFuncSetAttribute(fixpoint_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
   StreamArgs a{};
@@ -490,6 +624,7 @@ cudaError_t launch_fixpoint_stream(const FixArgs& f, const StreamLayout& L, int 
   a.n_groups = L.n_groups;
   a.xs_words = xs_words;
   a.sec_a_words = (L.n_sec_a + 31) / 32;
+  a.own_words = own_words;
   a.monotone = f.rows_init ? 0 : 1;
   a.x0 = f.x0;
   a.x1 = f.x1;

@@ -50,21 +50,27 @@ struct HostMatrix {
   std::vector<uint32_t> desc;      // n_pad
   std::vector<int32_t> word_hdr;   // 2 * (n_pad / 32 + 1)
   std::vector<int32_t> and_col;    // entries of rule rows, in row order (+ padding)
-  std::vector<int32_t> groups;     // 4 per group: w0, w1, col0 (multiple of 4), ncol (-1: read from global)
+  std::vector<int32_t> groups;     // kGroupInts per group (see below)
   int32_t n_groups = 0;
-  int32_t n_sec_a = 0;  // rows of section A (original + barred atoms): every rule-row entry is one
+  int32_t n_sec_a = 0;  // leading rows referenced by rule rows: every rule-row entry is below it
 };
 
-// Stage geometry of the streamed least-model kernel (shared by compile_host and the kernel).
-constexpr int kGroupWordsMax = 64;                 // words (x32 rows) per group, even
-constexpr int kStageHdrBytes = kGroupWordsMax * 8;
-constexpr int kStageDescBytes = kGroupWordsMax * 128;
-constexpr int kStageColInts = 6016;
-constexpr int kStageBytes = kStageHdrBytes + kStageDescBytes + kStageColInts * 4;  // 32 KiB
+// Stage geometry of the streamed least-model kernel (shared by compile_host and the kernel):
+// word headers | row descriptors | slice of the vector for OR rows | rule-row entries.
+constexpr int kGroupWordsMax = 62;                 // words (x32 rows) per group: 2 per consumer warp
+constexpr int kStageHdrBytes = 64 * 8;             // room for 64 word headers
+constexpr int kStageDescBytes = 64 * 128;          // room for 64 words of row descriptors
+constexpr int kStageXWords = 512;                  // vector words for the OR rows of a group
+constexpr int kStageXBytes = kStageXWords * 4;
+constexpr int kStageColInts = 5504;
+constexpr int kStageBytes = kStageHdrBytes + kStageDescBytes + kStageXBytes + kStageColInts * 4;  // 32 KiB
 static_assert(kStageBytes == 32768, "stage layout");
+constexpr int kGroupInts = 8;  // w0, w1, col0, ncol (-1: global), xw0, nxw (-1: global), 0, 0
 
 enum StreamKind : uint32_t { SK_RULE = 0, SK_OR = 1, SK_SELF = 2 };
-constexpr uint32_t kLongWord = 0x80000000u;  // header flag: descriptors hold lengths only
+constexpr uint32_t kLongWord = 0x80000000u;  // header (second int) flag: descriptors hold lengths only
+constexpr uint32_t kHasOr = 0x80000000u;     // header (first int) flag: the word has OR-rule rows
+constexpr uint32_t kHasSelf = 0x40000000u;   // header (first int) flag: the word has self-loops
 
 // Builds the matrix; returns LP_OK or LP_ERR_INVALID / LP_ERR_OOM with a message in err.
 lp_status compile_host(int32_t n_atoms, int64_t n_rules, const int32_t* head, const int64_t* body_off,

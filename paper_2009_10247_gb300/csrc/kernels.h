@@ -33,6 +33,7 @@ struct FixArgs {
   uint64_t* out;
   const int32_t* perm;         // canonical -> internal
   int32_t n_out;
+  int32_t n_sec_a;             // leading rows that rule rows refer to (used by the streamed kernel)
 };
 
 constexpr int kFixBlock = 256;
@@ -44,13 +45,13 @@ struct StreamLayout {
   const uint32_t* desc;     // n_pad row descriptors
   const int32_t* word_hdr;  // 2 * (n_pad / 32 + 1)
   const int32_t* and_col;   // rule-row entries (+ padding)
-  const int32_t* groups;    // 4 per group
+  const int32_t* groups;    // kGroupInts per group (device)
   int32_t n_groups;
   int32_t n_sec_a;          // leading rows that rule rows refer to (staged in shared memory)
+  const int32_t* host_groups;  // the same group records on the host (launch geometry)
 };
 cudaError_t launch_fixpoint_stream(const FixArgs& a, const StreamLayout& layout, int grid, cudaStream_t s);
 int fixpoint_stream_blocks_per_sm();
-int fixpoint_stream_xs_words(int n_sec_a);  // words of the vector the kernel stages
 
 // Algorithms 2 + 3 over tiles of 64-bit guess words (persistent cooperative kernel).
 struct StableArgs {

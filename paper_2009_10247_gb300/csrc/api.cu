@@ -415,7 +415,9 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   const int64_t n_gwords = (n_guesses + 63) / 64;
   const int32_t atom_words = (hm.n + 63) / 64;
   // tile width: largest power of two <= 32 words whose two iterate buffers fit the budget
-  int64_t budget = 64ll << 20;
+  // (wider tiles mean fewer tile iterations and grid barriers; 1 GiB covers 32-word tiles for
+  // programs up to ~2M rows)
+  int64_t budget = 1ll << 30;
   if (const char* env = std::getenv("LP_TILE_BYTES")) budget = std::max<int64_t>(1, std::atoll(env));
   int log2W = 0;
   while (log2W < 5 && (int64_t(1) << (log2W + 1)) <= n_gwords &&

@@ -154,6 +154,38 @@ lp_status lp_stable_models(lp_program* prog, const uint64_t* guesses, int64_t n_
                            uint64_t* stable_mask, uint64_t* models, int64_t max_models,
                            int64_t* n_stable_out, int32_t max_iters, void* cuda_stream);
 
+/*
+ * Relaxed (differentiable) fixpoint -- not in the paper: a smooth version of Algorithm 1 for
+ * gradient-based learning. Each step applies, row by row, a sigmoid of temperature tau to the
+ * row sums x = M_P v of the program matrix (Def. 2/7) in place of theta (Def. 5):
+ *   rule row of rule r with m body atoms:  u = sigmoid(w_r (x - 1 + 1/(2m)) / tau), x = the mean
+ *   OR-rule row:                           u = sigmoid((x - 1/2) / tau),            x = the sum
+ *   self-loop (fact or barred atom):       u = v;     empty row: u = 0.
+ * For binary inputs the logit is at least w_r/(2 m tau) in magnitude, so as tau -> 0 each step is
+ * theta exactly. Vectors are batches of b columns stored row-major: float [n'][b] over all rows in
+ * canonical order (lp_compile). weights: float [n_rules], one per rule given to lp_compile (facts
+ * have none: their entry is ignored and their gradient is 0). All buffers are device memory.
+ *
+ * lp_relaxed_workspace: sizes in floats of the checkpoint buffer (forward -> backward) and the
+ * backward scratch for a batch of b columns, `steps` steps and a checkpoint every ckpt_every steps.
+ */
+lp_status lp_relaxed_workspace(lp_program* prog, int32_t batch, int32_t steps, int32_t ckpt_every,
+                               int64_t* ckpt_floats, int64_t* scratch_floats);
+
+/* Forward: v_0 = v0 (float [n'][b]), v_{t+1} = step(v_t), t < steps; vT receives v_steps. ckpt
+ * (ckpt_floats, written) keeps every ckpt_every-th iterate for lp_relaxed_backward. Asynchronous on
+ * cuda_stream. Errors: LP_ERR_INVALID (sizes, tau <= 0, host pointers), LP_ERR_CUDA. */
+lp_status lp_relaxed_forward(lp_program* prog, const float* weights, const float* v0, int32_t batch, int32_t steps,
+                             float tau, int32_t ckpt_every, float* ckpt, float* vT, void* cuda_stream);
+
+/* Adjoint of lp_relaxed_forward (same weights, batch, steps, tau, ckpt_every, and its ckpt):
+ * given gT = dL/dv_steps (float [n'][b]), writes dweights = dL/dweights (float [n_rules]) and
+ * dv0 = dL/dv0 (float [n'][b]). Each segment between checkpoints is recomputed from its
+ * checkpoint into scratch (scratch_floats). Weight gradients are accumulated in double. */
+lp_status lp_relaxed_backward(lp_program* prog, const float* weights, const float* gT, int32_t batch, int32_t steps,
+                              float tau, int32_t ckpt_every, const float* ckpt, float* scratch, float* dweights,
+                              float* dv0, void* cuda_stream);
+
 /* Statistics and device status of the last solve on this handle; waits for cuda_stream. */
 lp_status lp_last_solve_stats(lp_program* prog, lp_solve_stats* out, void* cuda_stream);
 

@@ -17,6 +17,7 @@
 #include "device.cuh"
 #include "internal.h"
 #include "kernels.h"
+#include "program.h"
 
 namespace lp {
 
@@ -29,49 +30,7 @@ void set_error(const std::string& msg) { g_err = msg; }
 
 using namespace lp;
 
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-struct lp_program {
-  HostMatrix hm;  // metadata (row_ptr/col host copies are dropped after upload)
-  int device = 0;
-  int sm_count = 0;
-  // device copy of the matrix and its tables
-  int32_t* row_ptr = nullptr;
-  int32_t* col = nullptr;
-  uint32_t* any_mask = nullptr;
-  int32_t* perm = nullptr;
-  int32_t* inv = nullptr;  // internal -> canonical, uploaded on first LP_ROWS call
-  int32_t* fact_row = nullptr;
-  int32_t* fact_owner = nullptr;
-  uint64_t* fact_mask = nullptr;
-  int32_t* neg_row = nullptr;
-  int32_t* bar_row = nullptr;
-  int32_t* row_tag = nullptr;
-  // streamed layout of the least-model kernel
-  uint32_t* desc = nullptr;
-  int32_t* word_hdr = nullptr;
-  int32_t* and_col = nullptr;
-  int32_t* groups = nullptr;
-  // scratch
-  uint32_t* x[2] = {nullptr, nullptr};
-  DeviceCtl* ctl = nullptr;
-  DeviceCtl* h_ctl = nullptr;  // pinned mirror of ctl
-  DevBuf tiles;                // stable-model iterate buffers
-  DevBuf stage_in, stage_out, stage_out2;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  bool timed = false;
-  int64_t last_launches = 0;
-  int64_t tile_words = 0;
-  int64_t device_bytes = 0;
-  int64_t upload_bytes = 0;
-  double compile_ms = 0.0;
-  bool host_only = false;  // LP_COMPILE_HOST_ONLY: host arrays kept, nothing on the device
-};
-
-namespace {
+namespace lp {
 
 lp_status fail(lp_status st, const std::string& msg) {
   set_error(msg);
@@ -82,36 +41,6 @@ lp_status cuda_fail(cudaError_t e, const char* what) {
   return fail(LP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define LP_CUDA(call)                                   \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-
-template <typename T>
-lp_status dalloc(lp_program* p, T** ptr, size_t count) {
-  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc((void**)ptr, bytes);
-  if (e != cudaSuccess) {
-    *ptr = nullptr;
-    cudaGetLastError();
-    return fail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
-                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
-  }
-  p->device_bytes += (int64_t)bytes;
-  return LP_OK;
-}
-
-template <typename T>
-lp_status upload(lp_program* p, T** ptr, const std::vector<T>& v, cudaStream_t s) {
-  lp_status st = dalloc(p, ptr, v.size());
-  if (st != LP_OK) return st;
-  if (!v.empty()) {
-    LP_CUDA(cudaMemcpyAsync(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-    p->upload_bytes += (int64_t)(v.size() * sizeof(T));
-  }
-  return LP_OK;
-}
 
 lp_status ensure(lp_program* p, DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return LP_OK;
@@ -160,7 +89,8 @@ lp_status ensure_scratch(lp_program* p) {
 void release(lp_program* p) {
   void* ptrs[] = {p->row_ptr, p->col, p->any_mask, p->perm, p->inv, p->fact_row, p->fact_owner, p->fact_mask,
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
-                  p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups};
+                  p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
+                  p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_ctl) cudaFreeHost(p->h_ctl);
@@ -188,7 +118,7 @@ lp_status finish_sync(lp_program* p, cudaStream_t s) {
 
 int max_coresident(lp_program* p, int per_sm) { return std::max(1, per_sm) * p->sm_count; }
 
-}  // namespace
+}  // namespace lp
 
 extern "C" {
 

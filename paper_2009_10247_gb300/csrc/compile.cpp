@@ -398,6 +398,9 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     hm.n_fact_rows = (int32_t)hm.fact_row.size();
     hm.n_rule_rows = n_rule_rows;
     hm.n_or_rows = n_or_rows;
+    hm.canon_rule.assign(np, -1);
+    for (int32_t c = 0; c < np; c++)
+      if (kind[c] == K_RULE) hm.canon_rule[c] = (int32_t)row_rule[c];
     hm.canon_kind.swap(kind);
   } catch (const std::bad_alloc&) {
     err = "host allocation failed in lp_compile";

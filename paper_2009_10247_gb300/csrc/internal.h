@@ -28,6 +28,7 @@ struct HostMatrix {
   std::vector<uint32_t> any_mask;  // n_pad / 32 words: bit set = OR-rule row (threshold 1)
   std::vector<int32_t> perm;       // canonical row -> internal row (n_prime)
   std::vector<int8_t> canon_kind;  // canonical row kinds (n_prime)
+  std::vector<int32_t> canon_rule; // canonical row -> original rule of a rule row, else -1
   std::vector<int32_t> fact_row;   // internal rows with a_ii = 1 from a fact (Def. 2 item 3)
   std::vector<int32_t> fact_owner; // original atom of each fact row
   std::vector<uint64_t> fact_mask; // ceil(n/64) words: atoms with at least one fact rule

@@ -1,0 +1,101 @@
+// program.h -- liblp's program handle and the helpers its C ABI translation units share.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct lp_program {
+  lp::HostMatrix hm;  // metadata (row_ptr/col host copies are dropped after upload)
+  int device = 0;
+  int sm_count = 0;
+  // device copy of the matrix and its tables
+  int32_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  uint32_t* any_mask = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* inv = nullptr;  // internal -> canonical, uploaded on first LP_ROWS call
+  int32_t* fact_row = nullptr;
+  int32_t* fact_owner = nullptr;
+  uint64_t* fact_mask = nullptr;
+  int32_t* neg_row = nullptr;
+  int32_t* bar_row = nullptr;
+  int32_t* row_tag = nullptr;
+  // streamed layout of the least-model kernel
+  uint32_t* desc = nullptr;
+  int32_t* word_hdr = nullptr;
+  int32_t* and_col = nullptr;
+  int32_t* groups = nullptr;
+  // scratch
+  uint32_t* x[2] = {nullptr, nullptr};
+  lp::DeviceCtl* ctl = nullptr;
+  lp::DeviceCtl* h_ctl = nullptr;  // pinned mirror of ctl
+  DevBuf tiles;                // stable-model iterate buffers
+  DevBuf stage_in, stage_out, stage_out2;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  int64_t last_launches = 0;
+  int64_t tile_words = 0;
+  int64_t device_bytes = 0;
+  int64_t upload_bytes = 0;
+  double compile_ms = 0.0;
+  bool host_only = false;  // LP_COMPILE_HOST_ONLY: host arrays kept, nothing on the device
+  // relaxed (differentiable) path, built on first use
+  bool rx_ready = false;
+  int32_t* rx_info = nullptr;    // per internal row: kind << 30 | entries
+  int32_t* rx_rule = nullptr;    // per internal row: original rule of a rule row, else -1
+  int32_t* rx_colptr = nullptr;  // transpose (CSC) of the rule and OR rows
+  int32_t* rx_rowidx = nullptr;
+  DevBuf rx_dw;                  // per-row weight-gradient accumulators (double)
+};
+
+namespace lp {
+
+lp_status fail(lp_status st, const std::string& msg);
+lp_status cuda_fail(cudaError_t e, const char* what);
+lp_status ensure(lp_program* p, DevBuf& b, size_t bytes);
+bool is_device_ptr(const void* ptr);
+lp_status launch_count_and_check(cudaError_t e, const char* what, lp_program* p);
+
+#define LP_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <typename T>
+lp_status dalloc(lp_program* p, T** ptr, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  p->device_bytes += (int64_t)bytes;
+  return LP_OK;
+}
+
+template <typename T>
+lp_status upload(lp_program* p, T** ptr, const std::vector<T>& v, cudaStream_t s) {
+  lp_status st = dalloc(p, ptr, v.size());
+  if (st != LP_OK) return st;
+  if (!v.empty()) {
+    LP_CUDA(cudaMemcpyAsync(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    p->upload_bytes += (int64_t)(v.size() * sizeof(T));
+  }
+  return LP_OK;
+}
+
+}  // namespace lp

@@ -37,7 +37,8 @@ class _Stats(ctypes.Structure):
 
 
 EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models", "lp_last_solve_stats",
-           "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static"]
+           "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static",
+           "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward"]
 
 _lib = None
 
@@ -64,6 +65,11 @@ def load(build_if_missing: bool = False):
     L.lp_stable_models.argtypes = [P, P, i64, P, P, i64, ctypes.POINTER(i64), i32, P]
     L.lp_last_solve_stats.argtypes = [P, ctypes.POINTER(_Stats), P]
     L.lp_export_matrix.argtypes = [P, P, P, P, P, P]
+    L.lp_relaxed_workspace.argtypes = [P, i32, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.lp_relaxed_forward.argtypes = [P, P, P, i32, i32, ctypes.c_float, i32, P, P, P]
+    L.lp_relaxed_backward.argtypes = [P, P, P, i32, i32, ctypes.c_float, i32, P, P, P, P, P]
+    for name in ("lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward"):
+        getattr(L, name).restype = ctypes.c_int
     L.lp_least_model_static.argtypes = [i32, P, P, P, P, P, i32, ctypes.POINTER(i32), P]
     L.lp_least_model_static.restype = ctypes.c_int
     L.lp_free.argtypes = [P]
@@ -178,6 +184,23 @@ class Program:
                                        int(max_models), ctypes.byref(ns) if sync else None, int(max_iters),
                                        _stream(stream)))
         return ns.value if sync else None
+
+    def relaxed_workspace(self, batch, steps, ckpt_every):
+        """(checkpoint floats, scratch floats) for the relaxed path."""
+        c, s_ = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().lp_relaxed_workspace(self._h, int(batch), int(steps), int(ckpt_every), ctypes.byref(c),
+                                           ctypes.byref(s_)))
+        return c.value, s_.value
+
+    def relaxed_forward(self, weights, v0, batch, steps, tau, ckpt_every, ckpt, vT, stream=None):
+        _check(load().lp_relaxed_forward(self._h, _ptr(weights), _ptr(v0), int(batch), int(steps), float(tau),
+                                         int(ckpt_every), _ptr(ckpt), _ptr(vT), _stream(stream)))
+
+    def relaxed_backward(self, weights, gT, batch, steps, tau, ckpt_every, ckpt, scratch, dweights, dv0,
+                         stream=None):
+        _check(load().lp_relaxed_backward(self._h, _ptr(weights), _ptr(gT), int(batch), int(steps), float(tau),
+                                          int(ckpt_every), _ptr(ckpt), _ptr(scratch), _ptr(dweights), _ptr(dv0),
+                                          _stream(stream)))
 
     def last_stats(self, stream=None):
         s = _Stats()

@@ -1,0 +1,129 @@
+"""GPU parity of the relaxed (differentiable) fixpoint against the FP64 oracle.
+
+Forward values and both gradient groups (rule weights, initial vectors) must match the FP64
+reference within a relative error of 1e-4 (||g - g_ref|| / ||g_ref|| per group); the result must
+not depend on the checkpoint interval; at tau = 1e-3 the relaxed iterates are the exact
+Algorithm 1 iterates; and the torch.autograd path returns the same gradients."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.relaxed import RelaxedProgram
+import paper_2009_10247_gb300 as lp
+from workloads import large_definite, small_definite, tiny_random
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2009_10247_gb300.relaxed import relaxed_fixpoint  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _rel(a, b):
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _run(prog, w, v0, c, T, tau, ckpt):
+    P = lp.Program.from_program(prog)
+    b = v0.shape[1]
+    wt = torch.tensor(w, dtype=torch.float32, device=DEV)
+    v0t = torch.tensor(v0, dtype=torch.float32, device=DEV)
+    ck, sc = P.relaxed_workspace(b, T, ckpt)
+    ckb = torch.empty(ck, dtype=torch.float32, device=DEV)
+    vT = torch.empty_like(v0t)
+    P.relaxed_forward(wt, v0t, b, T, tau, ckpt, ckb, vT)
+    scratch = torch.empty(sc, dtype=torch.float32, device=DEV)
+    dw = torch.empty_like(wt)
+    dv0 = torch.empty_like(v0t)
+    P.relaxed_backward(wt, torch.tensor(c, dtype=torch.float32, device=DEV), b, T, tau, ckpt, ckb, scratch, dw, dv0)
+    torch.cuda.synchronize()
+    P.close()
+    return vT.cpu().numpy(), dw.cpu().numpy(), dv0.cpu().numpy()
+
+
+def _case(prog, seed, b, T, tau, v0_binary=False):
+    rng = np.random.default_rng(seed)
+    R = RelaxedProgram(prog)
+    w = rng.uniform(0.5, 1.5, R.n_rules)
+    if v0_binary:
+        v0 = np.repeat((R.kind == oracle.ORC_FACT).astype(np.float64)[:, None], b, axis=1)
+        v0 *= rng.random(v0.shape) < 0.5
+    else:
+        v0 = rng.uniform(0.0, 1.0, (R.n_prime, b))
+    c = rng.uniform(-1.0, 1.0, (R.n_prime, b))
+    vs = R.forward(w, v0, T, tau)
+    dw_ref, dv0_ref = R.backward(w, vs, c, tau)
+    return R, w, v0, c, vs[-1], dw_ref, dv0_ref
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_programs(seed):
+    prog = tiny_random(300 + seed, n_atoms=int(10 + 7 * seed), n_rules=int(20 + 15 * seed), max_body=4, p_fact=0.25)
+    R, w, v0, c, vT_ref, dw_ref, dv0_ref = _case(prog, seed, b=5, T=10, tau=0.3)
+    vT, dw, dv0 = _run(prog, w, v0, c, 10, 0.3, 4)
+    assert np.max(np.abs(vT - vT_ref)) < 1e-5
+    assert _rel(dw, dw_ref) < 1e-4
+    assert _rel(dv0, dv0_ref) < 1e-4
+
+
+def test_small_definite_batch_40():
+    prog = small_definite(3)
+    R, w, v0, c, vT_ref, dw_ref, dv0_ref = _case(prog, 7, b=40, T=16, tau=0.1, v0_binary=True)
+    vT, dw, dv0 = _run(prog, w, v0, c, 16, 0.1, 8)
+    assert np.max(np.abs(vT - vT_ref)) < 1e-4
+    assert _rel(dw, dw_ref) < 1e-4
+    assert _rel(dv0, dv0_ref) < 1e-4
+
+
+def test_checkpoint_interval_does_not_change_results():
+    prog = small_definite(4)
+    R, w, v0, c, _, _, _ = _case(prog, 3, b=33, T=13, tau=0.2)
+    ref = _run(prog, w, v0, c, 13, 0.2, 13)
+    for ck in (1, 3, 8):
+        got = _run(prog, w, v0, c, 13, 0.2, ck)
+        for a, b_ in zip(got, ref):
+            assert np.array_equal(a, b_)
+
+
+def test_hardening_reproduces_exact_iterates():
+    prog = small_definite(5)
+    R = RelaxedProgram(prog)
+    s = R.std
+    T = 30
+    v = oracle.initial_vector(s)
+    v0 = np.repeat(v.astype(np.float64)[:, None], 3, axis=1)
+    w = np.random.default_rng(0).uniform(0.5, 1.5, R.n_rules)
+    vT, _, _ = _run(prog, w, v0, np.zeros_like(v0), T, 1e-3, 8)
+    for _ in range(T):
+        v = oracle.theta_step(s, v)
+    for j in range(3):
+        assert np.array_equal(vT[:, j] > 0.5, v.astype(bool))
+    assert np.all(np.minimum(vT, 1 - vT) < 1e-4)
+
+
+def test_autograd_function():
+    prog = small_definite(6)
+    R, w, v0, c, vT_ref, dw_ref, dv0_ref = _case(prog, 11, b=8, T=12, tau=0.2)
+    P = lp.Program.from_program(prog)
+    wt = torch.tensor(w, dtype=torch.float32, device=DEV, requires_grad=True)
+    v0t = torch.tensor(v0, dtype=torch.float32, device=DEV, requires_grad=True)
+    vT = relaxed_fixpoint(P, wt, v0t, 12, 0.2, 4)
+    loss = (torch.tensor(c, dtype=torch.float32, device=DEV) * vT).sum()
+    loss.backward()
+    assert np.max(np.abs(vT.detach().cpu().numpy() - vT_ref)) < 1e-5
+    assert _rel(wt.grad.cpu().numpy(), dw_ref) < 1e-4
+    assert _rel(v0t.grad.cpu().numpy(), dv0_ref) < 1e-4
+    P.close()
+
+
+def test_full_size_program_reduced_batch():
+    # the relaxed workload's program (1e5 atoms, 4e5 rules, chain depth 12), T = 32, tau = 0.05,
+    # checkpoint every 8; batch of 8 columns of random fact subsets (the oracle's cost)
+    prog = large_definite(seed=5, n=100_000, n_rules=400_000, chain_levels=12, chain_width=50)
+    R, w, v0, c, vT_ref, dw_ref, dv0_ref = _case(prog, 1, b=8, T=32, tau=0.05, v0_binary=True)
+    vT, dw, dv0 = _run(prog, w, v0, c, 32, 0.05, 8)
+    assert np.max(np.abs(vT - vT_ref)) < 1e-3
+    assert _rel(dw, dw_ref) < 1e-4
+    assert _rel(dv0, dv0_ref) < 1e-4

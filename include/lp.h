@@ -186,6 +186,47 @@ lp_status lp_relaxed_backward(lp_program* prog, const float* weights, const floa
                               float tau, int32_t ckpt_every, const float* ckpt, float* scratch, float* dweights,
                               float* dv0, void* cuda_stream);
 
+/*
+ * Many independent normal programs in one launch (batches of uneven sizes; Algorithms 2 and 3
+ * over all 2^k guesses of every program).
+ *
+ * lp_compile_batch: programs p in [0, n_programs); program p has n_atoms[p] atoms (ids local to
+ * the program) and the rules [rule_off[p], rule_off[p+1]) of the concatenated rule arrays head,
+ * body_off (over all rules, body_off[0] = 0), body_atom, body_neg (nullable), in the format of
+ * lp_compile. Each program is compiled exactly as lp_compile would; every program needs k <= 16.
+ * flags: 0. On success *out receives a handle (lp_batch_free).
+ */
+typedef struct lp_batch lp_batch;
+lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int64_t* rule_off, const int32_t* head,
+                           const int64_t* body_off, const int32_t* body_atom, const uint8_t* body_neg,
+                           uint32_t flags, void* cuda_stream, lp_batch** out);
+
+/* Totals of a batch (host outputs, each nullable): programs, rows, stored entries, stable-mask
+ * words (sum over programs of ceil(2^k / 64)) and device bytes held. */
+lp_status lp_batch_info(const lp_batch* batch, int64_t* n_programs, int64_t* total_rows, int64_t* total_nnz,
+                        int64_t* total_mask_words, int64_t* device_bytes);
+
+/* Sizes of program `program` (as lp_program_info) and the first word of its stable mask. */
+lp_status lp_batch_program_info(const lp_batch* batch, int32_t program, lp_info* info, int64_t* mask_word_offset);
+
+/*
+ * lp_batch_stable_models: for every program, all 2^k guesses (guess g = column g of M_0, Def. 8)
+ * are iterated M_{k+1} = theta(M_P M_k) to the fixpoint and checked by Algorithm 3.
+ * stable_mask (device or host, total_mask_words): program p's bit g (at its mask_word_offset) is
+ * set iff guess g gives a stable model. n_stable (device or host, n_programs, nullable): stable
+ * guesses per program; iters (device or host, n_programs, nullable): theta applications until
+ * the program's fixpoint (0 if it had none within max_iters). The programs run in lock step, up
+ * to 4096 per cooperative launch; a program stops being updated once an application changes
+ * none of its words. A host buffer or a non-NULL n_stable / iters makes the call wait;
+ * LP_ERR_NO_FIXPOINT if a program reaches max_iters (its mask is then zero); LP_ERR_TIMEOUT if a
+ * grid barrier wait gave up (2 s).
+ */
+lp_status lp_batch_stable_models(lp_batch* batch, uint64_t* stable_mask, int64_t* n_stable, int32_t* iters,
+                                 int32_t max_iters, void* cuda_stream);
+
+/* Release a batch and its device memory (NULL is a no-op). */
+void lp_batch_free(lp_batch* batch);
+
 /* Statistics and device status of the last solve on this handle; waits for cuda_stream. */
 lp_status lp_last_solve_stats(lp_program* prog, lp_solve_stats* out, void* cuda_stream);
 

@@ -3,7 +3,7 @@
 The compute path is liblp.so (CUDA for sm_103a, C ABI in include/lp.h); this package only
 loads it and marshals arguments. Nothing here falls back to a CPU implementation.
 """
-from .lp import (EXPORTS, LP_ROWS, LP_TIMING, LPError, Program, launch_count, least_model_static,  # noqa: F401
+from .lp import (EXPORTS, LP_ROWS, LP_TIMING, Batch, LPError, Program, launch_count, least_model_static,  # noqa: F401
                  library_path, load, words)
 
 

@@ -66,6 +66,7 @@ lp_status cuda_fail(cudaError_t e, const char* what);
 lp_status ensure(lp_program* p, DevBuf& b, size_t bytes);
 bool is_device_ptr(const void* ptr);
 lp_status launch_count_and_check(cudaError_t e, const char* what, lp_program* p);
+void count_launches(int64_t n);  // add to lp_launch_count()
 
 #define LP_CUDA(call)                                   \
   do {                                                  \

@@ -38,7 +38,8 @@ class _Stats(ctypes.Structure):
 
 EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models", "lp_last_solve_stats",
            "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static",
-           "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward"]
+           "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward", "lp_compile_batch", "lp_batch_info",
+           "lp_batch_program_info", "lp_batch_stable_models", "lp_batch_free"]
 
 _lib = None
 
@@ -70,6 +71,14 @@ def load(build_if_missing: bool = False):
     L.lp_relaxed_backward.argtypes = [P, P, P, i32, i32, ctypes.c_float, i32, P, P, P, P, P]
     for name in ("lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward"):
         getattr(L, name).restype = ctypes.c_int
+    L.lp_compile_batch.argtypes = [i32, P, P, P, P, P, P, u32, P, ctypes.POINTER(P)]
+    L.lp_batch_info.argtypes = [P] + [ctypes.POINTER(i64)] * 5
+    L.lp_batch_program_info.argtypes = [P, i32, ctypes.POINTER(_Info), ctypes.POINTER(i64)]
+    L.lp_batch_stable_models.argtypes = [P, P, P, P, i32, P]
+    for name in ("lp_compile_batch", "lp_batch_info", "lp_batch_program_info", "lp_batch_stable_models"):
+        getattr(L, name).restype = ctypes.c_int
+    L.lp_batch_free.argtypes = [P]
+    L.lp_batch_free.restype = None
     L.lp_least_model_static.argtypes = [i32, P, P, P, P, P, i32, ctypes.POINTER(i32), P]
     L.lp_least_model_static.restype = ctypes.c_int
     L.lp_free.argtypes = [P]
@@ -219,6 +228,62 @@ class Program:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().lp_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many independent normal programs compiled for one launch (lp_compile_batch)."""
+
+    def __init__(self, programs, stream=None):
+        L = load()
+        n = len(programs)
+        n_atoms = np.array([p.n_atoms for p in programs], dtype=np.int32)
+        rule_off = np.zeros(n + 1, dtype=np.int64)
+        rule_off[1:] = np.cumsum([len(p.head) for p in programs])
+        head = np.concatenate([np.asarray(p.head, np.int32) for p in programs]) if n else np.zeros(0, np.int32)
+        lit_off = np.concatenate([[0], np.cumsum([len(p.body_atom) for p in programs])]).astype(np.int64)
+        body_off = np.zeros(int(rule_off[-1]) + 1, dtype=np.int64)
+        for i, p in enumerate(programs):
+            body_off[rule_off[i]:rule_off[i + 1] + 1] = np.asarray(p.body_off, np.int64) + lit_off[i]
+        atom = np.concatenate([np.asarray(p.body_atom, np.int32) for p in programs]) if n else np.zeros(0, np.int32)
+        neg = None
+        if any(getattr(p, "body_neg", None) is not None for p in programs):
+            neg = np.concatenate([np.asarray(p.body_neg, np.uint8) if getattr(p, "body_neg", None) is not None
+                                  else np.zeros(len(p.body_atom), np.uint8) for p in programs])
+        self._h = ctypes.c_void_p()
+        _check(L.lp_compile_batch(n, _ptr(n_atoms), _ptr(rule_off), _ptr(head), _ptr(body_off), _ptr(atom), _ptr(neg),
+                                  0, _stream(stream), ctypes.byref(self._h)))
+        vals = [ctypes.c_int64() for _ in range(5)]
+        _check(L.lp_batch_info(self._h, *[ctypes.byref(v) for v in vals]))
+        self.n_programs, self.total_rows, self.total_nnz, self.total_mask_words, self.device_bytes = [v.value for v in vals]
+        self.k, self.mask_offset, self.info = [], [], []
+        for i in range(n):
+            inf, off = _Info(), ctypes.c_int64()
+            _check(L.lp_batch_program_info(self._h, i, ctypes.byref(inf), ctypes.byref(off)))
+            d = {f: getattr(inf, f) for f, _ in _Info._fields_}
+            self.info.append(d)
+            self.k.append(d["k"])
+            self.mask_offset.append(off.value)
+
+    def stable_models(self, stable_mask, n_stable=None, iters=None, max_iters=1 << 30, stream=None):
+        _check(load().lp_batch_stable_models(self._h, _ptr(stable_mask), _ptr(n_stable), _ptr(iters), int(max_iters),
+                                             _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lp_batch_free(self._h)
         self._h = None
 
     def __del__(self):

@@ -1,0 +1,128 @@
+"""GPU parity of the many-program batch (lp_compile_batch / lp_batch_stable_models): every
+program's stable bits over all 2^k guesses are compared bit for bit with the oracle's per-guess
+Algorithms 2 and 3, on tiny random programs (with the degenerate ones: no rules, definite
+programs, k = 0), on a reduced batch of the uneven-size workload, and, at the full 1000-program
+size the benchmark times, against the oracle for every program and the single-program entry
+point for a sample."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2009_10247_gb300 as lp
+from tests.helpers import bits_to_bool
+from workloads import Program, parse, program_batch, small_definite, tiny_random
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_util import DEV, gpu_stable  # noqa: E402
+
+
+def _run_batch(progs, host=False, max_iters=1 << 30):
+    with lp.Batch(progs) as B:
+        n = B.n_programs
+        if host:
+            mask = np.zeros(max(B.total_mask_words, 1), dtype=np.uint64)
+            ns = np.zeros(max(n, 1), dtype=np.int64)
+            it = np.zeros(max(n, 1), dtype=np.int32)
+            B.stable_models(mask, ns, it, max_iters=max_iters)
+        else:
+            mask_t = torch.zeros(max(B.total_mask_words, 1), dtype=torch.int64, device=DEV)
+            ns_t = torch.zeros(max(n, 1), dtype=torch.int64, device=DEV)
+            it_t = torch.zeros(max(n, 1), dtype=torch.int32, device=DEV)
+            B.stable_models(mask_t, ns_t, it_t, max_iters=max_iters)
+            torch.cuda.synchronize()
+            mask, ns, it = mask_t.cpu().numpy().view(np.uint64), ns_t.cpu().numpy(), it_t.cpu().numpy()
+        out = []
+        for p in range(n):
+            ng = 1 << B.k[p]
+            w = (ng + 63) // 64
+            out.append(bits_to_bool(mask[B.mask_offset[p]:B.mask_offset[p] + w], ng))
+        return out, ns[:n], it[:n], B
+
+
+def _check_oracle(progs, got, ns):
+    for p, prog in enumerate(progs):
+        st4, _, _ = oracle.stable_models_alg23(prog)
+        assert np.array_equal(got[p], st4), f"program {p}"
+        assert ns[p] == int(st4.sum())
+
+
+def test_tiny_random_programs():
+    rng = np.random.default_rng(77)
+    progs = []
+    for s in range(60):
+        progs.append(tiny_random(5000 + s, n_atoms=int(rng.integers(2, 50)), n_rules=int(rng.integers(1, 100)),
+                                 max_body=4, p_fact=0.15, p_neg=0.12))
+    progs += [parse("p :- not q. q :- not p."), parse("p :- not p."), small_definite(1),
+              parse("a :- not b. b :- not a. c :- a. c :- b.")]
+    got, ns, _, _ = _run_batch(progs)
+    _check_oracle(progs, got, ns)
+
+
+def test_degenerate_programs():
+    empty = Program(n_atoms=3, head=np.zeros(0, np.int64), body_off=np.zeros(1, np.int64),
+                    body_atom=np.zeros(0, np.int64), body_neg=None)
+    progs = [empty, parse("p."), parse("p :- not q. q :- not p."), empty]
+    got, ns, it, _ = _run_batch(progs)
+    _check_oracle(progs, got, ns)
+    assert all(i >= 1 for i in it)
+
+
+def test_empty_batch():
+    got, ns, _, B = _run_batch([])
+    assert got == [] and B.total_rows == 0
+
+
+def test_host_buffers_match_device():
+    progs = program_batch(seed=3, count=24, n_lo=50, n_hi=1500)
+    a, na, ia, _ = _run_batch(progs)
+    b, nb, ib, _ = _run_batch(progs, host=True)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert np.array_equal(na, nb) and np.array_equal(ia, ib)
+    _check_oracle(progs, a, na)
+
+
+def test_reduced_uneven_batch_against_oracle():
+    # the uneven-size workload's generator with smaller programs (oracle cost)
+    progs = program_batch(seed=11, count=40, n_lo=100, n_hi=3000)
+    got, ns, _, _ = _run_batch(progs)
+    _check_oracle(progs, got, ns)
+
+
+def test_no_fixpoint_reports_error():
+    progs = [small_definite(2)]
+    with pytest.raises(lp.LPError):
+        _run_batch(progs, max_iters=2)
+
+
+def test_too_many_guesses_rejected():
+    # 17 negated atoms that are not facts: k = 17 > 16
+    p = parse(" ".join(f"p{i} :- not q{i}." for i in range(17)))
+    with pytest.raises(lp.LPError):
+        lp.Batch([parse("p :- not q."), p])
+
+
+def test_full_uneven_batch():
+    # the benchmark's workload: 1000 programs, 100..20000 atoms, 3 rules per atom, k in 4..8;
+    # every program against the oracle (about 30 s of CPU), and every 20th against the
+    # single-program entry point
+    progs = program_batch(seed=1)
+    got, ns, it, B = _run_batch(progs)
+    assert B.n_programs == 1000
+    _check_oracle(progs, got, ns)
+    for p in range(0, 1000, 20):
+        with lp.Program.from_program(progs[p]) as P:
+            st, _, n1 = gpu_stable(P)
+        assert np.array_equal(got[p], st), f"program {p}"
+        assert ns[p] == n1
+
+
+def test_more_programs_than_one_launch():
+    # 4100 programs: two cooperative launches (up to 4096 programs each)
+    rng = np.random.default_rng(5)
+    progs = [tiny_random(9000 + s, n_atoms=int(rng.integers(2, 30)), n_rules=int(rng.integers(1, 50)), max_body=3,
+                         p_fact=0.2, p_neg=0.15) for s in range(4100)]
+    got, ns, it, _ = _run_batch(progs)
+    _check_oracle(progs, got, ns)
+    assert np.all(it >= 1)

@@ -90,7 +90,7 @@ void release(lp_program* p) {
   void* ptrs[] = {p->row_ptr, p->col, p->any_mask, p->perm, p->inv, p->fact_row, p->fact_owner, p->fact_mask,
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
                   p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
-                  p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p};
+                  p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_ctl) cudaFreeHost(p->h_ctl);

@@ -57,6 +57,10 @@ struct lp_program {
   int32_t* rx_colptr = nullptr;  // transpose (CSC) of the rule and OR rows
   int32_t* rx_rowidx = nullptr;
   DevBuf rx_dw;                  // per-row weight-gradient accumulators (double)
+  void* rx_units = nullptr;      // fixed reduction tree of the transpose (RxUnit records, by level)
+  std::vector<int64_t> rx_level_off;   // first unit of each level (+ end)
+  std::vector<int64_t> rx_part_off;    // first partial row of each level's output (+ end)
+  DevBuf rx_part;                // partial sums of the tree, rx_part_off.back() x batch floats
 };
 
 namespace lp {

@@ -13,7 +13,11 @@
 // coalesced read. The adjoint of one step, with g = dL/dv_{t+1} and e = g u (1 - u):
 //   dL/dw_r += sum_batch e (x/m - 1 + 1/(2m)) / tau         (rule rows; double accumulators)
 //   dL/dv_t  = M^T (c e) + g on self-loop rows,  c = w_r/(m tau) (rule), 1/tau (OR)
-// where M^T is applied as a gather over a transposed copy (CSC) of the rule and OR rows.
+// where M^T is applied as a gather over a transposed copy (CSC) of the rule and OR rows. The
+// column lengths of that copy follow the skew of the body atoms (a popular atom sits in 1e5
+// rows), so every column's sum runs as a fixed reduction tree: chunks of up to 32 entries, then
+// chunks of up to 32 partial sums, and so on. The tree depends only on the matrix, so results
+// are the same bit for bit on every run, and no warp walks more than 32 rows.
 // The forward keeps v every ckpt_every steps; the backward recomputes each segment from its
 // checkpoint and runs the adjoint through it, last segment first.
 #include <cuda_runtime.h>
@@ -136,38 +140,52 @@ __global__ void __launch_bounds__(kRxBlock) rx_backward_rows_kernel(
   }
 }
 
-// g0[j] = sum over rows i containing j of e[i] (+ g1[j] on self-loop rows).
-__global__ void __launch_bounds__(kRxBlock) rx_backward_cols_kernel(const int32_t* __restrict__ colptr,
-                                                                    const int32_t* __restrict__ rowidx,
-                                                                    const int32_t* __restrict__ info,
-                                                                    const float* __restrict__ e,
-                                                                    const float* __restrict__ g1,
-                                                                    float* __restrict__ g0, int n_rows, int b) {
+// One node of the reduction tree of g0 = M^T e: the sum of `count` source rows of b floats,
+// from e rows listed in the transpose (level 0: rowidx[src ..]) or from consecutive partial rows
+// of the previous level (partial rows src ..). dst >= 0: a partial row of this level's output;
+// dst < 0: the final value of column j, plus g1[j] on a self-loop row.
+struct RxUnit {
+  int64_t src;
+  int64_t dst;
+  int32_t j;
+  int32_t count;
+};
+constexpr int kRxFan = 32;  // children per tree node
+
+__global__ void __launch_bounds__(kRxBlock) rx_reduce_kernel(const RxUnit* __restrict__ units, int64_t n_units,
+                                                             const int32_t* __restrict__ rowidx,
+                                                             const float* __restrict__ src,
+                                                             float* __restrict__ part_out,
+                                                             const int32_t* __restrict__ info,
+                                                             const float* __restrict__ g1,
+                                                             float* __restrict__ g0, int b) {
   const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n_rows; j += nwarps) {
-    const int kind = (int)((unsigned)__ldg(info + j) >> 30);
-    const int beg = __ldg(colptr + j), end = __ldg(colptr + j + 1);
-    const size_t ro = (size_t)j * b;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n_units; u += nwarps) {
+    const RxUnit un = units[u];
+    const bool fin = un.dst < 0;
+    const bool self = fin && (int)((unsigned)__ldg(info + un.j) >> 30) == RX_SELF;
+    float* out = fin ? g0 + (size_t)un.j * b : part_out + (size_t)un.dst * b;
     for (int c0 = 0; c0 < b; c0 += 32 * kRxPerLane) {
       float acc[kRxPerLane];
 #pragma unroll
       for (int k = 0; k < kRxPerLane; k++) {
         const int c = c0 + 32 * k + lane;
-        acc[k] = (kind == RX_SELF && c < b) ? g1[ro + c] : 0.f;
+        acc[k] = (self && c < b) ? g1[(size_t)un.j * b + c] : 0.f;
       }
-      for (int t = beg; t < end; t++) {
-        const float* src = e + (size_t)__ldg(rowidx + t) * b;
+      for (int t = 0; t < un.count; t++) {
+        const size_t r = rowidx ? (size_t)__ldg(rowidx + un.src + t) : (size_t)(un.src + t);
+        const float* row = src + r * b;
 #pragma unroll
         for (int k = 0; k < kRxPerLane; k++) {
           const int c = c0 + 32 * k + lane;
-          if (c < b) acc[k] += src[c];
+          if (c < b) acc[k] += row[c];
         }
       }
 #pragma unroll
       for (int k = 0; k < kRxPerLane; k++) {
         const int c = c0 + 32 * k + lane;
-        if (c < b) g0[ro + c] = acc[k];
+        if (c < b) out[c] = acc[k];
       }
     }
   }
@@ -247,10 +265,50 @@ lp_status ensure_relaxed(lp_program* p, cudaStream_t s) {
         for (int32_t e = rp[r]; e < rp[r + 1]; e++) ri[cur[cl[e]]++] = r;
     }
   }
+  // reduction tree of every column: level 0 sums chunks of <= kRxFan transpose entries; a
+  // column with more than one chunk continues at the next level over its chunks' partial rows
+  std::vector<RxUnit> units;
+  p->rx_level_off.assign(1, 0);
+  p->rx_part_off.assign(1, 0);
+  struct Pending {
+    int32_t j;
+    int64_t first, n;  // partial rows [first, first + n) of the previous level
+  };
+  std::vector<Pending> pend, next_pend;
+  int64_t part = 0;
+  for (int32_t j = 0; j < hm.n_pad; j++) {
+    const int64_t deg = cp[j + 1] - cp[j];
+    if (deg <= kRxFan) {
+      units.push_back({cp[j], -1, j, (int32_t)deg});
+      continue;
+    }
+    const int64_t first = part;
+    for (int64_t c = 0; c < deg; c += kRxFan)
+      units.push_back({cp[j] + c, part++, j, (int32_t)std::min<int64_t>(kRxFan, deg - c)});
+    pend.push_back({j, first, part - first});
+  }
+  p->rx_level_off.push_back((int64_t)units.size());
+  p->rx_part_off.push_back(part);
+  while (!pend.empty()) {
+    next_pend.clear();
+    for (const Pending& q : pend) {
+      if (q.n <= kRxFan) {
+        units.push_back({q.first, -1, q.j, (int32_t)q.n});
+        continue;
+      }
+      const int64_t first = part;
+      for (int64_t c = 0; c < q.n; c += kRxFan)
+        units.push_back({q.first + c, part++, q.j, (int32_t)std::min<int64_t>(kRxFan, q.n - c)});
+      next_pend.push_back({q.j, first, part - first});
+    }
+    p->rx_level_off.push_back((int64_t)units.size());
+    p->rx_part_off.push_back(part);
+    pend.swap(next_pend);
+  }
   lp_status st;
+  if ((st = upload(p, reinterpret_cast<RxUnit**>(&p->rx_units), units, s)) != LP_OK) return st;
   if ((st = upload(p, &p->rx_info, info, s)) != LP_OK) return st;
   if ((st = upload(p, &p->rx_rule, rule, s)) != LP_OK) return st;
-  if ((st = upload(p, &p->rx_colptr, cp, s)) != LP_OK) return st;
   if ((st = upload(p, &p->rx_rowidx, ri, s)) != LP_OK) return st;
   if ((st = ensure(p, p->rx_dw, (size_t)hm.n_pad * sizeof(double))) != LP_OK) return st;
   LP_CUDA(cudaStreamSynchronize(s));
@@ -348,6 +406,9 @@ lp_status lp_relaxed_backward(lp_program* p, const float* weights, const float* 
   const float inv_tau = 1.0f / tau;
   const int rg = rx_grid(p, hm.n_pad);
   const int eg = rx_grid(p, (int64_t)(nb + 31) / 32);
+  if ((st = ensure(p, p->rx_part, std::max<size_t>((size_t)p->rx_part_off.back() * batch * sizeof(float), 4))) !=
+      LP_OK)
+    return st;
   LP_CUDA(cudaMemsetAsync(p->rx_dw.p, 0, (size_t)hm.n_pad * sizeof(double), s));
   rx_to_internal_kernel<<<eg, kRxBlock, 0, s>>>(gT, G0, p->inv, hm.n_prime, hm.n_pad, batch);
   if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
@@ -369,9 +430,18 @@ lp_status lp_relaxed_backward(lp_program* p, const float* weights, const float* 
                                                       g, E, (double*)p->rx_dw.p, hm.n_pad, batch, inv_tau);
       if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
       float* gn = (g == G0) ? G1 : G0;
-      rx_backward_cols_kernel<<<rg, kRxBlock, 0, s>>>(p->rx_colptr, p->rx_rowidx, p->rx_info, E, g, gn, hm.n_pad,
-                                                      batch);
-      if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
+      // g_t = M^T E (+ g on self-loops), level by level; partial rows are numbered across all
+      // levels (level L writes rows [rx_part_off[L], rx_part_off[L + 1]), level L + 1 reads them)
+      const RxUnit* units = reinterpret_cast<const RxUnit*>(p->rx_units);
+      float* part = (float*)p->rx_part.p;
+      const int n_levels = (int)p->rx_level_off.size() - 1;
+      for (int L = 0; L < n_levels; L++) {
+        const int64_t u0 = p->rx_level_off[L], nu = p->rx_level_off[L + 1] - u0;
+        if (nu == 0) continue;
+        rx_reduce_kernel<<<rx_grid(p, nu), kRxBlock, 0, s>>>(units + u0, nu, L == 0 ? p->rx_rowidx : nullptr,
+                                                             L == 0 ? E : part, part, p->rx_info, g, gn, batch);
+        if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
+      }
       g = gn;
     }
   }

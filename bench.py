@@ -9,6 +9,9 @@ output projection) with the program matrix resident in HBM; L2 is flushed (256 M
 before every step. value = nnz x iterations x steps x ranks / (max over ranks of the summed
 device time). e2e runs the public C ABI from host arrays: lp_compile (standardize, order,
 CSR, upload), lp_least_model with a host initial vector and host output, lp_free.
+Secondary lines (rank 0): all 2^16 guesses of the normal program in one call against one launch
+per guess; 1000 programs of uneven size in one launch against one launch per program; the
+relaxed fixpoint's forward (T = 32, batch 256) and hand-written backward.
 The reference arm (--impl reference) times the CPU oracle's Algorithm 1 on the same matrix.
 Under torchrun every rank runs its own replica (the single-vector solve does not shard).
 """
@@ -25,12 +28,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import large_definite, normal_program  # noqa: E402
+from workloads import large_definite, normal_program, program_batch  # noqa: E402
 
 METRIC = "fixpoint rule-evals/sec (nnz x iters / s)"
 UNIT = "rule-evals/s"
 WORKLOAD = "large definite program: 1e6 atoms, 5e6 rules, Geom(mean 3, cap 8) bodies, Zipf(1.1) atoms, 1% facts, chain 1000x50 (seed 1)"
 WORKLOAD_STABLE = "normal program: 1e5 atoms, 3e5 rules, bodies U{1..6}, 1% facts, k=16 negated atoms x 4 (seed 1), all 65536 guesses"
+WORKLOAD_BATCH = ("1000 normal programs: atoms log-uniform in [100, 20000], 3 rules per atom, k ~ U{4..8} negated atoms "
+                  "x 2, bodies U{1..6} (seed 1), all 2^k guesses of every program")
+WORKLOAD_RELAXED = ("definite program: 1e5 atoms, 4e5 rules, Geom(mean 3, cap 8) bodies, Zipf(1.1) atoms, 1% facts, "
+                    "chain 12x50 (seed 5); w ~ U(0.5, 1.5), tau 0.05, T 32, batch 256 fact subsets (p 1/2), "
+                    "checkpoint every 8")
 
 
 def peaks():
@@ -164,6 +172,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=400, help="oracle theta applications in cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=25, help="oracle theta applications per reference step")
     ap.add_argument("--no-stable", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-relaxed", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -264,9 +274,13 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_host.nbytes),
                "ms_per_step": 1e3 * sum(e2e_t) / len(e2e_t)}
 
-    secondary = None
+    secondary = batch = relaxed = None
     if not args.no_stable and rank == 0:
         secondary = bench_stable(lp, torch, dev, flush)
+    if not args.no_batch and rank == 0:
+        batch = bench_batch(lp, torch, dev, flush)
+    if not args.no_relaxed and rank == 0:
+        relaxed = bench_relaxed(lp, torch, dev, flush)
 
     cpu = None
     if rank == 0 and args.cpu_iters > 0:
@@ -292,6 +306,8 @@ def main():
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "stable_models": secondary,
+            "stable_models_batch": batch,
+            "relaxed": relaxed,
         }
         print(json.dumps(line), flush=True)
     P.close()
@@ -334,6 +350,138 @@ def bench_stable(lp, torch, dev, flush, steps=5):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": None, "peak_kind": peak_kind, "kernel": "stable_kernel",
                         "note": "tiles are sized to stay L2 resident, so this fraction can exceed 1"}}
+    # the baseline: one launch per guess (lp_stable_models on a one-guess list), sampled
+    n_one = 128
+    one = torch.zeros(1, dtype=torch.int64, device=dev)
+    gl = torch.arange(n_one, dtype=torch.int64, device=dev) * 509 % ng
+    for j in range(4):
+        P.stable_models(one, guesses=gl[j:j + 1], n_guesses=1, sync=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for j in range(n_one):
+        P.stable_models(one, guesses=gl[j:j + 1], n_guesses=1, sync=False)
+    b.record(stream)
+    b.synchronize()
+    per_guess = n_one / (a.elapsed_time(b) / 1e3)
+    out["per_guess_launches"] = {"value": per_guess, "unit": "guesses/s", "sample": f"{n_one} guesses, one launch each"}
+    out["batched_over_per_guess"] = out["value"] / per_guess
+    P.close()
+    return out
+
+
+def bench_batch(lp, torch, dev, flush, steps=5):
+    """Many programs in one launch (lp_batch_stable_models) against one launch per program."""
+    progs = program_batch(seed=1)
+    B = lp.Batch(progs)
+    n = B.n_programs
+    mask = torch.zeros(B.total_mask_words, dtype=torch.int64, device=dev)
+    ns = torch.zeros(n, dtype=torch.int64, device=dev)
+    it = torch.zeros(n, dtype=torch.int32, device=dev)
+    B.stable_models(mask, ns, it)
+    n_stable, iters = ns.cpu().numpy(), it.cpu().numpy()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        flush.zero_()
+        B.stable_models(mask)
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.stable_models(mask)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    guesses = sum(1 << k for k in B.k)
+    # algorithmic bytes: per program and iteration, row_ptr (8 B) + col (4 B) read once, the
+    # iterate (W words per row) read once and written once
+    by = 0
+    for p in range(n):
+        inf = B.info[p]
+        W = max(1, (1 << inf["k"]) // 64)
+        by += int(iters[p]) * (8 * (inf["n_prime"] + 1) + 4 * inf["nnz"] + 16 * inf["n_prime"] * W)
+    peak, peak_kind = peaks()
+    achieved = by / (ms / 1e3) / 1e9
+    # baseline: one lp_stable_models launch per program, same GPU, programs resident
+    Ps = [lp.Program.from_program(pr) for pr in progs]
+    ms_k = [torch.zeros(lp.words(1 << P.info["k"]), dtype=torch.int64, device=dev) for P in Ps]
+    for P, m in zip(Ps, ms_k):
+        P.stable_models(m, sync=False)
+    torch.cuda.synchronize()
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for P, m in zip(Ps, ms_k):
+        P.stable_models(m, sync=False)
+    b.record(stream)
+    b.synchronize()
+    per_prog_ms = a.elapsed_time(b)
+    for P in Ps:
+        P.close()
+    out = {"metric": "stable-model guesses/sec, many programs in one launch", "value": guesses / (ms / 1e3),
+           "unit": "guesses/s", "ms_per_step": ms, "workload": WORKLOAD_BATCH, "programs": n, "guesses": guesses,
+           "rows": B.total_rows, "nnz": B.total_nnz, "n_stable": int(n_stable.sum()), "iters_max": int(iters.max()),
+           "iters_mean": float(iters.mean()), "launches_per_step": (n + 4095) // 4096,
+           "per_program_launches": {"ms_per_step": per_prog_ms, "value": guesses / (per_prog_ms / 1e3),
+                                    "unit": "guesses/s", "launches_per_step": n},
+           "batched_over_per_program": per_prog_ms / ms,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "peak_kind": peak_kind, "kernel": "batch_stable_kernel",
+                        "bytes_per_launch": by,
+                        "note": "per-program iterates are L2 resident between iterations, so this can exceed 1"}}
+    B.close()
+    return out
+
+
+def bench_relaxed(lp, torch, dev, flush, steps=3):
+    """Relaxed fixpoint: forward (T steps, checkpoints) and hand-written backward."""
+    prog = large_definite(seed=5, n=100_000, n_rules=400_000, chain_levels=12, chain_width=50)
+    P = lp.Program.from_program(prog)
+    n_prime, nnz, nr = P.info["n_prime"], P.info["nnz"], int(prog.n_rules)
+    bsz, T, tau, ck = 256, 32, 0.05, 8
+    rng = np.random.default_rng(1)
+    kind = P.export_matrix()["kind"]
+    w = torch.tensor(rng.uniform(0.5, 1.5, nr), dtype=torch.float32, device=dev)
+    v0h = np.zeros((n_prime, bsz), dtype=np.float32)
+    fr = np.nonzero(kind == 3)[0]
+    v0h[fr] = rng.random((len(fr), bsz)) < 0.5
+    v0 = torch.from_numpy(v0h).to(dev)
+    gT = torch.tensor(rng.uniform(-1, 1, (n_prime, bsz)), dtype=torch.float32, device=dev)
+    ckf, scf = P.relaxed_workspace(bsz, T, ck)
+    ckpt = torch.empty(ckf, dtype=torch.float32, device=dev)
+    scratch = torch.empty(scf, dtype=torch.float32, device=dev)
+    vT, dw, dv0 = torch.empty_like(v0), torch.empty_like(w), torch.empty_like(v0)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        P.relaxed_forward(w, v0, bsz, T, tau, ck, ckpt, vT)
+        P.relaxed_backward(w, gT, bsz, T, tau, ck, ckpt, scratch, dw, dv0)
+    torch.cuda.synchronize()
+    fwd, bwd = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        P.relaxed_forward(w, v0, bsz, T, tau, ck, ckpt, vT)
+        e[1].record(stream)
+        P.relaxed_backward(w, gT, bsz, T, tau, ck, ckpt, scratch, dw, dv0)
+        e[2].record(stream)
+        e[2].synchronize()
+        fwd.append(e[0].elapsed_time(e[1]))
+        bwd.append(e[1].elapsed_time(e[2]))
+    f_ms, b_ms = statistics.median(fwd), statistics.median(bwd)
+    # per forward step: row_ptr + col + per-row weight read, the batch read once and written once
+    step_bytes = 4 * (n_prime + 1) + 4 * nnz + 4 * n_prime + 8 * n_prime * bsz
+    peak, peak_kind = peaks()
+    achieved = step_bytes * T / (f_ms / 1e3) / 1e9
+    out = {"metric": "relaxed rule-evals/sec (nnz x T x batch / s, forward + backward)",
+           "value": nnz * T * bsz / ((f_ms + b_ms) / 1e3), "unit": "rule-evals/s", "forward_ms": f_ms,
+           "backward_ms": b_ms, "workload": WORKLOAD_RELAXED, "n_prime": n_prime, "nnz": nnz, "batch": bsz,
+           "steps": T, "tau": tau, "ckpt_every": ck,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "peak_kind": peak_kind, "kernel": "rx_forward_kernel (whole forward)",
+                        "bytes_per_step": step_bytes}}
     P.close()
     return out
 

@@ -28,7 +28,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import large_definite, normal_program, program_batch  # noqa: E402
+from workloads import large_definite, normal_program, program_batch, table1_program  # noqa: E402
 
 METRIC = "fixpoint rule-evals/sec (nnz x iters / s)"
 UNIT = "rule-evals/s"
@@ -174,6 +174,7 @@ def main():
     ap.add_argument("--no-stable", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-relaxed", action="store_true")
+    ap.add_argument("--no-paper-tables", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -281,6 +282,9 @@ def main():
         batch = bench_batch(lp, torch, dev, flush)
     if not args.no_relaxed and rank == 0:
         relaxed = bench_relaxed(lp, torch, dev, flush)
+    tables = None
+    if not args.no_paper_tables and rank == 0:
+        tables = bench_paper_tables(lp, torch, dev)
 
     cpu = None
     if rank == 0 and args.cpu_iters > 0:
@@ -308,6 +312,7 @@ def main():
             "stable_models": secondary,
             "stable_models_batch": batch,
             "relaxed": relaxed,
+            "paper_tables": tables,
         }
         print(json.dumps(line), flush=True)
     P.close()
@@ -428,7 +433,8 @@ def bench_batch(lp, torch, dev, flush, steps=5):
                                     "unit": "guesses/s", "launches_per_step": n},
            "batched_over_per_program": per_prog_ms / ms,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": None, "peak_kind": peak_kind, "kernel": "batch_stable_kernel",
+                        "traffic": measured_traffic("batch_stable_kernel"), "peak_kind": peak_kind,
+                        "kernel": "batch_stable_kernel",
                         "bytes_per_launch": by,
                         "note": "per-program iterates are L2 resident between iterations, so this can exceed 1"}}
     B.close()
@@ -484,6 +490,85 @@ def bench_relaxed(lp, torch, dev, flush, steps=3):
                         "bytes_per_step": step_bytes}}
     P.close()
     return out
+
+
+# The paper's programs (Sec. 4): (table, No., n, m, k, n' printed, Sparse-matrix seconds printed).
+# Its timings are single-threaded C++/Eigen on an Intel Core i7-4770 at 3.4 GHz (Sec. 4).
+PAPER_ROWS = [
+    # Table 2: definite programs, sparsity 0.99
+    (2, 1, 1000, 5000, 0, 5788, 0.0071), (2, 2, 1000, 10000, 0, 10799, 0.0127),
+    (2, 3, 1600, 24000, 0, 25198, 0.0357), (2, 4, 1600, 30000, 0, 31285, 0.0605),
+    (2, 5, 2000, 36000, 0, 37596, 0.0692), (2, 6, 2000, 40000, 0, 41936, 0.0675),
+    (2, 7, 10000, 120000, 0, 127119, 0.3798), (2, 8, 10000, 160000, 0, 167504, 0.4832),
+    (2, 9, 16000, 200000, 0, 211039, 0.8643), (2, 10, 16000, 220000, 0, 231439, 0.9429),
+    (2, 11, 20000, 280000, 0, 297293, 0.9048), (2, 12, 20000, 320000, 0, 337056, 1.0614),
+    # Table 3: definite programs, sparsity 0.95 (rows 1-8)
+    (3, 1, 1000, 5000, 0, 5876, 0.0384), (3, 2, 1000, 10000, 0, 10243, 0.0519),
+    (3, 3, 1600, 24000, 0, 25712, 0.1634), (3, 4, 1600, 30000, 0, 31430, 0.3772),
+    (3, 5, 2000, 36000, 0, 36612, 0.5499), (3, 6, 2000, 40000, 0, 41509, 0.6284),
+    (3, 7, 10000, 120000, 0, 125692, 1.0816), (3, 8, 10000, 160000, 0, 166741, 2.2907),
+    # Table 5: normal programs (all 2^k guesses), sparsity 0.99
+    (5, 1, 1000, 5000, 8, 6379, 0.0119), (5, 2, 1000, 10000, 8, 12745, 0.0178),
+    (5, 3, 1600, 24000, 8, 30061, 0.0559), (5, 4, 1600, 30000, 7, 36402, 0.0832),
+    (5, 5, 2000, 36000, 5, 42039, 0.0897), (5, 6, 2000, 40000, 8, 48187, 0.0991),
+    (5, 7, 10000, 120000, 6, 171967, 0.7124), (5, 8, 10000, 160000, 7, 207432, 0.8424),
+    (5, 9, 16000, 200000, 5, 250194, 1.5603), (5, 10, 16000, 220000, 6, 278190, 1.8314),
+    (5, 11, 20000, 280000, 4, 357001, 1.9170), (5, 12, 20000, 320000, 4, 396128, 2.1066),
+    # Table 6: normal programs, sparsity 0.95 (rows 1-8)
+    (6, 1, 1000, 5000, 7, 6385, 0.1133), (6, 2, 1000, 10000, 8, 12294, 0.1867),
+    (6, 3, 1600, 24000, 7, 33172, 0.2219), (6, 4, 1600, 30000, 8, 35091, 0.3462),
+    (6, 5, 2000, 36000, 8, 44145, 0.4131), (6, 6, 2000, 40000, 7, 49080, 0.4895),
+    (6, 7, 10000, 120000, 8, 181550, 3.2504), (6, 8, 10000, 160000, 6, 203576, 4.0186),
+]
+
+
+def bench_paper_tables(lp, torch, dev, reps=5):
+    """Programs shaped like each row of the paper's Tables 2, 3, 5 and 6 (table1_program with
+    the row's n, m, k; dense for Tables 3 and 6): the solve on the GPU (CUDA events, median of
+    reps, program resident) and end to end from host arrays (lp_compile + solve + result on the
+    host), beside the paper's own Sparse-matrix time for that row."""
+    stream = torch.cuda.current_stream()
+    rows = []
+    for table, no, n, m, k, n_prime_paper, paper_s in PAPER_ROWS:
+        prog = table1_program(seed=1000 * table + no, n=n, m=m, dense=table in (3, 6), k=k)
+        t0 = time.perf_counter()
+        P = lp.Program.from_program(prog)
+        if k:
+            ng = 1 << P.info["k"]
+            host = np.zeros(lp.words(ng), dtype=np.uint64)
+            ns = P.stable_models(host)
+            out = torch.zeros(lp.words(ng), dtype=torch.int64, device=dev)
+            run = lambda: P.stable_models(out, sync=False)  # noqa: E731
+        else:
+            host = np.zeros(lp.words(n), dtype=np.uint64)
+            iters = P.least_model(host)
+            out = torch.zeros(lp.words(n), dtype=torch.int64, device=dev)
+            run = lambda: P.least_model(out, sync=False)  # noqa: E731
+        e2e_ms = 1e3 * (time.perf_counter() - t0)
+        for _ in range(2):
+            run()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        gpu_ms = statistics.median(ts)
+        row = {"table": table, "no": no, "n": n, "m": m, "n_prime": P.info["n_prime"], "n_prime_paper": n_prime_paper,
+               "nnz": P.info["nnz"], "gpu_ms": round(gpu_ms, 4), "e2e_ms": round(e2e_ms, 2),
+               "paper_sparse_ms": paper_s * 1e3, "paper_over_gpu": round(paper_s * 1e3 / gpu_ms, 1)}
+        if k:
+            row.update({"k": P.info["k"], "n_stable": int(ns)})
+        else:
+            row["iters"] = int(iters)
+        rows.append(row)
+        P.close()
+    return {"workload": "table1_program per row of Tables 2, 3 (rows 1-8), 5, 6 (rows 1-8); seed 1000*table+No.",
+            "paper_hardware": "Intel Core i7-4770 @3.4 GHz, one thread, C++/Eigen 3 sparse (Sec. 4)",
+            "note": "the paper's times are context, not a target: another machine, and its timed region is not stated",
+            "rows": rows}
 
 
 if __name__ == "__main__":

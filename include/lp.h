@@ -227,6 +227,53 @@ lp_status lp_batch_stable_models(lp_batch* batch, uint64_t* stable_mask, int64_t
 /* Release a batch and its device memory (NULL is a no-op). */
 void lp_batch_free(lp_batch* batch);
 
+/*
+ * Schedules and the autotuner. A schedule fixes how the solves of one handle map onto the GPU:
+ * which least-model kernel runs and with how many resident CTAs per SM, and how wide the
+ * stable-model column tiles are (Algorithm 2 processes the 2^k columns of M_0 a tile at a
+ * time). Every schedule computes the same result; only the time differs. A new handle starts
+ * with all fields 0 (LP_FIXPOINT=stream in the environment makes fixpoint_kernel default to 1).
+ */
+typedef struct {
+  int32_t fixpoint_kernel;        /* least model: 0 = one warp per 32-row output word, the word's
+                                     entries in 32-entry chunks; 1 = rows streamed through shared
+                                     memory in bulk-copy stages                                   */
+  int32_t fixpoint_blocks_per_sm; /* least model: resident CTAs per SM; 0 = all that fit        */
+  int32_t stable_tile_words;      /* stable models: 64-bit guess words per tile, 1, 2, 4, 8, 16
+                                     or 32 (capped at the guesses' words); 0 = the widest whose
+                                     two iterate buffers fit 1 GiB                               */
+  int32_t stable_blocks_per_sm;   /* stable models: resident CTAs per SM; 0 = all that fit      */
+} lp_schedule;
+
+typedef struct {
+  lp_schedule schedule;
+  int32_t solve;                  /* LP_TUNE_LEAST or LP_TUNE_STABLE: the solve that was timed   */
+  float ms;                       /* median time of the timed runs; -1 if the schedule could not
+                                     run (e.g. its tiles did not fit in device memory)           */
+} lp_tune_record;
+
+#define LP_TUNE_LEAST 1u   /* time lp_least_model from the fact vector                         */
+#define LP_TUNE_STABLE 2u  /* time lp_stable_models on all 2^k guesses (k > 16: the first 2^16) */
+
+/* Read / replace the handle's schedule. lp_set_schedule rejects values outside the ranges
+ * above with LP_ERR_INVALID and leaves the schedule unchanged. */
+lp_status lp_get_schedule(const lp_program* prog, lp_schedule* out);
+lp_status lp_set_schedule(lp_program* prog, const lp_schedule* schedule);
+
+/*
+ * lp_autotune -- run every candidate schedule of the selected solves (what: LP_TUNE_LEAST
+ * and/or LP_TUNE_STABLE) on this program: one warm-up run, then reps (>= 1) runs timed with
+ * CUDA events on cuda_stream; keep the fastest for each solve in the handle. Every
+ * candidate's result (least model, stable mask) is compared bit for bit with the first
+ * candidate's; a difference returns LP_ERR_CUDA. records (host, nullable): up to
+ * max_records entries, one per candidate in the order run; *n_records (nullable) = number of
+ * candidates. Blocks the calling thread. Candidates: least model, kernel 0 with all / 4 / 2
+ * CTAs per SM and kernel 1 with all / 1; stable models, tile widths 1..32 with all / half the
+ * CTAs per SM.
+ */
+lp_status lp_autotune(lp_program* prog, uint32_t what, int32_t reps, lp_tune_record* records, int32_t max_records,
+                      int32_t* n_records, void* cuda_stream);
+
 /* Statistics and device status of the last solve on this handle; waits for cuda_stream. */
 lp_status lp_last_solve_stats(lp_program* prog, lp_solve_stats* out, void* cuda_stream);
 

@@ -90,7 +90,8 @@ void release(lp_program* p) {
   void* ptrs[] = {p->row_ptr, p->col, p->any_mask, p->perm, p->inv, p->fact_row, p->fact_owner, p->fact_mask,
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
                   p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
-                  p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p};
+                  p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p,
+                  p->tune_out.p, p->tune_in.p};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_ctl) cudaFreeHost(p->h_ctl);
@@ -136,6 +137,10 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   if (flags & ~LP_COMPILE_HOST_ONLY) return fail(LP_ERR_INVALID, "unknown flags");
   auto t0 = std::chrono::steady_clock::now();
   lp_program* p = new (std::nothrow) lp_program();
+  if (p) {
+    const char* env = std::getenv("LP_FIXPOINT");  // A/B switch for the least-model kernel
+    p->sched.fixpoint_kernel = (env && std::strcmp(env, "stream") == 0) ? 1 : 0;
+  }
   if (!p) return fail(LP_ERR_OOM, "host allocation failed");
   std::string err;
   lp_status st = compile_host(n_atoms, n_rules, head, body_off, body_atom, body_neg, p->hm, err);
@@ -275,26 +280,22 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
   a.n_out = n_in;
   a.n_sec_a = hm.n_sec_a;
 
-  // Kernel choice: the one-warp-per-word kernel (default) or the streamed kernel
-  // (LP_FIXPOINT=stream), both exact; the environment variable exists for A/B measurement.
-  static int variant = -1;
-  if (variant < 0) {
-    const char* env = std::getenv("LP_FIXPOINT");
-    variant = (env && std::strcmp(env, "stream") == 0) ? 1 : 0;
-  }
+  // Kernel and residency from the handle's schedule (both kernels are exact).
   cudaError_t le;
-  if (variant == 1) {
-    static int per_sm_s = -1;
-    if (per_sm_s < 0) per_sm_s = fixpoint_stream_blocks_per_sm();
-    if (per_sm_s <= 0) return fail(LP_ERR_CUDA, "streamed fixpoint kernel cannot be resident");
+  if (p->sched.fixpoint_kernel == 1) {
+    static int occ_s = -1;
+    if (occ_s < 0) occ_s = fixpoint_stream_blocks_per_sm();
+    if (occ_s <= 0) return fail(LP_ERR_CUDA, "streamed fixpoint kernel cannot be resident");
+    const int per_sm_s = p->sched.fixpoint_blocks_per_sm > 0 ? std::min(occ_s, p->sched.fixpoint_blocks_per_sm) : occ_s;
     StreamLayout L{p->desc, p->word_hdr, p->and_col, p->groups, hm.n_groups, hm.n_sec_a, hm.groups.data()};
     int grid = std::max(1, std::min(max_coresident(p, per_sm_s), hm.n_groups));
     if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
     le = launch_fixpoint_stream(a, L, grid, s);
   } else {
-    static int per_sm = -1;
-    if (per_sm < 0) per_sm = fixpoint_blocks_per_sm();
-    if (per_sm <= 0) return fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident");
+    static int occ = -1;
+    if (occ < 0) occ = fixpoint_blocks_per_sm();
+    if (occ <= 0) return fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident");
+    const int per_sm = p->sched.fixpoint_blocks_per_sm > 0 ? std::min(occ, p->sched.fixpoint_blocks_per_sm) : occ;
     const int warps_per_block = kFixBlock / 32;
     int grid = std::min(max_coresident(p, per_sm), std::max(1, (a.n_words + warps_per_block - 1) / warps_per_block));
     if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
@@ -352,9 +353,13 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   int64_t budget = 1ll << 30;
   if (const char* env = std::getenv("LP_TILE_BYTES")) budget = std::max<int64_t>(1, std::atoll(env));
   int log2W = 0;
-  while (log2W < 5 && (int64_t(1) << (log2W + 1)) <= n_gwords &&
-         2ll * hm.n_pad * 8 * (int64_t(1) << (log2W + 1)) <= budget)
-    log2W++;
+  if (p->sched.stable_tile_words > 0) {  // the schedule's width, capped at the guesses' words
+    while ((1 << log2W) < p->sched.stable_tile_words && (int64_t(1) << log2W) < n_gwords) log2W++;
+  } else {
+    while (log2W < 5 && (int64_t(1) << (log2W + 1)) <= n_gwords &&
+           2ll * hm.n_pad * 8 * (int64_t(1) << (log2W + 1)) <= budget)
+      log2W++;
+  }
   const int W = 1 << log2W;
   const int64_t n_tiles = (n_gwords + W - 1) / W;
   if ((st = ensure(p, p->tiles, (size_t)2 * hm.n_pad * W * 8)) != LP_OK) return st;
@@ -407,9 +412,10 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   a.n_atom_words = atom_words;
   a.max_iters = max_iters;
   a.ctl = p->ctl;
-  static int per_sm = -1;
-  if (per_sm < 0) per_sm = stable_blocks_per_sm();
-  if (per_sm <= 0) return fail(LP_ERR_CUDA, "stable kernel cannot be resident");
+  static int occ = -1;
+  if (occ < 0) occ = stable_blocks_per_sm();
+  if (occ <= 0) return fail(LP_ERR_CUDA, "stable kernel cannot be resident");
+  const int per_sm = p->sched.stable_blocks_per_sm > 0 ? std::min(occ, p->sched.stable_blocks_per_sm) : occ;
   const int64_t rows_per_block = (int64_t)(kStableBlock / 32) * (32 / W);
   int grid = (int)std::min<int64_t>(max_coresident(p, per_sm), std::max<int64_t>(1, hm.n_pad / rows_per_block));
   if ((st = launch_count_and_check(launch_stable(a, grid, s), "launch stable kernel", p)) != LP_OK) return st;
@@ -421,6 +427,23 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
     if (n_stable_out) *n_stable_out = p->h_ctl->n_stable;
     return st;
   }
+  return LP_OK;
+}
+
+lp_status lp_get_schedule(const lp_program* p, lp_schedule* out) {
+  if (!p || !out) return fail(LP_ERR_INVALID, "NULL argument");
+  *out = p->sched;
+  return LP_OK;
+}
+
+lp_status lp_set_schedule(lp_program* p, const lp_schedule* in) {
+  if (!p || !in) return fail(LP_ERR_INVALID, "NULL argument");
+  const int32_t W = in->stable_tile_words;
+  if (in->fixpoint_kernel < 0 || in->fixpoint_kernel > 1) return fail(LP_ERR_INVALID, "fixpoint_kernel must be 0 or 1");
+  if (in->fixpoint_blocks_per_sm < 0 || in->stable_blocks_per_sm < 0)
+    return fail(LP_ERR_INVALID, "blocks per SM must be >= 0");
+  if (W < 0 || W > 32 || (W & (W - 1)) != 0) return fail(LP_ERR_INVALID, "stable_tile_words must be 0 or 1, 2, 4, 8, 16, 32");
+  p->sched = *in;
   return LP_OK;
 }
 

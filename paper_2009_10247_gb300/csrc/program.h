@@ -44,6 +44,8 @@ struct lp_program {
   DevBuf stage_in, stage_out, stage_out2;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
+  lp_schedule sched{};         // schedule of the solves (lp_set_schedule / lp_autotune)
+  DevBuf tune_out, tune_in;    // autotuner result and guess buffers
   int64_t last_launches = 0;
   int64_t tile_words = 0;
   int64_t device_bytes = 0;

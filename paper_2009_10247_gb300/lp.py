@@ -39,7 +39,20 @@ class _Stats(ctypes.Structure):
 EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models", "lp_last_solve_stats",
            "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static",
            "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward", "lp_compile_batch", "lp_batch_info",
-           "lp_batch_program_info", "lp_batch_stable_models", "lp_batch_free"]
+           "lp_batch_program_info", "lp_batch_stable_models", "lp_batch_free", "lp_get_schedule", "lp_set_schedule",
+           "lp_autotune"]
+
+LP_TUNE_LEAST = 1
+LP_TUNE_STABLE = 2
+SCHEDULE_FIELDS = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "stable_tile_words", "stable_blocks_per_sm")
+
+
+class _Schedule(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in SCHEDULE_FIELDS]
+
+
+class _TuneRecord(ctypes.Structure):
+    _fields_ = [("schedule", _Schedule), ("solve", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 _lib = None
 
@@ -79,6 +92,11 @@ def load(build_if_missing: bool = False):
         getattr(L, name).restype = ctypes.c_int
     L.lp_batch_free.argtypes = [P]
     L.lp_batch_free.restype = None
+    L.lp_get_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
+    L.lp_set_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
+    L.lp_autotune.argtypes = [P, u32, i32, ctypes.POINTER(_TuneRecord), i32, ctypes.POINTER(i32), P]
+    for name in ("lp_get_schedule", "lp_set_schedule", "lp_autotune"):
+        getattr(L, name).restype = ctypes.c_int
     L.lp_least_model_static.argtypes = [i32, P, P, P, P, P, i32, ctypes.POINTER(i32), P]
     L.lp_least_model_static.restype = ctypes.c_int
     L.lp_free.argtypes = [P]
@@ -210,6 +228,33 @@ class Program:
         _check(load().lp_relaxed_backward(self._h, _ptr(weights), _ptr(gT), int(batch), int(steps), float(tau),
                                           int(ckpt_every), _ptr(ckpt), _ptr(scratch), _ptr(dweights), _ptr(dv0),
                                           _stream(stream)))
+
+    @property
+    def schedule(self):
+        """The handle's schedule (lp_get_schedule) as a dict."""
+        sc = _Schedule()
+        _check(load().lp_get_schedule(self._h, ctypes.byref(sc)))
+        return {f: getattr(sc, f) for f in SCHEDULE_FIELDS}
+
+    def set_schedule(self, **fields):
+        """Change some fields of the schedule (lp_set_schedule)."""
+        cur = self.schedule
+        cur.update(fields)
+        sc = _Schedule(**cur)
+        _check(load().lp_set_schedule(self._h, ctypes.byref(sc)))
+
+    def autotune(self, what=LP_TUNE_LEAST | LP_TUNE_STABLE, reps=3, stream=None):
+        """Time the candidate schedules (lp_autotune); returns [{schedule..., "solve", "ms"}] in run order."""
+        recs = (_TuneRecord * 64)()
+        n = ctypes.c_int32()
+        _check(load().lp_autotune(self._h, int(what), int(reps), recs, 64, ctypes.byref(n), _stream(stream)))
+        out = []
+        for r in recs[:min(n.value, 64)]:
+            d = {f: getattr(r.schedule, f) for f in SCHEDULE_FIELDS}
+            d["solve"] = "least" if r.solve == LP_TUNE_LEAST else "stable"
+            d["ms"] = r.ms
+            out.append(d)
+        return out
 
     def last_stats(self, stream=None):
         s = _Stats()

@@ -114,3 +114,37 @@ def test_host_only_handle_refuses_solves(lib):
         with pytest.raises(lp.LPError) as e:
             P.least_model(out)
         assert e.value.status == 1
+
+
+def test_schedule_get_set_validates(lib):
+    with lp.Program.from_program(small_definite(1), host_only=True) as P:
+        assert P.schedule == {"fixpoint_kernel": 0, "fixpoint_blocks_per_sm": 0, "stable_tile_words": 0,
+                              "stable_blocks_per_sm": 0}
+        P.set_schedule(fixpoint_kernel=1, fixpoint_blocks_per_sm=2, stable_tile_words=8, stable_blocks_per_sm=1)
+        assert P.schedule["stable_tile_words"] == 8 and P.schedule["fixpoint_kernel"] == 1
+        for bad in ({"fixpoint_kernel": 2}, {"stable_tile_words": 3}, {"stable_tile_words": 64},
+                    {"fixpoint_blocks_per_sm": -1}, {"stable_blocks_per_sm": -2}):
+            with pytest.raises(lp.LPError):
+                P.set_schedule(**bad)
+        assert P.schedule["stable_tile_words"] == 8  # unchanged by the rejected calls
+        with pytest.raises(lp.LPError):
+            P.autotune()  # a host-only handle cannot run solves
+
+
+def test_batch_entry_points_validate_without_gpu(lib):
+    out = ctypes.c_void_p()
+    one = np.array([2], np.int32)
+    off = np.array([0, 1], np.int64)
+    head = np.array([0], np.int32)
+    boff = np.array([0, 0], np.int64)
+    atom = np.zeros(1, np.int32)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    assert lib.lp_compile_batch(1, ptr(one), ptr(off), ptr(head), ptr(boff), ptr(atom), None, 1, None,
+                                ctypes.byref(out)) == 1  # flags must be 0
+    bad_off = np.array([1, 1], np.int64)
+    assert lib.lp_compile_batch(1, ptr(one), ptr(bad_off), ptr(head), ptr(boff), ptr(atom), None, 0, None,
+                                ctypes.byref(out)) == 1  # rule_off[0] must be 0
+    assert lib.lp_compile_batch(1, ptr(one), ptr(off), ptr(head), ptr(boff), ptr(atom), None, 0, None, None) == 1
+    assert lib.lp_batch_info(None, None, None, None, None, None) == 1
+    assert lib.lp_batch_stable_models(None, None, None, None, 10, None) == 1
+    lib.lp_batch_free(None)

@@ -1,0 +1,45 @@
+"""GPU parity on programs shaped like the paper's experiments (Tables 2, 3, 5, 6): least models
+and stable-model bits against the oracle, on small rows in every variant (sparse, dense,
+normal) and on the largest rows the benchmark times."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2009_10247_gb300 as lp
+from workloads import table1_program
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_util import gpu_least_model, gpu_stable  # noqa: E402
+
+
+def _least(prog):
+    want, want_it = oracle.least_model(prog)
+    with lp.Program.from_program(prog) as P:
+        got, it = gpu_least_model(P)
+    assert it == want_it and np.array_equal(got, want)
+
+
+def _stable(prog):
+    st4, _, _ = oracle.stable_models_alg23(prog)
+    with lp.Program.from_program(prog) as P:
+        st, _, ns = gpu_stable(P)
+    assert np.array_equal(st, st4) and ns == int(st4.sum())
+
+
+@pytest.mark.parametrize("dense", [False, True])
+@pytest.mark.parametrize("seed", range(4))
+def test_small_rows(dense, seed):
+    _least(table1_program(seed, 1000, 5000, dense=dense))
+    _stable(table1_program(100 + seed, 1000, 5000, dense=dense, k=4 + seed))
+
+
+def test_largest_sparse_rows():
+    _least(table1_program(2012, 20000, 320000))          # Table 2 row 12
+    _stable(table1_program(5012, 20000, 320000, k=4))    # Table 5 row 12
+
+
+def test_largest_dense_rows_in_the_benchmark():
+    _least(table1_program(3008, 10000, 160000, dense=True))          # Table 3 row 8 (73M entries)
+    _stable(table1_program(6006, 2000, 40000, dense=True, k=7))      # Table 6 row 6 (oracle cost)

@@ -13,5 +13,7 @@ from .programs import (  # noqa: F401
     transitive_closure,
     normal_program,
     program_batch,
+    table1_program,
+    TABLE1_LENGTH_SHARE,
     random_fact_subsets,
 )

@@ -268,6 +268,74 @@ def program_batch(seed: int = 1, count: int = 1000, n_lo: int = 100, n_hi: int =
     return out
 
 
+# Share of the non-fact rules by body length 1..8 (the paper's Table 1).
+TABLE1_LENGTH_SHARE = (0.04, 0.04, 0.10, 0.40, 0.35, 0.04, 0.02, 0.01)
+
+
+def table1_program(seed: int, n: int, m: int, dense: bool = False, k: int = 0) -> Program:
+    """Random program shaped like the paper's experiments (Sec. 4, Table 1): m rules over n
+    atoms. Facts: a seeded share u*n of the atoms, u ~ U(0.1, 1/3) (the table allows fewer than
+    n/3); each fact atom heads only its fact. Other heads are uniform over the non-fact atoms,
+    body atoms uniform over all atoms, distinct within a body. Body lengths follow Table 1; with
+    dense=True the lengths 1 and 2 keep their 4 % shares and every other rule takes each atom
+    with probability 0.05 (a body of about 5 % of n), the lower-sparsity programs of Tables 3
+    and 6. k > 0 negates one body occurrence of each of k distinct non-fact atoms (Tables 5, 6)."""
+    rng = np.random.default_rng(seed)
+    n_f = int(round(n * rng.uniform(0.1, 1.0 / 3.0)))
+    perm = rng.permutation(n)
+    facts, nonfacts = perm[:n_f], perm[n_f:]
+    nr = m - n_f
+    if dense:
+        u = rng.random(nr)
+        kind = np.where(u < 0.04, 1, np.where(u < 0.08, 2, 0))  # 0: about 5 % of n
+        short = np.nonzero(kind > 0)[0]
+        bodies = [None] * nr
+        for r in short:
+            bodies[r] = rng.choice(n, size=int(kind[r]), replace=False)
+        wide = np.nonzero(kind == 0)[0]
+        chunk = max(1, (64 << 20) // max(n, 1))
+        for c0 in range(0, len(wide), chunk):
+            rows = wide[c0:c0 + chunk]
+            sel = rng.random((len(rows), n), dtype=np.float32) < 0.05
+            sel[np.arange(len(rows)), rng.integers(0, n, len(rows))] = True  # never empty
+            rr, cc = np.nonzero(sel)
+            splits = np.searchsorted(rr, np.arange(1, len(rows)))
+            for r, body in zip(rows, np.split(cc, splits)):
+                bodies[r] = body
+        lens = np.array([len(x) for x in bodies], dtype=np.int64)
+        atoms = np.concatenate(bodies) if nr else np.zeros(0, np.int64)
+        off = np.zeros(nr + 1, dtype=np.int64)
+        np.cumsum(lens, out=off[1:])
+    else:
+        lens = np.minimum(rng.choice(np.arange(1, 9), size=nr, p=np.array(TABLE1_LENGTH_SHARE)), n).astype(np.int64)
+        off = np.zeros(nr + 1, dtype=np.int64)
+        np.cumsum(lens, out=off[1:])
+        atoms = rng.integers(0, n, int(off[-1]))
+        rule_of = np.repeat(np.arange(nr), lens)
+        for _ in range(64):  # redraw repeated atoms of a body
+            key = rule_of * n + atoms
+            order = np.argsort(key, kind="stable")
+            dup = np.zeros(len(key), dtype=bool)
+            dup[order[1:]] = key[order[1:]] == key[order[:-1]]
+            if not dup.any():
+                break
+            atoms[dup] = rng.integers(0, n, int(dup.sum()))
+    heads = np.concatenate([facts, nonfacts[rng.integers(0, len(nonfacts), nr)]])
+    all_lens = np.concatenate([np.zeros(n_f, np.int64), lens])
+    negs = None
+    if k > 0:
+        negs = np.zeros(len(atoms), dtype=np.uint8)
+        q = rng.choice(nonfacts, size=k, replace=False)
+        for a in q:
+            pos = np.nonzero(atoms == a)[0]
+            if len(pos) == 0:  # the atom occurs in no body: put it into a random body
+                pos = np.array([off[int(rng.integers(nr))]])
+                atoms[pos[0]] = a
+            negs[pos[int(rng.integers(len(pos)))]] = 1
+    h, ln, a, ng = _permute_rules(rng, heads, all_lens, atoms, negs)
+    return _pack(n, h, ln, a, ng, name="table1_dense" if dense else "table1", seed=seed, k=k)
+
+
 def tiny_random(seed: int, n_atoms: int = 8, n_rules: int = 12, max_body: int = 3, p_fact: float = 0.2,
                 p_neg: float = 0.0) -> Program:
     """Tiny random program for brute-force checks: heads and body atoms uniform (so facts may

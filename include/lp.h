@@ -274,6 +274,24 @@ lp_status lp_set_schedule(lp_program* prog, const lp_schedule* schedule);
 lp_status lp_autotune(lp_program* prog, uint32_t what, int32_t reps, lp_tune_record* records, int32_t max_records,
                       int32_t* n_records, void* cuda_stream);
 
+/*
+ * lp_stable_search -- stable models by fixed-budget guess sampling and local search, for k too
+ * large to enumerate 2^k columns (the paper's future work, Sec. 5). A population of
+ * `population` (1..2048) guesses -- k-bit words as in lp_stable_models -- is drawn from a
+ * counter-based generator (SplitMix64 of seed, round, column). Each of `rounds` rounds runs
+ * Algorithm 2 on the population (one column tile) and Algorithm 3 on every column. A stable
+ * column's guess is recorded, and the column restarts from a fresh random guess. A failed
+ * column moves to the guess its fixpoint implies (bit j = 1 iff the j-th guessed atom is false
+ * there); if that is the guess it held one round earlier, the bits that step would flip are
+ * drawn at random instead.
+ * Every reported guess is stable (Algorithm 3 accepted it); the search is not complete.
+ * found (device or host, max_found words, nullable if max_found = 0): the distinct stable
+ * guesses found, ascending; *n_found (host, required): how many there are (may exceed
+ * max_found). Waits for cuda_stream. k <= 64. The handle's schedule is left unchanged.
+ */
+lp_status lp_stable_search(lp_program* prog, int32_t population, int32_t rounds, uint64_t seed, uint64_t* found,
+                           int64_t max_found, int64_t* n_found, void* cuda_stream);
+
 /* Statistics and device status of the last solve on this handle; waits for cuda_stream. */
 lp_status lp_last_solve_stats(lp_program* prog, lp_solve_stats* out, void* cuda_stream);
 

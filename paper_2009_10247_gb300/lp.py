@@ -40,7 +40,7 @@ EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models"
            "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static",
            "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward", "lp_compile_batch", "lp_batch_info",
            "lp_batch_program_info", "lp_batch_stable_models", "lp_batch_free", "lp_get_schedule", "lp_set_schedule",
-           "lp_autotune"]
+           "lp_autotune", "lp_stable_search"]
 
 LP_TUNE_LEAST = 1
 LP_TUNE_STABLE = 2
@@ -95,7 +95,8 @@ def load(build_if_missing: bool = False):
     L.lp_get_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
     L.lp_set_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
     L.lp_autotune.argtypes = [P, u32, i32, ctypes.POINTER(_TuneRecord), i32, ctypes.POINTER(i32), P]
-    for name in ("lp_get_schedule", "lp_set_schedule", "lp_autotune"):
+    L.lp_stable_search.argtypes = [P, i32, i32, ctypes.c_uint64, P, i64, ctypes.POINTER(i64), P]
+    for name in ("lp_get_schedule", "lp_set_schedule", "lp_autotune", "lp_stable_search"):
         getattr(L, name).restype = ctypes.c_int
     L.lp_least_model_static.argtypes = [i32, P, P, P, P, P, i32, ctypes.POINTER(i32), P]
     L.lp_least_model_static.restype = ctypes.c_int
@@ -255,6 +256,15 @@ class Program:
             d["ms"] = r.ms
             out.append(d)
         return out
+
+    def stable_search(self, population=1024, rounds=16, seed=1, max_found=1 << 16, stream=None):
+        """Sampled guesses + local search (lp_stable_search); returns the distinct stable guesses
+        found (uint64 numpy array, ascending) and their total count."""
+        out = np.zeros(max(int(max_found), 1), dtype=np.uint64)
+        n = ctypes.c_int64()
+        _check(load().lp_stable_search(self._h, int(population), int(rounds), ctypes.c_uint64(seed), _ptr(out),
+                                       int(max_found), ctypes.byref(n), _stream(stream)))
+        return out[:min(n.value, int(max_found))], n.value
 
     def last_stats(self, stream=None):
         s = _Stats()

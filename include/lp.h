@@ -239,6 +239,8 @@ typedef struct {
                                      entries in 32-entry chunks; 1 = rows streamed through shared
                                      memory in bulk-copy stages                                   */
   int32_t fixpoint_blocks_per_sm; /* least model: resident CTAs per SM; 0 = all that fit        */
+  int32_t fixpoint_row_split;     /* least model, kernel 0: warps sharing one 32-row output word
+                                     (1, 2, 4 or 8; 0 = 1): more for programs with long rows    */
   int32_t stable_tile_words;      /* stable models: 64-bit guess words per tile, 1, 2, 4, 8, 16
                                      or 32 (capped at the guesses' words); 0 = the widest whose
                                      two iterate buffers fit 1 GiB                               */
@@ -268,8 +270,8 @@ lp_status lp_set_schedule(lp_program* prog, const lp_schedule* schedule);
  * candidate's; a difference returns LP_ERR_CUDA. records (host, nullable): up to
  * max_records entries, one per candidate in the order run; *n_records (nullable) = number of
  * candidates. Blocks the calling thread. Candidates: least model, kernel 0 with all / 4 / 2
- * CTAs per SM and kernel 1 with all / 1; stable models, tile widths 1..32 with all / half the
- * CTAs per SM.
+ * CTAs per SM, kernel 0 with row splits 2, 4, 8, and kernel 1 with all / 1 CTAs per SM; stable
+ * models, tile widths 1..32 with all / half the CTAs per SM.
  */
 lp_status lp_autotune(lp_program* prog, uint32_t what, int32_t reps, lp_tune_record* records, int32_t max_records,
                       int32_t* n_records, void* cuda_stream);
@@ -291,6 +293,19 @@ lp_status lp_autotune(lp_program* prog, uint32_t what, int32_t reps, lp_tune_rec
  */
 lp_status lp_stable_search(lp_program* prog, int32_t population, int32_t rounds, uint64_t seed, uint64_t* found,
                            int64_t max_found, int64_t* n_found, void* cuda_stream);
+
+/*
+ * lp_check_grid_barrier -- diagnostics, no counterpart in the paper: runs the bounded grid
+ * barrier that every persistent kernel of liblp meets once per theta iteration, alone, with
+ * `blocks` co-resident CTAs of which the first `absent` never arrive (like a block or rank that
+ * has left). The others wait at most limit_us microseconds (1..2e6), then record
+ * LP_ERR_TIMEOUT, raise the abort flag and return, so the context stays usable. *status_out
+ * (host) receives LP_OK if the barrier completed, else the device status (LP_ERR_TIMEOUT);
+ * *ms_out (host, nullable) the kernel's duration. Waits for cuda_stream. LP_ERR_INVALID if
+ * `blocks` cannot be co-resident.
+ */
+lp_status lp_check_grid_barrier(int32_t blocks, int32_t absent, int32_t limit_us, int32_t* status_out, float* ms_out,
+                                void* cuda_stream);
 
 /* Statistics and device status of the last solve on this handle; waits for cuda_stream. */
 lp_status lp_last_solve_stats(lp_program* prog, lp_solve_stats* out, void* cuda_stream);

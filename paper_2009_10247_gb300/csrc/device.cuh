@@ -58,8 +58,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // launch from 1; every block must call it the same number of times. Release: fence before the
 // arrival; acquire: acquire loads while waiting and a fence after, then a CTA barrier, so
 // ordinary loads after it see every write made before it by any block. Returns false if the
-// grid is aborting (this or another block gave up waiting); callers must then return.
-__device__ __forceinline__ bool grid_barrier(DeviceCtl* ctl, unsigned long long round, int status_on_timeout) {
+// grid is aborting (this or another block gave up waiting); callers must then return. A wait
+// gives up after limit_ns (2 s unless a caller passes less).
+__device__ __forceinline__ bool grid_barrier(DeviceCtl* ctl, unsigned long long round, int status_on_timeout,
+                                             unsigned long long limit_ns = kWaitLimitNs) {
   __shared__ unsigned s_abort;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -74,7 +76,7 @@ __device__ __forceinline__ bool grid_barrier(DeviceCtl* ctl, unsigned long long 
       if (++polls == 64) t0 = global_ns();
       if (polls > 64) {
         __nanosleep(100);
-        if ((polls & 255) == 0 && global_ns() - t0 > kWaitLimitNs) {
+        if ((polls & 255) == 0 && global_ns() - t0 > limit_ns) {
           atomicExch(&ctl->abort, 1u);
           atomicCAS(&ctl->status, 0, status_on_timeout);
           atomicExch(&ctl->timeout_site, round);

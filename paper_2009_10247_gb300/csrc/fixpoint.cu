@@ -14,7 +14,9 @@
 // contiguous column range 32 entries at a time with coalesced loads, gathers one bit per
 // entry from the bit-packed vector (L1/L2 resident), and a ballot turns the 32 bits into a
 // mask; every lane then pops the bits of its own row's sub-range. Row lengths never cause
-// divergence; the cost is one gather per stored entry.
+// divergence; the cost is one gather per stored entry. With a row split G > 1 (programs whose
+// words hold thousands of entries), G warps of a block share a word: each counts a contiguous
+// share of its chunks and the partial counts meet in shared memory.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -54,10 +56,46 @@ __device__ __forceinline__ uint32_t theta_word(const int32_t* __restrict__ row_p
   return __ballot_sync(FULL, cnt >= thr);
 }
 
+// Row split (G > 1 warps per word, for long rows): part `part` of G counts the true entries of
+// every row of word w within its share of the word's 32-entry chunks; the G partial counts are
+// summed in shared memory before the threshold. Returns this lane's partial count; *len_out is
+// the lane's row length.
+__device__ __forceinline__ int theta_word_part(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                               const uint32_t* src, int w, int lane, int part, int G,
+                                               int* len_out) {
+  const int r = (w << 5) + lane;
+  const int beg = __ldg(row_ptr + r);
+  int end = __shfl_down_sync(FULL, beg, 1);
+  if (lane == 31) end = __ldg(row_ptr + r + 1);
+  const int base = __shfl_sync(FULL, beg, 0);
+  const int stop = __shfl_sync(FULL, end, 31);
+  const int n_chunks = (stop - base + 31) >> 5;
+  const int c_lo = base + 32 * (n_chunks * part / G), c_hi = min(stop, base + 32 * (n_chunks * (part + 1) / G));
+  int cnt = 0;
+  for (int c = c_lo; c < c_hi; c += 32) {
+    const int e = c + lane;
+    uint32_t bit = 0;
+    if (e < c_hi) {
+      const int j = __ldg(col + e);
+      bit = (src[j >> 5] >> (j & 31)) & 1u;
+    }
+    const uint32_t m = __ballot_sync(FULL, bit);
+    const int lo = max(beg - c, 0), hi = min(end - c, 32);
+    if (hi > lo) {
+      const uint32_t sel = (hi - lo == 32) ? FULL : (((1u << (hi - lo)) - 1u) << lo);
+      cnt += __popc(m & sel);
+    }
+  }
+  *len_out = end - beg;
+  return cnt;
+}
+
 __device__ __forceinline__ uint32_t get_bit(const uint32_t* v, int i) { return (v[i >> 5] >> (i & 31)) & 1u; }
 
+template <int G>
 __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
   __shared__ int s_flag;
+  __shared__ int s_cnt[G > 1 ? kFixBlock : 1];
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -101,11 +139,36 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
     const uint32_t* src = (it & 1) ? a.x1 : a.x0;
     uint32_t* dst = (it & 1) ? a.x0 : a.x1;
     bool changed = false;
-    for (int w = gwarp; w < a.n_words; w += nwarps) {
-      const uint32_t u = theta_word(a.row_ptr, a.col, a.any_mask, src, w, lane);
-      if (lane == 0) {
-        dst[w] = u;
-        changed |= (u != src[w]);
+    if (G == 1) {
+      for (int w = gwarp; w < a.n_words; w += nwarps) {
+        const uint32_t u = theta_word(a.row_ptr, a.col, a.any_mask, src, w, lane);
+        if (lane == 0) {
+          dst[w] = u;
+          changed |= (u != src[w]);
+        }
+      }
+    } else {
+      // kFixBlock / 32 / G words per block and round; the loop bound is uniform in the block
+      const int warp = threadIdx.x >> 5, slot = warp / G, part = warp % G;
+      const int per_block = (kFixBlock / 32) / G;
+      for (int wb = blockIdx.x * per_block; wb < a.n_words; wb += gridDim.x * per_block) {
+        const int w = wb + slot;
+        int len = 0, cnt = 0;
+        if (w < a.n_words) cnt = theta_word_part(a.row_ptr, a.col, src, w, lane, part, G, &len);
+        s_cnt[threadIdx.x] = cnt;
+        __syncthreads();
+        if (part == 0 && w < a.n_words) {
+          int total = 0;
+#pragma unroll
+          for (int q = 0; q < G; q++) total += s_cnt[threadIdx.x + 32 * q];
+          const bool any = (__ldg(a.any_mask + w) >> lane) & 1u;
+          const uint32_t u = __ballot_sync(FULL, total >= (any ? 1 : max(len, 1)));
+          if (lane == 0) {
+            dst[w] = u;
+            changed |= (u != src[w]);
+          }
+        }
+        __syncthreads();
       }
     }
     const int any_changed = __syncthreads_or(changed);
@@ -141,15 +204,25 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
   }
 }
 
-cudaError_t launch_fixpoint(const FixArgs& a, int grid, cudaStream_t s) {
-  FixArgs copy = a;
-  void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)fixpoint_kernel, dim3(grid), dim3(kFixBlock), params, 0, s);
+static const void* fixpoint_entry(int G) {
+  switch (G) {
+    case 2: return (const void*)fixpoint_kernel<2>;
+    case 4: return (const void*)fixpoint_kernel<4>;
+    case 8: return (const void*)fixpoint_kernel<8>;
+    default: return (const void*)fixpoint_kernel<1>;
+  }
 }
 
-int fixpoint_blocks_per_sm() {
+cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, cudaStream_t s) {
+  FixArgs copy = a;
+  void* params[] = {&copy};
+  return cudaLaunchCooperativeKernel(fixpoint_entry(row_split), dim3(grid), dim3(kFixBlock), params, 0, s);
+}
+
+int fixpoint_blocks_per_sm(int row_split) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fixpoint_kernel, kFixBlock, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fixpoint_entry(row_split), kFixBlock, 0) != cudaSuccess)
+    return 0;
   return nb;
 }
 

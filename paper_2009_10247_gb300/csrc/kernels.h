@@ -37,8 +37,9 @@ struct FixArgs {
 };
 
 constexpr int kFixBlock = 256;
-cudaError_t launch_fixpoint(const FixArgs& a, int grid, cudaStream_t s);
-int fixpoint_blocks_per_sm();
+// row_split: warps per 32-row output word (1, 2, 4 or 8)
+cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, cudaStream_t s);
+int fixpoint_blocks_per_sm(int row_split);
 
 // The same loop with the matrix streamed through shared memory (fixpoint_stream.cu).
 struct StreamLayout {

@@ -78,12 +78,14 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     const size_t out_bytes = (size_t)((hm.n + 63) / 64) * 8;
     if ((st = ensure(p, p->tune_out, std::max<size_t>(out_bytes, 8))) != LP_OK) return st;
     uint64_t* out = (uint64_t*)p->tune_out.p;
-    const int occ0 = fixpoint_blocks_per_sm(), occ1 = fixpoint_stream_blocks_per_sm();
+    const int occ0 = fixpoint_blocks_per_sm(1), occ1 = fixpoint_stream_blocks_per_sm();
+    const int32_t W0 = base.stable_tile_words, B0 = base.stable_blocks_per_sm;
     std::vector<lp_schedule> cands;
     for (int b : {0, 4, 2})
-      if (b == 0 || b < occ0) cands.push_back({0, b, base.stable_tile_words, base.stable_blocks_per_sm});
+      if (b == 0 || b < occ0) cands.push_back({0, b, 1, W0, B0});
+    for (int G : {2, 4, 8}) cands.push_back({0, 0, G, W0, B0});
     for (int b : {0, 1})
-      if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back({1, b, base.stable_tile_words, base.stable_blocks_per_sm});
+      if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back({1, b, 1, W0, B0});
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
     for (const lp_schedule& c : cands) {
@@ -133,7 +135,9 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     for (int W = 1; W <= 32; W *= 2) {
       if (W > 1 && W / 2 >= n_gwords) break;  // wider tiles than the guesses only repeat
       for (int b : {0, occ / 2})
-        if (b == 0 || (b > 0 && b < occ)) cands.push_back({best_least.fixpoint_kernel, best_least.fixpoint_blocks_per_sm, W, b});
+        if (b == 0 || (b > 0 && b < occ))
+          cands.push_back({best_least.fixpoint_kernel, best_least.fixpoint_blocks_per_sm, best_least.fixpoint_row_split,
+                           W, b});
     }
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
@@ -169,6 +173,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
   if (what & LP_TUNE_LEAST) {
     chosen.fixpoint_kernel = best_least.fixpoint_kernel;
     chosen.fixpoint_blocks_per_sm = best_least.fixpoint_blocks_per_sm;
+    chosen.fixpoint_row_split = best_least.fixpoint_row_split;
   }
   if (what & LP_TUNE_STABLE) {
     chosen.stable_tile_words = best_stable.stable_tile_words;

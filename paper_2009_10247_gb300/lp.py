@@ -40,11 +40,12 @@ EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models"
            "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static",
            "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward", "lp_compile_batch", "lp_batch_info",
            "lp_batch_program_info", "lp_batch_stable_models", "lp_batch_free", "lp_get_schedule", "lp_set_schedule",
-           "lp_autotune", "lp_stable_search"]
+           "lp_autotune", "lp_stable_search", "lp_check_grid_barrier"]
 
 LP_TUNE_LEAST = 1
 LP_TUNE_STABLE = 2
-SCHEDULE_FIELDS = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "stable_tile_words", "stable_blocks_per_sm")
+SCHEDULE_FIELDS = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "fixpoint_row_split", "stable_tile_words",
+                   "stable_blocks_per_sm")
 
 
 class _Schedule(ctypes.Structure):
@@ -96,7 +97,8 @@ def load(build_if_missing: bool = False):
     L.lp_set_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
     L.lp_autotune.argtypes = [P, u32, i32, ctypes.POINTER(_TuneRecord), i32, ctypes.POINTER(i32), P]
     L.lp_stable_search.argtypes = [P, i32, i32, ctypes.c_uint64, P, i64, ctypes.POINTER(i64), P]
-    for name in ("lp_get_schedule", "lp_set_schedule", "lp_autotune", "lp_stable_search"):
+    L.lp_check_grid_barrier.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), P]
+    for name in ("lp_get_schedule", "lp_set_schedule", "lp_autotune", "lp_stable_search", "lp_check_grid_barrier"):
         getattr(L, name).restype = ctypes.c_int
     L.lp_least_model_static.argtypes = [i32, P, P, P, P, P, i32, ctypes.POINTER(i32), P]
     L.lp_least_model_static.restype = ctypes.c_int
@@ -151,6 +153,14 @@ def least_model_static(n_rows, row_ptr, col, threshold, v0, out, max_iters=1 << 
     _check(load().lp_least_model_static(int(n_rows), _ptr(row_ptr), _ptr(col), _ptr(threshold), _ptr(v0), _ptr(out),
                                         int(max_iters), ctypes.byref(it) if sync else None, _stream(stream)))
     return it.value if sync else None
+
+
+def check_grid_barrier(blocks, absent, limit_us, stream=None):
+    """lp_check_grid_barrier: (status, ms) of one bounded grid barrier with `absent` blocks missing."""
+    st, ms = ctypes.c_int32(), ctypes.c_float()
+    _check(load().lp_check_grid_barrier(int(blocks), int(absent), int(limit_us), ctypes.byref(st), ctypes.byref(ms),
+                                        _stream(stream)))
+    return st.value, ms.value
 
 
 def launch_count() -> int:

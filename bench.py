@@ -353,7 +353,7 @@ def bench_stable(lp, torch, dev, flush, steps=5):
            "ms_per_step": ms, "workload": WORKLOAD_STABLE, "n_prime": info["n_prime"], "nnz": info["nnz"], "k": k,
            "n_stable": ns, "tiles": st["tiles"], "tile_words": W, "tile_iters_max": st["max_tile_iters"],
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": None, "peak_kind": peak_kind, "kernel": "stable_kernel",
+                        "traffic": measured_traffic("stable_kernel"), "peak_kind": peak_kind, "kernel": "stable_kernel",
                         "note": "tiles are sized to stay L2 resident, so this fraction can exceed 1"}}
     # the baseline: one launch per guess (lp_stable_models on a one-guess list), sampled
     n_one = 128
@@ -486,8 +486,8 @@ def bench_relaxed(lp, torch, dev, flush, steps=3):
            "backward_ms": b_ms, "workload": WORKLOAD_RELAXED, "n_prime": n_prime, "nnz": nnz, "batch": bsz,
            "steps": T, "tau": tau, "ckpt_every": ck,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": None, "peak_kind": peak_kind, "kernel": "rx_forward_kernel (whole forward)",
-                        "bytes_per_step": step_bytes}}
+                        "traffic": measured_traffic("rx_forward_kernel"), "peak_kind": peak_kind,
+                        "kernel": "rx_forward_kernel (whole forward; traffic per step)", "bytes_per_step": step_bytes}}
     P.close()
     return out
 

@@ -13,10 +13,12 @@
 // Work mapping: a warp owns one 32-bit output word = 32 consecutive rows. It walks the rows'
 // contiguous column range 32 entries at a time with coalesced loads, gathers one bit per
 // entry from the bit-packed vector (L1/L2 resident), and a ballot turns the 32 bits into a
-// mask; every lane then pops the bits of its own row's sub-range. Row lengths never cause
-// divergence; the cost is one gather per stored entry. With a row split G > 1 (programs whose
-// words hold thousands of entries), G warps of a block share a word: each counts a contiguous
-// share of its chunks and the partial counts meet in shared memory.
+// mask; each lane then counts its own row's bits. Row lengths never cause divergence; the
+// cost is one gather per stored entry. A warp takes two words per step (their loads overlap)
+// and counts a word's rows from a prefix sum of its chunk ballots (prefix_count). With a row
+// split G > 1 (programs whose words hold thousands of entries), G warps of a block share a
+// word: each counts a contiguous share of its chunks and the partial counts meet in shared
+// memory.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -24,7 +26,39 @@
 
 namespace lp {
 
+// True entries of this lane's row [beg, end) among the word's entries [c_lo, c_hi), walked 32
+// at a time (XN chunks per step: all their column loads, then all their gathers, then the
+// ballots, which shortens the dependent-load chain of words with many chunks).
+template <int XN>
+__device__ __forceinline__ int count_chunks(const int32_t* __restrict__ col, const uint32_t* src, int beg, int end,
+                                            int c_lo, int c_hi, int lane) {
+  int cnt = 0;
+  for (int c0 = c_lo; c0 < c_hi; c0 += 32 * XN) {
+    int j[XN];
+#pragma unroll
+    for (int q = 0; q < XN; q++) {
+      const int e = c0 + 32 * q + lane;
+      j[q] = e < c_hi ? __ldg(col + e) : -1;
+    }
+    uint32_t bit[XN];
+#pragma unroll
+    for (int q = 0; q < XN; q++) bit[q] = j[q] >= 0 ? (src[j[q] >> 5] >> (j[q] & 31)) & 1u : 0u;
+#pragma unroll
+    for (int q = 0; q < XN; q++) {
+      const int c = c0 + 32 * q;
+      const uint32_t m = __ballot_sync(FULL, bit[q]);
+      const int lo = max(beg - c, 0), hi = min(end - c, 32);
+      if (hi > lo) {
+        const uint32_t sel = (hi - lo == 32) ? FULL : (((1u << (hi - lo)) - 1u) << lo);
+        cnt += __popc(m & sel);
+      }
+    }
+  }
+  return cnt;
+}
+
 // u bits of the 32 rows of word w, given the bit vector src.
+template <int XN>
 __device__ __forceinline__ uint32_t theta_word(const int32_t* __restrict__ row_ptr,
                                                const int32_t* __restrict__ col,
                                                const uint32_t* __restrict__ any_mask,
@@ -35,21 +69,7 @@ __device__ __forceinline__ uint32_t theta_word(const int32_t* __restrict__ row_p
   if (lane == 31) end = __ldg(row_ptr + r + 1);
   const int base = __shfl_sync(FULL, beg, 0);
   const int stop = __shfl_sync(FULL, end, 31);
-  int cnt = 0;
-  for (int c = base; c < stop; c += 32) {
-    const int e = c + lane;
-    uint32_t bit = 0;
-    if (e < stop) {
-      const int j = __ldg(col + e);
-      bit = (src[j >> 5] >> (j & 31)) & 1u;
-    }
-    const uint32_t m = __ballot_sync(FULL, bit);
-    const int lo = max(beg - c, 0), hi = min(end - c, 32);
-    if (hi > lo) {
-      const uint32_t sel = (hi - lo == 32) ? FULL : (((1u << (hi - lo)) - 1u) << lo);
-      cnt += __popc(m & sel);
-    }
-  }
+  const int cnt = count_chunks<XN>(col, src, beg, end, base, stop, lane);
   const int len = end - beg;
   const bool any = (__ldg(any_mask + w) >> lane) & 1u;
   const int thr = any ? 1 : max(len, 1);  // an empty row never fires
@@ -60,6 +80,7 @@ __device__ __forceinline__ uint32_t theta_word(const int32_t* __restrict__ row_p
 // every row of word w within its share of the word's 32-entry chunks; the G partial counts are
 // summed in shared memory before the threshold. Returns this lane's partial count; *len_out is
 // the lane's row length.
+template <int XN>
 __device__ __forceinline__ int theta_word_part(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                                const uint32_t* src, int w, int lane, int part, int G,
                                                int* len_out) {
@@ -71,28 +92,76 @@ __device__ __forceinline__ int theta_word_part(const int32_t* __restrict__ row_p
   const int stop = __shfl_sync(FULL, end, 31);
   const int n_chunks = (stop - base + 31) >> 5;
   const int c_lo = base + 32 * (n_chunks * part / G), c_hi = min(stop, base + 32 * (n_chunks * (part + 1) / G));
-  int cnt = 0;
-  for (int c = c_lo; c < c_hi; c += 32) {
-    const int e = c + lane;
-    uint32_t bit = 0;
-    if (e < c_hi) {
-      const int j = __ldg(col + e);
-      bit = (src[j >> 5] >> (j & 31)) & 1u;
-    }
-    const uint32_t m = __ballot_sync(FULL, bit);
-    const int lo = max(beg - c, 0), hi = min(end - c, 32);
-    if (hi > lo) {
-      const uint32_t sel = (hi - lo == 32) ? FULL : (((1u << (hi - lo)) - 1u) << lo);
-      cnt += __popc(m & sel);
-    }
-  }
   *len_out = end - beg;
-  return cnt;
+  return count_chunks<XN>(col, src, beg, end, c_lo, c_hi, lane);
+}
+
+// Count of this lane's row [beg, end) from a word's per-chunk ballots (word of at most 32
+// chunks): lane q holds the ballot of chunk q. An exclusive warp scan of their popcounts gives
+// P(x), the true entries before offset x of the word's entry range; the row's count is
+// P(end) - P(beg) (offsets relative to the word's first entry).
+__device__ __forceinline__ int prefix_count(uint32_t mine, int lane, int xb, int xe) {
+  const int pc = __popc(mine);
+  int incl = pc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += t;
+  }
+  const int excl = incl - pc;
+  const int qb = xb >> 5, qe = xe >> 5;  // chunk of each offset (32 = just past chunk 31)
+  const int qb2 = qb > 31 ? 31 : qb, qe2 = qe > 31 ? 31 : qe;
+  const uint32_t lb = qb > 31 ? FULL : ((1u << (xb & 31)) - 1u), le = qe > 31 ? FULL : ((1u << (xe & 31)) - 1u);
+  const int pb = __shfl_sync(FULL, excl, qb2) + __popc(__shfl_sync(FULL, mine, qb2) & lb);
+  const int pe = __shfl_sync(FULL, excl, qe2) + __popc(__shfl_sync(FULL, mine, qe2) & le);
+  return pe - pb;
+}
+
+// Two words per warp step (w1, w2): their loads interleave, so each warp keeps twice the
+// memory requests in flight. Words of at most 32 chunks use prefix_count; longer ones the
+// chunk-by-chunk count.
+template <int XN>
+__device__ __forceinline__ void theta_word_pair(const FixArgs& a, const uint32_t* src, int w1, int w2, int lane,
+                                                uint32_t* u1, uint32_t* u2) {
+  const int r1 = (w1 << 5) + lane, r2 = (w2 << 5) + lane;
+  const int b1 = __ldg(a.row_ptr + r1), b2 = __ldg(a.row_ptr + r2);
+  int e1 = __shfl_down_sync(FULL, b1, 1), e2 = __shfl_down_sync(FULL, b2, 1);
+  if (lane == 31) {
+    e1 = __ldg(a.row_ptr + r1 + 1);
+    e2 = __ldg(a.row_ptr + r2 + 1);
+  }
+  const int s1 = __shfl_sync(FULL, b1, 0), t1 = __shfl_sync(FULL, e1, 31);
+  const int s2 = __shfl_sync(FULL, b2, 0), t2 = __shfl_sync(FULL, e2, 31);
+  const int n1 = (t1 - s1 + 31) >> 5, n2 = (t2 - s2 + 31) >> 5;
+  int c1, c2;
+  if (n1 <= 32 && n2 <= 32) {
+    uint32_t m1 = 0, m2 = 0;
+    const int nmax = max(n1, n2);
+    for (int q = 0; q < nmax; q++) {
+      const int ea = s1 + 32 * q + lane, eb = s2 + 32 * q + lane;
+      const int ja = ea < t1 ? __ldg(a.col + ea) : -1, jb = eb < t2 ? __ldg(a.col + eb) : -1;
+      const uint32_t ba = ja >= 0 ? (src[ja >> 5] >> (ja & 31)) & 1u : 0u;
+      const uint32_t bb = jb >= 0 ? (src[jb >> 5] >> (jb & 31)) & 1u : 0u;
+      const uint32_t ma = __ballot_sync(FULL, ba), mb = __ballot_sync(FULL, bb);
+      if (lane == q) {
+        m1 = ma;
+        m2 = mb;
+      }
+    }
+    c1 = prefix_count(m1, lane, b1 - s1, e1 - s1);
+    c2 = prefix_count(m2, lane, b2 - s2, e2 - s2);
+  } else {
+    c1 = count_chunks<XN>(a.col, src, b1, e1, s1, t1, lane);
+    c2 = count_chunks<XN>(a.col, src, b2, e2, s2, t2, lane);
+  }
+  const bool any1 = (__ldg(a.any_mask + w1) >> lane) & 1u, any2 = (__ldg(a.any_mask + w2) >> lane) & 1u;
+  *u1 = __ballot_sync(FULL, c1 >= (any1 ? 1 : max(e1 - b1, 1)));  // an empty row never fires
+  *u2 = __ballot_sync(FULL, c2 >= (any2 ? 1 : max(e2 - b2, 1)));
 }
 
 __device__ __forceinline__ uint32_t get_bit(const uint32_t* v, int i) { return (v[i >> 5] >> (i & 31)) & 1u; }
 
-template <int G>
+template <int G, int XN>
 __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
   __shared__ int s_flag;
   __shared__ int s_cnt[G > 1 ? kFixBlock : 1];
@@ -140,8 +209,18 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
     uint32_t* dst = (it & 1) ? a.x0 : a.x1;
     bool changed = false;
     if (G == 1) {
-      for (int w = gwarp; w < a.n_words; w += nwarps) {
-        const uint32_t u = theta_word(a.row_ptr, a.col, a.any_mask, src, w, lane);
+      int w = gwarp;
+      for (; w + nwarps < a.n_words; w += 2 * nwarps) {
+        uint32_t u1, u2;
+        theta_word_pair<XN>(a, src, w, w + nwarps, lane, &u1, &u2);
+        if (lane == 0) {
+          dst[w] = u1;
+          dst[w + nwarps] = u2;
+          changed |= (u1 != src[w]) | (u2 != src[w + nwarps]);
+        }
+      }
+      for (; w < a.n_words; w += nwarps) {  // a last single word
+        const uint32_t u = theta_word<XN>(a.row_ptr, a.col, a.any_mask, src, w, lane);
         if (lane == 0) {
           dst[w] = u;
           changed |= (u != src[w]);
@@ -154,7 +233,7 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
       for (int wb = blockIdx.x * per_block; wb < a.n_words; wb += gridDim.x * per_block) {
         const int w = wb + slot;
         int len = 0, cnt = 0;
-        if (w < a.n_words) cnt = theta_word_part(a.row_ptr, a.col, src, w, lane, part, G, &len);
+        if (w < a.n_words) cnt = theta_word_part<XN>(a.row_ptr, a.col, src, w, lane, part, G, &len);
         s_cnt[threadIdx.x] = cnt;
         __syncthreads();
         if (part == 0 && w < a.n_words) {
@@ -204,24 +283,34 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
   }
 }
 
-static const void* fixpoint_entry(int G) {
+static const void* fixpoint_entry(int G, int XN) {
+  if (XN == 4) {
+    switch (G) {
+      case 2: return (const void*)fixpoint_kernel<2, 4>;
+      case 4: return (const void*)fixpoint_kernel<4, 4>;
+      case 8: return (const void*)fixpoint_kernel<8, 4>;
+      default: return (const void*)fixpoint_kernel<1, 4>;
+    }
+  }
   switch (G) {
-    case 2: return (const void*)fixpoint_kernel<2>;
-    case 4: return (const void*)fixpoint_kernel<4>;
-    case 8: return (const void*)fixpoint_kernel<8>;
-    default: return (const void*)fixpoint_kernel<1>;
+    case 2: return (const void*)fixpoint_kernel<2, 1>;
+    case 4: return (const void*)fixpoint_kernel<4, 1>;
+    case 8: return (const void*)fixpoint_kernel<8, 1>;
+    default: return (const void*)fixpoint_kernel<1, 1>;
   }
 }
 
-cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, cudaStream_t s) {
+cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, cudaStream_t s) {
   FixArgs copy = a;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(fixpoint_entry(row_split), dim3(grid), dim3(kFixBlock), params, 0, s);
+  return cudaLaunchCooperativeKernel(fixpoint_entry(row_split, chunk_batch), dim3(grid), dim3(kFixBlock), params, 0,
+                                     s);
 }
 
-int fixpoint_blocks_per_sm(int row_split) {
+int fixpoint_blocks_per_sm(int row_split, int chunk_batch) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fixpoint_entry(row_split), kFixBlock, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fixpoint_entry(row_split, chunk_batch), kFixBlock, 0) !=
+      cudaSuccess)
     return 0;
   return nb;
 }

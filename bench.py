@@ -524,9 +524,10 @@ PAPER_ROWS = [
 
 def bench_paper_tables(lp, torch, dev, reps=5):
     """Programs shaped like each row of the paper's Tables 2, 3, 5 and 6 (table1_program with
-    the row's n, m, k; dense for Tables 3 and 6): the solve on the GPU (CUDA events, median of
-    reps, program resident) and end to end from host arrays (lp_compile + solve + result on the
-    host), beside the paper's own Sparse-matrix time for that row."""
+    the row's n, m, k; dense for Tables 3 and 6): end to end from host arrays (lp_compile +
+    solve + result on the host, default schedule), then the schedule lp_autotune picks for the
+    row, then the solve on the GPU under it (CUDA events, median of reps, program resident),
+    beside the paper's own Sparse-matrix time for that row."""
     stream = torch.cuda.current_stream()
     rows = []
     for table, no, n, m, k, n_prime_paper, paper_s in PAPER_ROWS:
@@ -545,6 +546,7 @@ def bench_paper_tables(lp, torch, dev, reps=5):
             out = torch.zeros(lp.words(n), dtype=torch.int64, device=dev)
             run = lambda: P.least_model(out, sync=False)  # noqa: E731
         e2e_ms = 1e3 * (time.perf_counter() - t0)
+        P.autotune(lp.LP_TUNE_STABLE if k else lp.LP_TUNE_LEAST, reps=2)  # schedule for this row's shape
         for _ in range(2):
             run()
         ts = []
@@ -559,6 +561,10 @@ def bench_paper_tables(lp, torch, dev, reps=5):
         row = {"table": table, "no": no, "n": n, "m": m, "n_prime": P.info["n_prime"], "n_prime_paper": n_prime_paper,
                "nnz": P.info["nnz"], "gpu_ms": round(gpu_ms, 4), "e2e_ms": round(e2e_ms, 2),
                "paper_sparse_ms": paper_s * 1e3, "paper_over_gpu": round(paper_s * 1e3 / gpu_ms, 1)}
+        sched = P.schedule
+        row["schedule"] = ("W%d" % sched["stable_tile_words"]) if k else (
+            "stream" if sched["fixpoint_kernel"] == 1 else
+            "split%d,batch%d" % (max(1, sched["fixpoint_row_split"]), max(1, sched["fixpoint_chunk_batch"])))
         if k:
             row.update({"k": P.info["k"], "n_stable": int(ns)})
         else:

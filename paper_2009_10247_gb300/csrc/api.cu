@@ -293,15 +293,16 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
     le = launch_fixpoint_stream(a, L, grid, s);
   } else {
     const int split = std::max(1, p->sched.fixpoint_row_split);
-    static int occ_by_split[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
-    int& occ = occ_by_split[split];
-    if (occ < 0) occ = fixpoint_blocks_per_sm(split);
+    const int xn = p->sched.fixpoint_chunk_batch == 4 ? 4 : 1;
+    static int occ_by_variant[2][9] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1, -1}};
+    int& occ = occ_by_variant[xn == 4][split];
+    if (occ < 0) occ = fixpoint_blocks_per_sm(split, xn);
     if (occ <= 0) return fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident");
     const int per_sm = p->sched.fixpoint_blocks_per_sm > 0 ? std::min(occ, p->sched.fixpoint_blocks_per_sm) : occ;
     const int words_per_block = kFixBlock / 32 / split;
     int grid = std::min(max_coresident(p, per_sm), std::max(1, (a.n_words + words_per_block - 1) / words_per_block));
     if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
-    le = launch_fixpoint(a, grid, split, s);
+    le = launch_fixpoint(a, grid, split, xn, s);
   }
   if ((st = launch_count_and_check(le, "launch fixpoint kernel", p)) != LP_OK) return st;
   if (p->timed) LP_CUDA(cudaEventRecord(p->ev1, s));
@@ -448,6 +449,9 @@ lp_status lp_set_schedule(lp_program* p, const lp_schedule* in) {
   if (G != 0 && G != 1 && G != 2 && G != 4 && G != 8)
     return fail(LP_ERR_INVALID, "fixpoint_row_split must be 0, 1, 2, 4 or 8");
   if (G > 1 && in->fixpoint_kernel != 0) return fail(LP_ERR_INVALID, "a row split needs fixpoint_kernel 0");
+  const int32_t X = in->fixpoint_chunk_batch;
+  if (X != 0 && X != 1 && X != 4) return fail(LP_ERR_INVALID, "fixpoint_chunk_batch must be 0, 1 or 4");
+  if (X == 4 && in->fixpoint_kernel != 0) return fail(LP_ERR_INVALID, "a chunk batch needs fixpoint_kernel 0");
   if (W < 0 || W > 32 || (W & (W - 1)) != 0) return fail(LP_ERR_INVALID, "stable_tile_words must be 0 or 1, 2, 4, 8, 16, 32");
   p->sched = *in;
   return LP_OK;

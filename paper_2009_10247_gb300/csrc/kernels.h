@@ -36,10 +36,11 @@ struct FixArgs {
   int32_t n_sec_a;             // leading rows that rule rows refer to (used by the streamed kernel)
 };
 
-constexpr int kFixBlock = 256;
-// row_split: warps per 32-row output word (1, 2, 4 or 8)
-cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, cudaStream_t s);
-int fixpoint_blocks_per_sm(int row_split);
+constexpr int kFixBlock = 512;
+// row_split: warps per 32-row output word (1, 2, 4 or 8); chunk_batch: 32-entry chunks whose
+// loads a warp issues together (1 or 4)
+cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, cudaStream_t s);
+int fixpoint_blocks_per_sm(int row_split, int chunk_batch);
 
 // The same loop with the matrix streamed through shared memory (fixpoint_stream.cu).
 struct StreamLayout {

@@ -78,14 +78,15 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     const size_t out_bytes = (size_t)((hm.n + 63) / 64) * 8;
     if ((st = ensure(p, p->tune_out, std::max<size_t>(out_bytes, 8))) != LP_OK) return st;
     uint64_t* out = (uint64_t*)p->tune_out.p;
-    const int occ0 = fixpoint_blocks_per_sm(1), occ1 = fixpoint_stream_blocks_per_sm();
+    const int occ0 = fixpoint_blocks_per_sm(1, 1), occ1 = fixpoint_stream_blocks_per_sm();
     const int32_t W0 = base.stable_tile_words, B0 = base.stable_blocks_per_sm;
     std::vector<lp_schedule> cands;
     for (int b : {0, 4, 2})
-      if (b == 0 || b < occ0) cands.push_back({0, b, 1, W0, B0});
-    for (int G : {2, 4, 8}) cands.push_back({0, 0, G, W0, B0});
+      if (b == 0 || b < occ0) cands.push_back({0, b, 1, 1, W0, B0});
+    for (int G : {2, 4, 8}) cands.push_back({0, 0, G, 1, W0, B0});
+    for (int G : {1, 2, 4, 8}) cands.push_back({0, 0, G, 4, W0, B0});
     for (int b : {0, 1})
-      if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back({1, b, 1, W0, B0});
+      if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back({1, b, 1, 1, W0, B0});
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
     for (const lp_schedule& c : cands) {
@@ -137,7 +138,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
       for (int b : {0, occ / 2})
         if (b == 0 || (b > 0 && b < occ))
           cands.push_back({best_least.fixpoint_kernel, best_least.fixpoint_blocks_per_sm, best_least.fixpoint_row_split,
-                           W, b});
+                           best_least.fixpoint_chunk_batch, W, b});
     }
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
@@ -174,6 +175,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     chosen.fixpoint_kernel = best_least.fixpoint_kernel;
     chosen.fixpoint_blocks_per_sm = best_least.fixpoint_blocks_per_sm;
     chosen.fixpoint_row_split = best_least.fixpoint_row_split;
+    chosen.fixpoint_chunk_batch = best_least.fixpoint_chunk_batch;
   }
   if (what & LP_TUNE_STABLE) {
     chosen.stable_tile_words = best_stable.stable_tile_words;

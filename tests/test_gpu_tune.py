@@ -14,16 +14,18 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_util import gpu_least_model, gpu_stable  # noqa: E402
 
 
-@pytest.mark.parametrize("kernel,bpsm,split", [(0, 0, 1), (0, 2, 1), (0, 1, 1), (0, 0, 2), (0, 0, 4), (0, 3, 8),
-                                               (1, 0, 1), (1, 1, 1)])
-def test_least_model_every_schedule(kernel, bpsm, split):
+@pytest.mark.parametrize("kernel,bpsm,split,xn", [(0, 0, 1, 1), (0, 2, 1, 1), (0, 1, 1, 1), (0, 0, 2, 1), (0, 0, 4, 1),
+                                                  (0, 3, 8, 1), (0, 0, 1, 4), (0, 0, 2, 4), (0, 2, 8, 4), (1, 0, 1, 1),
+                                                  (1, 1, 1, 1)])
+def test_least_model_every_schedule(kernel, bpsm, split, xn):
     progs = [small_definite(2), tiny_random(77, n_atoms=40, n_rules=90, max_body=4, p_fact=0.2),
              large_definite(seed=3, n=20_000, n_rules=100_000, chain_levels=60, chain_width=20),
              table1_program(31, 1000, 5000, dense=True), table1_program(32, 1600, 24000)]
     for prog in progs:
         want, want_it = oracle.least_model(prog)
         with lp.Program.from_program(prog) as P:
-            P.set_schedule(fixpoint_kernel=kernel, fixpoint_blocks_per_sm=bpsm, fixpoint_row_split=split)
+            P.set_schedule(fixpoint_kernel=kernel, fixpoint_blocks_per_sm=bpsm, fixpoint_row_split=split,
+                           fixpoint_chunk_batch=xn)
             got, it = gpu_least_model(P)
         assert it == want_it and np.array_equal(got, want)
 
@@ -47,11 +49,11 @@ def test_autotune_keeps_fastest_and_stays_exact():
         sched = P.schedule
         least = [r for r in recs if r["solve"] == "least"]
         stable = [r for r in recs if r["solve"] == "stable"]
-        assert len(least) >= 6 and len(stable) >= 2 and all(r["ms"] >= 0 for r in recs)
+        assert len(least) >= 10 and len(stable) >= 2 and all(r["ms"] >= 0 for r in recs)
         assert {r["fixpoint_row_split"] for r in least} == {1, 2, 4, 8}
         bl, bs = min(least, key=lambda r: r["ms"]), min(stable, key=lambda r: r["ms"])
-        assert (sched["fixpoint_kernel"], sched["fixpoint_blocks_per_sm"], sched["fixpoint_row_split"]) == (
-            bl["fixpoint_kernel"], bl["fixpoint_blocks_per_sm"], bl["fixpoint_row_split"])
+        keys = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "fixpoint_row_split", "fixpoint_chunk_batch")
+        assert all(sched[k] == bl[k] for k in keys)
         assert (sched["stable_tile_words"], sched["stable_blocks_per_sm"]) == (bs["stable_tile_words"],
                                                                               bs["stable_blocks_per_sm"])
         # k = 10: 16 guess words, so tiles wider than 16 words are not candidates

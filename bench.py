@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 from workloads import large_definite, normal_program, program_batch, table1_program  # noqa: E402
 
 METRIC = "fixpoint rule-evals/sec (nnz x iters / s)"
+# the schedule the recorded ncu traffic of the least-model kernel was taken with
+DEFAULT_SCHEDULE = {"fixpoint_kernel": 0, "fixpoint_blocks_per_sm": 0, "fixpoint_row_split": 1, "fixpoint_chunk_batch": 1,
+                    "stable_tile_words": 0, "stable_blocks_per_sm": 0}
 UNIT = "rule-evals/s"
 WORKLOAD = "large definite program: 1e6 atoms, 5e6 rules, Geom(mean 3, cap 8) bodies, Zipf(1.1) atoms, 1% facts, chain 1000x50 (seed 1)"
 WORKLOAD_STABLE = "normal program: 1e5 atoms, 3e5 rules, bodies U{1..6}, 1% facts, k=16 negated atoms x 4 (seed 1), all 65536 guesses"
@@ -175,6 +178,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-paper-tables", action="store_true")
+    ap.add_argument("--n-atoms", type=int, default=1_000_000,
+                    help="atoms of the least-model workload (5 rules per atom); smaller for profiler captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -185,7 +190,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        run_reference(args, large_definite(seed=1))
+        run_reference(args, large_definite(seed=1, n=args.n_atoms, n_rules=5 * args.n_atoms))
         return
 
     import torch
@@ -199,7 +204,7 @@ def main():
     dev = torch.device("cuda", local)
     lp.load()
 
-    prog = large_definite(seed=1)
+    prog = large_definite(seed=1, n=args.n_atoms, n_rules=5 * args.n_atoms)
     P = lp.Program.from_program(prog)
     info = P.info
     n, n_prime, nnz = info["n_atoms"], info["n_prime"], info["nnz"]
@@ -207,6 +212,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    tuned = P.autotune(lp.LP_TUNE_LEAST, reps=2)  # the schedule the autotuner picks for this program
     iters = P.least_model(out)  # checks status once, synchronously
     for _ in range(args.warmup):
         flush.zero_()
@@ -298,11 +304,15 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_atoms": n, "n_rules": int(prog.n_rules), "n_prime": n_prime,
+            "config": {"workload": WORKLOAD if n == 1_000_000 else WORKLOAD.replace("1e6 atoms, 5e6 rules",
+                                                                                    f"{n} atoms, {5 * n} rules"),
+                       "n_atoms": n, "n_rules": int(prog.n_rules), "n_prime": n_prime,
                        "nnz": nnz, "iters": iters, "parallelism": f"replicas x{world}",
+                       "schedule": P.schedule, "tuned_candidates": len(tuned),
                        "l2": "flushed before every step (256 MiB write)", "wall_s": round(wall, 3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": measured_traffic("fixpoint_kernel"),
+                         "frac": achieved / peak,
+                         "traffic": measured_traffic("fixpoint_kernel") if P.schedule == DEFAULT_SCHEDULE else None,
                          "peak_kind": peak_kind, "kernel": "fixpoint_kernel", "kernel_ms": k_ms, "bytes_per_launch": per_launch_bytes,
                          "bytes_per_iter": alg_bytes_per_iter(n_prime, nnz)},
             "e2e": e2e,
@@ -328,6 +338,7 @@ def bench_stable(lp, torch, dev, flush, steps=5):
     k = P.info["k"]
     ng = 1 << k
     mask = torch.zeros(lp.words(ng), dtype=torch.int64, device=dev)
+    P.autotune(lp.LP_TUNE_STABLE, reps=2)
     ns = P.stable_models(mask)
     stream = torch.cuda.current_stream()
     for _ in range(2):
@@ -352,6 +363,7 @@ def bench_stable(lp, torch, dev, flush, steps=5):
     out = {"metric": "stable-model guesses/sec", "value": ng / (ms / 1e3), "unit": "guesses/s",
            "ms_per_step": ms, "workload": WORKLOAD_STABLE, "n_prime": info["n_prime"], "nnz": info["nnz"], "k": k,
            "n_stable": ns, "tiles": st["tiles"], "tile_words": W, "tile_iters_max": st["max_tile_iters"],
+           "schedule": P.schedule,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": measured_traffic("stable_kernel"), "peak_kind": peak_kind, "kernel": "stable_kernel",
                         "note": "tiles are sized to stay L2 resident, so this fraction can exceed 1"}}

@@ -216,8 +216,9 @@ lp_status lp_batch_program_info(const lp_batch* batch, int32_t program, lp_info*
  * set iff guess g gives a stable model. n_stable (device or host, n_programs, nullable): stable
  * guesses per program; iters (device or host, n_programs, nullable): theta applications until
  * the program's fixpoint (0 if it had none within max_iters). The programs run in lock step, up
- * to 4096 per cooperative launch; a program stops being updated once an application changes
- * none of its words. A host buffer or a non-NULL n_stable / iters makes the call wait;
+ * to 4096 per cooperative launch (the environment variable LP_BATCH_GROUP_BYTES, read by
+ * lp_compile_batch, also caps a launch's matrix + iterate bytes); a program stops being
+ * updated once an application changes none of its words. A host buffer or a non-NULL n_stable / iters makes the call wait;
  * LP_ERR_NO_FIXPOINT if a program reaches max_iters (its mask is then zero); LP_ERR_TIMEOUT if a
  * grid barrier wait gave up (2 s).
  */

@@ -126,3 +126,12 @@ def test_more_programs_than_one_launch():
     got, ns, it, _ = _run_batch(progs)
     _check_oracle(progs, got, ns)
     assert np.all(it >= 1)
+
+
+def test_many_small_launches(monkeypatch):
+    # a 2 MB group budget splits the uneven-size batch into many cooperative launches
+    monkeypatch.setenv("LP_BATCH_GROUP_BYTES", str(2_000_000))
+    progs = program_batch(seed=12, count=60, n_lo=100, n_hi=4000)
+    got, ns, it, B = _run_batch(progs)
+    _check_oracle(progs, got, ns)
+    assert np.all(it >= 1)

@@ -174,10 +174,6 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   if ((st = upload(p, &p->neg_row, hm.neg_row, s)) != LP_OK) return cleanup(st);
   if ((st = upload(p, &p->bar_row, hm.bar_row, s)) != LP_OK) return cleanup(st);
   if ((st = upload(p, &p->row_tag, hm.row_tag, s)) != LP_OK) return cleanup(st);
-  if ((st = upload(p, &p->desc, hm.desc, s)) != LP_OK) return cleanup(st);
-  if ((st = upload(p, &p->word_hdr, hm.word_hdr, s)) != LP_OK) return cleanup(st);
-  if ((st = upload(p, &p->and_col, hm.and_col, s)) != LP_OK) return cleanup(st);
-  if ((st = upload(p, &p->groups, hm.groups, s)) != LP_OK) return cleanup(st);
   // iterate vectors, padded so 16-byte vector loads of a staged prefix stay inside
   if ((st = dalloc(p, &p->x[0], (size_t)hm.n_pad / 32 + 4)) != LP_OK) return cleanup(st);
   if ((st = dalloc(p, &p->x[1], (size_t)hm.n_pad / 32 + 4)) != LP_OK) return cleanup(st);
@@ -187,9 +183,6 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   std::vector<int32_t>().swap(hm.row_ptr);
   std::vector<int32_t>().swap(hm.col);
   std::vector<int32_t>().swap(hm.row_tag);
-  std::vector<uint32_t>().swap(hm.desc);
-  std::vector<int32_t>().swap(hm.word_hdr);
-  std::vector<int32_t>().swap(hm.and_col);
   p->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
   return LP_OK;
@@ -213,6 +206,36 @@ lp_status lp_program_info(const lp_program* p, lp_info* out) {
   out->compile_ms = p->compile_ms;
   return LP_OK;
 }
+
+namespace {
+
+// The streamed kernel's layout, built on its first use from the device CSR.
+lp_status ensure_stream_layout(lp_program* p, cudaStream_t s) {
+  if (p->desc) return LP_OK;
+  HostMatrix& hm = p->hm;
+  hm.row_ptr.resize((size_t)hm.n_pad + 1);
+  hm.col.resize((size_t)std::max<int64_t>(hm.nnz, 1));
+  LP_CUDA(cudaMemcpyAsync(hm.row_ptr.data(), p->row_ptr, hm.row_ptr.size() * 4, cudaMemcpyDeviceToHost, s));
+  if (hm.nnz) LP_CUDA(cudaMemcpyAsync(hm.col.data(), p->col, (size_t)hm.nnz * 4, cudaMemcpyDeviceToHost, s));
+  LP_CUDA(cudaStreamSynchronize(s));
+  std::string err;
+  lp_status st = build_stream_layout(hm, err);
+  if (st == LP_OK && (st = upload(p, &p->desc, hm.desc, s)) == LP_OK && (st = upload(p, &p->word_hdr, hm.word_hdr, s)) == LP_OK &&
+      (st = upload(p, &p->and_col, hm.and_col, s)) == LP_OK && (st = upload(p, &p->groups, hm.groups, s)) == LP_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "upload of the streamed layout");
+  } else if (!err.empty()) {
+    st = fail(st, err);
+  }
+  std::vector<int32_t>().swap(hm.row_ptr);
+  std::vector<int32_t>().swap(hm.col);
+  std::vector<uint32_t>().swap(hm.desc);
+  std::vector<int32_t>().swap(hm.word_hdr);
+  std::vector<int32_t>().swap(hm.and_col);
+  return st;
+}
+
+}  // namespace
 
 lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int32_t max_iters, uint32_t flags,
                          int32_t* iters_out, void* cuda_stream) {
@@ -283,6 +306,7 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
   // Kernel and residency from the handle's schedule (both kernels are exact).
   cudaError_t le;
   if (p->sched.fixpoint_kernel == 1) {
+    if ((st = ensure_stream_layout(p, s)) != LP_OK) return st;
     static int occ_s = -1;
     if (occ_s < 0) occ_s = fixpoint_stream_blocks_per_sm();
     if (occ_s <= 0) return fail(LP_ERR_CUDA, "streamed fixpoint kernel cannot be resident");

@@ -21,6 +21,9 @@
 #ifdef _OPENMP
 #include <omp.h>
 #endif
+#if defined(_OPENMP) && defined(__GLIBCXX__)
+#include <parallel/algorithm>
+#endif
 
 namespace lp {
 
@@ -40,6 +43,15 @@ inline void sort_small(int32_t* a, int64_t m) {
     }
     a[j + 1] = x;
   }
+}
+
+// Sort of 64-bit keys, in parallel where libstdc++'s parallel mode is available.
+inline void parallel_sort(std::vector<uint64_t>& v) {
+#if defined(_OPENMP) && defined(__GLIBCXX__)
+  __gnu_parallel::sort(v.begin(), v.end());
+#else
+  std::sort(v.begin(), v.end());
+#endif
 }
 
 }  // namespace
@@ -86,22 +98,56 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     return LP_ERR_INVALID;
   }
 
+  if (n_rules >= (int64_t(1) << 31) - 1) {
+    err = "too many rules (must be < 2^31 - 1)";
+    return LP_ERR_INVALID;
+  }
+
   try {
     // ---- rules per head, negated atoms, barred ids (canonical: n + rank of q)
     std::vector<int32_t> cnt(n, 0);
     std::vector<int32_t> bar_id(n, -1);
-    for (int64_t r = 0; r < n_rules; r++) cnt[head[r]]++;
-    if (body_neg)
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n_rules; r++) __atomic_fetch_add(&cnt[head[r]], 1, __ATOMIC_RELAXED);
+    if (body_neg) {
+#pragma omp parallel for schedule(static)
       for (int64_t e = 0; e < total; e++)
-        if (body_neg[e]) bar_id[body_atom[e]] = 0;
+        if (body_neg[e]) bar_id[body_atom[e]] = 0;  // every writer stores the same value
+    }
     int32_t nb = 0;
     for (int32_t a = 0; a < n; a++)
       if (bar_id[a] == 0) bar_id[a] = n + nb++;
-    // new atoms for the rules of multi-rule heads, in rule order
+    // new atoms for the rules of multi-rule heads, in rule order (blocked prefix count)
     std::vector<int32_t> aux(n_rules, -1);
     int64_t naux = 0;
-    for (int64_t r = 0; r < n_rules; r++)
-      if (cnt[head[r]] >= 2) aux[r] = (int32_t)std::min<int64_t>(INT32_MAX, (int64_t)n + nb + naux++);
+    {
+      // ranges follow the team that actually runs (one thread when this compile is itself
+      // inside a parallel region, as in lp_compile_batch)
+      std::vector<int64_t> part;
+      int nt = 1;
+#pragma omp parallel
+      {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#pragma omp single
+        nt = omp_get_num_threads();
+#endif
+#pragma omp single
+        part.assign((size_t)nt + 1, 0);
+        const int64_t r0 = n_rules * t / nt, r1 = n_rules * (t + 1) / nt;
+        int64_t c = 0;
+        for (int64_t r = r0; r < r1; r++) c += cnt[head[r]] >= 2;
+        part[t + 1] = c;
+#pragma omp barrier
+#pragma omp single
+        for (int q = 0; q < nt; q++) part[q + 1] += part[q];
+        int64_t k = part[t];
+        for (int64_t r = r0; r < r1; r++)
+          if (cnt[head[r]] >= 2) aux[r] = (int32_t)std::min<int64_t>(INT32_MAX, (int64_t)n + nb + k++);
+      }
+      naux = part[nt];
+    }
     const int64_t n_prime64 = (int64_t)n + nb + naux;
     if (n_prime64 >= (int64_t(1) << 31) - 128) {
       err = "standardized program too large (n' must be < 2^31 - 128)";
@@ -127,29 +173,35 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       setlen[r] = (int32_t)u;
     }
 
-    // ---- canonical rows: kind, defining rule, rules of each OR head
-    std::vector<int8_t> kind(np, K_EMPTY);
-    std::vector<int64_t> row_rule(np, -1);  // rule defining a RULE/FACT row
+    // ---- canonical rows: kind, defining rule, rules of each head (in rule order)
+    // One parallel sort of (head, rule) keys groups the rules by head; every pass after it
+    // writes contiguous ranges.
     std::vector<int64_t> hr_off((size_t)n + 1, 0);
+    for (int32_t a = 0; a < n; a++) hr_off[a + 1] = hr_off[a] + cnt[a];
+    std::vector<uint64_t> hk(n_rules);
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n_rules; r++) hk[r] = ((uint64_t)(uint32_t)head[r] << 32) | (uint64_t)r;
+    parallel_sort(hk);
+    auto rule_at = [&](int64_t t) -> int32_t { return (int32_t)(hk[t] & 0xffffffffu); };
+    std::vector<int8_t> kind(np, K_EMPTY);
+    std::vector<int32_t> row_rule(np, -1);  // rule defining a RULE/FACT row
+#pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < n_rules; r++)
-      if (cnt[head[r]] >= 2) hr_off[head[r] + 1]++;
-    for (int32_t a = 0; a < n; a++) hr_off[a + 1] += hr_off[a];
-    std::vector<int64_t> hr_rule(hr_off[n]);
-    {
-      std::vector<int64_t> cur(hr_off.begin(), hr_off.end() - 1);
-      for (int64_t r = 0; r < n_rules; r++) {
-        int32_t h = head[r];
-        if (cnt[h] >= 2) {
-          kind[h] = K_OR;
-          hr_rule[cur[h]++] = r;
-          kind[aux[r]] = setlen[r] == 0 ? K_FACT : K_RULE;
-          row_rule[aux[r]] = r;
-        } else {
-          kind[h] = setlen[r] == 0 ? K_FACT : K_RULE;
-          row_rule[h] = r;
-        }
+      if (aux[r] >= 0) {  // a rule of a multi-rule head defines its new atom's row
+        kind[aux[r]] = setlen[r] == 0 ? K_FACT : K_RULE;
+        row_rule[aux[r]] = (int32_t)r;
+      }
+#pragma omp parallel for schedule(static)
+    for (int32_t a = 0; a < n; a++) {
+      if (cnt[a] >= 2) {
+        kind[a] = K_OR;
+      } else if (cnt[a] == 1) {
+        const int32_t r = rule_at(hr_off[a]);
+        kind[a] = setlen[r] == 0 ? K_FACT : K_RULE;
+        row_rule[a] = r;
       }
     }
+#pragma omp parallel for schedule(static)
     for (int32_t a = 0; a < n; a++)
       if (bar_id[a] >= 0) kind[bar_id[a]] = K_BARRED;
 
@@ -164,44 +216,86 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     };
 
     // ---- references per canonical column (for the internal order)
-    std::vector<int64_t> deg(np, 0);
     int64_t nnz = 0;
+#pragma omp parallel for reduction(+ : nnz) schedule(static)
     for (int32_t c = 0; c < np; c++) nnz += row_len(c);
     if (nnz >= (int64_t(1) << 31)) {
       err = "too many matrix entries (nnz must be < 2^31)";
       return LP_ERR_INVALID;
     }
-    for (int32_t c = 0; c < np; c++) {
-      if (kind[c] == K_RULE) {
-        int64_t r = row_rule[c];
-        const int32_t* s = rb.data() + body_off[r];
-        for (int32_t i = 0; i < setlen[r]; i++) deg[s[i]]++;
-      }  // OR entries point at new atoms, which are placed by their OR row; self-loops read
-    }    // their own bit: only rule-row entries count as references (gathers)
+    const int32_t nA = n + nb;
+    // Only rule-row entries count as references (gathers): OR entries point at new atoms,
+    // which are placed by their OR row, and self-loops read their own bit. Every body atom is
+    // an original or barred atom (< nA); per-thread histograms are summed at the end.
+    std::vector<int64_t> deg(nA, 0);
+    {
+      std::vector<int32_t> local;
+      int nt = 1;
+#pragma omp parallel
+      {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#pragma omp single
+        nt = omp_get_num_threads();
+#endif
+#pragma omp single
+        local.assign((size_t)nt * nA, 0);
+        int32_t* h = local.data() + (size_t)t * nA;
+#pragma omp for schedule(static)
+        for (int64_t r = 0; r < n_rules; r++) {
+          if (setlen[r] == 0) continue;  // facts define self-loop rows
+          const int32_t* s = rb.data() + body_off[r];
+          for (int32_t i = 0; i < setlen[r]; i++) h[s[i]]++;
+        }
+#pragma omp for schedule(static)
+        for (int32_t c = 0; c < nA; c++) {
+          int64_t d = 0;
+          for (int q = 0; q < nt; q++) d += local[(size_t)q * nA + c];
+          deg[c] = d;
+        }
+      }
+    }
 
     // ---- internal order
-    const int32_t nA = n + nb;
     std::vector<int32_t> inv(np);  // internal -> canonical
-    std::iota(inv.begin(), inv.begin() + nA, 0);
-    std::stable_sort(inv.begin(), inv.begin() + nA, [&](int32_t x, int32_t y) { return deg[x] > deg[y]; });
     {
-      int64_t pos = nA;
+      // section A by descending references, ties by canonical id: unique keys, so any sort
+      // gives the same order
+      int64_t maxdeg = 0;
+      for (int32_t c = 0; c < nA; c++) maxdeg = std::max(maxdeg, deg[c]);
+      std::vector<uint64_t> key(nA);
+#pragma omp parallel for schedule(static)
+      for (int32_t c = 0; c < nA; c++) key[c] = ((uint64_t)(maxdeg - deg[c]) << 32) | (uint32_t)c;
+      parallel_sort(key);
+#pragma omp parallel for schedule(static)
+      for (int32_t i = 0; i < nA; i++) inv[i] = (int32_t)(key[i] & 0xffffffffu);
+      // section B: each OR row's new atoms, OR rows in section-A order
+      std::vector<int64_t> bpos((size_t)nA + 1, 0);
       for (int32_t i = 0; i < nA; i++) {
-        int32_t c = inv[i];
-        if (kind[c] == K_OR)
-          for (int64_t t = hr_off[c]; t < hr_off[c + 1]; t++) inv[pos++] = aux[hr_rule[t]];
+        const int32_t c = inv[i];
+        bpos[i + 1] = bpos[i] + (kind[c] == K_OR ? hr_off[c + 1] - hr_off[c] : 0);
       }
-      if (pos != np) {
+      if (nA + bpos[nA] != np) {
         err = "internal error: new atoms not covered by OR rows";
         return LP_ERR_INVALID;
       }
+#pragma omp parallel for schedule(dynamic, 4096)
+      for (int32_t i = 0; i < nA; i++) {
+        const int32_t c = inv[i];
+        if (kind[c] != K_OR) continue;
+        int64_t pos = nA + bpos[i];
+        for (int64_t t = hr_off[c]; t < hr_off[c + 1]; t++) inv[pos++] = aux[rule_at(t)];
+      }
     }
     hm.perm.assign(np, 0);
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < np; i++) hm.perm[inv[i]] = i;
     const int32_t npad = (int32_t)(((int64_t)np + 63) / 64 * 64);
 
     // ---- internal CSR
     hm.row_ptr.assign((size_t)npad + 1, 0);
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < np; i++) hm.row_ptr[i + 1] = (int32_t)row_len(inv[i]);
     for (int32_t i = 0; i < npad; i++) hm.row_ptr[i + 1] += hm.row_ptr[i];
     hm.col.assign((size_t)nnz, 0);
@@ -218,7 +312,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
           break;
         }
         case K_OR:
-          for (int64_t t = hr_off[c]; t < hr_off[c + 1]; t++) d[m++] = hm.perm[aux[hr_rule[t]]];
+          for (int64_t t = hr_off[c]; t < hr_off[c + 1]; t++) d[m++] = hm.perm[aux[rule_at(t)]];
           break;
         case K_FACT:
         case K_BARRED:
@@ -230,14 +324,23 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       sort_small(d, m);
     }
     hm.any_mask.assign((size_t)npad / 32, 0u);
-    for (int32_t i = 0; i < np; i++)
-      if (kind[inv[i]] == K_OR) hm.any_mask[i >> 5] |= 1u << (i & 31);
+#pragma omp parallel for schedule(static)
+    for (int32_t w = 0; w < np / 32 + 1; w++) {
+      uint32_t bits = 0;
+      for (int l = 0; l < 32; l++) {
+        const int32_t i = 32 * w + l;
+        if (i < np && kind[inv[i]] == K_OR) bits |= 1u << l;
+      }
+      if (w < npad / 32) hm.any_mask[w] = bits;
+    }
 
     // ---- facts, negated atoms, guesses (Def. 4 and Def. 8)
     std::vector<int32_t> owner_of_row(np);
+#pragma omp parallel for schedule(static)
     for (int32_t c = 0; c < np; c++) owner_of_row[c] = c < n ? c : -1;
     for (int32_t a = 0; a < n; a++)
       if (bar_id[a] >= 0) owner_of_row[bar_id[a]] = a;
+#pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < n_rules; r++)
       if (aux[r] >= 0) owner_of_row[aux[r]] = head[r];
     hm.fact_row.clear();
@@ -272,8 +375,45 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         hm.guess_row.push_back(hm.perm[bar_id[a]]);
       }
     }
+    // rule rows refer only to the leading section-A rows that have references
+    {
+      int32_t ng_atoms = 0;
+      while (ng_atoms < nA && deg[inv[ng_atoms]] > 0) ng_atoms++;
+      hm.n_sec_a = ng_atoms;
+    }
 
-    // ---- streamed layout (row descriptors, word headers, rule-row entries, stage groups)
+    hm.n = n;
+    hm.n_rules = n_rules;
+    hm.n_prime = np;
+    hm.n_pad = npad;
+    hm.nnz = nnz;
+    hm.n_barred = nb;
+    hm.n_aux = (int32_t)naux;
+    hm.k = (int32_t)hm.guess_row.size();
+    hm.n_fact_rows = (int32_t)hm.fact_row.size();
+    hm.n_rule_rows = n_rule_rows;
+    hm.n_or_rows = n_or_rows;
+    hm.canon_rule.assign(np, -1);
+#pragma omp parallel for schedule(static)
+    for (int32_t c = 0; c < np; c++)
+      if (kind[c] == K_RULE) hm.canon_rule[c] = row_rule[c];
+    hm.canon_kind.swap(kind);
+  } catch (const std::bad_alloc&) {
+    err = "host allocation failed in lp_compile";
+    return LP_ERR_OOM;
+  }
+  return LP_OK;
+}
+
+// Streamed layout of the least-model kernel (row descriptors, word headers, rule-row entries,
+// stage groups), from the internal CSR in hm.row_ptr / hm.col. Built on first use of that
+// kernel only.
+lp_status build_stream_layout(HostMatrix& hm, std::string& err) {
+  const int32_t np = hm.n_prime, npad = hm.n_pad, nA = hm.n + hm.n_barred;
+  std::vector<int32_t> inv(np);
+  for (int32_t c = 0; c < np; c++) inv[hm.perm[c]] = c;
+  const std::vector<int8_t>& kind = hm.canon_kind;
+  try {
     {
       const int32_t nw = npad / 32;
       hm.desc.assign(npad, 0u);
@@ -381,29 +521,10 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         w = w1;
       }
       hm.n_groups = (int32_t)(hm.groups.size() / kGroupInts);
-      // rule rows refer only to the leading section-A rows that have references
-      int32_t ng_atoms = 0;
-      while (ng_atoms < nA && deg[inv[ng_atoms]] > 0) ng_atoms++;
-      hm.n_sec_a = ng_atoms;
     }
 
-    hm.n = n;
-    hm.n_rules = n_rules;
-    hm.n_prime = np;
-    hm.n_pad = npad;
-    hm.nnz = nnz;
-    hm.n_barred = nb;
-    hm.n_aux = (int32_t)naux;
-    hm.k = (int32_t)hm.guess_row.size();
-    hm.n_fact_rows = (int32_t)hm.fact_row.size();
-    hm.n_rule_rows = n_rule_rows;
-    hm.n_or_rows = n_or_rows;
-    hm.canon_rule.assign(np, -1);
-    for (int32_t c = 0; c < np; c++)
-      if (kind[c] == K_RULE) hm.canon_rule[c] = (int32_t)row_rule[c];
-    hm.canon_kind.swap(kind);
   } catch (const std::bad_alloc&) {
-    err = "host allocation failed in lp_compile";
+    err = "host allocation failed building the streamed layout";
     return LP_ERR_OOM;
   }
   return LP_OK;

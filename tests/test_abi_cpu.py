@@ -150,3 +150,25 @@ def test_batch_entry_points_validate_without_gpu(lib):
     assert lib.lp_batch_info(None, None, None, None, None, None) == 1
     assert lib.lp_batch_stable_models(None, None, None, None, 10, None) == 1
     lib.lp_batch_free(None)
+
+
+@pytest.mark.parametrize("threads", ["1", "3"])
+def test_compile_is_independent_of_thread_count(lib, threads):
+    # the host compiler splits work by the team that runs it (one thread when lp_compile_batch
+    # runs it inside its own parallel loop): the matrix must not depend on it
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, oracle, paper_2009_10247_gb300 as lp\n"
+        "from workloads import large_definite, normal_program\n"
+        "for prog in [normal_program(seed=2, n=3000, n_rules=9000, k=6),\n"
+        "             large_definite(seed=2, n=20000, n_rules=100000, chain_levels=20, chain_width=10)]:\n"
+        "    with lp.Program.from_program(prog, host_only=True) as P:\n"
+        "        m = P.export_matrix()\n"
+        "    s = oracle.standardize(prog)\n"
+        "    assert np.array_equal(m['row_ptr'], s.row_ptr) and np.array_equal(m['col'], s.col)\n"
+        "print('ok')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, OMP_NUM_THREADS=threads, PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300, cwd=root)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr[-2000:]

@@ -38,6 +38,55 @@ constexpr int kRxPerLane = 8;  // batch values per lane per pass (256 columns pe
 
 __device__ __forceinline__ float rx_sigmoid(float z) { return 1.0f / (1.0f + __expf(-z)); }
 
+// A warp pass covers 256 batch columns, 8 per lane. Scalar layout (any b): slot k of a lane is
+// column c0 + 32 k + lane. Vector layout (b a multiple of 4, 16-byte aligned rows): slots
+// 4j..4j+3 are the float4 at column c0 + 128 j + 4 lane, so a warp moves 512 contiguous bytes
+// per load instruction.
+template <bool VEC>
+__device__ __forceinline__ int rx_col(int c0, int lane, int k) {
+  return VEC ? c0 + 128 * (k >> 2) + 4 * lane + (k & 3) : c0 + 32 * k + lane;
+}
+
+template <bool VEC>
+__device__ __forceinline__ void rx_load(const float* row, int c0, int lane, int b, float (&v)[kRxPerLane]) {
+  if (VEC) {
+#pragma unroll
+    for (int j = 0; j < kRxPerLane / 4; j++) {
+      const int cb = c0 + 128 * j + 4 * lane;
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (cb < b) q = *reinterpret_cast<const float4*>(row + cb);
+      v[4 * j] = q.x;
+      v[4 * j + 1] = q.y;
+      v[4 * j + 2] = q.z;
+      v[4 * j + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kRxPerLane; k++) {
+      const int c = c0 + 32 * k + lane;
+      v[k] = c < b ? row[c] : 0.f;
+    }
+  }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void rx_store(float* row, int c0, int lane, int b, const float (&v)[kRxPerLane]) {
+  if (VEC) {
+#pragma unroll
+    for (int j = 0; j < kRxPerLane / 4; j++) {
+      const int cb = c0 + 128 * j + 4 * lane;
+      if (cb < b) *reinterpret_cast<float4*>(row + cb) = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kRxPerLane; k++) {
+      const int c = c0 + 32 * k + lane;
+      if (c < b) row[c] = v[k];
+    }
+  }
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(kRxBlock) rx_forward_kernel(const int32_t* __restrict__ row_ptr,
                                                               const int32_t* __restrict__ col,
                                                               const int32_t* __restrict__ info,
@@ -60,35 +109,34 @@ __global__ void __launch_bounds__(kRxBlock) rx_forward_kernel(const int32_t* __r
       inv_m = 1.0f / (float)len;
     }
     for (int c0 = 0; c0 < b; c0 += 32 * kRxPerLane) {
-      float x[kRxPerLane];
+      float x[kRxPerLane], t[kRxPerLane];
 #pragma unroll
       for (int k = 0; k < kRxPerLane; k++) x[k] = 0.f;
       if ((kind == RX_RULE || kind == RX_OR) && len > 0) {
         for (int e = 0; e < len; e++) {
-          const float* src = vin + (size_t)__ldg(col + beg + e) * b;
+          rx_load<VEC>(vin + (size_t)__ldg(col + beg + e) * b, c0, lane, b, t);
 #pragma unroll
-          for (int k = 0; k < kRxPerLane; k++) {
-            const int c = c0 + 32 * k + lane;
-            if (c < b) x[k] += src[c];
-          }
+          for (int k = 0; k < kRxPerLane; k++) x[k] += t[k];
         }
+      } else if (kind == RX_SELF) {
+        rx_load<VEC>(vin + ro, c0, lane, b, x);
       }
 #pragma unroll
       for (int k = 0; k < kRxPerLane; k++) {
-        const int c = c0 + 32 * k + lane;
-        if (c >= b) continue;
         float u;
-        if (kind == RX_SELF) u = vin[ro + c];
+        if (kind == RX_SELF) u = x[k];
         else if (kind == RX_OR && len > 0) u = rx_sigmoid((x[k] - 0.5f) * inv_tau);
         else if (kind == RX_RULE && len > 0) u = rx_sigmoid(wr * (x[k] * inv_m - 1.0f + 0.5f * inv_m) * inv_tau);
         else u = 0.f;
-        vout[ro + c] = u;
+        t[k] = u;
       }
+      rx_store<VEC>(vout + ro, c0, lane, b, t);
     }
   }
 }
 
 // e_out = c * g * u (1 - u) for rule and OR rows; weight-gradient accumulation for rule rows.
+template <bool VEC>
 __global__ void __launch_bounds__(kRxBlock) rx_backward_rows_kernel(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ info,
     const int32_t* __restrict__ rule, const float* __restrict__ w, const float* __restrict__ vt,
@@ -109,28 +157,25 @@ __global__ void __launch_bounds__(kRxBlock) rx_backward_rows_kernel(
     const float coef = is_rule ? wr * inv_m * inv_tau : inv_tau;
     double dsum = 0.0;
     for (int c0 = 0; c0 < b; c0 += 32 * kRxPerLane) {
-      float x[kRxPerLane];
+      float x[kRxPerLane], t[kRxPerLane], u[kRxPerLane], g[kRxPerLane];
 #pragma unroll
       for (int k = 0; k < kRxPerLane; k++) x[k] = 0.f;
       if (is_rule) {  // the row sum again (for the weight gradient)
         for (int e = 0; e < len; e++) {
-          const float* src = vt + (size_t)__ldg(col + beg + e) * b;
+          rx_load<VEC>(vt + (size_t)__ldg(col + beg + e) * b, c0, lane, b, t);
 #pragma unroll
-          for (int k = 0; k < kRxPerLane; k++) {
-            const int c = c0 + 32 * k + lane;
-            if (c < b) x[k] += src[c];
-          }
+          for (int k = 0; k < kRxPerLane; k++) x[k] += t[k];
         }
       }
+      rx_load<VEC>(u_t1 + ro, c0, lane, b, u);
+      rx_load<VEC>(g1 + ro, c0, lane, b, g);
 #pragma unroll
       for (int k = 0; k < kRxPerLane; k++) {
-        const int c = c0 + 32 * k + lane;
-        if (c >= b) continue;
-        const float u = u_t1[ro + c];
-        const float e = g1[ro + c] * u * (1.0f - u);
-        e_out[ro + c] = coef * e;
-        if (is_rule) dsum += (double)e * (double)(x[k] * inv_m - 1.0f + 0.5f * inv_m);
+        const float e = g[k] * u[k] * (1.0f - u[k]);
+        t[k] = coef * e;
+        if (is_rule && rx_col<VEC>(c0, lane, k) < b) dsum += (double)e * (double)(x[k] * inv_m - 1.0f + 0.5f * inv_m);
       }
+      rx_store<VEC>(e_out + ro, c0, lane, b, t);
     }
     if (is_rule) {
 #pragma unroll
@@ -152,6 +197,7 @@ struct RxUnit {
 };
 constexpr int kRxFan = 32;  // children per tree node
 
+template <bool VEC>
 __global__ void __launch_bounds__(kRxBlock) rx_reduce_kernel(const RxUnit* __restrict__ units, int64_t n_units,
                                                              const int32_t* __restrict__ rowidx,
                                                              const float* __restrict__ src,
@@ -167,26 +213,20 @@ __global__ void __launch_bounds__(kRxBlock) rx_reduce_kernel(const RxUnit* __res
     const bool self = fin && (int)((unsigned)__ldg(info + un.j) >> 30) == RX_SELF;
     float* out = fin ? g0 + (size_t)un.j * b : part_out + (size_t)un.dst * b;
     for (int c0 = 0; c0 < b; c0 += 32 * kRxPerLane) {
-      float acc[kRxPerLane];
+      float acc[kRxPerLane], t[kRxPerLane];
+      if (self) {
+        rx_load<VEC>(g1 + (size_t)un.j * b, c0, lane, b, acc);
+      } else {
 #pragma unroll
-      for (int k = 0; k < kRxPerLane; k++) {
-        const int c = c0 + 32 * k + lane;
-        acc[k] = (self && c < b) ? g1[(size_t)un.j * b + c] : 0.f;
+        for (int k = 0; k < kRxPerLane; k++) acc[k] = 0.f;
       }
-      for (int t = 0; t < un.count; t++) {
-        const size_t r = rowidx ? (size_t)__ldg(rowidx + un.src + t) : (size_t)(un.src + t);
-        const float* row = src + r * b;
+      for (int q = 0; q < un.count; q++) {
+        const size_t r = rowidx ? (size_t)__ldg(rowidx + un.src + q) : (size_t)(un.src + q);
+        rx_load<VEC>(src + r * b, c0, lane, b, t);
 #pragma unroll
-        for (int k = 0; k < kRxPerLane; k++) {
-          const int c = c0 + 32 * k + lane;
-          if (c < b) acc[k] += row[c];
-        }
+        for (int k = 0; k < kRxPerLane; k++) acc[k] += t[k];
       }
-#pragma unroll
-      for (int k = 0; k < kRxPerLane; k++) {
-        const int c = c0 + 32 * k + lane;
-        if (c < b) out[c] = acc[k];
-      }
+      rx_store<VEC>(out, c0, lane, b, acc);
     }
   }
 }
@@ -326,6 +366,10 @@ lp_status rx_check(lp_program* p, int32_t b, int32_t steps, float tau, int32_t c
 
 lp_status rx_launched(cudaError_t e, lp_program* p) { return launch_count_and_check(e, "launch relaxed kernel", p); }
 
+// float4 row access: every [row][b] buffer the kernels touch starts at base + a multiple of
+// n_pad * b floats, so b % 4 == 0 and a 16-byte aligned base keep every row 16-byte aligned
+bool vec_rows(int32_t b, const void* base) { return b % 4 == 0 && ((uintptr_t)base & 15u) == 0; }
+
 }  // namespace
 }  // namespace lp
 
@@ -370,12 +414,17 @@ lp_status lp_relaxed_forward(lp_program* p, const float* weights, const float* v
   if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
   const float inv_tau = 1.0f / tau;
   const int rg = rx_grid(p, hm.n_pad);
+  const bool vec = vec_rows(batch, ckpt);
   float* cur = ckpt;
   for (int t = 0; t < steps; t++) {
     float* next = ((t + 1) % ckpt_every == 0 && t + 1 < steps) ? ckpt + (size_t)((t + 1) / ckpt_every) * nb
                                                                 : (cur == tmp0 ? tmp1 : tmp0);
-    rx_forward_kernel<<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights, cur, next,
-                                              hm.n_pad, batch, inv_tau);
+    if (vec)
+      rx_forward_kernel<true><<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights, cur, next,
+                                                      hm.n_pad, batch, inv_tau);
+    else
+      rx_forward_kernel<false><<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights, cur,
+                                                       next, hm.n_pad, batch, inv_tau);
     if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
     cur = next;
   }
@@ -406,6 +455,7 @@ lp_status lp_relaxed_backward(lp_program* p, const float* weights, const float* 
   const float inv_tau = 1.0f / tau;
   const int rg = rx_grid(p, hm.n_pad);
   const int eg = rx_grid(p, (int64_t)(nb + 31) / 32);
+  const bool vec = vec_rows(batch, ckpt) && vec_rows(batch, scratch);
   if ((st = ensure(p, p->rx_part, std::max<size_t>((size_t)p->rx_part_off.back() * batch * sizeof(float), 4))) !=
       LP_OK)
     return st;
@@ -418,16 +468,26 @@ lp_status lp_relaxed_backward(lp_program* p, const float* weights, const float* 
     const float* prev = ckpt + (size_t)c * nb;
     for (int t = t0; t < t1; t++) {  // recompute v_{t0+1} .. v_{t1}
       float* next = seg + (size_t)(t - t0) * nb;
-      rx_forward_kernel<<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights, prev, next,
-                                                hm.n_pad, batch, inv_tau);
+      if (vec)
+        rx_forward_kernel<true><<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights, prev,
+                                                        next, hm.n_pad, batch, inv_tau);
+      else
+        rx_forward_kernel<false><<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights, prev,
+                                                         next, hm.n_pad, batch, inv_tau);
       if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
       prev = next;
     }
     for (int t = t1 - 1; t >= t0; t--) {
       const float* vt = (t == t0) ? ckpt + (size_t)c * nb : seg + (size_t)(t - t0 - 1) * nb;
       const float* vt1 = seg + (size_t)(t - t0) * nb;
-      rx_backward_rows_kernel<<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights, vt, vt1,
-                                                      g, E, (double*)p->rx_dw.p, hm.n_pad, batch, inv_tau);
+      if (vec)
+        rx_backward_rows_kernel<true><<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights, vt,
+                                                              vt1, g, E, (double*)p->rx_dw.p, hm.n_pad, batch,
+                                                              inv_tau);
+      else
+        rx_backward_rows_kernel<false><<<rg, kRxBlock, 0, s>>>(p->row_ptr, p->col, p->rx_info, p->rx_rule, weights,
+                                                               vt, vt1, g, E, (double*)p->rx_dw.p, hm.n_pad, batch,
+                                                               inv_tau);
       if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
       float* gn = (g == G0) ? G1 : G0;
       // g_t = M^T E (+ g on self-loops), level by level; partial rows are numbered across all
@@ -438,8 +498,13 @@ lp_status lp_relaxed_backward(lp_program* p, const float* weights, const float* 
       for (int L = 0; L < n_levels; L++) {
         const int64_t u0 = p->rx_level_off[L], nu = p->rx_level_off[L + 1] - u0;
         if (nu == 0) continue;
-        rx_reduce_kernel<<<rx_grid(p, nu), kRxBlock, 0, s>>>(units + u0, nu, L == 0 ? p->rx_rowidx : nullptr,
-                                                             L == 0 ? E : part, part, p->rx_info, g, gn, batch);
+        if (vec)
+          rx_reduce_kernel<true><<<rx_grid(p, nu), kRxBlock, 0, s>>>(units + u0, nu, L == 0 ? p->rx_rowidx : nullptr,
+                                                                     L == 0 ? E : part, part, p->rx_info, g, gn, batch);
+        else
+          rx_reduce_kernel<false><<<rx_grid(p, nu), kRxBlock, 0, s>>>(units + u0, nu, L == 0 ? p->rx_rowidx : nullptr,
+                                                                      L == 0 ? E : part, part, p->rx_info, g, gn,
+                                                                      batch);
         if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
       }
       g = gn;

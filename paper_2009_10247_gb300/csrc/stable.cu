@@ -90,13 +90,23 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
         const int row = g * rows_per_warp + sub;
         const int beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
         const bool any = (__ldg(a.any_mask + (row >> 5)) >> (row & 31)) & 1u;
-        uint64_t acc = (end > beg) ? (any ? 0ull : ~0ull) : 0ull;
-        for (int e = beg; e < end; ++e) {
-          const uint64_t v = src[((long long)__ldg(a.col + e) << a.log2W) + wl];
-          acc = any ? (acc | v) : (acc & v);
-        }
+        const uint64_t ident = any ? 0ull : ~0ull;
+        uint64_t acc = (end > beg) ? ident : 0ull;
         const long long o = ((long long)row << a.log2W) + wl;
-        changed |= (acc != src[o]);
+        const uint64_t old = src[o];
+        // four entries per step: their column loads, then their gathers, so that a row costs
+        // two dependent memory latencies per four body atoms
+        for (int e = beg; e < end; e += 4) {
+          int cc[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++) cc[j] = e + j < end ? __ldg(a.col + e + j) : -1;
+          uint64_t vv[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++) vv[j] = cc[j] >= 0 ? src[((long long)cc[j] << a.log2W) + wl] : ident;
+          const uint64_t orv = vv[0] | vv[1] | vv[2] | vv[3], andv = vv[0] & vv[1] & vv[2] & vv[3];
+          acc = any ? (acc | orv) : (acc & andv);
+        }
+        changed |= (acc != old);
         dst[o] = acc;
       }
       const int any_changed = __syncthreads_or(changed);

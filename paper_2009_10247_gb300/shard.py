@@ -1,11 +1,12 @@
-"""Stable models sharded over ranks, one GPU per rank.
+"""Stable models and relaxed batches sharded over ranks, one GPU per rank.
 
 The 2^k guesses of Algorithm 2 are independent columns (Def. 8), so ranks take contiguous
 guess ranges and need no exchange while they iterate; the only collective is one gather of the
 stable masks at the end. Ranges start on multiples of 64 guesses, so each rank's mask words
 concatenate without shifting. Programs of a batch shard the same way (contiguous program
 ranges). The per-range solve runs in liblp (`Program.stable_models` on an explicit guess list);
-this module only splits ranges and gathers results.
+this module only splits ranges and gathers results. Relaxed batches split by columns; their
+rule-weight gradients meet in one all-reduce per backward pass.
 """
 from typing import Callable, Optional, Tuple
 
@@ -83,3 +84,20 @@ def _liblp_range(prog):
         return mask.cpu().numpy().view(np.uint64)
 
     return run
+
+
+def batch_range(batch: int, rank: int, world: int) -> Tuple[int, int]:
+    """[lo, hi) of rank's columns of a relaxed batch (contiguous, balanced)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank / world")
+    return batch * rank // world, batch * (rank + 1) // world
+
+
+def allreduce_weight_grad(dweights, group=None):
+    """Sum of the per-rank rule-weight gradients, in place on every rank: the weight gradient
+    is a sum over batch columns, so ranks that hold disjoint column ranges of one batch meet in
+    this single all-reduce per backward pass (the initial-vector gradients stay per rank)."""
+    import torch.distributed as dist
+
+    dist.all_reduce(dweights, op=dist.ReduceOp.SUM, group=group)
+    return dweights

@@ -84,3 +84,58 @@ def test_two_gloo_ranks_gather_the_full_mask(tmp_path):
     for r in range(2):
         got = np.load(tmp_path / f"mask{r}.npy")
         assert np.array_equal(got, want)
+
+
+def _relaxed_worker(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    from oracle.relaxed import RelaxedProgram
+    from paper_2009_10247_gb300.shard import allreduce_weight_grad, batch_range
+    from workloads import small_definite
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    R = RelaxedProgram(small_definite(4))
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.5, 1.5, R.n_rules)
+    v0 = rng.uniform(0.0, 1.0, (R.n_prime, 10))
+    c = rng.uniform(-1.0, 1.0, (R.n_prime, 10))
+    lo, hi = batch_range(10, rank, world)
+    vs = R.forward(w, v0[:, lo:hi], 8, 0.2)
+    dw, dv0 = R.backward(w, vs, c[:, lo:hi], 0.2)
+    t = torch.from_numpy(dw.copy())
+    allreduce_weight_grad(t)
+    np.save(os.path.join(out_dir, f"dw{rank}.npy"), t.numpy())
+    np.save(os.path.join(out_dir, f"dv{rank}.npy"), dv0)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_relaxed_columns_and_weight_allreduce(tmp_path):
+    import torch.multiprocessing as mp
+
+    from oracle.relaxed import RelaxedProgram
+    from workloads import small_definite
+
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_relaxed_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert all(p.exitcode == 0 for p in procs)
+    R = RelaxedProgram(small_definite(4))
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.5, 1.5, R.n_rules)
+    v0 = rng.uniform(0.0, 1.0, (R.n_prime, 10))
+    c = rng.uniform(-1.0, 1.0, (R.n_prime, 10))
+    dw, dv0 = R.backward(w, R.forward(w, v0, 8, 0.2), c, 0.2)
+    for r in range(2):
+        assert np.allclose(np.load(tmp_path / f"dw{r}.npy"), dw, rtol=1e-12, atol=1e-14)
+    assert np.allclose(np.concatenate([np.load(tmp_path / "dv0.npy"), np.load(tmp_path / "dv1.npy")], axis=1), dv0,
+                       rtol=1e-12, atol=1e-14)

@@ -181,7 +181,8 @@ lp_status lp_relaxed_forward(lp_program* prog, const float* weights, const float
 /* Adjoint of lp_relaxed_forward (same weights, batch, steps, tau, ckpt_every, and its ckpt):
  * given gT = dL/dv_steps (float [n'][b]), writes dweights = dL/dweights (float [n_rules]) and
  * dv0 = dL/dv0 (float [n'][b]). Each segment between checkpoints is recomputed from its
- * checkpoint into scratch (scratch_floats). Weight gradients are accumulated in double. */
+ * checkpoint into scratch (scratch_floats). Weight gradients are summed in float over each 256
+ * batch columns of a row and accumulated in double across those sums and the steps. */
 lp_status lp_relaxed_backward(lp_program* prog, const float* weights, const float* gT, int32_t batch, int32_t steps,
                               float tau, int32_t ckpt_every, const float* ckpt, float* scratch, float* dweights,
                               float* dv0, void* cuda_stream);

@@ -11,7 +11,8 @@
 // Batches of b vectors are stored row-major, [row][b] floats, so a row's b values are
 // contiguous: a warp handles one row and its lanes walk the batch, every gathered row is a
 // coalesced read. The adjoint of one step, with g = dL/dv_{t+1} and e = g u (1 - u):
-//   dL/dw_r += sum_batch e (x/m - 1 + 1/(2m)) / tau         (rule rows; double accumulators)
+//   dL/dw_r += sum_batch e (x/m - 1 + 1/(2m)) / tau         (rule rows; float per 256 columns,
+//                                                             double across passes and steps)
 //   dL/dv_t  = M^T (c e) + g on self-loop rows,  c = w_r/(m tau) (rule), 1/tau (OR)
 // where M^T is applied as a gather over a transposed copy (CSC) of the rule and OR rows. The
 // column lengths of that copy follow the skew of the body atoms (a popular atom sits in 1e5
@@ -155,9 +156,12 @@ __global__ void __launch_bounds__(kRxBlock) rx_backward_rows_kernel(
     const float inv_m = is_rule ? 1.0f / (float)len : 1.0f;
     const float wr = is_rule ? __ldg(w + __ldg(rule + i)) : 1.0f;
     const float coef = is_rule ? wr * inv_m * inv_tau : inv_tau;
+    // the row's weight gradient over the batch: float partial sums per 256-column pass (FP64
+    // arithmetic is scarce on this part), accumulated in double across passes and steps
     double dsum = 0.0;
     for (int c0 = 0; c0 < b; c0 += 32 * kRxPerLane) {
       float x[kRxPerLane], t[kRxPerLane], u[kRxPerLane], g[kRxPerLane];
+      float fsum = 0.0f;
 #pragma unroll
       for (int k = 0; k < kRxPerLane; k++) x[k] = 0.f;
       if (is_rule) {  // the row sum again (for the weight gradient)
@@ -173,15 +177,16 @@ __global__ void __launch_bounds__(kRxBlock) rx_backward_rows_kernel(
       for (int k = 0; k < kRxPerLane; k++) {
         const float e = g[k] * u[k] * (1.0f - u[k]);
         t[k] = coef * e;
-        if (is_rule && rx_col<VEC>(c0, lane, k) < b) dsum += (double)e * (double)(x[k] * inv_m - 1.0f + 0.5f * inv_m);
+        if (is_rule && rx_col<VEC>(c0, lane, k) < b) fsum += e * (x[k] * inv_m - 1.0f + 0.5f * inv_m);
       }
       rx_store<VEC>(e_out + ro, c0, lane, b, t);
-    }
-    if (is_rule) {
+      if (is_rule) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(FULL, dsum, o);
-      if (lane == 0) dw_row[i] += dsum * (double)inv_tau;
+        for (int o = 16; o > 0; o >>= 1) fsum += __shfl_xor_sync(FULL, fsum, o);
+        dsum += (double)fsum;
+      }
     }
+    if (is_rule && lane == 0) dw_row[i] += dsum * (double)inv_tau;
   }
 }
 

@@ -236,22 +236,30 @@ __global__ void __launch_bounds__(kRxBlock) rx_reduce_kernel(const RxUnit* __res
   }
 }
 
-// Canonical <-> internal row order of [row][b] arrays; internal padding rows are zero.
-__global__ void rx_to_internal_kernel(const float* __restrict__ src, float* __restrict__ dst,
-                                      const int32_t* __restrict__ inv, int n_prime, int n_pad, int b) {
-  const size_t total = (size_t)n_pad * b;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / b), c = (int)(t % b);
-    dst[t] = r < n_prime ? src[(size_t)__ldg(inv + r) * b + c] : 0.f;
-  }
-}
-
-__global__ void rx_to_canonical_kernel(const float* __restrict__ src, float* __restrict__ dst,
-                                       const int32_t* __restrict__ perm, int n_prime, int b) {
-  const size_t total = (size_t)n_prime * b;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(t / b), k = (int)(t % b);
-    dst[t] = src[(size_t)__ldg(perm + c) * b + k];
+// Canonical <-> internal row order of [row][b] arrays, one warp per destination row: row r of
+// dst is row map[r] of src (to internal: map = internal -> canonical, rows past n_src are zero;
+// to canonical: map = canonical -> internal).
+template <bool VEC>
+__global__ void __launch_bounds__(kRxBlock) rx_permute_rows_kernel(const float* __restrict__ src,
+                                                                   float* __restrict__ dst,
+                                                                   const int32_t* __restrict__ map, int n_src,
+                                                                   int n_dst, int b) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_dst; r += nwarps) {
+    const bool live = r < n_src;
+    const float* from = live ? src + (size_t)__ldg(map + r) * b : nullptr;
+    float* to = dst + (size_t)r * b;
+    for (int c0 = 0; c0 < b; c0 += 32 * kRxPerLane) {
+      float v[kRxPerLane];
+      if (live) {
+        rx_load<VEC>(from, c0, lane, b, v);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kRxPerLane; k++) v[k] = 0.f;
+      }
+      rx_store<VEC>(to, c0, lane, b, v);
+    }
   }
 }
 
@@ -414,12 +422,13 @@ lp_status lp_relaxed_forward(lp_program* p, const float* weights, const float* v
   const int n_ckpt = (steps + ckpt_every - 1) / ckpt_every;
   float* tmp0 = ckpt + (size_t)n_ckpt * nb;
   float* tmp1 = tmp0 + nb;
-  const int eg = rx_grid(p, (int64_t)(nb + 31) / 32);
-  rx_to_internal_kernel<<<eg, kRxBlock, 0, s>>>(v0, ckpt, p->inv, hm.n_prime, hm.n_pad, batch);
-  if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
   const float inv_tau = 1.0f / tau;
   const int rg = rx_grid(p, hm.n_pad);
   const bool vec = vec_rows(batch, ckpt);
+  const bool vec_io = vec && vec_rows(batch, v0) && vec_rows(batch, vT);
+  if (vec_io) rx_permute_rows_kernel<true><<<rg, kRxBlock, 0, s>>>(v0, ckpt, p->inv, hm.n_prime, hm.n_pad, batch);
+  else rx_permute_rows_kernel<false><<<rg, kRxBlock, 0, s>>>(v0, ckpt, p->inv, hm.n_prime, hm.n_pad, batch);
+  if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
   float* cur = ckpt;
   for (int t = 0; t < steps; t++) {
     float* next = ((t + 1) % ckpt_every == 0 && t + 1 < steps) ? ckpt + (size_t)((t + 1) / ckpt_every) * nb
@@ -433,7 +442,8 @@ lp_status lp_relaxed_forward(lp_program* p, const float* weights, const float* v
     if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
     cur = next;
   }
-  rx_to_canonical_kernel<<<eg, kRxBlock, 0, s>>>(cur, vT, p->perm, hm.n_prime, batch);
+  if (vec_io) rx_permute_rows_kernel<true><<<rg, kRxBlock, 0, s>>>(cur, vT, p->perm, hm.n_prime, hm.n_prime, batch);
+  else rx_permute_rows_kernel<false><<<rg, kRxBlock, 0, s>>>(cur, vT, p->perm, hm.n_prime, hm.n_prime, batch);
   return rx_launched(cudaGetLastError(), p);
 }
 
@@ -459,13 +469,14 @@ lp_status lp_relaxed_backward(lp_program* p, const float* weights, const float* 
   float* G1 = G0 + nb;
   const float inv_tau = 1.0f / tau;
   const int rg = rx_grid(p, hm.n_pad);
-  const int eg = rx_grid(p, (int64_t)(nb + 31) / 32);
   const bool vec = vec_rows(batch, ckpt) && vec_rows(batch, scratch);
   if ((st = ensure(p, p->rx_part, std::max<size_t>((size_t)p->rx_part_off.back() * batch * sizeof(float), 4))) !=
       LP_OK)
     return st;
   LP_CUDA(cudaMemsetAsync(p->rx_dw.p, 0, (size_t)hm.n_pad * sizeof(double), s));
-  rx_to_internal_kernel<<<eg, kRxBlock, 0, s>>>(gT, G0, p->inv, hm.n_prime, hm.n_pad, batch);
+  const bool vec_io = vec && vec_rows(batch, gT) && vec_rows(batch, dv0);
+  if (vec_io) rx_permute_rows_kernel<true><<<rg, kRxBlock, 0, s>>>(gT, G0, p->inv, hm.n_prime, hm.n_pad, batch);
+  else rx_permute_rows_kernel<false><<<rg, kRxBlock, 0, s>>>(gT, G0, p->inv, hm.n_prime, hm.n_pad, batch);
   if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
   float* g = G0;
   for (int c = n_ckpt - 1; c >= 0; c--) {
@@ -515,7 +526,8 @@ lp_status lp_relaxed_backward(lp_program* p, const float* weights, const float* 
       g = gn;
     }
   }
-  rx_to_canonical_kernel<<<eg, kRxBlock, 0, s>>>(g, dv0, p->perm, hm.n_prime, batch);
+  if (vec_io) rx_permute_rows_kernel<true><<<rg, kRxBlock, 0, s>>>(g, dv0, p->perm, hm.n_prime, hm.n_prime, batch);
+  else rx_permute_rows_kernel<false><<<rg, kRxBlock, 0, s>>>(g, dv0, p->perm, hm.n_prime, hm.n_prime, batch);
   if ((st = rx_launched(cudaGetLastError(), p)) != LP_OK) return st;
   LP_CUDA(cudaMemsetAsync(dweights, 0, (size_t)std::max<int64_t>(hm.n_rules, 0) * sizeof(float), s));
   rx_dw_out_kernel<<<rg, kRxBlock, 0, s>>>((const double*)p->rx_dw.p, p->rx_rule, dweights, hm.n_pad);

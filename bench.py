@@ -570,7 +570,11 @@ def bench_paper_tables(lp, torch, dev, reps=5):
             b.synchronize()
             ts.append(a.elapsed_time(b))
         gpu_ms = statistics.median(ts)
-        row = {"table": table, "no": no, "n": n, "m": m, "n_prime": P.info["n_prime"], "n_prime_paper": n_prime_paper,
+        # Eq. 5: 1 - (sum over rules of |body(r)|) / n^2
+        sparsity = 1.0 - len(prog.body_atom) / float(n) ** 2
+        row = {"table": table, "no": no, "n": n, "m": m, "sparsity": round(sparsity, 4),
+               "sparsity_paper": 0.95 if table in (3, 6) else 0.99, "n_prime": P.info["n_prime"],
+               "n_prime_paper": n_prime_paper,
                "nnz": P.info["nnz"], "gpu_ms": round(gpu_ms, 4), "e2e_ms": round(e2e_ms, 2),
                "paper_sparse_ms": paper_s * 1e3, "paper_over_gpu": round(paper_s * 1e3 / gpu_ms, 1)}
         sched = P.schedule

@@ -259,6 +259,9 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
 
     // ---- internal order
     std::vector<int32_t> inv(np);  // internal -> canonical
+    // bpos[i]: first section-B position (relative to nA) of the new atoms of the OR row at
+    // internal position i < nA; an OR row's entries are the run [nA + bpos[i], nA + bpos[i + 1])
+    std::vector<int64_t> bpos((size_t)nA + 1, 0);
     {
       // section A by descending references, ties by canonical id: unique keys, so any sort
       // gives the same order
@@ -271,7 +274,6 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
 #pragma omp parallel for schedule(static)
       for (int32_t i = 0; i < nA; i++) inv[i] = (int32_t)(key[i] & 0xffffffffu);
       // section B: each OR row's new atoms, OR rows in section-A order
-      std::vector<int64_t> bpos((size_t)nA + 1, 0);
       for (int32_t i = 0; i < nA; i++) {
         const int32_t c = inv[i];
         bpos[i + 1] = bpos[i] + (kind[c] == K_OR ? hr_off[c + 1] - hr_off[c] : 0);
@@ -299,29 +301,29 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     for (int32_t i = 0; i < np; i++) hm.row_ptr[i + 1] = (int32_t)row_len(inv[i]);
     for (int32_t i = 0; i < npad; i++) hm.row_ptr[i + 1] += hm.row_ptr[i];
     hm.col.assign((size_t)nnz, 0);
-#pragma omp parallel for schedule(dynamic, 2048)
-    for (int32_t i = 0; i < np; i++) {
-      int32_t c = inv[i];
+    // rule rows: walk the rules in order (sequential reads of the body sets) and scatter each
+    // body, mapped to internal ids and sorted, into its row
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t r = 0; r < n_rules; r++) {
+      if (setlen[r] == 0) continue;  // a fact: its row is a self-loop
+      const int32_t i = hm.perm[aux[r] >= 0 ? aux[r] : head[r]];
       int32_t* d = hm.col.data() + hm.row_ptr[i];
-      int64_t m = 0;
-      switch (kind[c]) {
-        case K_RULE: {
-          int64_t r = row_rule[c];
-          const int32_t* s = rb.data() + body_off[r];
-          for (int32_t t = 0; t < setlen[r]; t++) d[m++] = hm.perm[s[t]];
-          break;
-        }
-        case K_OR:
-          for (int64_t t = hr_off[c]; t < hr_off[c + 1]; t++) d[m++] = hm.perm[aux[rule_at(t)]];
-          break;
-        case K_FACT:
-        case K_BARRED:
-          d[m++] = i;
-          break;
-        default:
-          break;
+      const int32_t* sb = rb.data() + body_off[r];
+      for (int32_t t = 0; t < setlen[r]; t++) d[t] = hm.perm[sb[t]];
+      sort_small(d, setlen[r]);
+    }
+    // self-loop rows (facts, barred atoms) hold their own column
+#pragma omp parallel for schedule(static)
+    for (int32_t c = 0; c < np; c++)
+      if (kind[c] == K_FACT || kind[c] == K_BARRED) {
+        const int32_t i = hm.perm[c];
+        hm.col[hm.row_ptr[i]] = i;
       }
-      sort_small(d, m);
+    // OR rows: their new atoms sit consecutively in section B, in rule order
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int32_t i = 0; i < nA; i++) {
+      int32_t* d = hm.col.data() + hm.row_ptr[i];
+      for (int64_t t = bpos[i]; t < bpos[i + 1]; t++) *d++ = (int32_t)(nA + t);
     }
     hm.any_mask.assign((size_t)npad / 32, 0u);
 #pragma omp parallel for schedule(static)

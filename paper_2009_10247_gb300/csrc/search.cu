@@ -35,7 +35,7 @@ __device__ __forceinline__ uint64_t random_guess(uint64_t seed, int round, int c
   return splitmix64(splitmix64(seed ^ ((uint64_t)round << 32)) + (uint64_t)col) & kmask;
 }
 
-// Population of round 0.
+// Population of the first search round.
 __global__ void search_init_kernel(uint64_t* guess, uint64_t* prev, int P, uint64_t seed, uint64_t kmask) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P; c += gridDim.x * blockDim.x) {
     guess[c] = random_guess(seed, 0, c, kmask);

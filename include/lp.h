@@ -249,6 +249,8 @@ typedef struct {
                                      or 32 (capped at the guesses' words); 0 = the widest whose
                                      two iterate buffers fit 1 GiB                               */
   int32_t stable_blocks_per_sm;   /* stable models: resident CTAs per SM; 0 = all that fit      */
+  int32_t stable_row_split;       /* stable models: 1 = one row per warp, its entries split over
+                                     the warp's lane groups (long rows); 0 = 32 / W rows per warp */
 } lp_schedule;
 
 typedef struct {
@@ -276,7 +278,7 @@ lp_status lp_set_schedule(lp_program* prog, const lp_schedule* schedule);
  * candidates. Blocks the calling thread. Candidates: least model, kernel 0 with all / 4 / 2
  * CTAs per SM, kernel 0 with row splits 1, 2, 4, 8 and chunk batches 1, 4, and kernel 1 with
  * all / 1 CTAs per SM; stable
- * models, tile widths 1..32 with all / half the CTAs per SM.
+ * models, tile widths 1..32 with all / half the CTAs per SM, and each width with the row split.
  */
 lp_status lp_autotune(lp_program* prog, uint32_t what, int32_t reps, lp_tune_record* records, int32_t max_records,
                       int32_t* n_records, void* cuda_stream);

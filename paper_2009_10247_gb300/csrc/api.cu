@@ -439,13 +439,15 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   a.n_atom_words = atom_words;
   a.max_iters = max_iters;
   a.ctl = p->ctl;
-  static int occ = -1;
-  if (occ < 0) occ = stable_blocks_per_sm();
+  const bool split = p->sched.stable_row_split == 1;
+  static int occ_by_split[2] = {-1, -1};
+  int& occ = occ_by_split[split];
+  if (occ < 0) occ = stable_blocks_per_sm(split);
   if (occ <= 0) return fail(LP_ERR_CUDA, "stable kernel cannot be resident");
   const int per_sm = p->sched.stable_blocks_per_sm > 0 ? std::min(occ, p->sched.stable_blocks_per_sm) : occ;
   const int64_t rows_per_block = (int64_t)(kStableBlock / 32) * (32 / W);
   int grid = (int)std::min<int64_t>(max_coresident(p, per_sm), std::max<int64_t>(1, hm.n_pad / rows_per_block));
-  if ((st = launch_count_and_check(launch_stable(a, grid, s), "launch stable kernel", p)) != LP_OK) return st;
+  if ((st = launch_count_and_check(launch_stable(a, grid, split, s), "launch stable kernel", p)) != LP_OK) return st;
   LP_CUDA(cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s));
   if (host_mask) LP_CUDA(cudaMemcpyAsync(stable_mask, d_mask, (size_t)n_gwords * 8, cudaMemcpyDeviceToHost, s));
   if (host_models) LP_CUDA(cudaMemcpyAsync(models, d_models, (size_t)max_models * atom_words * 8, cudaMemcpyDeviceToHost, s));
@@ -476,6 +478,7 @@ lp_status lp_set_schedule(lp_program* p, const lp_schedule* in) {
   const int32_t X = in->fixpoint_chunk_batch;
   if (X != 0 && X != 1 && X != 4) return fail(LP_ERR_INVALID, "fixpoint_chunk_batch must be 0, 1 or 4");
   if (X == 4 && in->fixpoint_kernel != 0) return fail(LP_ERR_INVALID, "a chunk batch needs fixpoint_kernel 0");
+  if (in->stable_row_split != 0 && in->stable_row_split != 1) return fail(LP_ERR_INVALID, "stable_row_split must be 0 or 1");
   if (W < 0 || W > 32 || (W & (W - 1)) != 0) return fail(LP_ERR_INVALID, "stable_tile_words must be 0 or 1, 2, 4, 8, 16, 32");
   p->sched = *in;
   return LP_OK;

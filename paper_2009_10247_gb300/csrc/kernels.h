@@ -85,7 +85,8 @@ struct StableArgs {
 };
 
 constexpr int kStableBlock = 256;
-cudaError_t launch_stable(const StableArgs& a, int grid, cudaStream_t s);
-int stable_blocks_per_sm();
+// row_split: one row per warp, its entries split over the warp's 32 / W lane groups
+cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, cudaStream_t s);
+int stable_blocks_per_sm(bool row_split);
 
 }  // namespace lp

@@ -49,6 +49,10 @@ __device__ __forceinline__ uint64_t m0_word(int tag, long long gw, const StableA
   return w;
 }
 
+// SPLIT: a warp takes one row at a time and its 32 / W lane groups split the row's entries
+// (each group one word per lane), combining their partial AND / OR with shuffles; for long rows
+// (dense programs) this replaces one lane walking a whole row. With W = 32 both are the same.
+template <bool SPLIT>
 __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
   __shared__ int s_flag;
   __shared__ long long s_base;
@@ -86,6 +90,35 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
       const uint64_t* src = (it & 1) ? a.X1 : a.X0;
       uint64_t* dst = (it & 1) ? a.X0 : a.X1;
       bool changed = false;
+      if (SPLIT) {
+        const int S = 32 >> a.log2W;  // entry slots per warp
+        const int slot = lane >> a.log2W;
+        for (int row = gwarp; row < a.n_pad; row += nwarps) {
+          const int beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
+          const bool any = (__ldg(a.any_mask + (row >> 5)) >> (row & 31)) & 1u;
+          const uint64_t ident = any ? 0ull : ~0ull;
+          uint64_t acc = ident;
+          for (int e = beg + slot; e < end; e += 4 * S) {
+            int cc[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) cc[j] = e + j * S < end ? __ldg(a.col + e + j * S) : -1;
+            uint64_t vv[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) vv[j] = cc[j] >= 0 ? src[((long long)cc[j] << a.log2W) + wl] : ident;
+            acc = any ? (acc | vv[0] | vv[1] | vv[2] | vv[3]) : (acc & vv[0] & vv[1] & vv[2] & vv[3]);
+          }
+          for (int o = W; o < 32; o <<= 1) {  // combine the slots (lanes with the same word)
+            const uint64_t other = __shfl_xor_sync(FULL, acc, o);
+            acc = any ? (acc | other) : (acc & other);
+          }
+          if (end == beg) acc = 0ull;  // an empty row never fires
+          if (slot == 0) {
+            const long long o = ((long long)row << a.log2W) + wl;
+            changed |= (acc != src[o]);
+            dst[o] = acc;
+          }
+        }
+      } else
       for (int g = gwarp; g < n_groups; g += nwarps) {
         const int row = g * rows_per_warp + sub;
         const int beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
@@ -190,15 +223,17 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
   }
 }
 
-cudaError_t launch_stable(const StableArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, cudaStream_t s) {
   StableArgs copy = a;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)stable_kernel, dim3(grid), dim3(kStableBlock), params, 0, s);
+  const void* k = row_split ? (const void*)stable_kernel<true> : (const void*)stable_kernel<false>;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kStableBlock), params, 0, s);
 }
 
-int stable_blocks_per_sm() {
+int stable_blocks_per_sm(bool row_split) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stable_kernel, kStableBlock, 0) != cudaSuccess) return 0;
+  const void* k = row_split ? (const void*)stable_kernel<true> : (const void*)stable_kernel<false>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kStableBlock, 0) != cudaSuccess) return 0;
   return nb;
 }
 

@@ -79,14 +79,14 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     if ((st = ensure(p, p->tune_out, std::max<size_t>(out_bytes, 8))) != LP_OK) return st;
     uint64_t* out = (uint64_t*)p->tune_out.p;
     const int occ0 = fixpoint_blocks_per_sm(1, 1), occ1 = fixpoint_stream_blocks_per_sm();
-    const int32_t W0 = base.stable_tile_words, B0 = base.stable_blocks_per_sm;
+    const int32_t W0 = base.stable_tile_words, B0 = base.stable_blocks_per_sm, R0 = base.stable_row_split;
     std::vector<lp_schedule> cands;
     for (int b : {0, 4, 2})
-      if (b == 0 || b < occ0) cands.push_back({0, b, 1, 1, W0, B0});
-    for (int G : {2, 4, 8}) cands.push_back({0, 0, G, 1, W0, B0});
-    for (int G : {1, 2, 4, 8}) cands.push_back({0, 0, G, 4, W0, B0});
+      if (b == 0 || b < occ0) cands.push_back({0, b, 1, 1, W0, B0, R0});
+    for (int G : {2, 4, 8}) cands.push_back({0, 0, G, 1, W0, B0, R0});
+    for (int G : {1, 2, 4, 8}) cands.push_back({0, 0, G, 4, W0, B0, R0});
     for (int b : {0, 1})
-      if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back({1, b, 1, 1, W0, B0});
+      if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back({1, b, 1, 1, W0, B0, R0});
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
     for (const lp_schedule& c : cands) {
@@ -131,14 +131,17 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     }
     if ((st = ensure(p, p->tune_out, (size_t)n_gwords * 8)) != LP_OK) return st;
     uint64_t* mask = (uint64_t*)p->tune_out.p;
-    const int occ = stable_blocks_per_sm();
+    const int occ = stable_blocks_per_sm(false);
     std::vector<lp_schedule> cands;
     for (int W = 1; W <= 32; W *= 2) {
       if (W > 1 && W / 2 >= n_gwords) break;  // wider tiles than the guesses only repeat
       for (int b : {0, occ / 2})
         if (b == 0 || (b > 0 && b < occ))
           cands.push_back({best_least.fixpoint_kernel, best_least.fixpoint_blocks_per_sm, best_least.fixpoint_row_split,
-                           best_least.fixpoint_chunk_batch, W, b});
+                           best_least.fixpoint_chunk_batch, W, b, 0});
+      if (W < 32)  // with 32-word tiles the row split is the same mapping
+        cands.push_back({best_least.fixpoint_kernel, best_least.fixpoint_blocks_per_sm, best_least.fixpoint_row_split,
+                         best_least.fixpoint_chunk_batch, W, 0, 1});
     }
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
@@ -180,6 +183,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
   if (what & LP_TUNE_STABLE) {
     chosen.stable_tile_words = best_stable.stable_tile_words;
     chosen.stable_blocks_per_sm = best_stable.stable_blocks_per_sm;
+    chosen.stable_row_split = best_stable.stable_row_split;
   }
   p->sched = chosen;
   for (int32_t i = 0; i < max_records && i < (int32_t)recs.size(); i++) records[i] = recs[i];

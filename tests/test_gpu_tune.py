@@ -30,14 +30,17 @@ def test_least_model_every_schedule(kernel, bpsm, split, xn):
         assert it == want_it and np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("split", [0, 1])
 @pytest.mark.parametrize("W", [1, 2, 4, 8, 16, 32])
-def test_stable_models_every_tile_width(W):
-    prog = normal_program(seed=4, n=3000, n_rules=9000, k=12, per_atom=2)
-    st4, _, _ = oracle.stable_models_alg23(prog)
-    with lp.Program.from_program(prog) as P:
-        P.set_schedule(stable_tile_words=W, stable_blocks_per_sm=0 if W < 8 else 1)
-        st, _, ns = gpu_stable(P)
-    assert np.array_equal(st, st4) and ns == int(st4.sum())
+def test_stable_models_every_tile_width(W, split):
+    progs = [normal_program(seed=4, n=3000, n_rules=9000, k=12, per_atom=2),
+             table1_program(6101, 1000, 5000, dense=True, k=7)]
+    for prog in progs:
+        st4, _, _ = oracle.stable_models_alg23(prog)
+        with lp.Program.from_program(prog) as P:
+            P.set_schedule(stable_tile_words=W, stable_blocks_per_sm=0 if W < 8 else 1, stable_row_split=split)
+            st, _, ns = gpu_stable(P)
+        assert np.array_equal(st, st4) and ns == int(st4.sum())
 
 
 def test_autotune_keeps_fastest_and_stays_exact():

@@ -178,6 +178,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-paper-tables", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default schedules instead of lp_autotune's (for profiler captures: on the least-model and "
+                         "2^16-guess workloads the tuner picks the defaults)")
     ap.add_argument("--n-atoms", type=int, default=1_000_000,
                     help="atoms of the least-model workload (5 rules per atom); smaller for profiler captures")
     args = ap.parse_args()
@@ -212,7 +215,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    tuned = P.autotune(lp.LP_TUNE_LEAST, reps=2)  # the schedule the autotuner picks for this program
+    tuned = [] if args.no_tune else P.autotune(lp.LP_TUNE_LEAST, reps=2)  # the schedule the autotuner picks
     iters = P.least_model(out)  # checks status once, synchronously
     for _ in range(args.warmup):
         flush.zero_()
@@ -286,7 +289,7 @@ def main():
 
     secondary = batch = relaxed = None
     if not args.no_stable and rank == 0:
-        secondary = bench_stable(lp, torch, dev, flush)
+        secondary = bench_stable(lp, torch, dev, flush, tune=not args.no_tune)
     if not args.no_batch and rank == 0:
         batch = bench_batch(lp, torch, dev, flush)
     if not args.no_relaxed and rank == 0:
@@ -334,14 +337,15 @@ def main():
         dist.destroy_process_group()
 
 
-def bench_stable(lp, torch, dev, flush, steps=5):
+def bench_stable(lp, torch, dev, flush, steps=5, tune=True):
     """Batched stable models (Algorithms 2 + 3): all 2^16 guesses of the normal program."""
     prog = normal_program(seed=1)
     P = lp.Program.from_program(prog)
     k = P.info["k"]
     ng = 1 << k
     mask = torch.zeros(lp.words(ng), dtype=torch.int64, device=dev)
-    P.autotune(lp.LP_TUNE_STABLE, reps=2)
+    if tune:
+        P.autotune(lp.LP_TUNE_STABLE, reps=2)
     ns = P.stable_models(mask)
     stream = torch.cuda.current_stream()
     for _ in range(2):

@@ -45,6 +45,14 @@ inline void sort_small(int32_t* a, int64_t m) {
   }
 }
 
+inline int omp_max_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 // Sort of 64-bit keys, in parallel where libstdc++'s parallel mode is available.
 inline void parallel_sort(std::vector<uint64_t>& v) {
 #if defined(_OPENMP) && defined(__GLIBCXX__)
@@ -178,11 +186,43 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     // writes contiguous ranges.
     std::vector<int64_t> hr_off((size_t)n + 1, 0);
     for (int32_t a = 0; a < n; a++) hr_off[a + 1] = hr_off[a] + cnt[a];
-    std::vector<uint64_t> hk(n_rules);
-#pragma omp parallel for schedule(static)
-    for (int64_t r = 0; r < n_rules; r++) hk[r] = ((uint64_t)(uint32_t)head[r] << 32) | (uint64_t)r;
-    parallel_sort(hk);
-    auto rule_at = [&](int64_t t) -> int32_t { return (int32_t)(hk[t] & 0xffffffffu); };
+    // Rules grouped by head, in rule order within a head: a counting sort over contiguous rule
+    // ranges, one per thread (per-thread head counts, a scan over the threads per head, then
+    // each thread writes its range in order).
+    std::vector<int32_t> by_head(n_rules);
+    {
+      std::vector<int32_t> tcnt;
+      int nt = 1;
+#pragma omp parallel num_threads(std::min(16, std::max(1, omp_max_threads())))
+      {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#pragma omp single
+        nt = omp_get_num_threads();
+#endif
+#pragma omp single
+        tcnt.assign((size_t)nt * n, 0);
+        const int64_t r0 = n_rules * t / nt, r1 = n_rules * (t + 1) / nt;
+        int32_t* c = tcnt.data() + (size_t)t * n;
+        for (int64_t r = r0; r < r1; r++) c[head[r]]++;
+#pragma omp barrier
+#pragma omp for schedule(static)
+        for (int32_t a = 0; a < n; a++) {  // exclusive offsets of each thread within head a
+          int64_t off = hr_off[a];
+          for (int q = 0; q < nt; q++) {
+            const int32_t k = tcnt[(size_t)q * n + a];
+            tcnt[(size_t)q * n + a] = (int32_t)(off - hr_off[a]);
+            off += k;
+          }
+        }
+        for (int64_t r = r0; r < r1; r++) {
+          const int32_t h = head[r];
+          by_head[hr_off[h] + c[h]++] = (int32_t)r;
+        }
+      }
+    }
+    auto rule_at = [&](int64_t t) -> int32_t { return by_head[t]; };
     std::vector<int8_t> kind(np, K_EMPTY);
     std::vector<int32_t> row_rule(np, -1);  // rule defining a RULE/FACT row
 #pragma omp parallel for schedule(static)

@@ -127,3 +127,34 @@ def test_full_size_program_reduced_batch():
     assert np.max(np.abs(vT - vT_ref)) < 1e-3
     assert _rel(dw, dw_ref) < 1e-4
     assert _rel(dv0, dv0_ref) < 1e-4
+
+
+@pytest.mark.parametrize("b,T,ck", [(1, 1, 1), (1, 5, 100), (4, 1, 8), (7, 6, 6), (2, 9, 4)])
+def test_edge_sizes(b, T, ck):
+    # one column, one step, a checkpoint interval longer than the run, T a multiple of it
+    prog = small_definite(7)
+    R, w, v0, c, vT_ref, dw_ref, dv0_ref = _case(prog, 20 + T, b=b, T=T, tau=0.25)
+    vT, dw, dv0 = _run(prog, w, v0, c, T, 0.25, ck)
+    assert np.max(np.abs(vT - vT_ref)) < 1e-5
+    assert _rel(dw, dw_ref) < 1e-4
+    assert _rel(dv0, dv0_ref) < 1e-4
+
+
+def test_rejects_host_buffers_and_bad_arguments():
+    prog = small_definite(2)
+    with lp.Program.from_program(prog) as P:
+        n_prime = P.info["n_prime"]
+        ck, sc = P.relaxed_workspace(4, 8, 4)
+        w = torch.ones(len(prog.head), dtype=torch.float32, device=DEV)
+        v0 = torch.zeros((n_prime, 4), dtype=torch.float32, device=DEV)
+        ckpt = torch.empty(ck, dtype=torch.float32, device=DEV)
+        vT = torch.empty_like(v0)
+        with pytest.raises(lp.LPError):  # host input
+            P.relaxed_forward(w, v0.cpu().numpy(), 4, 8, 0.1, 4, ckpt, vT)
+        with pytest.raises(lp.LPError):  # tau must be positive
+            P.relaxed_forward(w, v0, 4, 8, 0.0, 4, ckpt, vT)
+        with pytest.raises(lp.LPError):  # at least one step
+            P.relaxed_forward(w, v0, 4, 0, 0.1, 4, ckpt, vT)
+        P.relaxed_forward(w, v0, 4, 8, 0.1, 4, ckpt, vT)  # still usable after the rejections
+        torch.cuda.synchronize()
+        assert torch.isfinite(vT).all()

@@ -98,7 +98,9 @@ typedef struct {
  * Arguments (host arrays, read only, copied): n_atoms >= 0; rules r in [0, n_rules) have
  * head[r] in [0, n_atoms) and body literals body_atom[body_off[r] .. body_off[r+1]) with
  * body_off[0] = 0 and body_off non-decreasing; body_neg (nullable) marks negated literals with
- * a non-zero byte. An empty body is a fact. n_prime and nnz must stay below 2^31.
+ * a non-zero byte. An empty body is a fact. n_rules, the body literals, n_prime and nnz must
+ * stay below 2^31. The host work runs on OpenMP threads; the matrix does not depend on their
+ * number.
  * flags: 0, or LP_COMPILE_HOST_ONLY (no device memory is touched; solves on such a handle return
  * LP_ERR_INVALID). cuda_stream: stream of the uploads. On success *out receives a new
  * handle (free it with lp_free). Errors: LP_ERR_INVALID (malformed program), LP_ERR_OOM,
@@ -237,9 +239,10 @@ void lp_batch_free(lp_batch* batch);
  * with all fields 0 (LP_FIXPOINT=stream in the environment makes fixpoint_kernel default to 1).
  */
 typedef struct {
-  int32_t fixpoint_kernel;        /* least model: 0 = one warp per 32-row output word, the word's
+  int32_t fixpoint_kernel;        /* least model: 0 = warps over 32-row output words, the words'
                                      entries in 32-entry chunks; 1 = rows streamed through shared
-                                     memory in bulk-copy stages                                   */
+                                     memory in bulk-copy stages (its layout is built from the
+                                     device matrix on first use, which downloads the CSR once)   */
   int32_t fixpoint_blocks_per_sm; /* least model: resident CTAs per SM; 0 = all that fit        */
   int32_t fixpoint_row_split;     /* least model, kernel 0: warps sharing one 32-row output word
                                      (1, 2, 4 or 8; 0 = 1): more for programs with long rows    */

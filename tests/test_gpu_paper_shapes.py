@@ -43,3 +43,25 @@ def test_largest_sparse_rows():
 def test_largest_dense_rows_in_the_benchmark():
     _least(table1_program(3008, 10000, 160000, dense=True))          # Table 3 row 8 (73M entries)
     _stable(table1_program(6006, 2000, 40000, dense=True, k=7))      # Table 6 row 6 (oracle cost)
+
+
+@pytest.mark.parametrize("nv,ne", [(65, 95), (28, 217), (77, 254)])
+def test_table4_graph_stand_ins(nv, ne):
+    # transitive closure of random digraphs with Table 4's node / edge counts: the oracle's
+    # least model, and path(x, y) true exactly when y is reachable from x in one or more edges
+    from workloads import transitive_closure_edges
+    prog = transitive_closure_edges(nv, ne, seed=4100 + nv)
+    _least(prog)
+    with lp.Program.from_program(prog) as P:
+        got, _ = gpu_least_model(P)
+    e = prog.meta["edges"]
+    adj = np.zeros((nv, nv), dtype=bool)
+    adj[e[:, 0], e[:, 1]] = True
+    reach = adj.copy()
+    for _ in range(nv):
+        nxt = reach | ((reach.astype(np.int32) @ adj.astype(np.int32)) > 0)
+        if np.array_equal(nxt, reach):
+            break
+        reach = nxt
+    E = len(e)
+    assert np.array_equal(got[E:].reshape(nv, nv), reach)

@@ -57,3 +57,15 @@ def test_standardized_size_close_to_paper(n, m, n_prime):
     # Table 2 prints n' for each (n, m); the generator's fact share is drawn, so allow 3 %
     s = oracle.standardize(table1_program(7, n, m))
     assert abs(s.n_prime - n_prime) / n_prime < 0.03
+
+
+def test_transitive_closure_edges_shape():
+    from workloads import transitive_closure_edges
+    for nv, ne in [(65, 95), (28, 217), (5, 20)]:
+        p = transitive_closure_edges(nv, ne, seed=3)
+        e = p.meta["edges"]
+        assert len(e) == min(ne, nv * (nv - 1))
+        assert len({(int(a), int(b)) for a, b in e}) == len(e)  # distinct
+        assert not np.any(e[:, 0] == e[:, 1])                   # no self-loops
+        assert p.n_atoms == len(e) + nv * nv
+        assert p.n_rules == 2 * len(e) + len(e) * nv            # facts, base rules, recursive rules

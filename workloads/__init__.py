@@ -11,6 +11,7 @@ from .programs import (  # noqa: F401
     small_definite,
     large_definite,
     transitive_closure,
+    transitive_closure_edges,
     normal_program,
     program_batch,
     table1_program,

@@ -207,8 +207,24 @@ def transitive_closure(n_nodes: int = 500, mean_outdeg: float = 4.0, seed: int =
         cand = np.where(cand >= x, cand + 1, cand)  # skip x itself
         src.extend([x] * d)
         dst.extend(sorted(cand.tolist()))
-    src = np.array(src, dtype=np.int64)
-    dst = np.array(dst, dtype=np.int64)
+    return _ground_closure(n_nodes, np.array(src, dtype=np.int64), np.array(dst, dtype=np.int64), seed)
+
+
+def transitive_closure_edges(n_nodes: int, n_edges: int, seed: int = 1) -> Program:
+    """The same grounding on a random digraph with exactly n_edges distinct edges (no
+    self-loops), drawn uniformly: a stand-in for a named graph of which only the node and edge
+    counts are known (the paper's Table 4)."""
+    rng = np.random.default_rng(seed)
+    n_edges = min(n_edges, n_nodes * (n_nodes - 1))
+    flat = rng.choice(n_nodes * (n_nodes - 1), size=n_edges, replace=False)
+    src = flat // (n_nodes - 1)
+    dst = flat % (n_nodes - 1)
+    dst = np.where(dst >= src, dst + 1, dst)
+    order = np.lexsort((dst, src))
+    return _ground_closure(n_nodes, src[order].astype(np.int64), dst[order].astype(np.int64), seed)
+
+
+def _ground_closure(n_nodes: int, src: np.ndarray, dst: np.ndarray, seed: int) -> Program:
     E = len(src)
     N = n_nodes
     n_atoms = E + N * N

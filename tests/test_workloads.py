@@ -69,3 +69,14 @@ def test_transitive_closure_edges_shape():
         assert not np.any(e[:, 0] == e[:, 1])                   # no self-loops
         assert p.n_atoms == len(e) + nv * nv
         assert p.n_rules == 2 * len(e) + len(e) * nv            # facts, base rules, recursive rules
+
+
+@pytest.mark.parametrize("nv,ne,n,m,n_prime", [(28, 217, 1512, 20629, 21924), (62, 159, 7564, 230861, 238266),
+                                               (77, 254, 11704, 445006, 456456)])
+def test_pair_grounding_reproduces_table4_sizes(nv, ne, n, m, n_prime):
+    # Table 4 prints n, m and n' per graph; grounding over all ordered pairs / triples of
+    # distinct nodes gives exactly those sizes
+    from workloads import transitive_closure_pairs
+    p = transitive_closure_pairs(nv, ne, seed=1)
+    assert (p.n_atoms, p.n_rules) == (n, m)
+    assert oracle.standardize(p).n_prime == n_prime

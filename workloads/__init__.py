@@ -12,6 +12,7 @@ from .programs import (  # noqa: F401
     large_definite,
     transitive_closure,
     transitive_closure_edges,
+    transitive_closure_pairs,
     normal_program,
     program_batch,
     table1_program,

@@ -224,6 +224,41 @@ def transitive_closure_edges(n_nodes: int, n_edges: int, seed: int = 1) -> Progr
     return _ground_closure(n_nodes, src[order].astype(np.int64), dst[order].astype(np.int64), seed)
 
 
+def transitive_closure_pairs(n_nodes: int, n_edges: int, seed: int = 1) -> Program:
+    """Transitive closure grounded over every ordered pair and triple of distinct nodes, the
+    grounding the paper's Table 4 sizes imply: atoms edge(x,y) and path(x,y) for all x != y
+    (n = 2 |V| (|V|-1)); facts edge(x,y) for the |E| edges of a uniform random digraph;
+    path(x,y) <- edge(x,y) for all x != y; path(x,y) <- edge(x,z) & path(z,y) for all distinct
+    x, z, y. Atom ids: edge(x,y) -> pair(x,y), path(x,y) -> |V|(|V|-1) + pair(x,y), pairs in
+    row-major order skipping x = y."""
+    rng = np.random.default_rng(seed)
+    N = n_nodes
+    NP = N * (N - 1)
+    n_edges = min(n_edges, NP)
+    flat = np.sort(rng.choice(NP, size=n_edges, replace=False))  # edge = pair index
+    src = flat // (N - 1)
+    dst = flat % (N - 1)
+    dst = np.where(dst >= src, dst + 1, dst)
+
+    def pair(x, y):  # x != y
+        return x * (N - 1) + np.where(y > x, y - 1, y)
+
+    x, z, y = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    keep = (x != z) & (z != y) & (x != y)
+    x, z, y = x[keep], z[keep], y[keep]
+    px, py = np.repeat(np.arange(N), N - 1), None
+    py = np.array([v for u in range(N) for v in range(N) if v != u], dtype=np.int64)
+    base_heads = NP + pair(px, py)
+    heads = [flat, base_heads, NP + pair(x, y)]
+    lens = [np.zeros(n_edges, np.int64), np.ones(NP, np.int64), np.full(len(x), 2, np.int64)]
+    rec = np.empty(2 * len(x), dtype=np.int64)
+    rec[0::2] = pair(x, z)
+    rec[1::2] = NP + pair(z, y)
+    atoms = [pair(px, py), rec]
+    return _pack(2 * NP, np.concatenate(heads), np.concatenate(lens), np.concatenate(atoms),
+                 name="transitive_closure_pairs", seed=seed, n_nodes=N, edges=np.stack([src, dst], 1))
+
+
 def _ground_closure(n_nodes: int, src: np.ndarray, dst: np.ndarray, seed: int) -> Program:
     E = len(src)
     N = n_nodes

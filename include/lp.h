@@ -365,6 +365,19 @@ lp_status lp_least_model_static(int32_t n_rows, const int32_t* row_ptr, const in
  * must make sure no enqueued work still uses it. */
 void lp_free(lp_program* prog);
 
+/* Diagnostics, no counterpart in the paper: checks the invariants the kernels rely on without
+ * re-checking them per access -- row pointers start at 0, never decrease and end at nnz; every
+ * column index is a row of the matrix; every fact row is a self-loop -- on the device copy
+ * (a small kernel; waits for cuda_stream) or, for an LP_COMPILE_HOST_ONLY handle, on the host
+ * copy. *n_bad (host) receives the number of violations (0 for every matrix lp_compile builds). */
+lp_status lp_check_matrix(const lp_program* prog, int64_t* n_bad, void* cuda_stream);
+
+/* Test hook, no counterpart in the paper: after `after` more successful device allocations by
+ * liblp, the next one fails (once) as if the device were out of memory, so that the
+ * LP_ERR_OOM paths of every call can be exercised without exhausting a GPU. -1 turns it off.
+ * Process-wide; not for concurrent use with other liblp calls. */
+void lp_debug_fail_alloc(int64_t after);
+
 /* Message of the last failed call on this thread ("" if none). Valid until the next call. */
 const char* lp_last_error(void);
 

@@ -42,6 +42,24 @@ lp_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 
+namespace {
+std::atomic<int64_t> g_fail_alloc_after{-1};  // lp_debug_fail_alloc: -1 = off
+}
+
+cudaError_t device_malloc(void** ptr, size_t bytes) {
+  int64_t left = g_fail_alloc_after.load();
+  while (left >= 0) {
+    if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+      if (left == 0) {  // this allocation is the one that fails (once)
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
 lp_status ensure(lp_program* p, DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return LP_OK;
   if (b.p) {
@@ -50,7 +68,7 @@ lp_status ensure(lp_program* p, DevBuf& b, size_t bytes) {
     b.p = nullptr;
     b.bytes = 0;
   }
-  cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 16));
+  cudaError_t e = device_malloc(&b.p, std::max<size_t>(bytes, 16));
   if (e != cudaSuccess) {
     cudaGetLastError();
     b.p = nullptr;
@@ -127,11 +145,14 @@ extern "C" {
 
 const char* lp_last_error(void) { return g_err.c_str(); }
 
+void lp_debug_fail_alloc(int64_t after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
+
 int64_t lp_launch_count(void) { return g_launches.load(); }
 
 lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, const int64_t* body_off,
                      const int32_t* body_atom, const uint8_t* body_neg, uint32_t flags, void* cuda_stream,
                      lp_program** out) {
+  NvtxRange nvtx("lp_compile");
   if (!out) return fail(LP_ERR_INVALID, "out must not be NULL");
   *out = nullptr;
   if (flags & ~LP_COMPILE_HOST_ONLY) return fail(LP_ERR_INVALID, "unknown flags");
@@ -143,7 +164,11 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   }
   if (!p) return fail(LP_ERR_OOM, "host allocation failed");
   std::string err;
-  lp_status st = compile_host(n_atoms, n_rules, head, body_off, body_atom, body_neg, p->hm, err);
+  lp_status st;
+  {
+    NvtxRange nvtx_host("lp_compile: standardize");
+    st = compile_host(n_atoms, n_rules, head, body_off, body_atom, body_neg, p->hm, err);
+  }
   if (st != LP_OK) {
     delete p;
     return fail(st, err);
@@ -239,6 +264,7 @@ lp_status ensure_stream_layout(lp_program* p, cudaStream_t s) {
 
 lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int32_t max_iters, uint32_t flags,
                          int32_t* iters_out, void* cuda_stream) {
+  NvtxRange nvtx("lp_least_model");
   if (!p || !out) return fail(LP_ERR_INVALID, "program and out must not be NULL");
   if (p->host_only) return fail(LP_ERR_INVALID, "program was compiled with LP_COMPILE_HOST_ONLY");
   if (max_iters < 1) return fail(LP_ERR_INVALID, "max_iters must be >= 1");
@@ -343,6 +369,7 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
 lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_guesses, uint64_t* stable_mask,
                            uint64_t* models, int64_t max_models, int64_t* n_stable_out, int32_t max_iters,
                            void* cuda_stream) {
+  NvtxRange nvtx("lp_stable_models");
   if (!p) return fail(LP_ERR_INVALID, "program must not be NULL");
   if (p->host_only) return fail(LP_ERR_INVALID, "program was compiled with LP_COMPILE_HOST_ONLY");
   if (max_iters < 1) return fail(LP_ERR_INVALID, "max_iters must be >= 1");

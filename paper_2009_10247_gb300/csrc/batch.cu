@@ -332,7 +332,7 @@ void batch_release(lp_batch* b) {
 template <typename T>
 lp_status bupload(lp_batch* b, T** ptr, const T* src, size_t count, cudaStream_t s) {
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  cudaError_t e = device_malloc((void**)ptr, bytes);
   if (e != cudaSuccess) {
     *ptr = nullptr;
     cudaGetLastError();
@@ -354,6 +354,7 @@ extern "C" {
 lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int64_t* rule_off, const int32_t* head,
                            const int64_t* body_off, const int32_t* body_atom, const uint8_t* body_neg, uint32_t flags,
                            void* cuda_stream, lp_batch** out) {
+  NvtxRange nvtx("lp_compile_batch");
   if (!out) return bfail(LP_ERR_INVALID, "out must not be NULL");
   *out = nullptr;
   if (flags != 0) return bfail(LP_ERR_INVALID, "flags must be 0");
@@ -528,6 +529,7 @@ lp_status lp_batch_program_info(const lp_batch* b, int32_t program, lp_info* inf
 
 lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_stable, int32_t* iters,
                                  int32_t max_iters, void* cuda_stream) {
+  NvtxRange nvtx("lp_batch_stable_models");
   if (!b) return bfail(LP_ERR_INVALID, "NULL batch");
   if (!stable_mask) return bfail(LP_ERR_INVALID, "stable_mask must not be NULL");
   if (max_iters < 1) return bfail(LP_ERR_INVALID, "max_iters must be >= 1");

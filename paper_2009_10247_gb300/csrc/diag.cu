@@ -1,8 +1,11 @@
-// diag.cu -- lp_check_grid_barrier (include/lp.h): the bounded grid barrier that every
-// persistent kernel of liblp uses, run alone, so that its failure path (a block that never
-// arrives) can be exercised without faulting or hanging the GPU.
+// diag.cu -- diagnostics (include/lp.h): lp_check_grid_barrier runs the bounded grid barrier
+// that every persistent kernel of liblp uses alone, so that its failure path (a block that
+// never arrives) can be exercised without faulting or hanging the GPU; lp_check_matrix checks
+// the invariants of a compiled matrix on the device (the kernels rely on them and do not
+// re-check them per access).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <string>
 
@@ -66,4 +69,61 @@ extern "C" lp_status lp_check_grid_barrier(int32_t blocks, int32_t absent, int32
   if (b) cudaEventDestroy(b);
   cudaFree(ctl);
   return st;
+}
+
+namespace lp {
+
+// Invariants of a compiled matrix: row_ptr starts at 0, never decreases and ends at nnz;
+// every column is a row of the matrix; every fact row is a self-loop (one entry, its own row).
+__global__ void matrix_check_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                    int32_t n_pad, int64_t nnz, const int32_t* __restrict__ fact_row,
+                                    int32_t n_facts, unsigned long long* bad) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  unsigned long long b = 0;
+  if (tid == 0) b += (row_ptr[0] != 0) + ((long long)row_ptr[n_pad] != nnz);
+  for (long long r = tid; r < n_pad; r += nth) b += row_ptr[r + 1] < row_ptr[r];
+  for (long long e = tid; e < nnz; e += nth) b += (unsigned)col[e] >= (unsigned)n_pad;
+  for (long long f = tid; f < n_facts; f += nth) {
+    const int32_t r = fact_row[f];
+    const bool ok = r >= 0 && r < n_pad && row_ptr[r + 1] - row_ptr[r] == 1 && col[row_ptr[r]] == r;
+    b += !ok;
+  }
+  if (b) atomicAdd(bad, b);
+}
+
+}  // namespace lp
+
+extern "C" lp_status lp_check_matrix(const lp_program* p, int64_t* n_bad, void* cuda_stream) {
+  if (!p || !n_bad) return fail(LP_ERR_INVALID, "NULL argument");
+  const HostMatrix& hm = p->hm;
+  if (p->host_only) {  // the host copy is kept: check it on the host
+    int64_t bad = (hm.row_ptr.empty() || hm.row_ptr[0] != 0) + ((int64_t)hm.row_ptr.back() != hm.nnz);
+    for (int32_t r = 0; r < hm.n_pad; r++) bad += hm.row_ptr[r + 1] < hm.row_ptr[r];
+    for (int64_t e = 0; e < hm.nnz; e++) bad += (unsigned)hm.col[e] >= (unsigned)hm.n_pad;
+    for (int32_t r : hm.fact_row)
+      bad += !(r >= 0 && r < hm.n_pad && hm.row_ptr[r + 1] - hm.row_ptr[r] == 1 && hm.col[hm.row_ptr[r]] == r);
+    *n_bad = bad;
+    return LP_OK;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned long long* d_bad = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d_bad, sizeof(unsigned long long));
+  if (e != cudaSuccess) return fail(LP_ERR_OOM, "cudaMalloc");
+  unsigned long long h_bad = 0;
+  if ((e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), s)) == cudaSuccess) {
+    const int blocks = (int)std::min<long long>(1024, std::max<long long>(1, (hm.nnz + 255) / 256));
+    matrix_check_kernel<<<blocks, 256, 0, s>>>(p->row_ptr, p->col, hm.n_pad, hm.nnz, p->fact_row, hm.n_fact_rows,
+                                                d_bad);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      count_launches(1);
+      if ((e = cudaMemcpyAsync(&h_bad, d_bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s)) == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    }
+  }
+  cudaFree(d_bad);
+  if (e != cudaSuccess) return fail(LP_ERR_CUDA, cudaGetErrorString(e));
+  *n_bad = (int64_t)h_bad;
+  return LP_OK;
 }

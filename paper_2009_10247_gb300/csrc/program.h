@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <string>
@@ -80,10 +81,23 @@ void count_launches(int64_t n);  // add to lp_launch_count()
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
+// cudaMalloc behind the allocation-failure hook (lp_debug_fail_alloc): every device allocation
+// of liblp's handles goes through here.
+cudaError_t device_malloc(void** ptr, size_t bytes);
+
+// NVTX range for the duration of a scope (shows liblp's calls in a profiler's timeline; free
+// when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 template <typename T>
 lp_status dalloc(lp_program* p, T** ptr, size_t count) {
   size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  cudaError_t e = device_malloc((void**)ptr, bytes);
   if (e != cudaSuccess) {
     *ptr = nullptr;
     cudaGetLastError();

@@ -403,6 +403,7 @@ lp_status lp_relaxed_workspace(lp_program* p, int32_t batch, int32_t steps, int3
 
 lp_status lp_relaxed_forward(lp_program* p, const float* weights, const float* v0, int32_t batch, int32_t steps,
                              float tau, int32_t ckpt_every, float* ckpt, float* vT, void* cuda_stream) {
+  NvtxRange nvtx("lp_relaxed_forward");
   lp_status st = rx_check(p, batch, steps, tau, ckpt_every);
   if (st != LP_OK) return st;
   if (!weights || !v0 || !ckpt || !vT) return fail(LP_ERR_INVALID, "NULL buffer");
@@ -450,6 +451,7 @@ lp_status lp_relaxed_forward(lp_program* p, const float* weights, const float* v
 lp_status lp_relaxed_backward(lp_program* p, const float* weights, const float* gT, int32_t batch, int32_t steps,
                               float tau, int32_t ckpt_every, const float* ckpt, float* scratch, float* dweights,
                               float* dv0, void* cuda_stream) {
+  NvtxRange nvtx("lp_relaxed_backward");
   lp_status st = rx_check(p, batch, steps, tau, ckpt_every);
   if (st != LP_OK) return st;
   if (!weights || !gT || !ckpt || !scratch || !dweights || !dv0) return fail(LP_ERR_INVALID, "NULL buffer");

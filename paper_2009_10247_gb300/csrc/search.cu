@@ -82,6 +82,7 @@ using namespace lp;
 
 extern "C" lp_status lp_stable_search(lp_program* p, int32_t population, int32_t rounds, uint64_t seed,
                                       uint64_t* found, int64_t max_found, int64_t* n_found, void* cuda_stream) {
+  NvtxRange nvtx("lp_stable_search");
   if (!p) return fail(LP_ERR_INVALID, "program must not be NULL");
   if (p->host_only) return fail(LP_ERR_INVALID, "program was compiled with LP_COMPILE_HOST_ONLY");
   if (population < 1 || population > 2048) return fail(LP_ERR_INVALID, "population must be in [1, 2048]");

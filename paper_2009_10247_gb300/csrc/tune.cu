@@ -62,6 +62,7 @@ using namespace lp;
 
 extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_tune_record* records,
                                  int32_t max_records, int32_t* n_records, void* cuda_stream) {
+  NvtxRange nvtx("lp_autotune");
   if (!p) return fail(LP_ERR_INVALID, "program must not be NULL");
   if (p->host_only) return fail(LP_ERR_INVALID, "program was compiled with LP_COMPILE_HOST_ONLY");
   if (what == 0 || (what & ~(LP_TUNE_LEAST | LP_TUNE_STABLE))) return fail(LP_ERR_INVALID, "unknown tune flags");

@@ -40,7 +40,7 @@ EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models"
            "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static",
            "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward", "lp_compile_batch", "lp_batch_info",
            "lp_batch_program_info", "lp_batch_stable_models", "lp_batch_free", "lp_get_schedule", "lp_set_schedule",
-           "lp_autotune", "lp_stable_search", "lp_check_grid_barrier"]
+           "lp_autotune", "lp_stable_search", "lp_check_grid_barrier", "lp_check_matrix", "lp_debug_fail_alloc"]
 
 LP_TUNE_LEAST = 1
 LP_TUNE_STABLE = 2
@@ -98,7 +98,11 @@ def load(build_if_missing: bool = False):
     L.lp_autotune.argtypes = [P, u32, i32, ctypes.POINTER(_TuneRecord), i32, ctypes.POINTER(i32), P]
     L.lp_stable_search.argtypes = [P, i32, i32, ctypes.c_uint64, P, i64, ctypes.POINTER(i64), P]
     L.lp_check_grid_barrier.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), P]
-    for name in ("lp_get_schedule", "lp_set_schedule", "lp_autotune", "lp_stable_search", "lp_check_grid_barrier"):
+    L.lp_check_matrix.argtypes = [P, ctypes.POINTER(i64), P]
+    L.lp_debug_fail_alloc.argtypes = [i64]
+    L.lp_debug_fail_alloc.restype = None
+    for name in ("lp_get_schedule", "lp_set_schedule", "lp_autotune", "lp_stable_search", "lp_check_grid_barrier",
+                 "lp_check_matrix"):
         getattr(L, name).restype = ctypes.c_int
     L.lp_least_model_static.argtypes = [i32, P, P, P, P, P, i32, ctypes.POINTER(i32), P]
     L.lp_least_model_static.restype = ctypes.c_int
@@ -161,6 +165,11 @@ def check_grid_barrier(blocks, absent, limit_us, stream=None):
     _check(load().lp_check_grid_barrier(int(blocks), int(absent), int(limit_us), ctypes.byref(st), ctypes.byref(ms),
                                         _stream(stream)))
     return st.value, ms.value
+
+
+def debug_fail_alloc(after: int) -> None:
+    """lp_debug_fail_alloc: the allocation after `after` more successful ones fails (once); -1 = off."""
+    load().lp_debug_fail_alloc(int(after))
 
 
 def launch_count() -> int:
@@ -275,6 +284,12 @@ class Program:
         _check(load().lp_stable_search(self._h, int(population), int(rounds), ctypes.c_uint64(seed), _ptr(out),
                                        int(max_found), ctypes.byref(n), _stream(stream)))
         return out[:min(n.value, int(max_found))], n.value
+
+    def check_matrix(self, stream=None) -> int:
+        """lp_check_matrix: number of violated invariants of the compiled matrix (0 expected)."""
+        n = ctypes.c_int64()
+        _check(load().lp_check_matrix(self._h, ctypes.byref(n), _stream(stream)))
+        return n.value
 
     def last_stats(self, stream=None):
         s = _Stats()

@@ -173,3 +173,12 @@ def test_compile_is_independent_of_thread_count(lib, threads):
     env = dict(os.environ, OMP_NUM_THREADS=threads, PYTHONPATH=root)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300, cwd=root)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr[-2000:]
+
+
+def test_check_matrix_on_host_copies(lib):
+    progs = [small_definite(1), normal_program(seed=3, n=2000, n_rules=6000, k=6),
+             transitive_closure(30, 2.0, 1)] + [tiny_random(800 + s, n_atoms=20, n_rules=40, p_neg=0.1)
+                                                for s in range(10)]
+    for prog in progs:
+        with lp.Program.from_program(prog, host_only=True) as P:
+            assert P.check_matrix() == 0

@@ -32,9 +32,6 @@ from workloads import (large_definite, normal_program, program_batch, table1_pro
                        transitive_closure_pairs)
 
 METRIC = "fixpoint rule-evals/sec (nnz x iters / s)"
-# the schedule the recorded ncu traffic of the least-model kernel was taken with
-DEFAULT_SCHEDULE = {"fixpoint_kernel": 0, "fixpoint_blocks_per_sm": 0, "fixpoint_row_split": 1, "fixpoint_chunk_batch": 1,
-                    "stable_tile_words": 0, "stable_blocks_per_sm": 0}
 UNIT = "rule-evals/s"
 WORKLOAD = "large definite program: 1e6 atoms, 5e6 rules, Geom(mean 3, cap 8) bodies, Zipf(1.1) atoms, 1% facts, chain 1000x50 (seed 1)"
 WORKLOAD_STABLE = "normal program: 1e5 atoms, 3e5 rules, bodies U{1..6}, 1% facts, k=16 negated atoms x 4 (seed 1), all 65536 guesses"
@@ -54,20 +51,37 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the kernel
-    sources as they are now (else None: the counters are stale)."""
+def _least_fields(sched):
+    """The least-model fields of a schedule, with 0 read as the default it stands for."""
+    return {"fixpoint_kernel": sched["fixpoint_kernel"], "fixpoint_row_split": max(1, sched["fixpoint_row_split"]),
+            "fixpoint_chunk_batch": max(1, sched["fixpoint_chunk_batch"]), "fixpoint_row_map": sched["fixpoint_row_map"]}
+
+
+def measured_traffic(kernel, sched=None):
+    """DRAM bytes per launch from the committed ncu summaries: the record of `kernel` taken on
+    the kernel sources as they are now and, for the least-model kernel, under the same schedule
+    (None if there is none: the counters are stale or belong to another variant)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f)[kernel]
-        h = hashlib.sha256()
-        for src in rec["sources"]:
-            with open(os.path.join(ROOT, src), "rb") as f:
-                h.update(f.read())
-        return rec["bytes_per_launch"] if h.hexdigest()[:16] == rec["source_sha"] else None
+            recs = json.load(f)
     except Exception:
         return None
+    for name, rec in recs.items():
+        if rec.get("kernel", name) != kernel:
+            continue
+        if sched is not None and rec.get("schedule_fields") != _least_fields(sched):
+            continue
+        try:
+            h = hashlib.sha256()
+            for src in rec["sources"]:
+                with open(os.path.join(ROOT, src), "rb") as f:
+                    h.update(f.read())
+        except OSError:
+            continue
+        if h.hexdigest()[:16] == rec["source_sha"]:
+            return rec["bytes_per_launch"]
+    return None
 
 
 def alg_bytes_per_iter(n_prime, nnz):
@@ -204,6 +218,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="default schedules instead of lp_autotune's (for profiler captures: on the least-model and "
                          "2^16-guess workloads the tuner picks the defaults)")
+    ap.add_argument("--schedule", default="",
+                    help="pin the least-model schedule instead of tuning it: comma-separated lp_schedule "
+                         "field=value pairs, e.g. fixpoint_row_map=1 (for profiler captures of one variant)")
     ap.add_argument("--n-atoms", type=int, default=1_000_000,
                     help="atoms of the least-model workload (5 rules per atom); smaller for profiler captures")
     args = ap.parse_args()
@@ -238,7 +255,11 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    tuned = [] if args.no_tune else P.autotune(lp.LP_TUNE_LEAST, reps=2)  # the schedule the autotuner picks
+    if args.schedule:
+        P.set_schedule(**{k: int(v) for k, v in (kv.split("=") for kv in args.schedule.split(","))})
+        tuned = []
+    else:
+        tuned = [] if args.no_tune else P.autotune(lp.LP_TUNE_LEAST, reps=2)  # the schedule the autotuner picks
     iters = P.least_model(out)  # checks status once, synchronously
     for _ in range(args.warmup):
         flush.zero_()
@@ -342,7 +363,7 @@ def main():
                        "l2": "flushed before every step (256 MiB write)", "wall_s": round(wall, 3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "frac_of_nominal_7900": achieved / 7900.0,
-                         "traffic": measured_traffic("fixpoint_kernel") if P.schedule == DEFAULT_SCHEDULE else None,
+                         "traffic": measured_traffic("fixpoint_kernel", P.schedule),
                          "peak_kind": peak_kind, "kernel": "fixpoint_kernel", "kernel_ms": k_ms, "bytes_per_launch": per_launch_bytes,
                          "bytes_per_iter": alg_bytes_per_iter(n_prime, nnz)},
             "e2e": e2e,
@@ -644,6 +665,7 @@ def bench_paper_tables(lp, torch, dev, reps=5):
         sched = P.schedule
         row["schedule"] = ("W%d" % sched["stable_tile_words"]) if k else (
             "stream" if sched["fixpoint_kernel"] == 1 else
+            "rows%d" % sched["fixpoint_row_map"] if sched["fixpoint_row_map"] else
             "split%d,batch%d" % (max(1, sched["fixpoint_row_split"]), max(1, sched["fixpoint_chunk_batch"])))
         if k:
             row.update({"k": P.info["k"], "n_stable": int(ns)})

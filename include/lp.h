@@ -248,6 +248,11 @@ typedef struct {
                                      (1, 2, 4 or 8; 0 = 1): more for programs with long rows    */
   int32_t fixpoint_chunk_batch;   /* least model, kernel 0: 32-entry chunks whose loads a warp
                                      issues together (1 or 4; 0 = 1): 4 for long rows            */
+  int32_t fixpoint_row_map;       /* least model, kernel 0: 0 = a warp per 32-row word (the
+                                     chunks above); a thread per row, for short rows: 1 = two
+                                     words per warp step, 2 = four words, 3 = loads pipelined
+                                     over the warp's words. 1-3 need row split and chunk batch
+                                     0 or 1                                                      */
   int32_t stable_tile_words;      /* stable models: 64-bit guess words per tile, 1, 2, 4, 8, 16
                                      or 32 (capped at the guesses' words); 0 = the widest whose
                                      two iterate buffers fit 1 GiB                               */
@@ -279,8 +284,8 @@ lp_status lp_set_schedule(lp_program* prog, const lp_schedule* schedule);
  * candidate's; a difference returns LP_ERR_CUDA. records (host, nullable): up to
  * max_records entries, one per candidate in the order run; *n_records (nullable) = number of
  * candidates. Blocks the calling thread. Candidates: least model, kernel 0 with all / 4 / 2
- * CTAs per SM, kernel 0 with row splits 1, 2, 4, 8 and chunk batches 1, 4, and kernel 1 with
- * all / 1 CTAs per SM; stable
+ * CTAs per SM, kernel 0 with row splits 1, 2, 4, 8 and chunk batches 1, 4, kernel 0 with row
+ * maps 1, 2, 3, and kernel 1 with all / 1 CTAs per SM; stable
  * models, tile widths 1..32 with all / half the CTAs per SM, and each width with the row split.
  */
 lp_status lp_autotune(lp_program* prog, uint32_t what, int32_t reps, lp_tune_record* records, int32_t max_records,

@@ -344,15 +344,23 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
   } else {
     const int split = std::max(1, p->sched.fixpoint_row_split);
     const int xn = p->sched.fixpoint_chunk_batch == 4 ? 4 : 1;
-    static int occ_by_variant[2][9] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1, -1}};
-    int& occ = occ_by_variant[xn == 4][split];
-    if (occ < 0) occ = fixpoint_blocks_per_sm(split, xn);
+    const int map = p->sched.fixpoint_row_map;
+    static int occ_by_variant[4][2][9];
+    static bool occ_init = false;
+    if (!occ_init) {
+      for (auto& m : occ_by_variant)
+        for (auto& x : m)
+          for (int& v : x) v = -1;
+      occ_init = true;
+    }
+    int& occ = occ_by_variant[map][xn == 4][split];
+    if (occ < 0) occ = fixpoint_blocks_per_sm(split, xn, map);
     if (occ <= 0) return fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident");
     const int per_sm = p->sched.fixpoint_blocks_per_sm > 0 ? std::min(occ, p->sched.fixpoint_blocks_per_sm) : occ;
     const int words_per_block = kFixBlock / 32 / split;
     int grid = std::min(max_coresident(p, per_sm), std::max(1, (a.n_words + words_per_block - 1) / words_per_block));
     if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
-    le = launch_fixpoint(a, grid, split, xn, s);
+    le = launch_fixpoint(a, grid, split, xn, map, s);
   }
   if ((st = launch_count_and_check(le, "launch fixpoint kernel", p)) != LP_OK) return st;
   if (p->timed) LP_CUDA(cudaEventRecord(p->ev1, s));
@@ -505,6 +513,10 @@ lp_status lp_set_schedule(lp_program* p, const lp_schedule* in) {
   const int32_t X = in->fixpoint_chunk_batch;
   if (X != 0 && X != 1 && X != 4) return fail(LP_ERR_INVALID, "fixpoint_chunk_batch must be 0, 1 or 4");
   if (X == 4 && in->fixpoint_kernel != 0) return fail(LP_ERR_INVALID, "a chunk batch needs fixpoint_kernel 0");
+  const int32_t R = in->fixpoint_row_map;
+  if (R < 0 || R > 3) return fail(LP_ERR_INVALID, "fixpoint_row_map must be 0, 1, 2 or 3");
+  if (R > 0 && (in->fixpoint_kernel != 0 || G > 1 || X == 4))
+    return fail(LP_ERR_INVALID, "a thread-per-row map needs fixpoint_kernel 0, no row split and no chunk batch");
   if (in->stable_row_split != 0 && in->stable_row_split != 1) return fail(LP_ERR_INVALID, "stable_row_split must be 0 or 1");
   if (W < 0 || W > 32 || (W & (W - 1)) != 0) return fail(LP_ERR_INVALID, "stable_tile_words must be 0 or 1, 2, 4, 8, 16, 32");
   p->sched = *in;

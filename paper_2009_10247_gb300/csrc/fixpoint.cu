@@ -18,7 +18,8 @@
 // and counts a word's rows from a prefix sum of its chunk ballots (prefix_count). With a row
 // split G > 1 (programs whose words hold thousands of entries), G warps of a block share a
 // word: each counts a contiguous share of its chunks and the partial counts meet in shared
-// memory.
+// memory. That is row map 0. Row maps 1-3 give each lane one row of the word instead (a thread
+// per row; see theta_pair_rows below), which suits programs whose rows hold a few entries.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -159,9 +160,155 @@ __device__ __forceinline__ void theta_word_pair(const FixArgs& a, const uint32_t
   *u2 = __ballot_sync(FULL, c2 >= (any2 ? 1 : max(e2 - b2, 1)));
 }
 
+// ---- Thread-per-row maps (row maps 1-3). Lane l owns row 32w + l of word w and walks its own
+// entries: U column ids are loaded together, then their U bits are gathered, so a row of at
+// most U entries costs one dependent load pair; longer rows continue U at a time. No ballot or
+// scan per chunk, so a short-row program issues fewer instructions per word than the chunked
+// map, at the price of lanes idling on the word's longest row.
+
+// Two words per warp step (w1, w2), their loads interleaved.
+template <int U>
+__device__ __forceinline__ void theta_pair_rows(const FixArgs& a, const uint32_t* src, int w1, int w2, int lane,
+                                                uint32_t* u1, uint32_t* u2) {
+  const int r1 = (w1 << 5) + lane, r2 = (w2 << 5) + lane;
+  const int b1 = __ldg(a.row_ptr + r1), b2 = __ldg(a.row_ptr + r2);
+  int e1 = __shfl_down_sync(FULL, b1, 1), e2 = __shfl_down_sync(FULL, b2, 1);
+  if (lane == 31) {
+    e1 = __ldg(a.row_ptr + r1 + 1);
+    e2 = __ldg(a.row_ptr + r2 + 1);
+  }
+  const int l1 = e1 - b1, l2 = e2 - b2;
+  const int lm = max(l1, l2);
+  int c1 = 0, c2 = 0;
+  for (int q = 0; q < lm; q += U) {
+    int j1[U], j2[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      j1[k] = q + k < l1 ? __ldg(a.col + b1 + q + k) : -1;
+      j2[k] = q + k < l2 ? __ldg(a.col + b2 + q + k) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      c1 += j1[k] >= 0 ? (src[j1[k] >> 5] >> (j1[k] & 31)) & 1 : 0;
+      c2 += j2[k] >= 0 ? (src[j2[k] >> 5] >> (j2[k] & 31)) & 1 : 0;
+    }
+  }
+  const bool any1 = (__ldg(a.any_mask + w1) >> lane) & 1u, any2 = (__ldg(a.any_mask + w2) >> lane) & 1u;
+  *u1 = __ballot_sync(FULL, c1 >= (any1 ? 1 : max(l1, 1)));  // an empty row never fires
+  *u2 = __ballot_sync(FULL, c2 >= (any2 ? 1 : max(l2, 1)));
+}
+
+// NW words per warp step (w0 + q * stride, q < NW).
+template <int NW, int U>
+__device__ __forceinline__ void theta_words_rows(const FixArgs& a, const uint32_t* src, int w0, int stride, int lane,
+                                                 uint32_t* u) {
+  int b[NW], l[NW];
+#pragma unroll
+  for (int q = 0; q < NW; q++) b[q] = __ldg(a.row_ptr + ((w0 + q * stride) << 5) + lane);
+  int lm = 0;
+#pragma unroll
+  for (int q = 0; q < NW; q++) {
+    int e = __shfl_down_sync(FULL, b[q], 1);
+    if (lane == 31) e = __ldg(a.row_ptr + ((w0 + q * stride) << 5) + 32);
+    l[q] = e - b[q];
+    lm = max(lm, l[q]);
+  }
+  int c[NW];
+#pragma unroll
+  for (int q = 0; q < NW; q++) c[q] = 0;
+  for (int k0 = 0; k0 < lm; k0 += U) {
+    int j[NW][U];
+#pragma unroll
+    for (int q = 0; q < NW; q++)
+#pragma unroll
+      for (int k = 0; k < U; k++) j[q][k] = k0 + k < l[q] ? __ldg(a.col + b[q] + k0 + k) : -1;
+#pragma unroll
+    for (int q = 0; q < NW; q++)
+#pragma unroll
+      for (int k = 0; k < U; k++) c[q] += j[q][k] >= 0 ? (src[j[q][k] >> 5] >> (j[q][k] & 31)) & 1 : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < NW; q++) {
+    const bool any = (__ldg(a.any_mask + w0 + q * stride) >> lane) & 1u;
+    u[q] = __ballot_sync(FULL, c[q] >= (any ? 1 : max(l[q], 1)));
+  }
+}
+
+// Row bounds of word w for the pipelined map: this lane's row begin, lane 31's row end, and
+// the word's OR-row mask (zeros past the last word).
+__device__ __forceinline__ void word_bounds(const FixArgs& a, int w, int lane, int* b, int* e31, uint32_t* anyw) {
+  if (w < a.n_words) {
+    const int r = (w << 5) + lane;
+    *b = __ldg(a.row_ptr + r);
+    *e31 = lane == 31 ? __ldg(a.row_ptr + r + 1) : 0;
+    *anyw = __ldg(a.any_mask + w);
+  } else {
+    *b = 0;
+    *e31 = 0;
+    *anyw = 0;
+  }
+}
+
+// One theta application over the warp's words gwarp, gwarp + nwarps, ..., software pipelined:
+// while the bits of word w are gathered, the column ids of the next word and the row bounds
+// of the one after are already in flight. U column ids per row are staged; the rest of a longer
+// row is read in a plain loop. Returns whether any of the warp's words changed (lane 0).
+template <int U>
+__device__ __forceinline__ bool theta_rows_pipelined(const FixArgs& a, const uint32_t* src, uint32_t* dst, int gwarp,
+                                                     int nwarps, int lane) {
+  bool changed = false;
+  int w = gwarp;
+  int b1, e1x, b2, e2x;
+  uint32_t any1, any2;
+  word_bounds(a, w, lane, &b1, &e1x, &any1);
+  int j0[U];
+  int l0, bb0;
+  uint32_t any0;
+  {
+    int e = __shfl_down_sync(FULL, b1, 1);
+    if (lane == 31) e = e1x;
+    l0 = w < a.n_words ? e - b1 : 0;
+    bb0 = b1;
+    any0 = any1;
+#pragma unroll
+    for (int k = 0; k < U; k++) j0[k] = k < l0 ? __ldg(a.col + b1 + k) : -1;
+  }
+  word_bounds(a, w + nwarps, lane, &b1, &e1x, &any1);
+  for (; w < a.n_words; w += nwarps) {  // w is uniform in the warp
+    word_bounds(a, w + 2 * nwarps, lane, &b2, &e2x, &any2);
+    int e = __shfl_down_sync(FULL, b1, 1);
+    if (lane == 31) e = e1x;
+    const int l1 = w + nwarps < a.n_words ? e - b1 : 0;
+    int j1[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) j1[k] = k < l1 ? __ldg(a.col + b1 + k) : -1;
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < U; k++) c += j0[k] >= 0 ? (src[j0[k] >> 5] >> (j0[k] & 31)) & 1 : 0;
+    for (int k = U; k < l0; k++) {
+      const int j = __ldg(a.col + bb0 + k);
+      c += (src[j >> 5] >> (j & 31)) & 1;
+    }
+    const uint32_t u = __ballot_sync(FULL, c >= (((any0 >> lane) & 1u) ? 1 : max(l0, 1)));
+    if (lane == 0) {
+      dst[w] = u;
+      changed |= (u != src[w]);
+    }
+#pragma unroll
+    for (int k = 0; k < U; k++) j0[k] = j1[k];
+    l0 = l1;
+    bb0 = b1;
+    any0 = any1;
+    b1 = b2;
+    e1x = e2x;
+    any1 = any2;
+  }
+  return changed;
+}
+
 __device__ __forceinline__ uint32_t get_bit(const uint32_t* v, int i) { return (v[i >> 5] >> (i & 31)) & 1u; }
 
-template <int G, int XN>
+template <int G, int XN, int MAP>
 __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
   __shared__ int s_flag;
   __shared__ int s_cnt[G > 1 ? kFixBlock : 1];
@@ -208,7 +355,49 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
     const uint32_t* src = (it & 1) ? a.x1 : a.x0;
     uint32_t* dst = (it & 1) ? a.x0 : a.x1;
     bool changed = false;
-    if (G == 1) {
+    if constexpr (MAP == 1) {
+      int w = gwarp;
+      for (; w + nwarps < a.n_words; w += 2 * nwarps) {
+        uint32_t u1, u2;
+        theta_pair_rows<8>(a, src, w, w + nwarps, lane, &u1, &u2);
+        if (lane == 0) {
+          dst[w] = u1;
+          dst[w + nwarps] = u2;
+          changed |= (u1 != src[w]) | (u2 != src[w + nwarps]);
+        }
+      }
+      for (; w < a.n_words; w += nwarps) {
+        uint32_t u[1];
+        theta_words_rows<1, 8>(a, src, w, nwarps, lane, u);
+        if (lane == 0) {
+          dst[w] = u[0];
+          changed |= (u[0] != src[w]);
+        }
+      }
+    } else if constexpr (MAP == 2) {
+      int w = gwarp;
+      for (; w + 3 * nwarps < a.n_words; w += 4 * nwarps) {
+        uint32_t u[4];
+        theta_words_rows<4, 8>(a, src, w, nwarps, lane, u);
+        if (lane == 0) {
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            dst[w + q * nwarps] = u[q];
+            changed |= (u[q] != src[w + q * nwarps]);
+          }
+        }
+      }
+      for (; w < a.n_words; w += nwarps) {
+        uint32_t u[1];
+        theta_words_rows<1, 8>(a, src, w, nwarps, lane, u);
+        if (lane == 0) {
+          dst[w] = u[0];
+          changed |= (u[0] != src[w]);
+        }
+      }
+    } else if constexpr (MAP == 3) {
+      changed = theta_rows_pipelined<4>(a, src, dst, gwarp, nwarps, lane);
+    } else if (G == 1) {
       int w = gwarp;
       for (; w + nwarps < a.n_words; w += 2 * nwarps) {
         uint32_t u1, u2;
@@ -283,33 +472,40 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
   }
 }
 
-static const void* fixpoint_entry(int G, int XN) {
+static const void* fixpoint_entry(int G, int XN, int MAP) {
+  switch (MAP) {  // the thread-per-row maps have no row split or chunk batch
+    case 1: return (const void*)fixpoint_kernel<1, 1, 1>;
+    case 2: return (const void*)fixpoint_kernel<1, 1, 2>;
+    case 3: return (const void*)fixpoint_kernel<1, 1, 3>;
+    default: break;
+  }
   if (XN == 4) {
     switch (G) {
-      case 2: return (const void*)fixpoint_kernel<2, 4>;
-      case 4: return (const void*)fixpoint_kernel<4, 4>;
-      case 8: return (const void*)fixpoint_kernel<8, 4>;
-      default: return (const void*)fixpoint_kernel<1, 4>;
+      case 2: return (const void*)fixpoint_kernel<2, 4, 0>;
+      case 4: return (const void*)fixpoint_kernel<4, 4, 0>;
+      case 8: return (const void*)fixpoint_kernel<8, 4, 0>;
+      default: return (const void*)fixpoint_kernel<1, 4, 0>;
     }
   }
   switch (G) {
-    case 2: return (const void*)fixpoint_kernel<2, 1>;
-    case 4: return (const void*)fixpoint_kernel<4, 1>;
-    case 8: return (const void*)fixpoint_kernel<8, 1>;
-    default: return (const void*)fixpoint_kernel<1, 1>;
+    case 2: return (const void*)fixpoint_kernel<2, 1, 0>;
+    case 4: return (const void*)fixpoint_kernel<4, 1, 0>;
+    case 8: return (const void*)fixpoint_kernel<8, 1, 0>;
+    default: return (const void*)fixpoint_kernel<1, 1, 0>;
   }
 }
 
-cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, cudaStream_t s) {
+cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, int row_map, cudaStream_t s) {
   FixArgs copy = a;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(fixpoint_entry(row_split, chunk_batch), dim3(grid), dim3(kFixBlock), params, 0,
-                                     s);
+  return cudaLaunchCooperativeKernel(fixpoint_entry(row_split, chunk_batch, row_map), dim3(grid), dim3(kFixBlock),
+                                     params, 0, s);
 }
 
-int fixpoint_blocks_per_sm(int row_split, int chunk_batch) {
+int fixpoint_blocks_per_sm(int row_split, int chunk_batch, int row_map) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fixpoint_entry(row_split, chunk_batch), kFixBlock, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fixpoint_entry(row_split, chunk_batch, row_map), kFixBlock,
+                                                    0) !=
       cudaSuccess)
     return 0;
   return nb;

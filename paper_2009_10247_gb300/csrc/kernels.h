@@ -37,10 +37,12 @@ struct FixArgs {
 };
 
 constexpr int kFixBlock = 512;
-// row_split: warps per 32-row output word (1, 2, 4 or 8); chunk_batch: 32-entry chunks whose
-// loads a warp issues together (1 or 4)
-cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, cudaStream_t s);
-int fixpoint_blocks_per_sm(int row_split, int chunk_batch);
+// row_map 0 (a warp per 32-row word, entries in 32-entry chunks): row_split = warps per word
+// (1, 2, 4 or 8), chunk_batch = chunks whose loads a warp issues together (1 or 4). row_map 1,
+// 2, 3 (a thread per row: two words per warp step, four words, pipelined over the warp's
+// words) take row_split = chunk_batch = 1.
+cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, int row_map, cudaStream_t s);
+int fixpoint_blocks_per_sm(int row_split, int chunk_batch, int row_map);
 
 // The same loop with the matrix streamed through shared memory (fixpoint_stream.cu).
 struct StreamLayout {

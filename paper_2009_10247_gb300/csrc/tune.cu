@@ -79,15 +79,24 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     const size_t out_bytes = (size_t)((hm.n + 63) / 64) * 8;
     if ((st = ensure(p, p->tune_out, std::max<size_t>(out_bytes, 8))) != LP_OK) return st;
     uint64_t* out = (uint64_t*)p->tune_out.p;
-    const int occ0 = fixpoint_blocks_per_sm(1, 1), occ1 = fixpoint_stream_blocks_per_sm();
-    const int32_t W0 = base.stable_tile_words, B0 = base.stable_blocks_per_sm, R0 = base.stable_row_split;
+    const int occ0 = fixpoint_blocks_per_sm(1, 1, 0), occ1 = fixpoint_stream_blocks_per_sm();
+    auto least = [&](int kernel, int blocks, int split, int batch, int map) {
+      lp_schedule c = base;  // stable fields stay as they are
+      c.fixpoint_kernel = kernel;
+      c.fixpoint_blocks_per_sm = blocks;
+      c.fixpoint_row_split = split;
+      c.fixpoint_chunk_batch = batch;
+      c.fixpoint_row_map = map;
+      return c;
+    };
     std::vector<lp_schedule> cands;
     for (int b : {0, 4, 2})
-      if (b == 0 || b < occ0) cands.push_back({0, b, 1, 1, W0, B0, R0});
-    for (int G : {2, 4, 8}) cands.push_back({0, 0, G, 1, W0, B0, R0});
-    for (int G : {1, 2, 4, 8}) cands.push_back({0, 0, G, 4, W0, B0, R0});
+      if (b == 0 || b < occ0) cands.push_back(least(0, b, 1, 1, 0));
+    for (int G : {2, 4, 8}) cands.push_back(least(0, 0, G, 1, 0));
+    for (int G : {1, 2, 4, 8}) cands.push_back(least(0, 0, G, 4, 0));
+    for (int m : {1, 2, 3}) cands.push_back(least(0, 0, 1, 1, m));
     for (int b : {0, 1})
-      if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back({1, b, 1, 1, W0, B0, R0});
+      if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back(least(1, b, 1, 1, 0));
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
     for (const lp_schedule& c : cands) {
@@ -133,16 +142,19 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     if ((st = ensure(p, p->tune_out, (size_t)n_gwords * 8)) != LP_OK) return st;
     uint64_t* mask = (uint64_t*)p->tune_out.p;
     const int occ = stable_blocks_per_sm(false);
+    auto stable = [&](int W, int blocks, int split) {
+      lp_schedule c = best_least;  // least-model fields as chosen above
+      c.stable_tile_words = W;
+      c.stable_blocks_per_sm = blocks;
+      c.stable_row_split = split;
+      return c;
+    };
     std::vector<lp_schedule> cands;
     for (int W = 1; W <= 32; W *= 2) {
       if (W > 1 && W / 2 >= n_gwords) break;  // wider tiles than the guesses only repeat
       for (int b : {0, occ / 2})
-        if (b == 0 || (b > 0 && b < occ))
-          cands.push_back({best_least.fixpoint_kernel, best_least.fixpoint_blocks_per_sm, best_least.fixpoint_row_split,
-                           best_least.fixpoint_chunk_batch, W, b, 0});
-      if (W < 32)  // with 32-word tiles the row split is the same mapping
-        cands.push_back({best_least.fixpoint_kernel, best_least.fixpoint_blocks_per_sm, best_least.fixpoint_row_split,
-                         best_least.fixpoint_chunk_batch, W, 0, 1});
+        if (b == 0 || (b > 0 && b < occ)) cands.push_back(stable(W, b, 0));
+      if (W < 32) cands.push_back(stable(W, 0, 1));  // with 32-word tiles the row split is the same mapping
     }
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
@@ -180,6 +192,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     chosen.fixpoint_blocks_per_sm = best_least.fixpoint_blocks_per_sm;
     chosen.fixpoint_row_split = best_least.fixpoint_row_split;
     chosen.fixpoint_chunk_batch = best_least.fixpoint_chunk_batch;
+    chosen.fixpoint_row_map = best_least.fixpoint_row_map;
   }
   if (what & LP_TUNE_STABLE) {
     chosen.stable_tile_words = best_stable.stable_tile_words;

@@ -45,7 +45,7 @@ EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models"
 LP_TUNE_LEAST = 1
 LP_TUNE_STABLE = 2
 SCHEDULE_FIELDS = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "fixpoint_row_split", "fixpoint_chunk_batch",
-                   "stable_tile_words", "stable_blocks_per_sm", "stable_row_split")
+                   "fixpoint_row_map", "stable_tile_words", "stable_blocks_per_sm", "stable_row_split")
 
 
 class _Schedule(ctypes.Structure):

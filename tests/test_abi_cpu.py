@@ -119,14 +119,22 @@ def test_host_only_handle_refuses_solves(lib):
 def test_schedule_get_set_validates(lib):
     with lp.Program.from_program(small_definite(1), host_only=True) as P:
         assert P.schedule == {"fixpoint_kernel": 0, "fixpoint_blocks_per_sm": 0, "fixpoint_row_split": 0,
-                              "fixpoint_chunk_batch": 0, "stable_tile_words": 0, "stable_blocks_per_sm": 0,
-                              "stable_row_split": 0}
+                              "fixpoint_chunk_batch": 0, "fixpoint_row_map": 0, "stable_tile_words": 0,
+                              "stable_blocks_per_sm": 0, "stable_row_split": 0}
+        for m in (1, 2, 3):
+            P.set_schedule(fixpoint_row_map=m)
+            assert P.schedule["fixpoint_row_map"] == m
+        for bad in ({"fixpoint_row_split": 2}, {"fixpoint_chunk_batch": 4}, {"fixpoint_kernel": 1}):
+            with pytest.raises(lp.LPError):  # a thread-per-row map takes neither
+                P.set_schedule(**bad)
+        P.set_schedule(fixpoint_row_map=0)
         P.set_schedule(fixpoint_kernel=1, fixpoint_blocks_per_sm=2, stable_tile_words=8, stable_blocks_per_sm=1)
         assert P.schedule["stable_tile_words"] == 8 and P.schedule["fixpoint_kernel"] == 1
         for bad in ({"fixpoint_kernel": 2}, {"stable_tile_words": 3}, {"stable_tile_words": 64},
                     {"fixpoint_row_split": 3}, {"fixpoint_row_split": 2},  # the second: kernel 1 is set
                     {"fixpoint_chunk_batch": 2}, {"fixpoint_chunk_batch": 4}, {"stable_row_split": 2},
-                    {"fixpoint_blocks_per_sm": -1}, {"stable_blocks_per_sm": -2}):
+                    {"fixpoint_blocks_per_sm": -1}, {"stable_blocks_per_sm": -2}, {"fixpoint_row_map": 4},
+                    {"fixpoint_row_map": -1}, {"fixpoint_row_map": 1}):  # the last: kernel 1 is set
             with pytest.raises(lp.LPError):
                 P.set_schedule(**bad)
         assert P.schedule["stable_tile_words"] == 8  # unchanged by the rejected calls

@@ -14,10 +14,13 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_util import gpu_least_model, gpu_stable  # noqa: E402
 
 
-@pytest.mark.parametrize("kernel,bpsm,split,xn", [(0, 0, 1, 1), (0, 2, 1, 1), (0, 1, 1, 1), (0, 0, 2, 1), (0, 0, 4, 1),
-                                                  (0, 3, 8, 1), (0, 0, 1, 4), (0, 0, 2, 4), (0, 2, 8, 4), (1, 0, 1, 1),
-                                                  (1, 1, 1, 1)])
-def test_least_model_every_schedule(kernel, bpsm, split, xn):
+@pytest.mark.parametrize("kernel,bpsm,split,xn,rmap", [
+    (0, 0, 1, 1, 0), (0, 2, 1, 1, 0), (0, 1, 1, 1, 0), (0, 0, 2, 1, 0), (0, 0, 4, 1, 0), (0, 3, 8, 1, 0),
+    (0, 0, 1, 4, 0), (0, 0, 2, 4, 0), (0, 2, 8, 4, 0), (0, 0, 1, 1, 1), (0, 1, 1, 1, 1), (0, 0, 1, 1, 2),
+    (0, 1, 1, 1, 2), (0, 0, 1, 1, 3), (0, 1, 1, 1, 3), (1, 0, 1, 1, 0), (1, 1, 1, 1, 0)])
+def test_least_model_every_schedule(kernel, bpsm, split, xn, rmap):
+    # the dense Table 1 shaped program has rows of about 50 entries: the thread-per-row maps
+    # take their multi-pass paths there; the others fill fewer words than there are warps
     progs = [small_definite(2), tiny_random(77, n_atoms=40, n_rules=90, max_body=4, p_fact=0.2),
              large_definite(seed=3, n=20_000, n_rules=100_000, chain_levels=60, chain_width=20),
              table1_program(31, 1000, 5000, dense=True), table1_program(32, 1600, 24000)]
@@ -25,7 +28,7 @@ def test_least_model_every_schedule(kernel, bpsm, split, xn):
         want, want_it = oracle.least_model(prog)
         with lp.Program.from_program(prog) as P:
             P.set_schedule(fixpoint_kernel=kernel, fixpoint_blocks_per_sm=bpsm, fixpoint_row_split=split,
-                           fixpoint_chunk_batch=xn)
+                           fixpoint_chunk_batch=xn, fixpoint_row_map=rmap)
             got, it = gpu_least_model(P)
         assert it == want_it and np.array_equal(got, want)
 
@@ -54,8 +57,10 @@ def test_autotune_keeps_fastest_and_stays_exact():
         stable = [r for r in recs if r["solve"] == "stable"]
         assert len(least) >= 10 and len(stable) >= 2 and all(r["ms"] >= 0 for r in recs)
         assert {r["fixpoint_row_split"] for r in least} == {1, 2, 4, 8}
+        assert {r["fixpoint_row_map"] for r in least} == {0, 1, 2, 3}
         bl, bs = min(least, key=lambda r: r["ms"]), min(stable, key=lambda r: r["ms"])
-        keys = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "fixpoint_row_split", "fixpoint_chunk_batch")
+        keys = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "fixpoint_row_split", "fixpoint_chunk_batch",
+                "fixpoint_row_map")
         assert all(sched[k] == bl[k] for k in keys)
         assert (sched["stable_tile_words"], sched["stable_blocks_per_sm"]) == (bs["stable_tile_words"],
                                                                               bs["stable_blocks_per_sm"])

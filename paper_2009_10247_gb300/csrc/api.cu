@@ -205,9 +205,9 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   if ((st = ensure_scratch(p)) != LP_OK) return cleanup(st);
   e = cudaStreamSynchronize(s);  // host vectors are pageable and about to be released
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "upload"));
-  std::vector<int32_t>().swap(hm.row_ptr);
-  std::vector<int32_t>().swap(hm.col);
-  std::vector<int32_t>().swap(hm.row_tag);
+  free_vec(hm.row_ptr);
+  free_vec(hm.col);
+  free_vec(hm.row_tag);
   p->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
   return LP_OK;
@@ -252,8 +252,8 @@ lp_status ensure_stream_layout(lp_program* p, cudaStream_t s) {
   } else if (!err.empty()) {
     st = fail(st, err);
   }
-  std::vector<int32_t>().swap(hm.row_ptr);
-  std::vector<int32_t>().swap(hm.col);
+  free_vec(hm.row_ptr);
+  free_vec(hm.col);
   std::vector<uint32_t>().swap(hm.desc);
   std::vector<int32_t>().swap(hm.word_hdr);
   std::vector<int32_t>().swap(hm.and_col);
@@ -552,8 +552,8 @@ lp_status lp_export_matrix(const lp_program* p, int64_t* row_ptr, int64_t* col, 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   std::vector<int32_t> rp, cl;
   if (p->host_only) {
-    rp = hm.row_ptr;
-    cl = hm.col;
+    rp.assign(hm.row_ptr.begin(), hm.row_ptr.end());
+    cl.assign(hm.col.begin(), hm.col.end());
     cl.resize(std::max<int64_t>(hm.nnz, 1));
   } else {
     rp.resize((size_t)hm.n_pad + 1);

@@ -54,12 +54,53 @@ inline int omp_max_threads() {
 }
 
 // Sort of 64-bit keys, in parallel where libstdc++'s parallel mode is available.
-inline void parallel_sort(std::vector<uint64_t>& v) {
+inline void parallel_sort(hvec<uint64_t>& v) {
 #if defined(_OPENMP) && defined(__GLIBCXX__)
   __gnu_parallel::sort(v.begin(), v.end());
 #else
   std::sort(v.begin(), v.end());
 #endif
+}
+
+// v = n copies of x, written by the team.
+template <class T>
+void par_fill(hvec<T>& v, size_t n, T x) {
+  v.resize(n);
+  T* d = v.data();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < (int64_t)n; i++) d[i] = x;
+}
+
+// Blocked exclusive scan over [0, m) on the OpenMP team that actually runs (one thread when
+// the caller is itself inside a parallel region, as lp_compile_batch's compiles are): each
+// thread counts its contiguous range (count(i0, i1)), one thread sizes the outputs for the
+// total (prepare(total)), then each thread writes its range from its offset (emit(i0, i1,
+// base)). The output order is the sequential one. Returns the total.
+template <typename Count, typename Prepare, typename Emit>
+int64_t blocked_scan(int64_t m, Count count, Prepare prepare, Emit emit) {
+  std::vector<int64_t> part;
+  int nt = 1;
+#pragma omp parallel
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#pragma omp single
+    nt = omp_get_num_threads();
+#endif
+#pragma omp single
+    part.assign((size_t)nt + 1, 0);
+    const int64_t i0 = m * t / nt, i1 = m * (t + 1) / nt;
+    part[t + 1] = count(i0, i1);
+#pragma omp barrier
+#pragma omp single
+    {
+      for (int q = 0; q < nt; q++) part[q + 1] += part[q];
+      prepare(part[nt]);
+    }
+    emit(i0, i1, part[t]);
+  }
+  return part[nt];
 }
 
 }  // namespace
@@ -79,15 +120,15 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     err = "body_off[0] must be 0";
     return LP_ERR_INVALID;
   }
-  for (int64_t r = 0; r < n_rules; r++) {
-    if (head[r] < 0 || head[r] >= n) {
-      err = "head atom out of range at rule " + std::to_string(r);
-      return LP_ERR_INVALID;
-    }
-    if (body_off[r + 1] < body_off[r]) {
-      err = "body_off decreases at rule " + std::to_string(r);
-      return LP_ERR_INVALID;
-    }
+  int64_t first_bad = n_rules;  // first rule with a bad head or a decreasing body_off
+#pragma omp parallel for reduction(min : first_bad) schedule(static)
+  for (int64_t r = 0; r < n_rules; r++)
+    if (head[r] < 0 || head[r] >= n || body_off[r + 1] < body_off[r]) first_bad = std::min(first_bad, r);
+  if (first_bad < n_rules) {
+    const int64_t r = first_bad;
+    err = (head[r] < 0 || head[r] >= n) ? "head atom out of range at rule " + std::to_string(r)
+                                        : "body_off decreases at rule " + std::to_string(r);
+    return LP_ERR_INVALID;
   }
   const int64_t total = n_rules > 0 ? body_off[n_rules] : 0;
   if (total > 0 && !body_atom) {
@@ -113,8 +154,9 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
 
   try {
     // ---- rules per head, negated atoms, barred ids (canonical: n + rank of q)
-    std::vector<int32_t> cnt(n, 0);
-    std::vector<int32_t> bar_id(n, -1);
+    hvec<int32_t> cnt, bar_id;
+    par_fill(cnt, (size_t)n, 0);
+    par_fill(bar_id, (size_t)n, -1);
 #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < n_rules; r++) __atomic_fetch_add(&cnt[head[r]], 1, __ATOMIC_RELAXED);
     if (body_neg) {
@@ -126,7 +168,8 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     for (int32_t a = 0; a < n; a++)
       if (bar_id[a] == 0) bar_id[a] = n + nb++;
     // new atoms for the rules of multi-rule heads, in rule order (blocked prefix count)
-    std::vector<int32_t> aux(n_rules, -1);
+    hvec<int32_t> aux;
+    par_fill(aux, (size_t)n_rules, -1);
     int64_t naux = 0;
     {
       // ranges follow the team that actually runs (one thread when this compile is itself
@@ -164,8 +207,8 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     const int32_t np = (int32_t)n_prime64;
 
     // ---- body sets in canonical columns (sorted, duplicates removed), in place per rule
-    std::vector<int32_t> rb(total);
-    std::vector<int32_t> setlen(n_rules);
+    hvec<int32_t> rb(total);  // every rule writes its whole range
+    hvec<int32_t> setlen(n_rules);
 #pragma omp parallel for schedule(dynamic, 4096)
     for (int64_t r = 0; r < n_rules; r++) {
       int64_t b = body_off[r], m = body_off[r + 1] - b;
@@ -184,14 +227,15 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     // ---- canonical rows: kind, defining rule, rules of each head (in rule order)
     // One parallel sort of (head, rule) keys groups the rules by head; every pass after it
     // writes contiguous ranges.
-    std::vector<int64_t> hr_off((size_t)n + 1, 0);
+    hvec<int64_t> hr_off((size_t)n + 1);
+    hr_off[0] = 0;
     for (int32_t a = 0; a < n; a++) hr_off[a + 1] = hr_off[a] + cnt[a];
     // Rules grouped by head, in rule order within a head: a counting sort over contiguous rule
     // ranges, one per thread (per-thread head counts, a scan over the threads per head, then
     // each thread writes its range in order).
-    std::vector<int32_t> by_head(n_rules);
+    hvec<int32_t> by_head(n_rules);
     {
-      std::vector<int32_t> tcnt;
+      hvec<int32_t> tcnt;
       int nt = 1;
 #pragma omp parallel num_threads(std::min(16, std::max(1, omp_max_threads())))
       {
@@ -202,9 +246,10 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         nt = omp_get_num_threads();
 #endif
 #pragma omp single
-        tcnt.assign((size_t)nt * n, 0);
+        tcnt.resize((size_t)nt * n);
         const int64_t r0 = n_rules * t / nt, r1 = n_rules * (t + 1) / nt;
         int32_t* c = tcnt.data() + (size_t)t * n;
+        std::fill(c, c + n, 0);  // each thread clears its own counts
         for (int64_t r = r0; r < r1; r++) c[head[r]]++;
 #pragma omp barrier
 #pragma omp for schedule(static)
@@ -223,8 +268,10 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       }
     }
     auto rule_at = [&](int64_t t) -> int32_t { return by_head[t]; };
-    std::vector<int8_t> kind(np, K_EMPTY);
-    std::vector<int32_t> row_rule(np, -1);  // rule defining a RULE/FACT row
+    hvec<int8_t> kind;
+    hvec<int32_t> row_rule;  // rule defining a RULE/FACT row
+    par_fill(kind, (size_t)np, (int8_t)K_EMPTY);
+    par_fill(row_rule, (size_t)np, -1);
 #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < n_rules; r++)
       if (aux[r] >= 0) {  // a rule of a multi-rule head defines its new atom's row
@@ -267,9 +314,9 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     // Only rule-row entries count as references (gathers): OR entries point at new atoms,
     // which are placed by their OR row, and self-loops read their own bit. Every body atom is
     // an original or barred atom (< nA); per-thread histograms are summed at the end.
-    std::vector<int64_t> deg(nA, 0);
+    hvec<int64_t> deg(nA);  // every entry is written below
     {
-      std::vector<int32_t> local;
+      hvec<int32_t> local;
       int nt = 1;
 #pragma omp parallel
       {
@@ -280,8 +327,9 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         nt = omp_get_num_threads();
 #endif
 #pragma omp single
-        local.assign((size_t)nt * nA, 0);
+        local.resize((size_t)nt * nA);
         int32_t* h = local.data() + (size_t)t * nA;
+        std::fill(h, h + nA, 0);  // each thread clears its own histogram
 #pragma omp for schedule(static)
         for (int64_t r = 0; r < n_rules; r++) {
           if (setlen[r] == 0) continue;  // facts define self-loop rows
@@ -298,7 +346,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     }
 
     // ---- internal order
-    std::vector<int32_t> inv(np);  // internal -> canonical
+    hvec<int32_t> inv(np);  // internal -> canonical (a permutation: every entry is written)
     // bpos[i]: first section-B position (relative to nA) of the new atoms of the OR row at
     // internal position i < nA; an OR row's entries are the run [nA + bpos[i], nA + bpos[i + 1])
     std::vector<int64_t> bpos((size_t)nA + 1, 0);
@@ -307,7 +355,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       // gives the same order
       int64_t maxdeg = 0;
       for (int32_t c = 0; c < nA; c++) maxdeg = std::max(maxdeg, deg[c]);
-      std::vector<uint64_t> key(nA);
+      hvec<uint64_t> key(nA);
 #pragma omp parallel for schedule(static)
       for (int32_t c = 0; c < nA; c++) key[c] = ((uint64_t)(maxdeg - deg[c]) << 32) | (uint32_t)c;
       parallel_sort(key);
@@ -330,17 +378,30 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         for (int64_t t = hr_off[c]; t < hr_off[c + 1]; t++) inv[pos++] = aux[rule_at(t)];
       }
     }
-    hm.perm.assign(np, 0);
+    hm.perm.resize(np);  // inv is a permutation
 #pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < np; i++) hm.perm[inv[i]] = i;
     const int32_t npad = (int32_t)(((int64_t)np + 63) / 64 * 64);
 
     // ---- internal CSR
-    hm.row_ptr.assign((size_t)npad + 1, 0);
-#pragma omp parallel for schedule(static)
-    for (int32_t i = 0; i < np; i++) hm.row_ptr[i + 1] = (int32_t)row_len(inv[i]);
-    for (int32_t i = 0; i < npad; i++) hm.row_ptr[i + 1] += hm.row_ptr[i];
-    hm.col.assign((size_t)nnz, 0);
+    hm.row_ptr.resize((size_t)npad + 1);
+    hm.row_ptr[0] = 0;
+    blocked_scan(
+        np,
+        [&](int64_t i0, int64_t i1) {
+          int64_t c = 0;
+          for (int64_t i = i0; i < i1; i++) c += row_len(inv[i]);
+          return c;
+        },
+        [](int64_t) {},
+        [&](int64_t i0, int64_t i1, int64_t base) {
+          for (int64_t i = i0; i < i1; i++) {
+            base += row_len(inv[i]);
+            hm.row_ptr[i + 1] = (int32_t)base;  // nnz < 2^31 was checked
+          }
+        });
+    for (int32_t i = np; i < npad; i++) hm.row_ptr[i + 1] = hm.row_ptr[i];  // empty padding rows
+    hm.col.resize((size_t)nnz);  // the passes below write every entry of every row
     // rule rows: walk the rules in order (sequential reads of the body sets) and scatter each
     // body, mapped to internal ids and sorted, into its row
 #pragma omp parallel for schedule(dynamic, 4096)
@@ -365,43 +426,59 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       int32_t* d = hm.col.data() + hm.row_ptr[i];
       for (int64_t t = bpos[i]; t < bpos[i + 1]; t++) *d++ = (int32_t)(nA + t);
     }
-    hm.any_mask.assign((size_t)npad / 32, 0u);
+    hm.any_mask.resize((size_t)npad / 32);
 #pragma omp parallel for schedule(static)
-    for (int32_t w = 0; w < np / 32 + 1; w++) {
+    for (int32_t w = 0; w < npad / 32; w++) {
       uint32_t bits = 0;
       for (int l = 0; l < 32; l++) {
         const int32_t i = 32 * w + l;
         if (i < np && kind[inv[i]] == K_OR) bits |= 1u << l;
       }
-      if (w < npad / 32) hm.any_mask[w] = bits;
+      hm.any_mask[w] = bits;
     }
 
     // ---- facts, negated atoms, guesses (Def. 4 and Def. 8)
-    std::vector<int32_t> owner_of_row(np);
+    hvec<int32_t> owner_of_row(np);
 #pragma omp parallel for schedule(static)
     for (int32_t c = 0; c < np; c++) owner_of_row[c] = c < n ? c : -1;
+#pragma omp parallel for schedule(static)
     for (int32_t a = 0; a < n; a++)
       if (bar_id[a] >= 0) owner_of_row[bar_id[a]] = a;
 #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < n_rules; r++)
       if (aux[r] >= 0) owner_of_row[aux[r]] = head[r];
-    hm.fact_row.clear();
-    hm.fact_owner.clear();
     hm.fact_mask.assign(((size_t)n + 63) / 64, 0ull);
-    int32_t n_rule_rows = 0, n_or_rows = 0;
+    int64_t n_rule_rows = 0, n_or_rows = 0;
+#pragma omp parallel for reduction(+ : n_rule_rows, n_or_rows) schedule(static)
     for (int32_t c = 0; c < np; c++) {
-      if (kind[c] == K_FACT) {
-        hm.fact_row.push_back(hm.perm[c]);
-        hm.fact_owner.push_back(owner_of_row[c]);
-        hm.fact_mask[owner_of_row[c] >> 6] |= 1ull << (owner_of_row[c] & 63);
-      } else if (kind[c] == K_RULE) {
-        n_rule_rows++;
-      } else if (kind[c] == K_OR) {
-        n_or_rows++;
-      }
+      n_rule_rows += kind[c] == K_RULE;
+      n_or_rows += kind[c] == K_OR;
     }
-    hm.row_tag.assign(npad, -1);
-    for (int32_t f : hm.fact_row) hm.row_tag[f] = -2;
+    // fact rows in canonical order, with their atoms
+    blocked_scan(
+        np,
+        [&](int64_t c0, int64_t c1) {
+          int64_t f = 0;
+          for (int64_t c = c0; c < c1; c++) f += kind[c] == K_FACT;
+          return f;
+        },
+        [&](int64_t total) {
+          hm.fact_row.resize((size_t)total);
+          hm.fact_owner.resize((size_t)total);
+        },
+        [&](int64_t c0, int64_t c1, int64_t f) {
+          for (int64_t c = c0; c < c1; c++)
+            if (kind[c] == K_FACT) {
+              const int32_t a = owner_of_row[c];
+              hm.fact_row[f] = hm.perm[c];
+              hm.fact_owner[f++] = a;
+              __atomic_fetch_or(&hm.fact_mask[a >> 6], 1ull << (a & 63), __ATOMIC_RELAXED);
+            }
+        });
+    par_fill(hm.row_tag, (size_t)npad, -1);
+    const int64_t n_fact = (int64_t)hm.fact_row.size();
+#pragma omp parallel for schedule(static)
+    for (int64_t f = 0; f < n_fact; f++) hm.row_tag[hm.fact_row[f]] = -2;
     hm.neg_row.clear();
     hm.bar_row.clear();
     hm.guess_row.clear();
@@ -433,9 +510,9 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     hm.n_aux = (int32_t)naux;
     hm.k = (int32_t)hm.guess_row.size();
     hm.n_fact_rows = (int32_t)hm.fact_row.size();
-    hm.n_rule_rows = n_rule_rows;
-    hm.n_or_rows = n_or_rows;
-    hm.canon_rule.assign(np, -1);
+    hm.n_rule_rows = (int32_t)n_rule_rows;
+    hm.n_or_rows = (int32_t)n_or_rows;
+    par_fill(hm.canon_rule, (size_t)np, -1);
 #pragma omp parallel for schedule(static)
     for (int32_t c = 0; c < np; c++)
       if (kind[c] == K_RULE) hm.canon_rule[c] = row_rule[c];
@@ -454,7 +531,7 @@ lp_status build_stream_layout(HostMatrix& hm, std::string& err) {
   const int32_t np = hm.n_prime, npad = hm.n_pad, nA = hm.n + hm.n_barred;
   std::vector<int32_t> inv(np);
   for (int32_t c = 0; c < np; c++) inv[hm.perm[c]] = c;
-  const std::vector<int8_t>& kind = hm.canon_kind;
+  const hvec<int8_t>& kind = hm.canon_kind;
   try {
     {
       const int32_t nw = npad / 32;

@@ -2,12 +2,48 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/lp.h"
 
 namespace lp {
+
+// Allocator whose argument-less construct() default-initializes: resize() of a vector of plain
+// integers leaves the new elements unwritten, so the host compiler sizes its large arrays
+// without a serial zero fill and writes them in parallel loops (which also spreads the first
+// touch of their pages over the threads).
+template <class T>
+struct uninit_alloc : std::allocator<T> {
+  using value_type = T;
+  template <class U>
+  struct rebind {
+    using other = uninit_alloc<U>;
+  };
+  uninit_alloc() noexcept = default;
+  template <class U>
+  uninit_alloc(const uninit_alloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using hvec = std::vector<T, uninit_alloc<T>>;
+
+// Releases a vector's storage.
+template <class V>
+void free_vec(V& v) {
+  V().swap(v);
+}
 
 // Canonical row kinds (the values lp_export_matrix reports).
 enum RowKind : int8_t { K_EMPTY = 0, K_RULE = 1, K_OR = 2, K_FACT = 3, K_BARRED = 4 };
@@ -23,19 +59,19 @@ struct HostMatrix {
   int32_t n_barred = 0, n_aux = 0, k = 0;
   int32_t n_fact_rows = 0, n_rule_rows = 0, n_or_rows = 0;
 
-  std::vector<int32_t> row_ptr;    // internal CSR, n_pad + 1
-  std::vector<int32_t> col;        // internal column ids, nnz
-  std::vector<uint32_t> any_mask;  // n_pad / 32 words: bit set = OR-rule row (threshold 1)
-  std::vector<int32_t> perm;       // canonical row -> internal row (n_prime)
-  std::vector<int8_t> canon_kind;  // canonical row kinds (n_prime)
-  std::vector<int32_t> canon_rule; // canonical row -> original rule of a rule row, else -1
-  std::vector<int32_t> fact_row;   // internal rows with a_ii = 1 from a fact (Def. 2 item 3)
-  std::vector<int32_t> fact_owner; // original atom of each fact row
+  hvec<int32_t> row_ptr;    // internal CSR, n_pad + 1
+  hvec<int32_t> col;        // internal column ids, nnz
+  hvec<uint32_t> any_mask;  // n_pad / 32 words: bit set = OR-rule row (threshold 1)
+  hvec<int32_t> perm;       // canonical row -> internal row (n_prime)
+  hvec<int8_t> canon_kind;  // canonical row kinds (n_prime)
+  hvec<int32_t> canon_rule; // canonical row -> original rule of a rule row, else -1
+  hvec<int32_t> fact_row;   // internal rows with a_ii = 1 from a fact (Def. 2 item 3)
+  hvec<int32_t> fact_owner; // original atom of each fact row
   std::vector<uint64_t> fact_mask; // ceil(n/64) words: atoms with at least one fact rule
   std::vector<int32_t> neg_row;    // per negated atom q (ascending id): internal row of q
   std::vector<int32_t> bar_row;    // ... and internal row of q-bar
   std::vector<int32_t> guess_row;  // internal rows of the k guessed barred atoms, bit order
-  std::vector<int32_t> row_tag;    // n_pad: -1 zero, -2 fact, j >= 0 guessed barred atom j,
+  hvec<int32_t> row_tag;    // n_pad: -1 zero, -2 fact, j >= 0 guessed barred atom j,
                                    //        -3 barred atom of a fact (initial column of Def. 8)
 
   // Streamed layout of the least-model kernel (see fixpoint_stream.cu). Row kinds: 0 = rule

@@ -108,8 +108,8 @@ lp_status dalloc(lp_program* p, T** ptr, size_t count) {
   return LP_OK;
 }
 
-template <typename T>
-lp_status upload(lp_program* p, T** ptr, const std::vector<T>& v, cudaStream_t s) {
+template <typename T, typename A>
+lp_status upload(lp_program* p, T** ptr, const std::vector<T, A>& v, cudaStream_t s) {
   lp_status st = dalloc(p, ptr, v.size());
   if (st != LP_OK) return st;
   if (!v.empty()) {

@@ -72,7 +72,13 @@ def test_transitive_closure_bfs_30():
 
 
 def test_transitive_closure_500():
-    _parity(transitive_closure(500, 4.0, seed=1))
+    p = transitive_closure(500, 4.0, seed=1)
+    want, want_it = oracle.least_model(p)
+    with lp.Program.from_program(p) as P:
+        for rmap in (0, 1, 2, 3):
+            P.set_schedule(fixpoint_row_map=rmap)
+            got, it = gpu_least_model(P)
+            assert it == want_it and np.array_equal(got, want), f"row map {rmap}"
 
 
 def test_large_definite_scaled():
@@ -80,11 +86,21 @@ def test_large_definite_scaled():
 
 
 def test_large_definite_full_size():
-    # the benchmark workload itself: 1e6 atoms, 5e6 rules, ~1000 iterations
+    # the benchmark workload itself: 1e6 atoms, 5e6 rules, ~1000 iterations, under the default
+    # schedule, every thread-per-row map, and the schedule the autotuner picks (which is what
+    # the benchmark times)
     p = large_definite(seed=1)
-    got, it = _parity(p)
-    assert it > 1000
-    assert is_model(p, got)
+    want, want_it = oracle.least_model(p)
+    assert want_it > 1000
+    assert is_model(p, want)
+    with lp.Program.from_program(p) as P:
+        for rmap in (0, 1, 2, 3):
+            P.set_schedule(fixpoint_row_map=rmap)
+            got, it = gpu_least_model(P)
+            assert it == want_it and np.array_equal(got, want), f"row map {rmap}"
+        P.autotune(lp.LP_TUNE_LEAST, reps=1)
+        got, it = gpu_least_model(P)
+        assert it == want_it and np.array_equal(got, want), f"tuned {P.schedule}"
 
 
 def test_rows_mode_matches_literal_algorithm1():

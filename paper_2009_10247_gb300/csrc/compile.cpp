@@ -384,19 +384,28 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     const int32_t npad = (int32_t)(((int64_t)np + 63) / 64 * 64);
 
     // ---- internal CSR
+    // Row lengths and kinds moved to internal order (sequential reads, one scattered write per
+    // row), their running sum into row_ptr, then the rows' entries.
     hm.row_ptr.resize((size_t)npad + 1);
     hm.row_ptr[0] = 0;
+    hvec<int8_t> ikind(np);  // kind of internal row i
+#pragma omp parallel for schedule(static)
+    for (int32_t c = 0; c < np; c++) {
+      const int32_t i = hm.perm[c];
+      hm.row_ptr[i + 1] = (int32_t)row_len(c);
+      ikind[i] = kind[c];
+    }
     blocked_scan(
         np,
         [&](int64_t i0, int64_t i1) {
           int64_t c = 0;
-          for (int64_t i = i0; i < i1; i++) c += row_len(inv[i]);
+          for (int64_t i = i0; i < i1; i++) c += hm.row_ptr[i + 1];
           return c;
         },
         [](int64_t) {},
         [&](int64_t i0, int64_t i1, int64_t base) {
           for (int64_t i = i0; i < i1; i++) {
-            base += row_len(inv[i]);
+            base += hm.row_ptr[i + 1];
             hm.row_ptr[i + 1] = (int32_t)base;  // nnz < 2^31 was checked
           }
         });
@@ -413,18 +422,16 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       for (int32_t t = 0; t < setlen[r]; t++) d[t] = hm.perm[sb[t]];
       sort_small(d, setlen[r]);
     }
-    // self-loop rows (facts, barred atoms) hold their own column
-#pragma omp parallel for schedule(static)
-    for (int32_t c = 0; c < np; c++)
-      if (kind[c] == K_FACT || kind[c] == K_BARRED) {
-        const int32_t i = hm.perm[c];
-        hm.col[hm.row_ptr[i]] = i;
-      }
-    // OR rows: their new atoms sit consecutively in section B, in rule order
+    // self-loop rows (facts, barred atoms) hold their own column; OR rows list their new
+    // atoms, which sit consecutively in section B in rule order
 #pragma omp parallel for schedule(dynamic, 4096)
-    for (int32_t i = 0; i < nA; i++) {
+    for (int32_t i = 0; i < np; i++) {
       int32_t* d = hm.col.data() + hm.row_ptr[i];
-      for (int64_t t = bpos[i]; t < bpos[i + 1]; t++) *d++ = (int32_t)(nA + t);
+      if (ikind[i] == K_FACT || ikind[i] == K_BARRED) {
+        *d = i;
+      } else if (ikind[i] == K_OR) {
+        for (int64_t t = bpos[i]; t < bpos[i + 1]; t++) *d++ = (int32_t)(nA + t);
+      }
     }
     hm.any_mask.resize((size_t)npad / 32);
 #pragma omp parallel for schedule(static)
@@ -432,7 +439,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       uint32_t bits = 0;
       for (int l = 0; l < 32; l++) {
         const int32_t i = 32 * w + l;
-        if (i < np && kind[inv[i]] == K_OR) bits |= 1u << l;
+        if (i < np && ikind[i] == K_OR) bits |= 1u << l;
       }
       hm.any_mask[w] = bits;
     }

@@ -1,9 +1,9 @@
 """GPU parity of the least-model path (Algorithm 1 in liblp) against the CPU oracle.
 
 Bit-exact comparison of every model bit and of the iteration count (theta applications),
-on the paper's example, tiny random programs with ragged sizes, every workload generator at
-test sizes, and the full-size large definite program in the launch configuration the
-benchmark times."""
+under every row map of the kernel, on the paper's example, tiny random programs with ragged
+sizes, every workload generator at test sizes, and the full-size large definite program in the
+launch configuration the benchmark times."""
 import numpy as np
 import pytest
 
@@ -18,12 +18,18 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_util import gpu_least_model  # noqa: E402
 
 
+ROW_MAPS = (0, 1, 2, 3)  # the warp-per-word map and the three thread-per-row maps
+
+
 def _parity(prog, init=None):
+    # every row map of the least-model kernel must give the oracle's model and iteration count
     want, want_it = oracle.least_model(prog, init=init)
     with lp.Program.from_program(prog) as P:
-        got, it = gpu_least_model(P, init=init)
-    assert np.array_equal(got, want), f"{np.count_nonzero(got != want)} atoms differ"
-    assert it == want_it
+        for rmap in ROW_MAPS:
+            P.set_schedule(fixpoint_row_map=rmap)
+            got, it = gpu_least_model(P, init=init)
+            assert np.array_equal(got, want), f"row map {rmap}: {np.count_nonzero(got != want)} atoms differ"
+            assert it == want_it, f"row map {rmap}"
     return got, it
 
 
@@ -108,9 +114,10 @@ def test_rows_mode_matches_literal_algorithm1():
     s = oracle.standardize(p)
     rng = np.random.default_rng(0)
     with lp.Program.from_program(p) as P:
-        for trial in range(4):
+        for trial in range(8):
             v0 = rng.random(s.n_prime) < 0.3
             want, want_it, ok = oracle.alg1(s, v0.astype(np.uint8), max_iters=500)
+            P.set_schedule(fixpoint_row_map=ROW_MAPS[trial % 4])
             if ok:
                 got, it = gpu_least_model(P, init=v0, rows=True, max_iters=500)
                 assert np.array_equal(got, want.astype(bool)) and it == want_it

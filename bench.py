@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-paper-tables", action="store_true")
+    ap.add_argument("--batch-iter-profile", action="store_true",
+                    help="add the program batch's cumulative time after each lock-step iteration")
     ap.add_argument("--no-tune", action="store_true",
                     help="default schedules instead of lp_autotune's (for profiler captures: on the least-model and "
                          "2^16-guess workloads the tuner picks the defaults)")
@@ -335,7 +337,7 @@ def main():
     if not args.no_stable and rank == 0:
         secondary = bench_stable(lp, torch, dev, flush, tune=not args.no_tune)
     if not args.no_batch and rank == 0:
-        batch = bench_batch(lp, torch, dev, flush)
+        batch = bench_batch(lp, torch, dev, flush, iter_profile=args.batch_iter_profile)
     if not args.no_relaxed and rank == 0:
         relaxed = bench_relaxed(lp, torch, dev, flush)
     tables = None
@@ -442,8 +444,10 @@ def bench_stable(lp, torch, dev, flush, steps=5, tune=True):
     return out
 
 
-def bench_batch(lp, torch, dev, flush, steps=5):
-    """Many programs in one launch (lp_batch_stable_models) against one launch per program."""
+def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
+    """Many programs in one launch (lp_batch_stable_models) against one launch per program.
+    iter_profile: also time the launch cut off after t lock-step iterations (max_iters = t), for
+    every t, with the programs and cells still active in iteration t."""
     progs = program_batch(seed=1)
     B = lp.Batch(progs)
     n = B.n_programs
@@ -503,7 +507,28 @@ def bench_batch(lp, torch, dev, flush, steps=5):
                         "traffic": measured_traffic("batch_stable_kernel"), "peak_kind": peak_kind,
                         "kernel": "batch_stable_kernel",
                         "bytes_per_launch": by,
-                        "note": "per-program iterates are L2 resident between iterations, so this can exceed 1"}}
+                        "note": "the iterate buffers and the CSR exceed L2: every lock-step iteration streams them"}}
+    if iter_profile:
+        cells = np.array([((inf["n_prime"] + 63) // 64 * 64) * max(1, (1 << inf["k"]) // 64) for inf in B.info])
+        prof = []
+        for t in range(1, int(iters.max()) + 1):
+            tt = []
+            for _ in range(3):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                try:
+                    B.stable_models(mask, max_iters=t)
+                except lp.LPError as e:  # programs still changing after t iterations
+                    if e.status != 4:
+                        raise
+                b.record(stream)
+                b.synchronize()
+                tt.append(a.elapsed_time(b))
+            act = iters >= t
+            prof.append({"max_iters": t, "ms": round(min(tt), 4), "active_programs": int(act.sum()),
+                         "active_cells": int(cells[act].sum())})
+        out["iteration_profile"] = prof
     B.close()
     return out
 

@@ -357,7 +357,7 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
     if (occ < 0) occ = fixpoint_blocks_per_sm(split, xn, map);
     if (occ <= 0) return fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident");
     const int per_sm = p->sched.fixpoint_blocks_per_sm > 0 ? std::min(occ, p->sched.fixpoint_blocks_per_sm) : occ;
-    const int words_per_block = kFixBlock / 32 / split;
+    const int words_per_block = fix_block(map) / 32 / split;
     int grid = std::min(max_coresident(p, per_sm), std::max(1, (a.n_words + words_per_block - 1) / words_per_block));
     if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
     le = launch_fixpoint(a, grid, split, xn, map, s);

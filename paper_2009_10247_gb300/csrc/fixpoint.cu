@@ -309,9 +309,10 @@ __device__ __forceinline__ bool theta_rows_pipelined(const FixArgs& a, const uin
 __device__ __forceinline__ uint32_t get_bit(const uint32_t* v, int i) { return (v[i >> 5] >> (i & 31)) & 1u; }
 
 template <int G, int XN, int MAP>
-__global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
+__global__ void __launch_bounds__(MAP == 0 ? kFixBlockMap0 : kFixBlockRows) fixpoint_kernel(FixArgs a) {
+  constexpr int kBlock = MAP == 0 ? kFixBlockMap0 : kFixBlockRows;
   __shared__ int s_flag;
-  __shared__ int s_cnt[G > 1 ? kFixBlock : 1];
+  __shared__ int s_cnt[G > 1 ? kBlock : 1];
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
         }
       }
     } else if constexpr (MAP == 3) {
-      changed = theta_rows_pipelined<4>(a, src, dst, gwarp, nwarps, lane);
+      changed = theta_rows_pipelined<6>(a, src, dst, gwarp, nwarps, lane);
     } else if (G == 1) {
       int w = gwarp;
       for (; w + nwarps < a.n_words; w += 2 * nwarps) {
@@ -416,9 +417,9 @@ __global__ void __launch_bounds__(kFixBlock) fixpoint_kernel(FixArgs a) {
         }
       }
     } else {
-      // kFixBlock / 32 / G words per block and round; the loop bound is uniform in the block
+      // kBlock / 32 / G words per block and round; the loop bound is uniform in the block
       const int warp = threadIdx.x >> 5, slot = warp / G, part = warp % G;
-      const int per_block = (kFixBlock / 32) / G;
+      const int per_block = (kBlock / 32) / G;
       for (int wb = blockIdx.x * per_block; wb < a.n_words; wb += gridDim.x * per_block) {
         const int w = wb + slot;
         int len = 0, cnt = 0;
@@ -498,16 +499,14 @@ static const void* fixpoint_entry(int G, int XN, int MAP) {
 cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, int row_map, cudaStream_t s) {
   FixArgs copy = a;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(fixpoint_entry(row_split, chunk_batch, row_map), dim3(grid), dim3(kFixBlock),
-                                     params, 0, s);
+  return cudaLaunchCooperativeKernel(fixpoint_entry(row_split, chunk_batch, row_map), dim3(grid),
+                                     dim3(fix_block(row_map)), params, 0, s);
 }
 
 int fixpoint_blocks_per_sm(int row_split, int chunk_batch, int row_map) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fixpoint_entry(row_split, chunk_batch, row_map), kFixBlock,
-                                                    0) !=
-      cudaSuccess)
-    return 0;
+  const void* k = fixpoint_entry(row_split, chunk_batch, row_map);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, fix_block(row_map), 0) != cudaSuccess) return 0;
   return nb;
 }
 

@@ -36,11 +36,16 @@ struct FixArgs {
   int32_t n_sec_a;             // leading rows that rule rows refer to (used by the streamed kernel)
 };
 
-constexpr int kFixBlock = 512;
+// Threads per block of the least-model kernel: 512 for row map 0 (40 registers, 3 blocks per
+// SM), 1024 for the thread-per-row maps (up to 64 registers, one block per SM, so half as many
+// blocks meet at each grid barrier as with two 512-thread blocks).
+constexpr int kFixBlockMap0 = 512, kFixBlockRows = 1024;
+inline int fix_block(int row_map) { return row_map == 0 ? kFixBlockMap0 : kFixBlockRows; }
 // row_map 0 (a warp per 32-row word, entries in 32-entry chunks): row_split = warps per word
 // (1, 2, 4 or 8), chunk_batch = chunks whose loads a warp issues together (1 or 4). row_map 1,
-// 2, 3 (a thread per row: two words per warp step, four words, pipelined over the warp's
-// words) take row_split = chunk_batch = 1.
+// 2, 3 (a thread per row: two words per warp step with 8 column ids per pass, four words, or
+// loads pipelined over the warp's words with 6 ids staged per row) take row_split =
+// chunk_batch = 1.
 cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, int row_map, cudaStream_t s);
 int fixpoint_blocks_per_sm(int row_split, int chunk_batch, int row_map);
 

@@ -129,6 +129,32 @@ def test_full_size_program_reduced_batch():
     assert _rel(dv0, dv0_ref) < 1e-4
 
 
+def test_full_size_bench_batch_sampled_columns():
+    # the benchmark's launch configuration: the relaxed workload's program with a batch of 256
+    # columns (float4 rows, one 256-column warp pass), T = 32, tau = 0.05, checkpoint every 8.
+    # Columns are independent in the forward pass, so the oracle checks a sample S of them; the
+    # cotangent is zero outside S, so dL/dw is the oracle's sum over S and dL/dv0 vanishes
+    # outside S.
+    prog = large_definite(seed=5, n=100_000, n_rules=400_000, chain_levels=12, chain_width=50)
+    R = RelaxedProgram(prog)
+    rng = np.random.default_rng(11)
+    b, T, tau = 256, 32, 0.05
+    w = rng.uniform(0.5, 1.5, R.n_rules)
+    v0 = np.repeat((R.kind == oracle.ORC_FACT).astype(np.float64)[:, None], b, axis=1)
+    v0 *= rng.random(v0.shape) < 0.5
+    S = np.array([0, 3, 127, 128, 200, 255])
+    c = np.zeros((R.n_prime, b))
+    c[:, S] = rng.uniform(-1.0, 1.0, (R.n_prime, len(S)))
+    vT, dw, dv0 = _run(prog, w, v0, c, T, tau, 8)
+    vs = R.forward(w, v0[:, S], T, tau)
+    dw_ref, dv0_ref = R.backward(w, vs, c[:, S], tau)
+    assert np.max(np.abs(vT[:, S] - vs[-1])) < 1e-3
+    assert _rel(dw, dw_ref) < 1e-4
+    assert _rel(dv0[:, S], dv0_ref) < 1e-4
+    rest = np.setdiff1d(np.arange(b), S)
+    assert not np.any(dv0[:, rest])
+
+
 @pytest.mark.parametrize("b,T,ck", [(1, 1, 1), (1, 5, 100), (4, 1, 8), (7, 6, 6), (2, 9, 4)])
 def test_edge_sizes(b, T, ck):
     # one column, one step, a checkpoint interval longer than the run, T a multiple of it

@@ -105,6 +105,9 @@ def test_full_size_2_16_guesses_sampled():
     with lp.Program.from_program(p) as P:
         assert P.info["k"] == 16
         st, models, ns = gpu_stable(P, max_models=256)
+        P.autotune(lp.LP_TUNE_STABLE, reps=1)  # the schedule the benchmark times
+        st_t, models_t, ns_t = gpu_stable(P, max_models=256)
+        assert np.array_equal(st_t, st) and ns_t == ns and np.array_equal(models_t, models)
     rng = np.random.default_rng(0)
     sample = np.unique(np.concatenate([rng.integers(0, 1 << 16, 96), np.nonzero(st)[0][:32], [0, 65535]]))
     st4, m4, _ = oracle.stable_models_alg23(p, guesses=sample.astype(np.uint64), std=s)

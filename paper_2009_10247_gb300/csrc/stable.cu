@@ -11,7 +11,9 @@
 //   1. M_0 words (Def. 8): fact rows all ones; guessed barred rows carry bit j of each guess
 //      (for the full enumeration, a fixed pattern for j < 6 and the guess-word index bits
 //      above); every other row zero;
-//   2. M_{k+1} = theta(M_P M_k) until no word changes (per-tile early exit);
+//   2. M_{k+1} = theta(M_P M_k) until no word changes (per-tile early exit). The columns only
+//      gain true bits from one iterate to the next (theta is monotone and M_1 >= M_0), so the
+//      number of true bits of the tile decides it, and a row's old words are never read;
 //   3. Algorithm 3: a column is stable iff a_q XOR a_q-bar = 1 for every negated atom q, so the
 //      stable bits of a word are the AND over q of (word of q) XOR (word of q-bar);
 //   4. the stable columns of the tile are numbered in guess order and their models (the
@@ -54,7 +56,7 @@ __device__ __forceinline__ uint64_t m0_word(int tag, long long gw, const StableA
 // (dense programs) this replaces one lane walking a whole row. With W = 32 both are the same.
 template <bool SPLIT>
 __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
-  __shared__ int s_flag;
+  __shared__ unsigned long long s_cnt;
   __shared__ long long s_base;
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -73,14 +75,26 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
   for (long long t = 0; t < a.n_tiles; ++t) {
     const long long gw0 = t * W;  // first guess word of the tile
     // The previous tile's readers of the change flags are all past its last barrier.
-    if (gtid == 0) ctl->flag[0] = ctl->flag[1] = ctl->flag[2] = 0u;
+    if (threadIdx.x == 0) s_cnt = 0ull;
+    __syncthreads();
     // ---- 1. M_0
+    unsigned cnt0 = 0;
     for (long long e = gtid; e < tile_words; e += nthreads) {
       const int row = (int)(e >> a.log2W);
       const int w = (int)(e & (W - 1));
-      a.X0[e] = m0_word(__ldg(a.row_tag + row), gw0 + w, a);
+      const uint64_t m0 = m0_word(__ldg(a.row_tag + row), gw0 + w, a);
+      a.X0[e] = m0;
+      cnt0 += __popcll(m0);
+    }
+    cnt0 = __reduce_add_sync(FULL, cnt0);
+    if (lane == 0 && cnt0) atomicAdd(&s_cnt, (unsigned long long)cnt0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_cnt) atomicAdd(&ctl->init_count, s_cnt);
+      s_cnt = 0ull;
     }
     if (!grid_barrier(ctl, ++round, 6)) return;
+    unsigned long long prev_count = ld_volatile64(&ctl->init_count);
 
     // ---- 2. M_{k+1} = theta(M_P M_k) until unchanged
     const uint64_t* fin = a.X0;
@@ -89,7 +103,7 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
     for (; it < a.max_iters; ++it) {
       const uint64_t* src = (it & 1) ? a.X1 : a.X0;
       uint64_t* dst = (it & 1) ? a.X0 : a.X1;
-      bool changed = false;
+      unsigned cnt = 0;  // true bits this thread wrote
       if (SPLIT) {
         const int S = 32 >> a.log2W;  // entry slots per warp
         const int slot = lane >> a.log2W;
@@ -114,7 +128,7 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
           if (end == beg) acc = 0ull;  // an empty row never fires
           if (slot == 0) {
             const long long o = ((long long)row << a.log2W) + wl;
-            changed |= (acc != src[o]);
+            cnt += __popcll(acc);
             dst[o] = acc;
           }
         }
@@ -126,7 +140,6 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
         const uint64_t ident = any ? 0ull : ~0ull;
         uint64_t acc = (end > beg) ? ident : 0ull;
         const long long o = ((long long)row << a.log2W) + wl;
-        const uint64_t old = src[o];
         // four entries per step: their column loads, then their gathers, so that a row costs
         // two dependent memory latencies per four body atoms
         for (int e = beg; e < end; e += 4) {
@@ -139,19 +152,25 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
           const uint64_t orv = vv[0] | vv[1] | vv[2] | vv[3], andv = vv[0] & vv[1] & vv[2] & vv[3];
           acc = any ? (acc | orv) : (acc & andv);
         }
-        changed |= (acc != old);
+        cnt += __popcll(acc);
         dst[o] = acc;
       }
-      const int any_changed = __syncthreads_or(changed);
+      // the iterates only grow (Def. 8 columns under a monotone theta), so the same number of
+      // true bits means the same iterate
+      cnt = __reduce_add_sync(FULL, cnt);
+      if (lane == 0 && cnt) atomicAdd(&s_cnt, (unsigned long long)cnt);
+      __syncthreads();
       if (threadIdx.x == 0) {
-        if (any_changed) atomicOr(&ctl->flag[it % 3], 1u);
-        if (blockIdx.x == 0) ctl->flag[(it + 1) % 3] = 0u;
+        if (s_cnt) atomicAdd(&ctl->count[it % 3], s_cnt);
+        s_cnt = 0ull;
+        if (blockIdx.x == 0) ctl->count[(it + 1) % 3] = 0ull;  // nobody reads or adds to it now
       }
       if (!grid_barrier(ctl, ++round, 6)) return;
-      if (threadIdx.x == 0) s_flag = (int)ld_volatile(&ctl->flag[it % 3]);
-      __syncthreads();
+      const unsigned long long now = ld_volatile64(&ctl->count[it % 3]);
+      const bool again = now != prev_count;
+      prev_count = now;
       fin = dst;
-      if (!s_flag) {
+      if (!again) {
         converged = true;
         ++it;
         break;
@@ -162,7 +181,7 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
         ctl->iters = it;
         atomicCAS(&ctl->status, 0, 4 /* LP_ERR_NO_FIXPOINT */);
       }
-      return;  // every block takes this branch: the flag it read is the same for all
+      return;  // every block takes this branch: the count it read is the same for all
     }
 
     // ---- 3. Algorithm 3 on the W words of the tile
@@ -217,6 +236,10 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
           if (lane == 0) dst[u] = word32;
         }
       }
+    }
+    if (gtid == 0) {  // every block is past this tile's convergence checks
+      ctl->init_count = 0ull;
+      ctl->count[0] = ctl->count[1] = ctl->count[2] = 0ull;
     }
     if (!grid_barrier(ctl, ++round, 6)) return;
     if (gtid == 0) ctl->n_stable = base + tile_count;  // everyone read base before the barrier

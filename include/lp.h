@@ -20,7 +20,10 @@
  *    device memory behind it (the program matrix and solver scratch), released by lp_free.
  *  - Errors: every call returns an lp_status; nothing is thrown across the ABI. The message of
  *    the last error of the calling thread is returned by lp_last_error().
- *  - A program handle must not be used by two calls at the same time (its scratch is shared).
+ *  - A program handle must not be used by two calls at the same time, nor by calls whose device
+ *    work may overlap (the same handle on two streams with no ordering between them): its
+ *    device scratch (iterate vectors, control block, tiles) is shared by its solves. Distinct
+ *    handles are independent and may run concurrently on different streams or threads.
  */
 #ifndef LP_H
 #define LP_H

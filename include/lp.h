@@ -23,7 +23,7 @@
  *  - A program handle must not be used by two calls at the same time, nor by calls whose device
  *    work may overlap (the same handle on two streams with no ordering between them): its
  *    device scratch (iterate vectors, control block, tiles) is shared by its solves. Distinct
- *    handles are independent and may run concurrently on different streams or threads.
+ *    handles share no device scratch (lp_least_model_static excepted, see there).
  */
 #ifndef LP_H
 #define LP_H

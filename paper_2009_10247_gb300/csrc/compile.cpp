@@ -164,9 +164,19 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       for (int64_t e = 0; e < total; e++)
         if (body_neg[e]) bar_id[body_atom[e]] = 0;  // every writer stores the same value
     }
-    int32_t nb = 0;
-    for (int32_t a = 0; a < n; a++)
-      if (bar_id[a] == 0) bar_id[a] = n + nb++;
+    // barred ids n, n + 1, ... in ascending atom order
+    const int32_t nb = (int32_t)blocked_scan(
+        n,
+        [&](int64_t a0, int64_t a1) {
+          int64_t c = 0;
+          for (int64_t a = a0; a < a1; a++) c += bar_id[a] == 0;
+          return c;
+        },
+        [](int64_t) {},
+        [&](int64_t a0, int64_t a1, int64_t k) {
+          for (int64_t a = a0; a < a1; a++)
+            if (bar_id[a] == 0) bar_id[a] = (int32_t)(n + k++);
+        });
     // new atoms for the rules of multi-rule heads, in rule order (blocked prefix count)
     hvec<int32_t> aux;
     par_fill(aux, (size_t)n_rules, -1);
@@ -229,7 +239,17 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     // writes contiguous ranges.
     hvec<int64_t> hr_off((size_t)n + 1);
     hr_off[0] = 0;
-    for (int32_t a = 0; a < n; a++) hr_off[a + 1] = hr_off[a] + cnt[a];
+    blocked_scan(
+        n,
+        [&](int64_t a0, int64_t a1) {
+          int64_t c = 0;
+          for (int64_t a = a0; a < a1; a++) c += cnt[a];
+          return c;
+        },
+        [](int64_t) {},
+        [&](int64_t a0, int64_t a1, int64_t off) {
+          for (int64_t a = a0; a < a1; a++) hr_off[a + 1] = off += cnt[a];
+        });
     // Rules grouped by head, in rule order within a head: a counting sort over contiguous rule
     // ranges, one per thread (per-thread head counts, a scan over the threads per head, then
     // each thread writes its range in order).
@@ -354,6 +374,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       // section A by descending references, ties by canonical id: unique keys, so any sort
       // gives the same order
       int64_t maxdeg = 0;
+#pragma omp parallel for reduction(max : maxdeg) schedule(static)
       for (int32_t c = 0; c < nA; c++) maxdeg = std::max(maxdeg, deg[c]);
       hvec<uint64_t> key(nA);
 #pragma omp parallel for schedule(static)
@@ -362,10 +383,21 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
 #pragma omp parallel for schedule(static)
       for (int32_t i = 0; i < nA; i++) inv[i] = (int32_t)(key[i] & 0xffffffffu);
       // section B: each OR row's new atoms, OR rows in section-A order
-      for (int32_t i = 0; i < nA; i++) {
+      auto n_new = [&](int64_t i) -> int64_t {
         const int32_t c = inv[i];
-        bpos[i + 1] = bpos[i] + (kind[c] == K_OR ? hr_off[c + 1] - hr_off[c] : 0);
-      }
+        return kind[c] == K_OR ? hr_off[c + 1] - hr_off[c] : 0;
+      };
+      blocked_scan(
+          nA,
+          [&](int64_t i0, int64_t i1) {
+            int64_t c = 0;
+            for (int64_t i = i0; i < i1; i++) c += n_new(i);
+            return c;
+          },
+          [](int64_t) {},
+          [&](int64_t i0, int64_t i1, int64_t off) {
+            for (int64_t i = i0; i < i1; i++) bpos[i + 1] = off += n_new(i);
+          });
       if (nA + bpos[nA] != np) {
         err = "internal error: new atoms not covered by OR rows";
         return LP_ERR_INVALID;

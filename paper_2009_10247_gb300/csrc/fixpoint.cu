@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(MAP == 0 ? kFixBlockMap0 : kFixBlockRows) fixp
         }
       }
     } else if constexpr (MAP == 3) {
-      changed = theta_rows_pipelined<6>(a, src, dst, gwarp, nwarps, lane);
+      changed = theta_rows_pipelined<5>(a, src, dst, gwarp, nwarps, lane);
     } else if (G == 1) {
       int w = gwarp;
       for (; w + nwarps < a.n_words; w += 2 * nwarps) {

@@ -44,7 +44,7 @@ inline int fix_block(int row_map) { return row_map == 0 ? kFixBlockMap0 : kFixBl
 // row_map 0 (a warp per 32-row word, entries in 32-entry chunks): row_split = warps per word
 // (1, 2, 4 or 8), chunk_batch = chunks whose loads a warp issues together (1 or 4). row_map 1,
 // 2, 3 (a thread per row: two words per warp step with 8 column ids per pass, four words, or
-// loads pipelined over the warp's words with 6 ids staged per row) take row_split =
+// loads pipelined over the warp's words with 5 ids staged per row) take row_split =
 // chunk_batch = 1.
 cudaError_t launch_fixpoint(const FixArgs& a, int grid, int row_split, int chunk_batch, int row_map, cudaStream_t s);
 int fixpoint_blocks_per_sm(int row_split, int chunk_batch, int row_map);

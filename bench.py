@@ -218,8 +218,8 @@ def main():
     ap.add_argument("--batch-iter-profile", action="store_true",
                     help="add the program batch's cumulative time after each lock-step iteration")
     ap.add_argument("--no-tune", action="store_true",
-                    help="default schedules instead of lp_autotune's (for profiler captures: on the least-model and "
-                         "2^16-guess workloads the tuner picks the defaults)")
+                    help="default schedules instead of lp_autotune's (for profiler captures: on the 2^16-guess "
+                         "workload the tuner picks the default; pin the least-model schedule with --schedule)")
     ap.add_argument("--schedule", default="",
                     help="pin the least-model schedule instead of tuning it: comma-separated lp_schedule "
                          "field=value pairs, e.g. fixpoint_row_map=1 (for profiler captures of one variant)")

@@ -445,10 +445,16 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     hm.col.resize((size_t)nnz);  // the passes below write every entry of every row
     // rule rows: walk the rules in order (sequential reads of the body sets) and scatter each
     // body, mapped to internal ids and sorted, into its row
+    // (the target row's position and entry range are random accesses: they are prefetched a
+    // few rules ahead)
+    constexpr int64_t kAhead = 16;
+    auto target = [&](int64_t r) { return aux[r] >= 0 ? aux[r] : head[r]; };
 #pragma omp parallel for schedule(dynamic, 4096)
     for (int64_t r = 0; r < n_rules; r++) {
+      if (r + kAhead < n_rules) __builtin_prefetch(&hm.perm[target(r + kAhead)]);
+      if (r + kAhead / 2 < n_rules) __builtin_prefetch(&hm.row_ptr[hm.perm[target(r + kAhead / 2)]]);
       if (setlen[r] == 0) continue;  // a fact: its row is a self-loop
-      const int32_t i = hm.perm[aux[r] >= 0 ? aux[r] : head[r]];
+      const int32_t i = hm.perm[target(r)];
       int32_t* d = hm.col.data() + hm.row_ptr[i];
       const int32_t* sb = rb.data() + body_off[r];
       for (int32_t t = 0; t < setlen[r]; t++) d[t] = hm.perm[sb[t]];

@@ -270,7 +270,10 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         const int64_t r0 = n_rules * t / nt, r1 = n_rules * (t + 1) / nt;
         int32_t* c = tcnt.data() + (size_t)t * n;
         std::fill(c, c + n, 0);  // each thread clears its own counts
-        for (int64_t r = r0; r < r1; r++) c[head[r]]++;
+        for (int64_t r = r0; r < r1; r++) {
+          if (r + 16 < r1) __builtin_prefetch(&c[head[r + 16]], 1);
+          c[head[r]]++;
+        }
 #pragma omp barrier
 #pragma omp for schedule(static)
         for (int32_t a = 0; a < n; a++) {  // exclusive offsets of each thread within head a
@@ -282,6 +285,10 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
           }
         }
         for (int64_t r = r0; r < r1; r++) {
+          if (r + 16 < r1) {
+            __builtin_prefetch(&hr_off[head[r + 16]]);
+            __builtin_prefetch(&c[head[r + 16]], 1);
+          }
           const int32_t h = head[r];
           by_head[hr_off[h] + c[h]++] = (int32_t)r;
         }
@@ -412,7 +419,10 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     }
     hm.perm.resize(np);  // inv is a permutation
 #pragma omp parallel for schedule(static)
-    for (int32_t i = 0; i < np; i++) hm.perm[inv[i]] = i;
+    for (int32_t i = 0; i < np; i++) {
+      if (i + 16 < np) __builtin_prefetch(&hm.perm[inv[i + 16]], 1);
+      hm.perm[inv[i]] = i;
+    }
     const int32_t npad = (int32_t)(((int64_t)np + 63) / 64 * 64);
 
     // ---- internal CSR
@@ -423,6 +433,10 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     hvec<int8_t> ikind(np);  // kind of internal row i
 #pragma omp parallel for schedule(static)
     for (int32_t c = 0; c < np; c++) {
+      if (c + 16 < np) {
+        __builtin_prefetch(&hm.row_ptr[hm.perm[c + 16] + 1], 1);
+        __builtin_prefetch(&ikind[hm.perm[c + 16]], 1);
+      }
       const int32_t i = hm.perm[c];
       hm.row_ptr[i + 1] = (int32_t)row_len(c);
       ikind[i] = kind[c];

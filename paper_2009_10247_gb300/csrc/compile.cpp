@@ -158,7 +158,10 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     par_fill(cnt, (size_t)n, 0);
     par_fill(bar_id, (size_t)n, -1);
 #pragma omp parallel for schedule(static)
-    for (int64_t r = 0; r < n_rules; r++) __atomic_fetch_add(&cnt[head[r]], 1, __ATOMIC_RELAXED);
+    for (int64_t r = 0; r < n_rules; r++) {
+      if (r + 16 < n_rules) __builtin_prefetch(&cnt[head[r + 16]], 1);
+      __atomic_fetch_add(&cnt[head[r]], 1, __ATOMIC_RELAXED);
+    }
     if (body_neg) {
 #pragma omp parallel for schedule(static)
       for (int64_t e = 0; e < total; e++)

@@ -85,6 +85,15 @@ def test_compile_generators(lib):
     _compare_with_oracle(normal_program(seed=4, n=3000, n_rules=9000, k=8, per_atom=3))
 
 
+def test_compile_full_size_programs(lib):
+    # the benchmark's programs at full size: the large definite program (5e6 rules) and the
+    # 2^16-guess normal program, compiled by the parallel host compiler, equal the oracle's
+    # standardization row for row (the internal order is checked by the solves on the GPU)
+    from workloads import large_definite
+    _compare_with_oracle(large_definite(seed=1))
+    _compare_with_oracle(normal_program(seed=1))
+
+
 def test_compile_rejects_malformed(lib):
     def compile_raw(n, head, off, atom, neg=None):
         return lp.Program(n, np.array(head), np.array(off), np.array(atom), neg, host_only=True)

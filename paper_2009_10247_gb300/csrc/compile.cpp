@@ -524,9 +524,9 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
           for (int64_t c = c0; c < c1; c++) f += kind[c] == K_FACT;
           return f;
         },
-        [&](int64_t total) {
-          hm.fact_row.resize((size_t)total);
-          hm.fact_owner.resize((size_t)total);
+        [&](int64_t n_fact_rows) {
+          hm.fact_row.resize((size_t)n_fact_rows);
+          hm.fact_owner.resize((size_t)n_fact_rows);
         },
         [&](int64_t c0, int64_t c1, int64_t f) {
           for (int64_t c = c0; c < c1; c++)

@@ -32,7 +32,7 @@ struct Timer {
 // One candidate: warm-up, reps timed runs (median), result copied to `bits` for comparison.
 // run() issues the solve on the stream; returns LP_OK or an error (candidate skipped on OOM).
 template <typename Run>
-lp_status time_candidate(lp_program* p, Run run, int reps, cudaStream_t s, const void* result, size_t result_bytes,
+lp_status time_candidate(Run run, int reps, cudaStream_t s, const void* result, size_t result_bytes,
                          std::vector<uint8_t>& bits, float* ms_out) {
   Timer t;
   lp_status st = run();
@@ -103,7 +103,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
       p->sched = c;
       float ms = -1.f;
       st = time_candidate(
-          p, [&] { return lp_least_model(p, nullptr, out, 1 << 30, 0u, nullptr, cuda_stream); }, reps, s, out,
+          [&] { return lp_least_model(p, nullptr, out, 1 << 30, 0u, nullptr, cuda_stream); }, reps, s, out,
           out_bytes, bits, &ms);
       if (st == LP_ERR_OOM) {
         recs.push_back({c, (int32_t)LP_TUNE_LEAST, -1.f});
@@ -162,7 +162,6 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
       p->sched = c;
       float ms = -1.f;
       st = time_candidate(
-          p,
           [&] { return lp_stable_models(p, guesses, n_guesses, mask, nullptr, 0, nullptr, 1 << 30, cuda_stream); },
           reps, s, mask, (size_t)n_gwords * 8, bits, &ms);
       if (st == LP_ERR_OOM) {

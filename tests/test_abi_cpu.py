@@ -79,6 +79,18 @@ def test_compile_tiny_random(lib, seed):
                                      max_body=5, p_fact=0.25, p_neg=0.2 if seed % 2 else 0.0))
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_compile_medium_random(lib, seed):
+    # larger random programs than the brute-force ones: many heads with several rules, facts
+    # that also head rules, repeated body atoms, negation on a third of the programs, and a few
+    # long bodies (the parallel compiler splits every phase over its threads)
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(50, 400))
+    _compare_with_oracle(tiny_random(900 + seed, n_atoms=n, n_rules=int(rng.integers(n, 6 * n)),
+                                     max_body=int(rng.choice([3, 8, 40])), p_fact=float(rng.uniform(0.02, 0.3)),
+                                     p_neg=0.15 if seed % 3 == 0 else 0.0))
+
+
 def test_compile_generators(lib):
     _compare_with_oracle(small_definite(2))
     _compare_with_oracle(transitive_closure(40, 3.0, seed=2))

@@ -211,3 +211,39 @@ def test_check_matrix_on_host_copies(lib):
     for prog in progs:
         with lp.Program.from_program(prog, host_only=True) as P:
             assert P.check_matrix() == 0
+
+
+def test_concurrent_host_compiles_and_thread_local_errors(lib):
+    # the host compiler may run on several caller threads at once (each with its own OpenMP
+    # team), and lp_last_error belongs to the calling thread
+    import threading
+
+    progs = [normal_program(seed=20 + i, n=2000, n_rules=6000, k=5) for i in range(4)]
+    want = [oracle.standardize(p) for p in progs]
+    results, errors = [None] * 4, [None] * 4
+    barrier = threading.Barrier(5)
+
+    def compile_one(i):
+        barrier.wait()
+        with lp.Program.from_program(progs[i], host_only=True) as P:
+            results[i] = P.export_matrix()
+
+    def fail_one():
+        barrier.wait()
+        for _ in range(20):
+            try:
+                lp.Program(2, np.array([0, 5]), np.array([0, 0, 1]), np.array([1]), None, host_only=True)
+            except lp.LPError as e:
+                errors[0] = str(e)
+        errors[1] = lib.lp_last_error().decode()  # this thread's last error, not another thread's
+
+    threads = [threading.Thread(target=compile_one, args=(i,)) for i in range(4)] + [threading.Thread(target=fail_one)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    for m, s in zip(results, want):
+        assert m is not None
+        assert np.array_equal(m["row_ptr"], s.row_ptr) and np.array_equal(m["col"], s.col)
+    assert errors[0] and "out of range" in errors[0]
+    assert "out of range" in errors[1]

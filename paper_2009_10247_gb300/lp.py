@@ -126,6 +126,8 @@ def _ptr(x):
     if x is None:
         return None
     if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensor must be contiguous (liblp reads and writes buffers as dense arrays)")
         return ctypes.c_void_p(x.data_ptr())
     if isinstance(x, np.ndarray):
         if not x.flags["C_CONTIGUOUS"]:

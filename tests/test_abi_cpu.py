@@ -247,3 +247,14 @@ def test_concurrent_host_compiles_and_thread_local_errors(lib):
         assert np.array_equal(m["row_ptr"], s.row_ptr) and np.array_equal(m["col"], s.col)
     assert errors[0] and "out of range" in errors[0]
     assert "out of range" in errors[1]
+
+
+def test_binding_rejects_strided_buffers(lib):
+    # liblp reads and writes dense arrays: a strided view must not reach it
+    import torch
+    t = torch.zeros(8, dtype=torch.int64)
+    with pytest.raises(ValueError):
+        lp.lp._ptr(t[::2])
+    with pytest.raises(ValueError):
+        lp.lp._ptr(np.zeros(8, np.int64)[::2])
+    assert lp.lp._ptr(t).value == t.data_ptr()

@@ -238,8 +238,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     }
 
     // ---- canonical rows: kind, defining rule, rules of each head (in rule order)
-    // One parallel sort of (head, rule) keys groups the rules by head; every pass after it
-    // writes contiguous ranges.
+    // hr_off: first position of each head's rules in the grouped order (a scan of the counts).
     hvec<int64_t> hr_off((size_t)n + 1);
     hr_off[0] = 0;
     blocked_scan(

@@ -219,6 +219,29 @@ def test_textbook_stable_models(text, expected):
     assert oracle.brute_stable_models(p) == want
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_stable_model_counts_in_closed_form(n):
+    # n independent even loops a_i <- not b_i, b_i <- not a_i: each picks one atom, 2^n models
+    # (every combination); adding n odd loops p_i <- not q_i, q_i <- not r_i, r_i <- not p_i
+    # leaves none; adding instead f <- a_0, not f removes the models with a_0: 2^(n-1)
+    pairs = " ".join(f"a{i} :- not b{i}. b{i} :- not a{i}." for i in range(n))
+    p = parse(pairs)
+    st, models, _ = oracle.stable_models_alg23(p)
+    got = _models_of(p, st, models)
+    names = p.names
+    want = sorted(sum(1 << names.index((f"a{i}" if (c >> i) & 1 else f"b{i}")) for i in range(n))
+                  for c in range(1 << n))
+    assert got == want
+    odd = " ".join(f"p{i} :- not q{i}. q{i} :- not r{i}. r{i} :- not p{i}." for i in range(n))
+    st, _, _ = oracle.stable_models_alg23(parse(pairs + " " + odd))
+    assert int(st.sum()) == 0
+    p = parse(pairs + " f :- a0, not f.")
+    st, models, _ = oracle.stable_models_alg23(p)
+    assert int(st.sum()) == 1 << (n - 1)
+    a0 = p.names.index("a0")
+    assert not any(models[i][a0] for i in np.nonzero(st)[0])
+
+
 @pytest.mark.parametrize("seed", range(40))
 def test_stable_models_alg23_equals_gl_and_brute(seed):
     rng = np.random.default_rng(1000 + seed)

@@ -92,6 +92,26 @@ def test_least_model_three_ways(seed):
     assert 1 <= iters <= s.n_prime + 1
 
 
+@pytest.mark.parametrize("length", [1, 2, 7, 40])
+def test_iteration_counts_in_closed_form(length):
+    # a chain a_0. a_i <- a_{i-1}: a_i becomes true in theta application i, and one more
+    # application shows no change, so length + 1 applications (Example 1 counts the same way)
+    rules = [(0, [])] + [(i, [i - 1]) for i in range(1, length + 1)]
+    got, iters = oracle.least_model(from_rules(length + 1, rules))
+    assert got.all() and iters == length + 1
+    # a rule joining the ends of two chains of lengths L and L // 2 fires one application
+    # after the longer chain's end: L + 2 applications; a second rule for the same head that
+    # also waits for that end turns it into an OR row over two new atoms, one more level: L + 3
+    short = length // 2
+    n = (length + 1) + (short + 1) + 1
+    rules = ([(0, [])] + [(i, [i - 1]) for i in range(1, length + 1)] + [(length + 1, [])]
+             + [(length + 1 + i, [length + i]) for i in range(1, short + 1)] + [(n - 1, [length, length + 1 + short])])
+    got, iters = oracle.least_model(from_rules(n, rules))
+    assert got.all() and iters == length + 2
+    got, iters = oracle.least_model(from_rules(n, rules + [(n - 1, [length])]))
+    assert got.all() and iters == length + 3
+
+
 @pytest.mark.parametrize("seed", range(20))
 def test_least_model_fact_subsets(seed):
     # An initial vector holding a subset of the facts computes the least model of the program

@@ -73,3 +73,19 @@ def test_committed_records_name_existing_sources(key):
         assert r["bytes_per_launch"] == r["dram_bytes_read"] + r["dram_bytes_write"]
         for src in r["sources"]:
             assert os.path.exists(os.path.join(ROOT, src)), src
+
+
+def test_profile_commands_use_existing_bench_options():
+    # every bench.py option that a committed ncu summary's command line uses exists, so the
+    # summaries' commands still run
+    import re
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    known = set(re.findall(r'add_argument\("(--[a-z0-9-]+)"', src))
+    prof = os.path.join(ROOT, "profiles")
+    used = set()
+    for name in os.listdir(prof):
+        if name.endswith(".md"):
+            text = open(os.path.join(prof, name)).read()
+            for cmd in re.findall(r"python bench\.py[^\n]*(?:\\\n[^\n]*)*", text):
+                used |= set(re.findall(r"(--[a-z0-9-]+)", cmd))
+    assert used and used <= known, sorted(used - known)

@@ -34,6 +34,13 @@ from workloads import (large_definite, normal_program, program_batch, table1_pro
 METRIC = "fixpoint rule-evals/sec (nnz x iters / s)"
 UNIT = "rule-evals/s"
 WORKLOAD = "large definite program: 1e6 atoms, 5e6 rules, Geom(mean 3, cap 8) bodies, Zipf(1.1) atoms, 1% facts, chain 1000x50 (seed 1)"
+
+
+def workload_name(n_atoms, seed):
+    """WORKLOAD for another size or seed of the same generator."""
+    w = WORKLOAD if n_atoms == 1_000_000 else WORKLOAD.replace("1e6 atoms, 5e6 rules",
+                                                               f"{n_atoms} atoms, {5 * n_atoms} rules")
+    return w.replace("(seed 1)", f"(seed {seed})")
 WORKLOAD_STABLE = "normal program: 1e5 atoms, 3e5 rules, bodies U{1..6}, 1% facts, k=16 negated atoms x 4 (seed 1), all 65536 guesses"
 WORKLOAD_BATCH = ("1000 normal programs: atoms log-uniform in [100, 20000], 3 rules per atom, k ~ U{4..8} negated atoms "
                   "x 2, bodies U{1..6} (seed 1), all 2^k guesses of every program")
@@ -152,12 +159,12 @@ def cpu_oracle_sample(prog, iters, std=None):
     return std, done, dt, oracle.num_threads()
 
 
-def cpu_oracle_single_thread(n_atoms, iters):
+def cpu_oracle_single_thread(n_atoms, iters, seed=1):
     """The same oracle sample with one OpenMP thread, in a child process (the thread count of
     the oracle's library is fixed when it loads)."""
     code = ("import time, oracle\n"
             "from workloads import large_definite\n"
-            f"p = large_definite(seed=1, n={n_atoms}, n_rules={5 * n_atoms})\n"
+            f"p = large_definite(seed={seed}, n={n_atoms}, n_rules={5 * n_atoms})\n"
             "s = oracle.standardize(p)\n"
             "v = oracle.initial_vector(s)\n"
             "t = time.perf_counter()\n"
@@ -195,7 +202,7 @@ def run_reference(args, prog):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_prime": std.n_prime, "nnz": std.nnz},
+        "config": {"workload": workload_name(args.n_atoms, args.seed), "n_prime": std.n_prime, "nnz": std.nnz},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -223,6 +230,7 @@ def main():
     ap.add_argument("--schedule", default="",
                     help="pin the least-model schedule instead of tuning it: comma-separated lp_schedule "
                          "field=value pairs, e.g. fixpoint_row_map=1 (for profiler captures of one variant)")
+    ap.add_argument("--seed", type=int, default=1, help="seed of the least-model workload (default 1)")
     ap.add_argument("--n-atoms", type=int, default=1_000_000,
                     help="atoms of the least-model workload (5 rules per atom); smaller for profiler captures")
     args = ap.parse_args()
@@ -235,7 +243,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        run_reference(args, large_definite(seed=1, n=args.n_atoms, n_rules=5 * args.n_atoms))
+        run_reference(args, large_definite(seed=args.seed, n=args.n_atoms, n_rules=5 * args.n_atoms))
         return
 
     import torch
@@ -249,7 +257,7 @@ def main():
     dev = torch.device("cuda", local)
     lp.load()
 
-    prog = large_definite(seed=1, n=args.n_atoms, n_rules=5 * args.n_atoms)
+    prog = large_definite(seed=args.seed, n=args.n_atoms, n_rules=5 * args.n_atoms)
     P = lp.Program.from_program(prog)
     info = P.info
     n, n_prime, nnz = info["n_atoms"], info["n_prime"], info["nnz"]
@@ -350,15 +358,14 @@ def main():
         cpu = {"value": std.nnz * done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"Algorithm 1 (oracle O2, OpenMP over rows) on the same full matrix, first {done} of "
                          f"{iters} theta applications from the fact vector ({dt:.1f} s)",
-               "single_thread": cpu_oracle_single_thread(args.n_atoms, max(1, args.cpu_iters // 10))}
+               "single_thread": cpu_oracle_single_thread(args.n_atoms, max(1, args.cpu_iters // 10), args.seed)}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if n == 1_000_000 else WORKLOAD.replace("1e6 atoms, 5e6 rules",
-                                                                                    f"{n} atoms, {5 * n} rules"),
+            "config": {"workload": workload_name(n, args.seed),
                        "n_atoms": n, "n_rules": int(prog.n_rules), "n_prime": n_prime,
                        "nnz": nnz, "iters": iters, "parallelism": f"replicas x{world}",
                        "schedule": P.schedule, "tuned_candidates": len(tuned),

@@ -278,6 +278,30 @@ class Program:
             out.append(d)
         return out
 
+    def autotune_cached(self, cache_path, what=LP_TUNE_LEAST | LP_TUNE_STABLE, reps=3, stream=None):
+        """lp_autotune once per program shape: the chosen schedule is stored in a JSON file under a
+        key of the program's sizes and reused on later calls (a schedule only changes the mapping
+        onto the GPU, never the result, so two programs of the same sizes may share one). Returns
+        True if the schedule came from the file, False if it was tuned now."""
+        import json
+        i = self.info
+        key = f"n'={i['n_prime']},nnz={i['nnz']},k={i['k']},or={i['n_or_rows']},what={int(what)}"
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            self.set_schedule(**{f: int(v) for f, v in cache[key].items() if f in SCHEDULE_FIELDS})
+            return True
+        self.autotune(what, reps, stream)
+        cache[key] = self.schedule
+        tmp = f"{cache_path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+        return False
+
     def stable_search(self, population=1024, rounds=16, seed=1, max_found=1 << 16, stream=None):
         """Sampled guesses + local search (lp_stable_search); returns the distinct stable guesses
         found (uint64 numpy array, ascending) and their total count."""

@@ -258,3 +258,20 @@ def test_binding_rejects_strided_buffers(lib):
     with pytest.raises(ValueError):
         lp.lp._ptr(np.zeros(8, np.int64)[::2])
     assert lp.lp._ptr(t).value == t.data_ptr()
+
+
+def test_autotune_cache_reuses_a_stored_schedule(lib, tmp_path):
+    # a stored schedule is applied without tuning (a host-only handle cannot run the tuner);
+    # a miss tunes, which a host-only handle refuses, and leaves the file as it was
+    import json
+    path = str(tmp_path / "schedules.json")
+    with lp.Program.from_program(small_definite(1), host_only=True) as P:
+        with pytest.raises(lp.LPError):
+            P.autotune_cached(path)
+        assert not os.path.exists(path)
+        i = P.info
+        key = f"n'={i['n_prime']},nnz={i['nnz']},k={i['k']},or={i['n_or_rows']},what={lp.LP_TUNE_LEAST | lp.LP_TUNE_STABLE}"
+        want = dict(P.schedule, fixpoint_row_map=3, stable_tile_words=8)
+        json.dump({key: want}, open(path, "w"))
+        assert P.autotune_cached(path) is True
+        assert P.schedule == want

@@ -43,3 +43,17 @@ def is_model(prog, I) -> bool:
     cs = np.concatenate([[0], np.cumsum(~I[prog.body_atom])])
     body_true = (cs[prog.body_off[1:]] - cs[prog.body_off[:-1]]) == 0
     return bool(np.all(~body_true | I[prog.head]))
+
+
+def program_fingerprint(prog) -> str:
+    """SHA-256 over a program's arrays (atom count, heads, body offsets, atoms, negation marks):
+    a stored expected value applies only to the program it was computed on."""
+    import hashlib
+
+    h = hashlib.sha256()
+    h.update(np.int64(prog.n_atoms).tobytes())
+    for a, dt in ((prog.head, np.int32), (prog.body_off, np.int64), (prog.body_atom, np.int32)):
+        h.update(np.ascontiguousarray(a, dtype=dt).tobytes())
+    if getattr(prog, "body_neg", None) is not None:
+        h.update(np.ascontiguousarray(prog.body_neg, dtype=np.uint8).tobytes())
+    return h.hexdigest()

@@ -3,8 +3,9 @@
 The stable bit of every guess and every returned model are compared bit for bit with the
 oracle's per-guess Algorithm 2/3 (and its Gelfond-Lifschitz check), on the paper's example,
 textbook programs, tiny random normal programs, multi-tile runs, explicit guess lists, and
-the full-size 2^16-guess workload in the configuration the benchmark times (sampled guesses
-plus a reduct check of every model found)."""
+the full-size 2^16-guess workload in the configuration the benchmark times (every one of the
+65,536 stable bits against the oracle's Algorithms 2/3, per-tile iteration counts, and a reduct
+check of the models found)."""
 import os
 
 import numpy as np
@@ -12,7 +13,7 @@ import pytest
 
 import oracle
 import paper_2009_10247_gb300 as lp
-from tests.helpers import golden
+from tests.helpers import golden, program_fingerprint
 from workloads import normal_program, parse, small_definite, tiny_random
 
 torch = pytest.importorskip("torch")
@@ -118,3 +119,38 @@ def test_full_size_2_16_guesses_sampled():
         st5, m5 = oracle.stable_models_gl(p, guesses=idx[:32].astype(np.uint64), std=s)
         assert st5.all()
         assert np.array_equal(models[:min(32, len(idx))], m5)
+
+
+def _full_size_expected(prog):
+    """Stable bits of all 2^16 guesses of normal_program(seed=1) by the oracle's Algorithms 2/3,
+    and per 64-guess word the largest iteration count of its columns: stored by
+    tests/golden/make_normal_program_stable.py, recomputed by the oracle (minutes) if the
+    generator yields another program than the one stored."""
+    g = golden("normal_program_seed1_stable.json")
+    if g["fingerprint"] == program_fingerprint(prog):
+        st = np.zeros(g["n_guesses"], dtype=bool)
+        st[np.asarray(g["stable"], dtype=np.int64)] = True
+        return st, np.asarray(g["word_max_iters"], dtype=np.int64)
+    st, _, iters = oracle.stable_models_alg23(prog, want_models=False)
+    return st, iters.reshape(-1, 64).max(axis=1)
+
+
+def test_full_size_2_16_guesses_every_bit():
+    # all 65,536 guesses in one call, default and tuned schedules: every stable bit equals the
+    # oracle's, and every tile's iteration count is the largest of its columns' counts
+    p = normal_program(seed=1)
+    want, word_iters = _full_size_expected(p)
+    assert len(want) == 1 << 16
+    with lp.Program.from_program(p) as P:
+        for tuned in (False, True):
+            if tuned:
+                P.autotune(lp.LP_TUNE_STABLE, reps=1)  # the schedule the benchmark times
+            st, _, ns = gpu_stable(P)
+            assert np.array_equal(st, want), f"tuned={tuned}: {np.count_nonzero(st != want)} guesses differ"
+            assert ns == int(want.sum())
+            stats = P.last_stats()
+            W = stats["tile_words"]
+            per_tile = word_iters.reshape(-1, W).max(axis=1)
+            assert stats["tiles"] == len(per_tile)
+            assert stats["max_tile_iters"] == per_tile.max()
+            assert stats["sum_tile_iters"] == per_tile.sum()

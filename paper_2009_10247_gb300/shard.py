@@ -31,9 +31,21 @@ def program_range(n_programs: int, rank: int, world: int) -> Tuple[int, int]:
     return n_programs * rank // world, n_programs * (rank + 1) // world
 
 
+def collective_device(group=None):
+    """Device of the tensors a collective on `group` takes: the current CUDA device for an NCCL
+    group (NCCL moves device memory only), the CPU for gloo and the others."""
+    import torch
+    import torch.distributed as dist
+
+    if dist.get_backend(group) == "nccl":
+        return torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cpu")
+
+
 def gather_mask(local_words: np.ndarray, n_guesses: int, group=None) -> np.ndarray:
     """Concatenate every rank's mask words (rank order) into the full mask of n_guesses bits,
-    on every rank. local_words: uint64 words of this rank's guess_range."""
+    on every rank. local_words: uint64 words of this rank's guess_range. The gather runs on
+    the group's collective device (collective_device)."""
     import torch
     import torch.distributed as dist
 
@@ -46,10 +58,10 @@ def gather_mask(local_words: np.ndarray, n_guesses: int, group=None) -> np.ndarr
     width = max(counts) if counts else 0
     mine = np.zeros(max(width, 1), dtype=np.uint64)
     mine[:len(local_words)] = local_words
-    t = torch.from_numpy(mine.view(np.int64).copy())
+    t = torch.from_numpy(mine.view(np.int64).copy()).to(collective_device(group))
     parts = [torch.zeros_like(t) for _ in range(world)]
     dist.all_gather(parts, t, group=group)
-    full = np.concatenate([p.numpy().view(np.uint64)[:c] for p, c in zip(parts, counts)]) if world else np.zeros(0)
+    full = np.concatenate([p.cpu().numpy().view(np.uint64)[:c] for p, c in zip(parts, counts)]) if world else np.zeros(0)
     assert len(full) == n_words
     return full
 

@@ -1,6 +1,7 @@
 """The sharded stable-model path with liblp doing each range (one rank here; the multi-rank
 host logic is covered on CPU): guess ranges through explicit guess lists gather to the same
-mask as one call over all 2^k guesses."""
+mask as one call over all 2^k guesses, through a gloo group and through an NCCL group (the
+backend the multi-GPU benchmark opens, which gathers device tensors)."""
 import os
 import socket
 
@@ -15,7 +16,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_sharded_equals_unsharded():
+@pytest.mark.parametrize("backend", ["gloo", "nccl"])
+def test_sharded_equals_unsharded(backend):
     import torch.distributed as dist
 
     s = socket.socket()
@@ -23,7 +25,11 @@ def test_sharded_equals_unsharded():
     port = s.getsockname()[1]
     s.close()
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=0, world_size=1)
+    torch.cuda.set_device(0)
+    if backend == "nccl":
+        dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda", 0))
+    else:
+        dist.init_process_group("gloo", rank=0, world_size=1)
     try:
         prog = normal_program(seed=6, n=5000, n_rules=15000, k=12, per_atom=2)
         with lp.Program.from_program(prog) as P:

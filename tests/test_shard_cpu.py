@@ -139,3 +139,17 @@ def test_relaxed_columns_and_weight_allreduce(tmp_path):
         assert np.allclose(np.load(tmp_path / f"dw{r}.npy"), dw, rtol=1e-12, atol=1e-14)
     assert np.allclose(np.concatenate([np.load(tmp_path / "dv0.npy"), np.load(tmp_path / "dv1.npy")], axis=1), dv0,
                        rtol=1e-12, atol=1e-14)
+
+
+def test_collective_device_follows_backend(monkeypatch):
+    # NCCL takes device tensors only; gloo takes host tensors
+    import torch
+    import torch.distributed as dist
+
+    from paper_2009_10247_gb300 import shard
+
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 3)
+    monkeypatch.setattr(dist, "get_backend", lambda group=None: "nccl")
+    assert shard.collective_device() == torch.device("cuda", 3)
+    monkeypatch.setattr(dist, "get_backend", lambda group=None: "gloo")
+    assert shard.collective_device() == torch.device("cpu")

@@ -245,7 +245,15 @@ typedef struct {
   int32_t fixpoint_kernel;        /* least model: 0 = warps over 32-row output words, the words'
                                      entries in 32-entry chunks; 1 = rows streamed through shared
                                      memory in bulk-copy stages (its layout is built from the
-                                     device matrix on first use, which downloads the CSR once)   */
+                                     device matrix on first use, which downloads the CSR once);
+                                     2 = a sliced layout: rows renumbered by length within
+                                     windows, 128-row groups padded to their longest row and
+                                     stored column-major, a lane per row, blocks given equal
+                                     shares of the work (built on the device from the CSR on
+                                     first use); 3 = one block with the
+                                     whole CSR and both vectors in shared memory, a block barrier
+                                     per iteration (small programs only: LP_ERR_INVALID if the
+                                     matrix does not fit one block's shared memory)              */
   int32_t fixpoint_blocks_per_sm; /* least model: resident CTAs per SM; 0 = all that fit        */
   int32_t fixpoint_row_split;     /* least model, kernel 0: warps sharing one 32-row output word
                                      (1, 2, 4 or 8; 0 = 1): more for programs with long rows    */
@@ -262,6 +270,9 @@ typedef struct {
   int32_t stable_blocks_per_sm;   /* stable models: resident CTAs per SM; 0 = all that fit      */
   int32_t stable_row_split;       /* stable models: 1 = one row per warp, its entries split over
                                      the warp's lane groups (long rows); 0 = 32 / W rows per warp */
+  int32_t fixpoint_stage;         /* least model, kernel 2: 0 = copy the vector prefix that rule
+                                     rows gather into shared memory every iteration when it fits
+                                     (160 KB); 1 = gather from global memory (through L1)         */
 } lp_schedule;
 
 typedef struct {
@@ -288,7 +299,8 @@ lp_status lp_set_schedule(lp_program* prog, const lp_schedule* schedule);
  * max_records entries, one per candidate in the order run; *n_records (nullable) = number of
  * candidates. Blocks the calling thread. Candidates: least model, kernel 0 with all / 4 / 2
  * CTAs per SM, kernel 0 with row splits 1, 2, 4, 8 and chunk batches 1, 4, kernel 0 with row
- * maps 1, 2, 3, and kernel 1 with all / 1 CTAs per SM; stable
+ * maps 1, 2, 3, kernel 1 with all / 1 CTAs per SM, kernel 2 with and without staging, and
+ * kernel 3 when the matrix fits one block's shared memory; stable
  * models, tile widths 1..32 with all / half the CTAs per SM, and each width with the row split.
  */
 lp_status lp_autotune(lp_program* prog, uint32_t what, int32_t reps, lp_tune_record* records, int32_t max_records,
@@ -357,6 +369,10 @@ lp_status lp_export_matrix(const lp_program* prog, int64_t* row_ptr, int64_t* co
  * Matrix (device, read only): row_ptr (n_rows + 1 int32, non-decreasing, row_ptr[0] = 0), col
  * (row_ptr[n_rows] int32 column ids in [0, n_rows); an id outside is reported as
  * LP_ERR_INVALID and counts as false), threshold (n_rows int32): row i becomes true when at
+ * least threshold[i] of its entries are true. The row pointers themselves are NOT checked: the
+ * kernel reads col[row_ptr[0] .. row_ptr[n_rows]), so row_ptr must be non-decreasing and its
+ * last value must not exceed the length of the col buffer (a larger one reads past the buffer).
+ * For the threshold: row i becomes true when at
  * least threshold[i] of its entries are true -- the body size for a rule (entries 1/m), 1 for an
  * OR-rule or a self-loop; values below 1 count as 1. lp_export_matrix returns this form.
  * v0 (device, ceil(n_rows/64) words): initial vector over the rows; out (device, same size,

@@ -12,13 +12,14 @@ same matrix and initial vector."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2009_10247_gb300 as lp
 from workloads import large_definite, small_definite, transitive_closure
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from tests.gpu_util import dev_words, to_dev_bits  # noqa: E402
+from tests.gpu_util import dev_words, from_dev_bits, to_dev_bits  # noqa: E402
 
 
 def _reference_and_inputs(prog):
@@ -62,3 +63,21 @@ def test_static_entry_point_rejects_oversize_and_host_buffers():
     with pytest.raises(lp.LPError) as e:
         lp.least_model_static(1, rp, rp, rp, np.zeros(1, np.uint64), np.zeros(1, np.uint64))
     assert e.value.status == 1
+
+
+def test_static_entry_point_equals_oracle():
+    # the same fixpoint as the CPU oracle's Algorithm 1 (exact rational row sums) on the same
+    # canonical matrix and fact vector, twice in a row
+    prog = small_definite(8)
+    s = oracle.standardize(prog)
+    v0 = oracle.initial_vector(s)
+    want, want_it, ok = oracle.alg1(s, v0)
+    assert ok
+    n, row_ptr, col, thr, v0_dev, _, _ = _reference_and_inputs(prog)
+    assert n == s.n_prime
+    for _ in range(2):
+        out = dev_words(n)
+        it = lp.least_model_static(n, row_ptr, col, thr, v0_dev, out)
+        torch.cuda.synchronize()
+        assert it == want_it
+        assert np.array_equal(from_dev_bits(out, n), want.astype(bool))

@@ -28,8 +28,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import (large_definite, normal_program, program_batch, table1_program,  # noqa: E402
-                       transitive_closure_pairs)
+from workloads import (large_definite, normal_program, program_batch, small_definite, table1_program,  # noqa: E402
+                       transitive_closure, transitive_closure_pairs)
 
 METRIC = "fixpoint rule-evals/sec (nnz x iters / s)"
 UNIT = "rule-evals/s"
@@ -41,6 +41,10 @@ def workload_name(n_atoms, seed):
     w = WORKLOAD if n_atoms == 1_000_000 else WORKLOAD.replace("1e6 atoms, 5e6 rules",
                                                                f"{n_atoms} atoms, {5 * n_atoms} rules")
     return w.replace("(seed 1)", f"(seed {seed})")
+WORKLOAD_SMALL = ("small definite program: 1000 atoms, 2000 rules, bodies U{1..5}, atoms uniform, 50 facts, "
+                  "chain 40x5 (seed 1)")
+WORKLOAD_TC = ("transitive closure: 500 nodes, out-degree Poisson(4), no self-loops, edge facts, path(x,y) <- edge(x,y), "
+               "path(x,y) <- edge(x,z) & path(z,y) over existing edges (seed 1)")
 WORKLOAD_STABLE = "normal program: 1e5 atoms, 3e5 rules, bodies U{1..6}, 1% facts, k=16 negated atoms x 4 (seed 1), all 65536 guesses"
 WORKLOAD_BATCH = ("1000 normal programs: atoms log-uniform in [100, 20000], 3 rules per atom, k ~ U{4..8} negated atoms "
                   "x 2, bodies U{1..6} (seed 1), all 2^k guesses of every program")
@@ -60,14 +64,18 @@ def peaks():
 
 def _least_fields(sched):
     """The least-model fields of a schedule, with 0 read as the default it stands for."""
-    return {"fixpoint_kernel": sched["fixpoint_kernel"], "fixpoint_row_split": max(1, sched["fixpoint_row_split"]),
-            "fixpoint_chunk_batch": max(1, sched["fixpoint_chunk_batch"]), "fixpoint_row_map": sched["fixpoint_row_map"]}
+    f = {"fixpoint_kernel": sched["fixpoint_kernel"], "fixpoint_row_split": max(1, sched["fixpoint_row_split"]),
+         "fixpoint_chunk_batch": max(1, sched["fixpoint_chunk_batch"]), "fixpoint_row_map": sched["fixpoint_row_map"]}
+    if sched.get("fixpoint_stage", 0):
+        f["fixpoint_stage"] = sched["fixpoint_stage"]
+    return f
 
 
-def measured_traffic(kernel, sched=None):
+def measured_traffic(kernel, sched=None, workload_key=None):
     """DRAM bytes per launch from the committed ncu summaries: the record of `kernel` taken on
     the kernel sources as they are now and, for the least-model kernel, under the same schedule
-    (None if there is none: the counters are stale or belong to another variant)."""
+    and on the same workload (`workload_key`; records without one are the headline workload's).
+    None if there is none: the counters are stale or belong to another variant."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -78,6 +86,8 @@ def measured_traffic(kernel, sched=None):
         if rec.get("kernel", name) != kernel:
             continue
         if sched is not None and rec.get("schedule_fields") != _least_fields(sched):
+            continue
+        if rec.get("workload_key") != workload_key:
             continue
         try:
             h = hashlib.sha256()
@@ -222,6 +232,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-paper-tables", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-closure", action="store_true")
     ap.add_argument("--batch-iter-profile", action="store_true",
                     help="add the program batch's cumulative time after each lock-step iteration")
     ap.add_argument("--no-tune", action="store_true",
@@ -341,7 +353,13 @@ def main():
                "ms_per_step": 1e3 * sum(e2e_t) / len(e2e_t),
                "compile_ms": sum(compile_ms) / len(compile_ms)}
 
-    secondary = batch = relaxed = None
+    secondary = batch = relaxed = small = closure = sharded = None
+    if not args.no_stable:  # every rank: the guess ranges of one 2^16-guess solve, one gather
+        sharded = bench_stable_sharded(lp, torch, dev, flush, dist, world)
+    if not args.no_small and rank == 0:
+        small = bench_small(lp, torch, dev, tune=not args.no_tune)
+    if not args.no_closure and rank == 0:
+        closure = bench_closure(lp, torch, dev, flush, tune=not args.no_tune)
     if not args.no_stable and rank == 0:
         secondary = bench_stable(lp, torch, dev, flush, tune=not args.no_tune)
     if not args.no_batch and rank == 0:
@@ -379,7 +397,10 @@ def main():
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "small_definite": small,
+            "transitive_closure": closure,
             "stable_models": secondary,
+            "stable_models_sharded": sharded,
             "stable_models_batch": batch,
             "relaxed": relaxed,
             "paper_tables": tables,
@@ -389,6 +410,189 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def host_bits(mask):
+    """Bool array -> little-endian 64-bit words (the bit layout of lp.h)."""
+    nw = max(1, (len(mask) + 63) // 64)
+    b = np.zeros(nw * 64, dtype=np.uint8)
+    b[: len(mask)] = mask
+    return np.packbits(b, bitorder="little").view(np.uint64).copy()
+
+
+def e2e_least(lp, prog, iters, want, steps):
+    """The public C ABI from host arrays, wall clock per step: lp_compile (host standardization +
+    upload), lp_least_model with a host initial vector (the facts) and a host output, lp_free."""
+    facts_host = host_bits(prog.fact_atoms())
+    out_host = np.zeros(lp.words(prog.n_atoms), dtype=np.uint64)
+    ts, cms, h2d = [], [], 0
+    for i in range(steps + 1):
+        t0 = time.perf_counter()
+        Q = lp.Program.from_program(prog)
+        it = Q.least_model(out_host, init=facts_host)
+        h2d = Q.info["upload_bytes"] + facts_host.nbytes
+        cms.append(Q.info["compile_ms"])
+        Q.close()
+        if i > 0:  # the first one warms the allocator
+            ts.append(time.perf_counter() - t0)
+        if it != iters or not np.array_equal(out_host, want):
+            raise RuntimeError("e2e result differs from the device-timed one")
+    ms = 1e3 * sum(ts) / len(ts)
+    return ms, {"h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_host.nbytes), "ms_per_step": ms,
+                "compile_ms": sum(cms[1:]) / len(ts)}
+
+
+def bench_small(lp, torch, dev, steps=2000, tune=True):
+    """Small definite program (1000 atoms, 2000 rules, 86 theta applications): latency-bound,
+    reported in microseconds per solve beside the oracle's Algorithm 1 on the host cores."""
+    import oracle
+    prog = small_definite(1)
+    P = lp.Program.from_program(prog)
+    inf = P.info
+    out = torch.zeros(lp.words(inf["n_atoms"]), dtype=torch.int64, device=dev)
+    tuned = P.autotune(lp.LP_TUNE_LEAST, reps=5) if tune else []
+    iters = P.least_model(out)
+    stream = torch.cuda.current_stream()
+    for _ in range(50):
+        P.least_model(out, sync=False)
+    torch.cuda.synchronize()
+    l0 = lp.launch_count()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        P.least_model(out, sync=False)
+    b.record(stream)
+    b.synchronize()
+    us = 1e3 * a.elapsed_time(b) / steps
+    launches = (lp.launch_count() - l0) / steps
+    P.least_model(out, sync=False, timing=True)
+    kernel_us = 1e3 * P.last_stats()["kernel_ms"]
+    want = out.cpu().numpy().view(np.uint64).copy()
+    e2e_ms, e2e = e2e_least(lp, prog, iters, want, 20)
+    # the oracle: standardization once, then Algorithm 1 from the fact vector, repeated
+    std = oracle.standardize(prog)
+    v0 = oracle.initial_vector(std)
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 2.0:
+        oracle.alg1(std, v0)
+        reps += 1
+    cpu_us = 1e6 * (time.perf_counter() - t0) / reps
+    out_d = {"metric": "least-model solves/sec (small definite program; latency-bound)", "value": 1e6 / us,
+             "unit": "solves/s", "us_per_solve": us, "us_per_iter": us / iters, "kernel_us": kernel_us,
+             "launches_per_solve": launches, "iters": iters, "workload": WORKLOAD_SMALL,
+             "n_prime": inf["n_prime"], "nnz": inf["nnz"], "rule_evals_per_s": inf["nnz"] * iters / (us / 1e6),
+             "schedule": P.schedule, "tuned_candidates": len(tuned),
+             "note": "solves issued back to back on one stream with the matrix resident; the whole fixpoint "
+                     "(init, iterations, projection) is one launch per solve",
+             "e2e": {"value": 1e3 / e2e_ms, "unit": "solves/s", **e2e},
+             "cpu_baseline": {"value": 1e6 / cpu_us, "unit": "solves/s", "us_per_solve": cpu_us,
+                              "cores": oracle.num_threads(), "kind": "oracle",
+                              "sample": f"Algorithm 1 (oracle O2) from the fact vector, {reps} solves in ~2 s"}}
+    P.close()
+    return out_d
+
+
+def bench_closure(lp, torch, dev, flush, steps=20, tune=True):
+    """Ground transitive closure of a 500-node digraph (out-degree Poisson(4)): rule-evals/s of
+    the least-model solve, its roofline, e2e through the C ABI, and the oracle beside it."""
+    import oracle
+    prog = transitive_closure(500, 4.0, seed=1)
+    P = lp.Program.from_program(prog)
+    inf = P.info
+    n_prime, nnz = inf["n_prime"], inf["nnz"]
+    out = torch.zeros(lp.words(inf["n_atoms"]), dtype=torch.int64, device=dev)
+    tuned = P.autotune(lp.LP_TUNE_LEAST, reps=3) if tune else []
+    iters = P.least_model(out)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        flush.zero_()
+        P.least_model(out, sync=False, timing=True)
+    torch.cuda.synchronize()
+    step_ms, kernel_ms = [], []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.least_model(out, sync=False, timing=True)
+        b.record(stream)
+        st = P.last_stats()
+        if st["status"] != 0 or st["iters"] != iters:
+            raise RuntimeError(f"solve failed: {st}")
+        step_ms.append(a.elapsed_time(b))
+        kernel_ms.append(st["kernel_ms"])
+    ms = sum(step_ms) / len(step_ms)
+    k_ms = sum(kernel_ms) / len(kernel_ms)
+    peak, peak_kind = peaks()
+    per_launch = alg_bytes_per_iter(n_prime, nnz) * iters
+    achieved = per_launch / (k_ms / 1e3) / 1e9
+    want = out.cpu().numpy().view(np.uint64).copy()
+    e2e_ms, e2e = e2e_least(lp, prog, iters, want, 3)
+    std, done, dt, cores = cpu_oracle_sample(prog, iters)
+    out_d = {"metric": "fixpoint rule-evals/sec (nnz x iters / s)", "value": nnz * iters / (ms / 1e3), "unit": UNIT,
+             "ms_per_step": ms, "iters": iters, "workload": WORKLOAD_TC, "n_atoms": inf["n_atoms"],
+             "n_rules": int(prog.n_rules), "n_prime": n_prime, "nnz": nnz, "schedule": P.schedule,
+             "tuned_candidates": len(tuned), "l2": "flushed before every step (256 MiB write)",
+             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                          "traffic": measured_traffic("fixpoint_kernel", P.schedule, "transitive_closure_500"),
+                          "peak_kind": peak_kind, "kernel": "fixpoint_kernel", "kernel_ms": k_ms,
+                          "bytes_per_launch": per_launch, "bytes_per_iter": alg_bytes_per_iter(n_prime, nnz),
+                          "note": "the 17 MB matrix stays in L2 across iterations"},
+             "e2e": {"value": nnz * iters / (e2e_ms / 1e3), "unit": UNIT, **e2e},
+             "cpu_baseline": {"value": std.nnz * done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                              "sample": f"Algorithm 1 (oracle O2, OpenMP over rows) on the same matrix, all {done} "
+                                        f"theta applications from the fact vector ({dt:.2f} s)"}}
+    P.close()
+    return out_d
+
+
+def bench_stable_sharded(lp, torch, dev, flush, dist, world, steps=5):
+    """All 2^16 guesses of the normal program split into contiguous guess ranges, one per rank
+    (Def. 8 columns are independent: no exchange while iterating), then one gather of the
+    stable masks. Timed per step from a barrier to the gathered mask on every rank; the value
+    is the guesses of the whole job over the slowest rank's time."""
+    from paper_2009_10247_gb300.shard import guess_range, stable_models_sharded
+    prog = normal_program(seed=1)
+    P = lp.Program.from_program(prog)
+    ng = 1 << P.info["k"]
+    rank = dist.get_rank() if dist else 0
+
+    def run():
+        if dist:
+            return stable_models_sharded(P)
+        g = torch.arange(0, ng, dtype=torch.int64, device=dev)
+        m = torch.zeros(lp.words(ng), dtype=torch.int64, device=dev)
+        P.stable_models(m, guesses=g, n_guesses=ng)
+        return m.cpu().numpy().view(np.uint64)
+
+    full = run()
+    for _ in range(2):
+        run()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        got = run()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        ts.append(dt)
+        if not np.array_equal(got, full):
+            raise RuntimeError("sharded stable mask changed between steps")
+    lo, hi = guess_range(ng, rank, world)
+    ms = 1e3 * statistics.median(ts)
+    P.close()
+    return {"metric": "stable-model guesses/sec, guess ranges over ranks", "value": ng / (ms / 1e3),
+            "unit": "guesses/s", "ms_per_step": ms, "n_gpus": world, "guesses": ng,
+            "guesses_per_rank": hi - lo, "n_stable": int(sum(bin(int(w)).count("1") for w in full)),
+            "scaling": "strong", "workload": WORKLOAD_STABLE,
+            "note": "wall clock from a barrier to the gathered mask (includes the gather and the mask's copy "
+                    "to the host), max over ranks; explicit guess lists per range"}
 
 
 def bench_stable(lp, torch, dev, flush, steps=5, tune=True):

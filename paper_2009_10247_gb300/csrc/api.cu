@@ -108,6 +108,7 @@ void release(lp_program* p) {
   void* ptrs[] = {p->row_ptr, p->col, p->any_mask, p->perm, p->inv, p->fact_row, p->fact_owner, p->fact_mask,
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
                   p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
+                  p->sl_q, p->sl_qinv, p->sl_hdr, p->sl_col, p->sl_fact_row, p->sl_perm,
                   p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p,
                   p->tune_out.p, p->tune_in.p};
   for (void* q : ptrs)
@@ -138,6 +139,18 @@ lp_status finish_sync(lp_program* p, cudaStream_t s) {
 }
 
 int max_coresident(lp_program* p, int per_sm) { return std::max(1, per_sm) * p->sm_count; }
+
+// Kernel 2 indexes its padded entries with int32.
+bool sliced_supported(const lp_program* p) { return p->hm.nnz <= (int64_t)INT32_MAX / 4; }
+bool block_kernel_fits(const lp_program* p) {
+  static int optin = -1;
+  if (optin < 0 && cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
+    cudaGetLastError();
+    optin = 0;
+  }
+  return block_kernel_smem_bytes(p->hm.n_pad / 32, p->hm.nnz) + 1024 <= (long long)optin;
+}
+const char* const sliced_unsupported_msg = "fixpoint_kernel 2 needs fewer than 2^29 entries (padded below 2^31)";
 
 }  // namespace lp
 
@@ -233,6 +246,58 @@ lp_status lp_program_info(const lp_program* p, lp_info* out) {
 }
 
 namespace {
+
+// The sliced layout of kernel 2, built on the device from the CSR on its first use: pass 1
+// (renumbering, slice headers, prefix sum), the entry count to the host, pass 2.
+lp_status ensure_sliced_layout(lp_program* p, cudaStream_t s) {
+  if (p->sl_entries >= 0) return LP_OK;
+  const HostMatrix& hm = p->hm;
+  const int32_t n_words = hm.n_pad / 32;
+  lp_status st;
+  int32_t* cnt = nullptr;
+  auto fail_clean = [&](lp_status code) {
+    if (cnt) cudaFree(cnt);
+    void** ptrs[] = {(void**)&p->sl_q, (void**)&p->sl_qinv, (void**)&p->sl_hdr, (void**)&p->sl_col,
+                     (void**)&p->sl_fact_row, (void**)&p->sl_perm};
+    for (void** q : ptrs)
+      if (*q) {
+        cudaFree(*q);
+        *q = nullptr;
+      }
+    return code;
+  };
+  if ((st = dalloc(p, &p->sl_q, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->sl_qinv, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
+  const int32_t n_groups = sliced_groups(hm.n_pad);
+  if ((st = dalloc(p, &p->sl_hdr, 3 * (size_t)n_groups + 3)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->sl_fact_row, (size_t)hm.n_fact_rows)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->sl_perm, (size_t)hm.n_prime)) != LP_OK) return fail_clean(st);
+  // scratch: per-group counts, then the total (8-byte aligned after the counts)
+  const size_t cnt_ints = ((size_t)n_groups + 2) & ~(size_t)1;
+  if (device_malloc((void**)&cnt, (cnt_ints + 2) * 4) != cudaSuccess) {
+    cnt = nullptr;
+    cudaGetLastError();
+    return fail_clean(fail(LP_ERR_OOM, "sliced layout scratch"));
+  }
+  long long* total_dev = reinterpret_cast<long long*>(cnt + cnt_ints);
+  cudaError_t e = build_sliced_pass1(p->row_ptr, p->col, p->any_mask, hm.n_sec_a, hm.n_pad, p->sl_q, p->sl_qinv,
+                                     p->sl_hdr, cnt, total_dev, s);
+  long long total = 0;
+  if (e == cudaSuccess && n_words > 0) e = cudaMemcpyAsync(&total, total_dev, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_clean(cuda_fail(e, "sliced layout pass 1"));
+  if (total > (long long)INT32_MAX - 256) return fail_clean(fail(LP_ERR_INVALID, sliced_unsupported_msg));
+  if ((st = dalloc(p, &p->sl_col, (size_t)total)) != LP_OK) return fail_clean(st);
+  e = build_sliced_pass2(p->row_ptr, p->col, p->sl_q, p->sl_qinv, p->sl_hdr, hm.n_pad, p->sl_col, p->fact_row,
+                         hm.n_fact_rows, p->sl_fact_row, p->perm, hm.n_prime, p->sl_perm, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(cnt);
+  cnt = nullptr;
+  if (e != cudaSuccess) return fail_clean(cuda_fail(e, "sliced layout pass 2"));
+  count_launches(n_words > 0 ? 6 : 0);
+  p->sl_entries = total;
+  return LP_OK;
+}
 
 // The streamed kernel's layout, built on its first use from the device CSR.
 lp_status ensure_stream_layout(lp_program* p, cudaStream_t s) {
@@ -331,7 +396,33 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
 
   // Kernel and residency from the handle's schedule (both kernels are exact).
   cudaError_t le;
-  if (p->sched.fixpoint_kernel == 1) {
+  if (p->sched.fixpoint_kernel == 3) {
+    if (!block_kernel_fits(p))
+      return fail(LP_ERR_INVALID, "fixpoint_kernel 3 needs the program's CSR to fit in one block's shared memory");
+    if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
+    le = launch_fixpoint_block(a, hm.nnz, s);
+  } else if (p->sched.fixpoint_kernel == 2) {
+    if (!sliced_supported(p)) return fail(LP_ERR_INVALID, sliced_unsupported_msg);
+    if ((st = ensure_sliced_layout(p, s)) != LP_OK) return st;
+    static int optin = -1;
+    if (optin < 0) LP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    // leave the rest of the unified L1/shared array to L1 (the OR rows' vector words);
+    // LP_SLICED_STAGE_BYTES lowers the cap (tests of the unstaged fallback)
+    int cap = kSlicedStageBytesMax;
+    if (const char* env = std::getenv("LP_SLICED_STAGE_BYTES")) cap = std::min(cap, std::max(0, std::atoi(env)));
+    const int max_stage_words = std::max(0, std::min(optin - 1024, cap)) / 16 * 4;
+    const int32_t need = (std::min(hm.n_sec_a, hm.n_pad) + 127) / 128 * 4;  // whole 16-byte units
+    const bool stage = p->sched.fixpoint_stage == 0 && need > 0 && need <= max_stage_words;
+    const int32_t stage_words = stage ? need : 0;
+    const int occ_c = fixpoint_sliced_blocks_per_sm(stage, stage_words);
+    if (occ_c <= 0) return fail(LP_ERR_CUDA, "sliced fixpoint kernel cannot be resident");
+    const int32_t n_groups = sliced_groups(hm.n_pad);
+    SlicedLayout L{p->sl_hdr, p->sl_col, p->sl_q, p->sl_fact_row, p->sl_perm, n_groups, p->sl_entries, stage_words};
+    if (rows) LP_CUDA(cudaMemsetAsync(p->x[0], 0, (size_t)hm.n_pad / 8, s));  // v0 is built with atomics
+    const int grid = std::min(max_coresident(p, occ_c), std::max(1, (n_groups + kSlicedBlock / 32 - 1) / (kSlicedBlock / 32)));
+    if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
+    le = launch_fixpoint_sliced(a, L, stage, grid, s);
+  } else if (p->sched.fixpoint_kernel == 1) {
     if ((st = ensure_stream_layout(p, s)) != LP_OK) return st;
     static int occ_s = -1;
     if (occ_s < 0) occ_s = fixpoint_stream_blocks_per_sm();
@@ -503,7 +594,11 @@ lp_status lp_get_schedule(const lp_program* p, lp_schedule* out) {
 lp_status lp_set_schedule(lp_program* p, const lp_schedule* in) {
   if (!p || !in) return fail(LP_ERR_INVALID, "NULL argument");
   const int32_t W = in->stable_tile_words;
-  if (in->fixpoint_kernel < 0 || in->fixpoint_kernel > 1) return fail(LP_ERR_INVALID, "fixpoint_kernel must be 0 or 1");
+  if (in->fixpoint_kernel < 0 || in->fixpoint_kernel > 3) return fail(LP_ERR_INVALID, "fixpoint_kernel must be 0, 1, 2 or 3");
+  if (in->fixpoint_kernel == 3 && !p->host_only && !block_kernel_fits(p))
+    return fail(LP_ERR_INVALID, "fixpoint_kernel 3 needs the program's CSR to fit in one block's shared memory");
+  if (in->fixpoint_stage != 0 && in->fixpoint_stage != 1) return fail(LP_ERR_INVALID, "fixpoint_stage must be 0 or 1");
+  if (in->fixpoint_kernel == 2 && !sliced_supported(p)) return fail(LP_ERR_INVALID, sliced_unsupported_msg);
   if (in->fixpoint_blocks_per_sm < 0 || in->stable_blocks_per_sm < 0)
     return fail(LP_ERR_INVALID, "blocks per SM must be >= 0");
   const int32_t G = in->fixpoint_row_split;

@@ -92,4 +92,49 @@ __device__ __forceinline__ bool grid_barrier(DeviceCtl* ctl, unsigned long long 
   return s_abort == 0;
 }
 
+// Grid-wide barrier that also ORs one flag over the grid, for the least-model loop: a block
+// adds 1 + (flag ? 2^32 : 0) to the counter of this round's slot (three slots rotate over the
+// rounds) and waits until the low half counts every block; the high half then says whether
+// any block raised its flag. One atomic and two CTA barriers per round. Block 0 clears the slot
+// of round + 1 before it arrives: that slot was last used three rounds back, and every block
+// finished reading it before arriving at the round in between, while nobody adds to it before
+// this round completes, which needs block 0's arrival. `ctl->count` must be zero at launch.
+// Returns false if the grid is aborting; *any_flag is valid when it returns true.
+__device__ __forceinline__ bool grid_barrier_or(DeviceCtl* ctl, unsigned long long round, bool flag,
+                                                bool* any_flag, int status_on_timeout,
+                                                unsigned long long limit_ns = kWaitLimitNs) {
+  __shared__ unsigned s_state;  // bit 0: abort, bit 1: some block raised its flag
+  const int mine = __syncthreads_or(flag);
+  if (threadIdx.x == 0) {
+    unsigned long long* slot = &ctl->count[round % 3];
+    if (blockIdx.x == 0) ctl->count[(round + 1) % 3] = 0ull;
+    __threadfence();
+    atomicAdd(slot, mine ? (1ull << 32) + 1ull : 1ull);
+    const unsigned long long target = gridDim.x;
+    unsigned polls = 0;
+    unsigned long long t0 = 0, v;
+    unsigned ab = 0;
+    while (((v = ld_acquire64(slot)) & 0xffffffffull) < target) {
+      if ((ab = ld_volatile(&ctl->abort)) != 0) break;
+      if (++polls == 64) t0 = global_ns();
+      if (polls > 64) {
+        __nanosleep(64);
+        if ((polls & 255) == 0 && global_ns() - t0 > limit_ns) {
+          atomicExch(&ctl->abort, 1u);
+          atomicCAS(&ctl->status, 0, status_on_timeout);
+          atomicExch(&ctl->timeout_site, round);
+          ab = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_state = (ab ? 1u : 0u) | ((v >> 32) ? 2u : 0u);
+  }
+  __syncthreads();
+  const unsigned st = s_state;
+  *any_flag = (st & 2u) != 0;
+  return (st & 1u) == 0;
+}
+
 }  // namespace lp

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include "device.cuh"
+#include "fixpoint_phases.cuh"
 #include "kernels.h"
 
 namespace lp {
@@ -306,8 +307,6 @@ __device__ __forceinline__ bool theta_rows_pipelined(const FixArgs& a, const uin
   return changed;
 }
 
-__device__ __forceinline__ uint32_t get_bit(const uint32_t* v, int i) { return (v[i >> 5] >> (i & 31)) & 1u; }
-
 template <int G, int XN, int MAP>
 __global__ void __launch_bounds__(MAP == 0 ? kFixBlockMap0 : kFixBlockRows) fixpoint_kernel(FixArgs a) {
   constexpr int kBlock = MAP == 0 ? kFixBlockMap0 : kFixBlockRows;
@@ -322,29 +321,7 @@ __global__ void __launch_bounds__(MAP == 0 ? kFixBlockMap0 : kFixBlockRows) fixp
   unsigned long long round = 0;
 
   // ---- initial vector v0
-  if (a.rows_init) {
-    // LP_ROWS: internal row r takes bit inv[r] of the caller's canonical vector.
-    for (int w = gwarp; w < a.n_words; w += nwarps) {
-      const int r = (w << 5) + lane;
-      uint32_t bit = 0;
-      if (r < a.n_prime) {
-        const int c = a.inv[r];
-        bit = (uint32_t)(a.rows_init[c >> 6] >> (c & 63)) & 1u;
-      }
-      const uint32_t word = __ballot_sync(FULL, bit);
-      if (lane == 0) a.x0[w] = word;
-    }
-  } else {
-    // Def. 4: a fact row is 1 (when its atom is selected); x0 was zeroed by the caller.
-    for (int i = gtid; i < a.n_facts; i += nthreads) {
-      const int own = a.fact_owner[i];
-      const bool sel = a.init ? ((a.init[own >> 6] >> (own & 63)) & 1ull) : true;
-      if (sel) atomicOr(a.x0 + (a.fact_row[i] >> 5), 1u << (a.fact_row[i] & 31));
-    }
-    if (a.init)
-      for (int i = gtid; i < a.n_atom_words; i += nthreads)
-        if (a.init[i] & ~a.fact_mask[i]) atomicCAS(&ctl->status, 0, 1 /* LP_ERR_INVALID */);
-  }
+  fix_init_phase(a, gwarp, nwarps, gtid, nthreads, lane);
   if (!grid_barrier(ctl, ++round, 6)) return;
   if (ld_volatile((const unsigned*)&ctl->status) != 0) return;
 
@@ -461,16 +438,7 @@ __global__ void __launch_bounds__(MAP == 0 ? kFixBlockMap0 : kFixBlockRows) fixp
   }
 
   // ---- output: bit a = fixpoint bit of internal row perm[a]
-  if (a.out) {
-    uint32_t* out32 = reinterpret_cast<uint32_t*>(a.out);
-    const int n32 = 2 * ((a.n_out + 63) >> 6);
-    for (int u = gwarp; u < n32; u += nwarps) {
-      const int i = (u << 5) + lane;
-      const uint32_t bit = i < a.n_out ? get_bit(fin, a.perm[i]) : 0u;
-      const uint32_t word = __ballot_sync(FULL, bit);
-      if (lane == 0) out32[u] = word;
-    }
-  }
+  fix_output_phase(a, fin, gwarp, nwarps, lane);
 }
 
 static const void* fixpoint_entry(int G, int XN, int MAP) {

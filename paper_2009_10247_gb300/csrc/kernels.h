@@ -62,6 +62,40 @@ struct StreamLayout {
 cudaError_t launch_fixpoint_stream(const FixArgs& a, const StreamLayout& layout, int grid, cudaStream_t s);
 int fixpoint_stream_blocks_per_sm();
 
+// The same loop on a sliced layout of M_P (fixpoint_sliced.cu): rows renumbered by (gather
+// class, length) within windows, 32-row slices stored column-major at the slice's width.
+struct SlicedLayout {
+  const int4* hdr;          // 3 per 128-row group: {first entry, width | staged flag}, OR masks, empty masks
+  const int32_t* col;       // entries, renumbered columns
+  const int32_t* q;         // internal row -> new row
+  const int32_t* fact_row;  // fact rows, renumbered
+  const int32_t* perm;      // canonical row -> new row (n' entries)
+  int32_t n_groups;         // ceil(n_pad / 128)
+  int64_t total_entries;    // stored entries (the groups' offsets end there)
+  int32_t n_stage_words;    // vector words staged in shared memory (covers the leading n_sec_a rows)
+};
+constexpr int kSlicedBlock = 1024;
+int sliced_windows(int32_t n_sec_a, int32_t n_pad);
+int sliced_groups(int32_t n_pad);
+// Build from the device CSR. Pass 1: renumbering q / qinv, group headers (3 int4 per group), and
+// *total_dev = entries to store (cnt: sliced_groups ints of scratch). Pass 2 (after scol of *total_dev ints is allocated):
+// the entries, and the fact rows and output permutation renumbered.
+cudaError_t build_sliced_pass1(const int32_t* row_ptr, const int32_t* col, const uint32_t* any_mask, int32_t n_sec_a,
+                               int32_t n_pad, int32_t* q, int32_t* qinv, int4* hdr, int32_t* cnt, long long* total_dev,
+                               cudaStream_t s);
+cudaError_t build_sliced_pass2(const int32_t* row_ptr, const int32_t* col, const int32_t* q, const int32_t* qinv,
+                               const int4* hdr, int32_t n_pad, int32_t* scol, const int32_t* fact_row, int32_t n_facts,
+                               int32_t* fact_row_out, const int32_t* perm, int32_t n_perm, int32_t* perm_out,
+                               cudaStream_t s);
+cudaError_t launch_fixpoint_sliced(const FixArgs& a, const SlicedLayout& L, bool stage, int grid, cudaStream_t s);
+int fixpoint_sliced_blocks_per_sm(bool stage, int stage_words);
+
+// The same loop in one block with the matrix in shared memory (fixpoint_block.cu), for programs
+// whose CSR fits: block_kernel_smem_bytes of the program at most the device's per-block limit.
+constexpr int kBlockThreads = 1024;
+long long block_kernel_smem_bytes(int n_words, long long nnz);
+cudaError_t launch_fixpoint_block(const FixArgs& a, long long nnz, cudaStream_t s);
+
 // Algorithms 2 + 3 over tiles of 64-bit guess words (persistent cooperative kernel).
 struct StableArgs {
   const int32_t* row_ptr;

@@ -37,6 +37,14 @@ struct lp_program {
   int32_t* word_hdr = nullptr;
   int32_t* and_col = nullptr;
   int32_t* groups = nullptr;
+  // sliced layout of the least-model kernel 2 (built on the device on first use)
+  int32_t* sl_q = nullptr;        // internal row -> slice row
+  int32_t* sl_qinv = nullptr;     // slice row -> internal row
+  int4* sl_hdr = nullptr;         // per slice
+  int32_t* sl_col = nullptr;      // entries
+  int32_t* sl_fact_row = nullptr;
+  int32_t* sl_perm = nullptr;
+  int64_t sl_entries = -1;        // stored entries; -1 = not built
   // scratch
   uint32_t* x[2] = {nullptr, nullptr};
   lp::DeviceCtl* ctl = nullptr;
@@ -84,6 +92,16 @@ void count_launches(int64_t n);  // add to lp_launch_count()
 // cudaMalloc behind the allocation-failure hook (lp_debug_fail_alloc): every device allocation
 // of liblp's handles goes through here.
 cudaError_t device_malloc(void** ptr, size_t bytes);
+
+// Least-model kernel 2 (sliced layout): whether the program fits its index widths, and the
+// message of LP_ERR_INVALID when it does not.
+bool sliced_supported(const lp_program* p);
+extern const char* const sliced_unsupported_msg;
+// Shared memory that kernel 2 uses at most for the staged vector prefix (the rest of the
+// unified L1 / shared array stays L1).
+constexpr int kSlicedStageBytesMax = 160 * 1024;
+// Least-model kernel 3 (one block, matrix in shared memory): whether the program's CSR fits.
+bool block_kernel_fits(const lp_program* p);
 
 // NVTX range for the duration of a scope (shows liblp's calls in a profiler's timeline; free
 // when no tool is attached).

@@ -87,6 +87,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
       c.fixpoint_row_split = split;
       c.fixpoint_chunk_batch = batch;
       c.fixpoint_row_map = map;
+      c.fixpoint_stage = 0;
       return c;
     };
     std::vector<lp_schedule> cands;
@@ -97,6 +98,13 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     for (int m : {1, 2, 3}) cands.push_back(least(0, 0, 1, 1, m));
     for (int b : {0, 1})
       if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back(least(1, b, 1, 1, 0));
+    if (block_kernel_fits(p)) cands.push_back(least(3, 0, 1, 1, 0));
+    if (sliced_supported(p))
+      for (int stage : {0, 1}) {
+        lp_schedule c = least(2, 0, 1, 1, 0);
+        c.fixpoint_stage = stage;
+        cands.push_back(c);
+      }
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
     for (const lp_schedule& c : cands) {
@@ -192,6 +200,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     chosen.fixpoint_row_split = best_least.fixpoint_row_split;
     chosen.fixpoint_chunk_batch = best_least.fixpoint_chunk_batch;
     chosen.fixpoint_row_map = best_least.fixpoint_row_map;
+    chosen.fixpoint_stage = best_least.fixpoint_stage;
   }
   if (what & LP_TUNE_STABLE) {
     chosen.stable_tile_words = best_stable.stable_tile_words;

@@ -45,7 +45,8 @@ EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models"
 LP_TUNE_LEAST = 1
 LP_TUNE_STABLE = 2
 SCHEDULE_FIELDS = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "fixpoint_row_split", "fixpoint_chunk_batch",
-                   "fixpoint_row_map", "stable_tile_words", "stable_blocks_per_sm", "stable_row_split")
+                   "fixpoint_row_map", "stable_tile_words", "stable_blocks_per_sm", "stable_row_split",
+                   "fixpoint_stage")
 
 
 class _Schedule(ctypes.Structure):
@@ -55,7 +56,23 @@ class _Schedule(ctypes.Structure):
 class _TuneRecord(ctypes.Structure):
     _fields_ = [("schedule", _Schedule), ("solve", ctypes.c_int32), ("ms", ctypes.c_float)]
 
+# Version of the schedule fields and their meaning (row maps, kernels); part of the key of
+# autotune_cached, so a cache written by another build is not applied.
+SCHEDULE_FORMAT = 2
+
 _lib = None
+
+
+def _device_key():
+    """Name and SM count of the current CUDA device: a tuned schedule belongs to one device."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            prop = torch.cuda.get_device_properties(torch.cuda.current_device())
+            return f"{prop.name}/{prop.multi_processor_count}SM"
+    except Exception:  # pragma: no cover
+        pass
+    return "nodevice"
 
 
 def library_path() -> str:
@@ -278,22 +295,31 @@ class Program:
             out.append(d)
         return out
 
+    def schedule_cache_key(self, what=LP_TUNE_LEAST | LP_TUNE_STABLE):
+        """Key of autotune_cached: the device (name, SM count), the schedule format of this build
+        and the program's sizes."""
+        i = self.info
+        return (f"{_device_key()},format={SCHEDULE_FORMAT},n'={i['n_prime']},nnz={i['nnz']},k={i['k']},"
+                f"or={i['n_or_rows']},what={int(what)}")
+
     def autotune_cached(self, cache_path, what=LP_TUNE_LEAST | LP_TUNE_STABLE, reps=3, stream=None):
         """lp_autotune once per program shape: the chosen schedule is stored in a JSON file under a
         key of the program's sizes and reused on later calls (a schedule only changes the mapping
         onto the GPU, never the result, so two programs of the same sizes may share one). Returns
         True if the schedule came from the file, False if it was tuned now."""
         import json
-        i = self.info
-        key = f"n'={i['n_prime']},nnz={i['nnz']},k={i['k']},or={i['n_or_rows']},what={int(what)}"
+        key = self.schedule_cache_key(what)
         try:
             with open(cache_path) as f:
                 cache = json.load(f)
         except (OSError, ValueError):
             cache = {}
         if key in cache:
-            self.set_schedule(**{f: int(v) for f, v in cache[key].items() if f in SCHEDULE_FIELDS})
-            return True
+            try:
+                self.set_schedule(**{f: int(v) for f, v in cache[key].items() if f in SCHEDULE_FIELDS})
+                return True
+            except LPError:  # a schedule this build rejects: tune again
+                pass
         self.autotune(what, reps, stream)
         cache[key] = self.schedule
         tmp = f"{cache_path}.tmp{os.getpid()}"

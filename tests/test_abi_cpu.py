@@ -141,7 +141,7 @@ def test_schedule_get_set_validates(lib):
     with lp.Program.from_program(small_definite(1), host_only=True) as P:
         assert P.schedule == {"fixpoint_kernel": 0, "fixpoint_blocks_per_sm": 0, "fixpoint_row_split": 0,
                               "fixpoint_chunk_batch": 0, "fixpoint_row_map": 0, "stable_tile_words": 0,
-                              "stable_blocks_per_sm": 0, "stable_row_split": 0}
+                              "stable_blocks_per_sm": 0, "stable_row_split": 0, "fixpoint_stage": 0}
         for m in (1, 2, 3):
             P.set_schedule(fixpoint_row_map=m)
             assert P.schedule["fixpoint_row_map"] == m
@@ -151,7 +151,7 @@ def test_schedule_get_set_validates(lib):
         P.set_schedule(fixpoint_row_map=0)
         P.set_schedule(fixpoint_kernel=1, fixpoint_blocks_per_sm=2, stable_tile_words=8, stable_blocks_per_sm=1)
         assert P.schedule["stable_tile_words"] == 8 and P.schedule["fixpoint_kernel"] == 1
-        for bad in ({"fixpoint_kernel": 2}, {"stable_tile_words": 3}, {"stable_tile_words": 64},
+        for bad in ({"fixpoint_kernel": 4}, {"fixpoint_stage": 2}, {"stable_tile_words": 3}, {"stable_tile_words": 64},
                     {"fixpoint_row_split": 3}, {"fixpoint_row_split": 2},  # the second: kernel 1 is set
                     {"fixpoint_chunk_batch": 2}, {"fixpoint_chunk_batch": 4}, {"stable_row_split": 2},
                     {"fixpoint_blocks_per_sm": -1}, {"stable_blocks_per_sm": -2}, {"fixpoint_row_map": 4},
@@ -269,9 +269,19 @@ def test_autotune_cache_reuses_a_stored_schedule(lib, tmp_path):
         with pytest.raises(lp.LPError):
             P.autotune_cached(path)
         assert not os.path.exists(path)
-        i = P.info
-        key = f"n'={i['n_prime']},nnz={i['nnz']},k={i['k']},or={i['n_or_rows']},what={lp.LP_TUNE_LEAST | lp.LP_TUNE_STABLE}"
+        key = P.schedule_cache_key()
+        assert "format=" in key and str(P.info["nnz"]) in key
         want = dict(P.schedule, fixpoint_row_map=3, stable_tile_words=8)
         json.dump({key: want}, open(path, "w"))
         assert P.autotune_cached(path) is True
+        assert P.schedule == want
+        # a schedule stored for another device or schedule format is not applied
+        other = key.replace("format=", "format=9")
+        json.dump({other: dict(want, fixpoint_row_map=1)}, open(path, "w"))
+        with pytest.raises(lp.LPError):
+            P.autotune_cached(path)
+        # nor is one this build rejects: the handle tunes again (refused here)
+        json.dump({key: dict(want, fixpoint_kernel=7)}, open(path, "w"))
+        with pytest.raises(lp.LPError):
+            P.autotune_cached(path)
         assert P.schedule == want

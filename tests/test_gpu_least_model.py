@@ -1,7 +1,8 @@
 """GPU parity of the least-model path (Algorithm 1 in liblp) against the CPU oracle.
 
 Bit-exact comparison of every model bit and of the iteration count (theta applications),
-under every row map of the kernel, on the paper's example, tiny random programs with ragged
+under every row map of kernel 0, the sliced kernel 2 (vector prefix staged in shared memory or
+not) and the one-block kernel 3 where the program fits it, on the paper's example, tiny random programs with ragged
 sizes, every workload generator at test sizes, and the full-size large definite program in the
 launch configuration the benchmark times."""
 import numpy as np
@@ -18,18 +19,36 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_util import gpu_least_model  # noqa: E402
 
 
-ROW_MAPS = (0, 1, 2, 3)  # the warp-per-word map and the three thread-per-row maps
+ROW_MAPS = (0, 1, 2, 3)  # the warp-per-word map and the three thread-per-row maps of kernel 0
+# kernel 0 under each row map, then the sliced kernel with and without the staged prefix
+# and the one-block kernel 3 (matrix in shared memory) wherever the program fits it
+SCHEDULES = tuple(dict(fixpoint_kernel=0, fixpoint_row_map=m, fixpoint_stage=0) for m in ROW_MAPS) + (
+    dict(fixpoint_kernel=2, fixpoint_row_map=0, fixpoint_stage=0),
+    dict(fixpoint_kernel=2, fixpoint_row_map=0, fixpoint_stage=1),
+    dict(fixpoint_kernel=3, fixpoint_row_map=0, fixpoint_stage=0))
+
+
+def _apply(P, sc):
+    """Set a schedule; False if it is kernel 3 and the program's matrix does not fit one block."""
+    try:
+        P.set_schedule(**sc)
+        return True
+    except lp.LPError as e:
+        if sc["fixpoint_kernel"] == 3 and e.status == lp.ERR_INVALID:
+            return False
+        raise
 
 
 def _parity(prog, init=None):
-    # every row map of the least-model kernel must give the oracle's model and iteration count
+    # every schedule of the least-model solve must give the oracle's model and iteration count
     want, want_it = oracle.least_model(prog, init=init)
     with lp.Program.from_program(prog) as P:
-        for rmap in ROW_MAPS:
-            P.set_schedule(fixpoint_row_map=rmap)
+        for sc in SCHEDULES:
+            if not _apply(P, sc):
+                continue
             got, it = gpu_least_model(P, init=init)
-            assert np.array_equal(got, want), f"row map {rmap}: {np.count_nonzero(got != want)} atoms differ"
-            assert it == want_it, f"row map {rmap}"
+            assert np.array_equal(got, want), f"{sc}: {np.count_nonzero(got != want)} atoms differ"
+            assert it == want_it, f"{sc}"
     return got, it
 
 
@@ -81,10 +100,11 @@ def test_transitive_closure_500():
     p = transitive_closure(500, 4.0, seed=1)
     want, want_it = oracle.least_model(p)
     with lp.Program.from_program(p) as P:
-        for rmap in (0, 1, 2, 3):
-            P.set_schedule(fixpoint_row_map=rmap)
+        for sc in SCHEDULES:
+            if not _apply(P, sc):
+                continue
             got, it = gpu_least_model(P)
-            assert it == want_it and np.array_equal(got, want), f"row map {rmap}"
+            assert it == want_it and np.array_equal(got, want), f"{sc}"
 
 
 def test_large_definite_scaled():
@@ -100,10 +120,11 @@ def test_large_definite_full_size():
     assert want_it > 1000
     assert is_model(p, want)
     with lp.Program.from_program(p) as P:
-        for rmap in (0, 1, 2, 3):
-            P.set_schedule(fixpoint_row_map=rmap)
+        for sc in SCHEDULES:
+            if not _apply(P, sc):
+                continue
             got, it = gpu_least_model(P)
-            assert it == want_it and np.array_equal(got, want), f"row map {rmap}"
+            assert it == want_it and np.array_equal(got, want), f"{sc}"
         P.autotune(lp.LP_TUNE_LEAST, reps=1)
         got, it = gpu_least_model(P)
         assert it == want_it and np.array_equal(got, want), f"tuned {P.schedule}"
@@ -117,7 +138,7 @@ def test_rows_mode_matches_literal_algorithm1():
         for trial in range(8):
             v0 = rng.random(s.n_prime) < 0.3
             want, want_it, ok = oracle.alg1(s, v0.astype(np.uint8), max_iters=500)
-            P.set_schedule(fixpoint_row_map=ROW_MAPS[trial % 4])
+            assert _apply(P, SCHEDULES[trial % len(SCHEDULES)])
             if ok:
                 got, it = gpu_least_model(P, init=v0, rows=True, max_iters=500)
                 assert np.array_equal(got, want.astype(bool)) and it == want_it
@@ -197,3 +218,45 @@ def test_rows_longer_than_a_stage():
     rules = [(0, list(range(1, 7001)))] + [(a, []) for a in range(1, 7000)] + [(7001, [0])]
     got, it = _parity(from_rules(7002, rules))
     assert not got[0] and not got[7001]
+
+
+@pytest.mark.parametrize("stage_bytes", ["16", "65536"])
+def test_sliced_kernel_stage_cap(stage_bytes, monkeypatch):
+    # a cap on the staged prefix: where the gathered rows do not fit, every slice reads global memory
+    monkeypatch.setenv("LP_SLICED_STAGE_BYTES", stage_bytes)
+    for prog in (small_definite(5), large_definite(seed=6, n=200_000, n_rules=1_000_000, chain_levels=50,
+                                                   chain_width=20)):
+        want, want_it = oracle.least_model(prog)
+        with lp.Program.from_program(prog) as P:
+            P.set_schedule(fixpoint_kernel=2)
+            got, it = gpu_least_model(P)
+        assert it == want_it and np.array_equal(got, want)
+
+
+def test_long_rows_and_mixed_slices():
+    # rows of 1 to 64 entries, OR rows and facts mixed: slices of many widths, rows padded by
+    # repeating their first entry, kernel 3's multi-chunk words
+    rules = []
+    n = 3000
+    rng = np.random.default_rng(3)
+    facts = list(range(200))
+    rules += [(f, []) for f in facts]
+    for h in range(200, 3000):
+        ln = int(rng.choice([1, 2, 8, 31, 32, 33, 40, 64]))
+        rules.append((h, [int(x) for x in rng.choice(h, size=min(ln, h), replace=False)]))
+    for h in range(200, 3000, 7):  # a second rule: OR rows
+        rules.append((h, [int(x) for x in rng.choice(h, size=2, replace=False)]))
+    from workloads import from_rules
+    _parity(from_rules(n, rules))
+
+
+def test_block_kernel_used_where_it_fits_and_refused_elsewhere():
+    # kernel 3 takes a program whose CSR fits one block's shared memory and refuses a larger one
+    with lp.Program.from_program(small_definite(2)) as P:
+        P.set_schedule(fixpoint_kernel=3)
+        assert P.schedule["fixpoint_kernel"] == 3
+    with lp.Program.from_program(large_definite(seed=2, n=100_000, n_rules=500_000, chain_levels=100,
+                                                chain_width=20)) as P:
+        with pytest.raises(lp.LPError) as e:
+            P.set_schedule(fixpoint_kernel=3)
+        assert e.value.status == lp.ERR_INVALID

@@ -17,7 +17,8 @@ from tests.gpu_util import gpu_least_model, gpu_stable  # noqa: E402
 @pytest.mark.parametrize("kernel,bpsm,split,xn,rmap", [
     (0, 0, 1, 1, 0), (0, 2, 1, 1, 0), (0, 1, 1, 1, 0), (0, 0, 2, 1, 0), (0, 0, 4, 1, 0), (0, 3, 8, 1, 0),
     (0, 0, 1, 4, 0), (0, 0, 2, 4, 0), (0, 2, 8, 4, 0), (0, 0, 1, 1, 1), (0, 1, 1, 1, 1), (0, 0, 1, 1, 2),
-    (0, 1, 1, 1, 2), (0, 0, 1, 1, 3), (0, 1, 1, 1, 3), (1, 0, 1, 1, 0), (1, 1, 1, 1, 0)])
+    (0, 1, 1, 1, 2), (0, 0, 1, 1, 3), (0, 1, 1, 1, 3), (1, 0, 1, 1, 0), (1, 1, 1, 1, 0), (2, 0, 1, 1, 0),
+    (2, 0, 1, 1, -1)])
 def test_least_model_every_schedule(kernel, bpsm, split, xn, rmap):
     # the dense Table 1 shaped program has rows of about 50 entries: the thread-per-row maps
     # take their multi-pass paths there; the others fill fewer words than there are warps
@@ -27,8 +28,9 @@ def test_least_model_every_schedule(kernel, bpsm, split, xn, rmap):
     for prog in progs:
         want, want_it = oracle.least_model(prog)
         with lp.Program.from_program(prog) as P:
+            # rmap -1: kernel 2 gathering from global memory (no staged prefix)
             P.set_schedule(fixpoint_kernel=kernel, fixpoint_blocks_per_sm=bpsm, fixpoint_row_split=split,
-                           fixpoint_chunk_batch=xn, fixpoint_row_map=rmap)
+                           fixpoint_chunk_batch=xn, fixpoint_row_map=max(rmap, 0), fixpoint_stage=int(rmap < 0))
             got, it = gpu_least_model(P)
         assert it == want_it and np.array_equal(got, want)
 
@@ -58,9 +60,10 @@ def test_autotune_keeps_fastest_and_stays_exact():
         assert len(least) >= 10 and len(stable) >= 2 and all(r["ms"] >= 0 for r in recs)
         assert {r["fixpoint_row_split"] for r in least} == {1, 2, 4, 8}
         assert {r["fixpoint_row_map"] for r in least} == {0, 1, 2, 3}
+        assert {0, 1, 2} <= {r["fixpoint_kernel"] for r in least}
         bl, bs = min(least, key=lambda r: r["ms"]), min(stable, key=lambda r: r["ms"])
         keys = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "fixpoint_row_split", "fixpoint_chunk_batch",
-                "fixpoint_row_map")
+                "fixpoint_row_map", "fixpoint_stage")
         assert all(sched[k] == bl[k] for k in keys)
         assert (sched["stable_tile_words"], sched["stable_blocks_per_sm"]) == (bs["stable_tile_words"],
                                                                               bs["stable_blocks_per_sm"])
@@ -80,4 +83,16 @@ def test_autotune_choice_is_min_of_records():
         s = P.schedule
         assert (s["fixpoint_kernel"], s["fixpoint_blocks_per_sm"]) == (best["fixpoint_kernel"],
                                                                       best["fixpoint_blocks_per_sm"])
-        assert {r["fixpoint_kernel"] for r in recs} == {0, 1}
+        assert {r["fixpoint_kernel"] for r in recs} == {0, 1, 2}  # too large for kernel 3
+
+
+def test_autotune_includes_block_kernel_where_it_fits():
+    # kernel 3 (one block, matrix in shared memory) is a candidate exactly when the program fits it
+    for prog, fits in ((small_definite(3), True),
+                       (large_definite(seed=4, n=50_000, n_rules=200_000, chain_levels=40, chain_width=30), False)):
+        want, want_it = oracle.least_model(prog)
+        with lp.Program.from_program(prog) as P:
+            recs = P.autotune(lp.LP_TUNE_LEAST, reps=1)
+            assert (3 in {r["fixpoint_kernel"] for r in recs}) == fits
+            got, it = gpu_least_model(P)
+        assert it == want_it and np.array_equal(got, want)

@@ -11,6 +11,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -139,6 +141,24 @@ lp_status finish_sync(lp_program* p, cudaStream_t s) {
 }
 
 int max_coresident(lp_program* p, int per_sm) { return std::max(1, per_sm) * p->sm_count; }
+
+cudaError_t set_kernel_smem(const void* kernel, int dyn_bytes, int carveout) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, std::pair<int, int>> last;  // (device, kernel) -> set values
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(dev, kernel);
+  auto it = last.find(key);
+  // a limit at least as large serves the launch as well
+  if (it != last.end() && it->second.first >= dyn_bytes && it->second.second == carveout) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+  if (e != cudaSuccess) return e;
+  last[key] = std::make_pair(dyn_bytes, carveout);
+  return cudaSuccess;
+}
 
 // Kernel 2 indexes its padded entries with int32.
 bool sliced_supported(const lp_program* p) { return p->hm.nnz <= (int64_t)INT32_MAX / 4; }
@@ -414,7 +434,15 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
     const int32_t need = (std::min(hm.n_sec_a, hm.n_pad) + 127) / 128 * 4;  // whole 16-byte units
     const bool stage = p->sched.fixpoint_stage == 0 && need > 0 && need <= max_stage_words;
     const int32_t stage_words = stage ? need : 0;
-    const int occ_c = fixpoint_sliced_blocks_per_sm(stage, stage_words);
+    static std::map<std::pair<int, int>, int> occ_cache;  // (stage, staged words) -> CTAs per SM
+    static std::mutex occ_mu;
+    int occ_c;
+    {
+      std::lock_guard<std::mutex> lock(occ_mu);
+      auto key = std::make_pair((int)stage, (int)stage_words);
+      auto f = occ_cache.find(key);
+      occ_c = f != occ_cache.end() ? f->second : (occ_cache[key] = fixpoint_sliced_blocks_per_sm(stage, stage_words));
+    }
     if (occ_c <= 0) return fail(LP_ERR_CUDA, "sliced fixpoint kernel cannot be resident");
     const int32_t n_groups = sliced_groups(hm.n_pad);
     SlicedLayout L{p->sl_hdr, p->sl_col, p->sl_q, p->sl_fact_row, p->sl_perm, n_groups, p->sl_entries, stage_words};

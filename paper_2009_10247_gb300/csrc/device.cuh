@@ -55,28 +55,32 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier for a co-resident (cooperative) grid. `round` counts the barriers of this
-// launch from 1; every block must call it the same number of times. Release: fence before the
-// arrival; acquire: acquire loads while waiting and a fence after, then a CTA barrier, so
-// ordinary loads after it see every write made before it by any block. Returns false if the
-// grid is aborting (this or another block gave up waiting); callers must then return. A wait
-// gives up after limit_ns (2 s unless a caller passes less).
+// launch from 1; every block must call it the same number of times. Arrival: a release
+// reduction on the monotone counter; wait: acquire loads until it counts round x gridDim.x
+// blocks; CTA barriers on both sides, so ordinary loads after it see every write made before
+// it by any block. Returns false if the grid is aborting (this or another block gave up
+// waiting); callers must then return. A wait gives up after limit_ns (2 s unless a caller
+// passes less).
+__device__ __forceinline__ void red_release_add64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_barrier(DeviceCtl* ctl, unsigned long long round, int status_on_timeout,
                                              unsigned long long limit_ns = kWaitLimitNs) {
   __shared__ unsigned s_abort;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(&ctl->bar, 1ull);
+    red_release_add64(&ctl->bar, 1ull);
     const unsigned long long target = round * gridDim.x;
     unsigned polls = 0;
     unsigned long long t0 = 0;
     unsigned ab = 0;
     while (ld_acquire64(&ctl->bar) < target) {
-      if ((ab = ld_volatile(&ctl->abort)) != 0) break;
-      if (++polls == 64) t0 = global_ns();
-      if (polls > 64) {
-        __nanosleep(100);
-        if ((polls & 255) == 0 && global_ns() - t0 > limit_ns) {
+      if (++polls == 1024) t0 = global_ns();
+      if (polls > 1024 && (polls & 63) == 0) {
+        if ((ab = ld_volatile(&ctl->abort)) != 0) break;
+        __nanosleep(32);
+        if (global_ns() - t0 > limit_ns) {
           atomicExch(&ctl->abort, 1u);
           atomicCAS(&ctl->status, 0, status_on_timeout);
           atomicExch(&ctl->timeout_site, round);
@@ -85,7 +89,6 @@ __device__ __forceinline__ bool grid_barrier(DeviceCtl* ctl, unsigned long long 
         }
       }
     }
-    __threadfence();
     s_abort = ab;
   }
   __syncthreads();
@@ -95,11 +98,15 @@ __device__ __forceinline__ bool grid_barrier(DeviceCtl* ctl, unsigned long long 
 // Grid-wide barrier that also ORs one flag over the grid, for the least-model loop: a block
 // adds 1 + (flag ? 2^32 : 0) to the counter of this round's slot (three slots rotate over the
 // rounds) and waits until the low half counts every block; the high half then says whether
-// any block raised its flag. One atomic and two CTA barriers per round. Block 0 clears the slot
-// of round + 1 before it arrives: that slot was last used three rounds back, and every block
-// finished reading it before arriving at the round in between, while nobody adds to it before
-// this round completes, which needs block 0's arrival. `ctl->count` must be zero at launch.
-// Returns false if the grid is aborting; *any_flag is valid when it returns true.
+// any block raised its flag. One atomic and two CTA barriers per round. The arrival is a
+// release reduction and the wait an acquire load (both at GPU scope); with the CTA barriers
+// around them every write a block made before the barrier is visible to every block after it.
+// Block 0 clears the slot of round + 1 before it arrives: that slot was last used three rounds
+// back, and every block finished reading it before arriving at the round in between, while
+// nobody adds to it before this round completes, which needs block 0's arrival. `ctl->count`
+// must be zero at launch. Returns false if the grid is aborting; *any_flag is valid when it
+// returns true.
+
 __device__ __forceinline__ bool grid_barrier_or(DeviceCtl* ctl, unsigned long long round, bool flag,
                                                 bool* any_flag, int status_on_timeout,
                                                 unsigned long long limit_ns = kWaitLimitNs) {
@@ -108,18 +115,17 @@ __device__ __forceinline__ bool grid_barrier_or(DeviceCtl* ctl, unsigned long lo
   if (threadIdx.x == 0) {
     unsigned long long* slot = &ctl->count[round % 3];
     if (blockIdx.x == 0) ctl->count[(round + 1) % 3] = 0ull;
-    __threadfence();
-    atomicAdd(slot, mine ? (1ull << 32) + 1ull : 1ull);
+    red_release_add64(slot, mine ? (1ull << 32) + 1ull : 1ull);
     const unsigned long long target = gridDim.x;
     unsigned polls = 0;
     unsigned long long t0 = 0, v;
     unsigned ab = 0;
     while (((v = ld_acquire64(slot)) & 0xffffffffull) < target) {
-      if ((ab = ld_volatile(&ctl->abort)) != 0) break;
-      if (++polls == 64) t0 = global_ns();
-      if (polls > 64) {
-        __nanosleep(64);
-        if ((polls & 255) == 0 && global_ns() - t0 > limit_ns) {
+      if (++polls == 1024) t0 = global_ns();
+      if (polls > 1024 && (polls & 63) == 0) {
+        if ((ab = ld_volatile(&ctl->abort)) != 0) break;
+        __nanosleep(32);
+        if (global_ns() - t0 > limit_ns) {
           atomicExch(&ctl->abort, 1u);
           atomicCAS(&ctl->status, 0, status_on_timeout);
           atomicExch(&ctl->timeout_site, round);
@@ -128,7 +134,6 @@ __device__ __forceinline__ bool grid_barrier_or(DeviceCtl* ctl, unsigned long lo
         }
       }
     }
-    __threadfence();
     s_state = (ab ? 1u : 0u) | ((v >> 32) ? 2u : 0u);
   }
   __syncthreads();

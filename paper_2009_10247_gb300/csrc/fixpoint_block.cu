@@ -164,7 +164,7 @@ long long block_kernel_smem_bytes(int n_words, long long nnz) { return 4ll * blo
 
 cudaError_t launch_fixpoint_block(const FixArgs& a, long long nnz, cudaStream_t s) {
   const long long bytes = block_kernel_smem_bytes(a.n_words, nnz);
-  cudaError_t e = cudaFuncSetAttribute(fixpoint_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = set_kernel_smem((const void*)fixpoint_block_kernel, (int)bytes, -1);
   if (e != cudaSuccess) return e;
   fixpoint_block_kernel<<<1, kBlockThreads, (size_t)bytes, s>>>(a, nnz);
   return cudaGetLastError();

@@ -42,11 +42,19 @@ constexpr int kGroupRows = 128;              // rows of a group: four 32-row out
 constexpr uint32_t kStagedFlag = 0x80000000u;  // header .y: every entry of the group is staged
 constexpr int kGroupCost = 2;                // per-group cost, in slots, of the block partition
 
-__device__ __forceinline__ int4 ld_stream4(const int4* p) {
+// The layout is read many times per solve and stays in L2: read-only loads with an evict-last
+// L2 policy (so that other data, such as dirty lines another kernel left behind, is evicted
+// first) that do not allocate in L1, which holds the gathered vector words.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ int4 ld_stream4(const int4* p, uint64_t pol) {
   int4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.b32 {%0, %1, %2, %3}, [%4];"
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
+               : "l"(p), "l"(pol));
   return v;
 }
 
@@ -199,17 +207,17 @@ __device__ __forceinline__ uint32_t rot(uint32_t x, int j) { return __funnelshif
 // The four output words of group g: acc[u] = AND over the slots of (bit XOR inv[u]).
 template <bool SMEM>
 __device__ __forceinline__ void group_acc(const int4* __restrict__ e, int K, const uint32_t* x, const uint32_t inv[4],
-                                          uint32_t acc[4]) {
+                                          uint32_t acc[4], uint64_t pol) {
   int k = 0;
   for (; k + 2 <= K; k += 2) {  // two slots per step: two 16-byte loads in flight, then 8 gathers
-    const int4 a = ld_stream4(e + 32 * k), b = ld_stream4(e + 32 * (k + 1));
+    const int4 a = ld_stream4(e + 32 * k, pol), b = ld_stream4(e + 32 * (k + 1), pol);
     acc[0] &= (rot(x[a.x >> 5], a.x) ^ inv[0]) & (rot(x[b.x >> 5], b.x) ^ inv[0]);
     acc[1] &= (rot(x[a.y >> 5], a.y) ^ inv[1]) & (rot(x[b.y >> 5], b.y) ^ inv[1]);
     acc[2] &= (rot(x[a.z >> 5], a.z) ^ inv[2]) & (rot(x[b.z >> 5], b.z) ^ inv[2]);
     acc[3] &= (rot(x[a.w >> 5], a.w) ^ inv[3]) & (rot(x[b.w >> 5], b.w) ^ inv[3]);
   }
   if (k < K) {
-    const int4 a = ld_stream4(e + 32 * k);
+    const int4 a = ld_stream4(e + 32 * k, pol);
     acc[0] &= rot(x[a.x >> 5], a.x) ^ inv[0];
     acc[1] &= rot(x[a.y >> 5], a.y) ^ inv[1];
     acc[2] &= rot(x[a.z >> 5], a.z) ^ inv[2];
@@ -231,6 +239,7 @@ __global__ void __launch_bounds__(kSlicedBlock, 1) fixpoint_sliced_kernel(FixArg
   unsigned long long round = 0;
   const int n_stage4 = STAGE ? L.n_stage_words >> 2 : 0;
   const int n_groups = L.n_groups;
+  const uint64_t pol = l2_evict_last_policy();
 
   // ---- this block's groups: an equal share of the cost (slots + kGroupCost per group); the
   // cost before group g is off_g / 128 + kGroupCost g (the offsets are a prefix sum)
@@ -297,9 +306,9 @@ __global__ void __launch_bounds__(kSlicedBlock, 1) fixpoint_sliced_kernel(FixArg
     g = __shfl_sync(FULL, g, 0);
     int4 h0, h1, h2;
     if (g < g1) {
-      h0 = ld_stream4(L.hdr + 3 * g);
-      h1 = ld_stream4(L.hdr + 3 * g + 1);
-      h2 = ld_stream4(L.hdr + 3 * g + 2);
+      h0 = ld_stream4(L.hdr + 3 * g, pol);
+      h1 = ld_stream4(L.hdr + 3 * g + 1, pol);
+      h2 = ld_stream4(L.hdr + 3 * g + 2, pol);
     }
     while (g < g1) {  // uniform in the warp
       int gn = 0;
@@ -307,9 +316,9 @@ __global__ void __launch_bounds__(kSlicedBlock, 1) fixpoint_sliced_kernel(FixArg
       gn = __shfl_sync(FULL, gn, 0);
       int4 n0, n1, n2;
       if (gn < g1) {
-        n0 = ld_stream4(L.hdr + 3 * gn);
-        n1 = ld_stream4(L.hdr + 3 * gn + 1);
-        n2 = ld_stream4(L.hdr + 3 * gn + 2);
+        n0 = ld_stream4(L.hdr + 3 * gn, pol);
+        n1 = ld_stream4(L.hdr + 3 * gn + 1, pol);
+        n2 = ld_stream4(L.hdr + 3 * gn + 2, pol);
       }
       const int w0 = g * (kGroupRows / 32);
       const uint32_t old = lane < 4 && w0 + lane < a.n_words ? src[w0 + lane] : 0u;
@@ -318,8 +327,8 @@ __global__ void __launch_bounds__(kSlicedBlock, 1) fixpoint_sliced_kernel(FixArg
                                ((uint32_t)h1.z >> lane) & 1u ? FULL : 0u, ((uint32_t)h1.w >> lane) & 1u ? FULL : 0u};
       uint32_t acc[4] = {FULL, FULL, FULL, FULL};
       const int4* e = reinterpret_cast<const int4*>(L.col + h0.x) + lane;
-      if (STAGE && ((uint32_t)h0.y & kStagedFlag)) group_acc<true>(e, K, s_x, inv, acc);
-      else group_acc<false>(e, K, src, inv, acc);
+      if (STAGE && ((uint32_t)h0.y & kStagedFlag)) group_acc<true>(e, K, s_x, inv, acc, pol);
+      else group_acc<false>(e, K, src, inv, acc, pol);
       const uint32_t u0 = __ballot_sync(FULL, ((acc[0] ^ inv[0]) & ~((uint32_t)h2.x >> lane)) & 1u);
       const uint32_t u1 = __ballot_sync(FULL, ((acc[1] ^ inv[1]) & ~((uint32_t)h2.y >> lane)) & 1u);
       const uint32_t u2 = __ballot_sync(FULL, ((acc[2] ^ inv[2]) & ~((uint32_t)h2.z >> lane)) & 1u);
@@ -408,7 +417,9 @@ cudaError_t launch_fixpoint_sliced(const FixArgs& a, const SlicedLayout& L, bool
   void* params[] = {&ca, &cl};
   const size_t smem = stage ? (size_t)L.n_stage_words * 4 : 0;
   const void* k = sliced_entry(stage);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the unified L1 / shared array: as much L1 as the staged prefix leaves (the gathers of the
+  // unstaged groups and of the OR rows go through L1)
+  cudaError_t e = set_kernel_smem(k, (int)smem, stage ? -1 : 0);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kSlicedBlock), params, smem, s);
 }
@@ -416,7 +427,7 @@ cudaError_t launch_fixpoint_sliced(const FixArgs& a, const SlicedLayout& L, bool
 int fixpoint_sliced_blocks_per_sm(bool stage, int stage_words) {
   const void* k = sliced_entry(stage);
   const size_t smem = stage ? (size_t)stage_words * 4 : 0;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (set_kernel_smem(k, (int)smem, stage ? -1 : 0) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kSlicedBlock, smem) != cudaSuccess) return 0;
   return nb;

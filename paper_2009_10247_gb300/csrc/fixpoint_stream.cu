@@ -614,7 +614,7 @@ cudaError_t launch_fixpoint_stream(const FixArgs& f, const StreamLayout& L, int 
   const int want = ((L.n_sec_a + 31) / 32 + 1 + 3) & ~3;  // the referenced words and a zero word
   const int xs_words = std::min(want, (budget / 16) * 4);
   const size_t dyn = (size_t)kStageRegion + 4 * (size_t)(xs_words + own_words);
-  cudaError_t e = cudaFuncSetAttribute(fixpoint_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  cudaError_t e = set_kernel_smem((const void*)fixpoint_stream_kernel, (int)dyn, -1);
   if (e != cudaSuccess) return e;
   StreamArgs a{};
   a.desc = L.desc;
@@ -651,7 +651,7 @@ cudaError_t launch_fixpoint_stream(const FixArgs& f, const StreamLayout& L, int 
 int fixpoint_stream_blocks_per_sm() {
   const int dyn = max_dyn_smem() - 1024;
   if (dyn <= kStageRegion) return 0;
-  if (cudaFuncSetAttribute(fixpoint_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+  if (set_kernel_smem((const void*)fixpoint_stream_kernel, dyn, -1) != cudaSuccess)
     return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fixpoint_stream_kernel, kStreamThreads, (size_t)dyn) !=

@@ -8,6 +8,11 @@ namespace lp {
 
 struct DeviceCtl;
 
+// Sets a kernel's dynamic shared-memory limit and L1 / shared carveout preference on the current
+// device only when they differ from the last values set there: the attribute call costs far more
+// host time than a launch, and it would sit inside every solve's timed window.
+cudaError_t set_kernel_smem(const void* kernel, int dyn_bytes, int carveout);
+
 // Algorithm 1 on one bit-packed vector (persistent cooperative kernel).
 struct FixArgs {
   const int32_t* row_ptr;   // n_pad + 1, internal order

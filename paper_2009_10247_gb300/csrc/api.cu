@@ -162,13 +162,70 @@ cudaError_t set_kernel_smem(const void* kernel, int dyn_bytes, int carveout) {
 
 // Kernel 2 indexes its padded entries with int32.
 bool sliced_supported(const lp_program* p) { return p->hm.nnz <= (int64_t)INT32_MAX / 4; }
-bool block_kernel_fits(const lp_program* p) {
-  static int optin = -1;
-  if (optin < 0 && cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
+// The sliced layout of kernel 2, built on the device from the CSR on its first use: pass 1
+// (renumbering, slice headers, prefix sum), the entry count to the host, pass 2.
+lp_status ensure_sliced_layout(lp_program* p, cudaStream_t s) {
+  if (p->sl_entries >= 0) return LP_OK;
+  const HostMatrix& hm = p->hm;
+  const int32_t n_words = hm.n_pad / 32;
+  lp_status st;
+  int32_t* cnt = nullptr;
+  auto fail_clean = [&](lp_status code) {
+    if (cnt) cudaFree(cnt);
+    void** ptrs[] = {(void**)&p->sl_q, (void**)&p->sl_qinv, (void**)&p->sl_hdr, (void**)&p->sl_col,
+                     (void**)&p->sl_fact_row, (void**)&p->sl_perm};
+    for (void** q : ptrs)
+      if (*q) {
+        cudaFree(*q);
+        *q = nullptr;
+      }
+    return code;
+  };
+  if ((st = dalloc(p, &p->sl_q, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->sl_qinv, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
+  const int32_t n_groups = sliced_groups(hm.n_pad);
+  if ((st = dalloc(p, &p->sl_hdr, 3 * (size_t)n_groups + 3)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->sl_fact_row, (size_t)hm.n_fact_rows)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->sl_perm, (size_t)hm.n_prime)) != LP_OK) return fail_clean(st);
+  // scratch: per-group counts, then the total (8-byte aligned after the counts)
+  const size_t cnt_ints = ((size_t)n_groups + 2) & ~(size_t)1;
+  if (device_malloc((void**)&cnt, (cnt_ints + 2) * 4) != cudaSuccess) {
+    cnt = nullptr;
     cudaGetLastError();
-    optin = 0;
+    return fail_clean(fail(LP_ERR_OOM, "sliced layout scratch"));
   }
-  return block_kernel_smem_bytes(p->hm.n_pad / 32, p->hm.nnz) + 1024 <= (long long)optin;
+  long long* total_dev = reinterpret_cast<long long*>(cnt + cnt_ints);
+  cudaError_t e = build_sliced_pass1(p->row_ptr, p->col, p->any_mask, hm.n_sec_a, hm.n_pad, p->sl_q, p->sl_qinv,
+                                     p->sl_hdr, cnt, total_dev, s);
+  long long total = 0;
+  if (e == cudaSuccess && n_words > 0) e = cudaMemcpyAsync(&total, total_dev, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_clean(cuda_fail(e, "sliced layout pass 1"));
+  if (total > (long long)INT32_MAX - 256) return fail_clean(fail(LP_ERR_INVALID, sliced_unsupported_msg));
+  if ((st = dalloc(p, &p->sl_col, (size_t)total)) != LP_OK) return fail_clean(st);
+  e = build_sliced_pass2(p->row_ptr, p->col, p->sl_q, p->sl_qinv, p->sl_hdr, hm.n_pad, p->sl_col, p->fact_row,
+                         hm.n_fact_rows, p->sl_fact_row, p->perm, hm.n_prime, p->sl_perm, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(cnt);
+  cnt = nullptr;
+  if (e != cudaSuccess) return fail_clean(cuda_fail(e, "sliced layout pass 2"));
+  count_launches(n_words > 0 ? 6 : 0);
+  p->sl_entries = total;
+  return LP_OK;
+}
+
+lp_status block_kernel_fits(lp_program* p, cudaStream_t s, bool* fits) {
+  *fits = false;
+  if (!sliced_supported(p)) return LP_OK;
+  static int optin = -1;
+  if (optin < 0) LP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+  // a cheap bound first: the layout holds at least nnz entries
+  const long long lower = block_kernel_smem_bytes(p->hm.n_pad / 32, sliced_groups(p->hm.n_pad), p->hm.nnz);
+  if (lower + 1024 > (long long)optin) return LP_OK;
+  lp_status st = ensure_sliced_layout(p, s);
+  if (st != LP_OK) return st;
+  *fits = block_kernel_smem_bytes(p->hm.n_pad / 32, sliced_groups(p->hm.n_pad), p->sl_entries) + 1024 <= (long long)optin;
+  return LP_OK;
 }
 const char* const sliced_unsupported_msg = "fixpoint_kernel 2 needs fewer than 2^29 entries (padded below 2^31)";
 
@@ -266,58 +323,6 @@ lp_status lp_program_info(const lp_program* p, lp_info* out) {
 }
 
 namespace {
-
-// The sliced layout of kernel 2, built on the device from the CSR on its first use: pass 1
-// (renumbering, slice headers, prefix sum), the entry count to the host, pass 2.
-lp_status ensure_sliced_layout(lp_program* p, cudaStream_t s) {
-  if (p->sl_entries >= 0) return LP_OK;
-  const HostMatrix& hm = p->hm;
-  const int32_t n_words = hm.n_pad / 32;
-  lp_status st;
-  int32_t* cnt = nullptr;
-  auto fail_clean = [&](lp_status code) {
-    if (cnt) cudaFree(cnt);
-    void** ptrs[] = {(void**)&p->sl_q, (void**)&p->sl_qinv, (void**)&p->sl_hdr, (void**)&p->sl_col,
-                     (void**)&p->sl_fact_row, (void**)&p->sl_perm};
-    for (void** q : ptrs)
-      if (*q) {
-        cudaFree(*q);
-        *q = nullptr;
-      }
-    return code;
-  };
-  if ((st = dalloc(p, &p->sl_q, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
-  if ((st = dalloc(p, &p->sl_qinv, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
-  const int32_t n_groups = sliced_groups(hm.n_pad);
-  if ((st = dalloc(p, &p->sl_hdr, 3 * (size_t)n_groups + 3)) != LP_OK) return fail_clean(st);
-  if ((st = dalloc(p, &p->sl_fact_row, (size_t)hm.n_fact_rows)) != LP_OK) return fail_clean(st);
-  if ((st = dalloc(p, &p->sl_perm, (size_t)hm.n_prime)) != LP_OK) return fail_clean(st);
-  // scratch: per-group counts, then the total (8-byte aligned after the counts)
-  const size_t cnt_ints = ((size_t)n_groups + 2) & ~(size_t)1;
-  if (device_malloc((void**)&cnt, (cnt_ints + 2) * 4) != cudaSuccess) {
-    cnt = nullptr;
-    cudaGetLastError();
-    return fail_clean(fail(LP_ERR_OOM, "sliced layout scratch"));
-  }
-  long long* total_dev = reinterpret_cast<long long*>(cnt + cnt_ints);
-  cudaError_t e = build_sliced_pass1(p->row_ptr, p->col, p->any_mask, hm.n_sec_a, hm.n_pad, p->sl_q, p->sl_qinv,
-                                     p->sl_hdr, cnt, total_dev, s);
-  long long total = 0;
-  if (e == cudaSuccess && n_words > 0) e = cudaMemcpyAsync(&total, total_dev, 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail_clean(cuda_fail(e, "sliced layout pass 1"));
-  if (total > (long long)INT32_MAX - 256) return fail_clean(fail(LP_ERR_INVALID, sliced_unsupported_msg));
-  if ((st = dalloc(p, &p->sl_col, (size_t)total)) != LP_OK) return fail_clean(st);
-  e = build_sliced_pass2(p->row_ptr, p->col, p->sl_q, p->sl_qinv, p->sl_hdr, hm.n_pad, p->sl_col, p->fact_row,
-                         hm.n_fact_rows, p->sl_fact_row, p->perm, hm.n_prime, p->sl_perm, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(cnt);
-  cnt = nullptr;
-  if (e != cudaSuccess) return fail_clean(cuda_fail(e, "sliced layout pass 2"));
-  count_launches(n_words > 0 ? 6 : 0);
-  p->sl_entries = total;
-  return LP_OK;
-}
 
 // The streamed kernel's layout, built on its first use from the device CSR.
 lp_status ensure_stream_layout(lp_program* p, cudaStream_t s) {
@@ -417,10 +422,13 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
   // Kernel and residency from the handle's schedule (both kernels are exact).
   cudaError_t le;
   if (p->sched.fixpoint_kernel == 3) {
-    if (!block_kernel_fits(p))
-      return fail(LP_ERR_INVALID, "fixpoint_kernel 3 needs the program's CSR to fit in one block's shared memory");
+    bool fits = false;
+    if ((st = block_kernel_fits(p, s, &fits)) != LP_OK) return st;
+    if (!fits) return fail(LP_ERR_INVALID, "fixpoint_kernel 3 needs the program's sliced layout to fit in one block's shared memory");
+    if (rows) LP_CUDA(cudaMemsetAsync(p->x[0], 0, (size_t)hm.n_pad / 8, s));
+    SlicedLayout L{p->sl_hdr, p->sl_col, p->sl_q, p->sl_fact_row, p->sl_perm, sliced_groups(hm.n_pad), p->sl_entries, 0};
     if (p->timed) LP_CUDA(cudaEventRecord(p->ev0, s));
-    le = launch_fixpoint_block(a, hm.nnz, s);
+    le = launch_fixpoint_block(a, L, s);
   } else if (p->sched.fixpoint_kernel == 2) {
     if (!sliced_supported(p)) return fail(LP_ERR_INVALID, sliced_unsupported_msg);
     if ((st = ensure_sliced_layout(p, s)) != LP_OK) return st;
@@ -623,8 +631,12 @@ lp_status lp_set_schedule(lp_program* p, const lp_schedule* in) {
   if (!p || !in) return fail(LP_ERR_INVALID, "NULL argument");
   const int32_t W = in->stable_tile_words;
   if (in->fixpoint_kernel < 0 || in->fixpoint_kernel > 3) return fail(LP_ERR_INVALID, "fixpoint_kernel must be 0, 1, 2 or 3");
-  if (in->fixpoint_kernel == 3 && !p->host_only && !block_kernel_fits(p))
-    return fail(LP_ERR_INVALID, "fixpoint_kernel 3 needs the program's CSR to fit in one block's shared memory");
+  if (in->fixpoint_kernel == 3 && !p->host_only) {
+    bool fits = false;
+    lp_status st = block_kernel_fits(p, nullptr, &fits);
+    if (st != LP_OK) return st;
+    if (!fits) return fail(LP_ERR_INVALID, "fixpoint_kernel 3 needs the program's sliced layout to fit in one block's shared memory");
+  }
   if (in->fixpoint_stage != 0 && in->fixpoint_stage != 1) return fail(LP_ERR_INVALID, "fixpoint_stage must be 0 or 1");
   if (in->fixpoint_kernel == 2 && !sliced_supported(p)) return fail(LP_ERR_INVALID, sliced_unsupported_msg);
   if (in->fixpoint_blocks_per_sm < 0 || in->stable_blocks_per_sm < 0)

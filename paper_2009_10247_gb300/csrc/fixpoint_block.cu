@@ -3,16 +3,12 @@
 //
 // A small program's solve is bound by latency, not bandwidth: its whole matrix is a few tens of
 // kilobytes, and every theta application of a multi-block persistent kernel pays a grid-wide
-// barrier through global memory (microseconds). Here one block of 1024 threads copies the CSR
-// (row pointers, column ids, OR-row mask) into shared memory once, keeps both iterate vectors
-// there, and meets at a block barrier per iteration, so the loop touches global memory only to
-// load the matrix, read the initial facts and write the projected fixpoint.
-//
-// theta(M_P v) per 32-row word, one warp per word as in kernel 0: the word's entries are walked
-// 32 at a time, each lane gathers one entry's bit from the shared vector, a ballot makes the
-// chunk's mask, and each lane counts the bits of its own row's entries; the row fires when the
-// count reaches its threshold (all m body atoms of a rule row, one entry of an OR row or a
-// self-loop) -- theta of Def. 5 in exact integers.
+// barrier through global memory (about 1.5 microseconds). Here one block of 1024 threads copies
+// the sliced layout of kernel 2 (fixpoint_sliced.cu: rows renumbered by length, 128-row groups
+// stored column-major at their width, a row's entries reduced as one AND with an XOR mask for OR
+// rows) into shared memory once, keeps both iterate vectors there, and meets at a block barrier
+// per iteration, so the loop touches global memory only to load the layout, read the initial
+// facts and write the projected fixpoint. Warps take groups from a shared counter.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -22,86 +18,60 @@ namespace lp {
 
 namespace {
 
-// Shared-memory layout (32-bit words): row_ptr (n_pad + 1), col (nnz), OR-row mask, x0, x1;
-// every part padded to a multiple of 4 words.
+constexpr int kGroupRows = 128;
+constexpr uint32_t kStagedFlag = 0x80000000u;
+
+// Shared-memory layout, in 16-byte units: x0 and x1 (n_pad / 32 words each, rounded up to whole
+// units), the group headers (3 units per group), the entries.
 struct BlockLayout {
-  int rp, col, any, x0, x1, total;
+  int x0, x1, hdr, col, total;
 };
 
-__host__ __device__ inline int pad4(long long n) { return (int)((n + 3) & ~3ll); }
-
-__host__ __device__ inline BlockLayout block_layout(int n_words, long long nnz) {
+__host__ __device__ inline BlockLayout block_layout(int n_words, int n_groups, long long entries) {
   BlockLayout L;
-  L.rp = 0;
-  L.col = L.rp + pad4(32ll * n_words + 1);
-  L.any = L.col + pad4(nnz);
-  L.x0 = L.any + pad4(n_words);
-  L.x1 = L.x0 + pad4(n_words);
-  L.total = L.x1 + pad4(n_words);
+  const int xu = (n_words + 3) / 4;
+  L.x0 = 0;
+  L.x1 = xu;
+  L.hdr = 2 * xu;
+  L.col = L.hdr + 3 * n_groups;
+  L.total = L.col + (int)((entries + 3) / 4);
   return L;
 }
 
-__device__ __forceinline__ uint32_t block_theta_word(const int* s_rp, const int* s_col, const uint32_t* s_any,
-                                                     const uint32_t* src, int w, int lane) {
-  const int r = (w << 5) + lane;
-  const int beg = s_rp[r], end = s_rp[r + 1];
-  const int base = __shfl_sync(FULL, beg, 0), stop = __shfl_sync(FULL, end, 31);
-  int cnt = 0;
-  for (int c = base; c < stop; c += 32) {
-    const int e = c + lane;
-    uint32_t bit = 0u;
-    if (e < stop) {
-      const int j = s_col[e];
-      bit = (src[j >> 5] >> (j & 31)) & 1u;
-    }
-    const uint32_t m = __ballot_sync(FULL, bit);
-    const int lo = max(beg - c, 0), hi = min(end - c, 32);
-    if (hi > lo) cnt += __popc(m & ((hi - lo == 32) ? FULL : (((1u << (hi - lo)) - 1u) << lo)));
-  }
-  const bool any = (s_any[w] >> lane) & 1u;
-  return __ballot_sync(FULL, cnt >= (any ? 1 : max(end - beg, 1)));  // an empty row never fires
-}
+__device__ __forceinline__ uint32_t rot(uint32_t x, int j) { return __funnelshift_r(x, x, (uint32_t)j); }
 
-__global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArgs a, long long nnz) {
-  extern __shared__ uint4 s_raw[];
-  __shared__ int s_bad;
-  uint32_t* sm = reinterpret_cast<uint32_t*>(s_raw);
-  const BlockLayout L = block_layout(a.n_words, nnz);
-  int* s_rp = reinterpret_cast<int*>(sm + L.rp);
-  int* s_col = reinterpret_cast<int*>(sm + L.col);
-  uint32_t* s_any = sm + L.any;
-  uint32_t* const s_x0 = sm + L.x0;
-  uint32_t* const s_x1 = sm + L.x1;
+__global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArgs a, SlicedLayout S) {
+  extern __shared__ int4 s_raw[];
+  __shared__ int s_bad, s_next;
+  const BlockLayout B = block_layout(a.n_words, S.n_groups, S.total_entries);
+  uint32_t* const s_x0 = reinterpret_cast<uint32_t*>(s_raw + B.x0);
+  uint32_t* const s_x1 = reinterpret_cast<uint32_t*>(s_raw + B.x1);
+  int4* const s_hdr = s_raw + B.hdr;
+  int4* const s_col = s_raw + B.col;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = blockDim.x >> 5;
-  const int n_rp = 32 * a.n_words + 1;
 
-  // ---- the matrix into shared memory; x0 = 0
-  for (int i = t; i < n_rp; i += blockDim.x) s_rp[i] = __ldg(a.row_ptr + i);
-  for (long long i = t; i < nnz; i += blockDim.x) s_col[i] = __ldg(a.col + i);
-  for (int i = t; i < a.n_words; i += blockDim.x) {
-    s_any[i] = __ldg(a.any_mask + i);
-    s_x0[i] = 0u;
-  }
+  // ---- the layout into shared memory; x0 = 0
+  for (int i = t; i < 3 * S.n_groups; i += blockDim.x) s_hdr[i] = __ldg(S.hdr + i);
+  const int4* gcol = reinterpret_cast<const int4*>(S.col);
+  for (int i = t; i < (int)(S.total_entries / 4); i += blockDim.x) s_col[i] = __ldg(gcol + i);
+  for (int i = t; i < a.n_words; i += blockDim.x) s_x0[i] = 0u;
   if (t == 0) s_bad = 0;
   __syncthreads();
 
-  // ---- initial vector v0 (Def. 4, or the caller's row vector in LP_ROWS mode)
+  // ---- initial vector v0 in the new numbering (Def. 4, or the caller's row vector)
   if (a.rows_init) {
-    for (int w = warp; w < a.n_words; w += nwarp) {
-      const int r = (w << 5) + lane;
-      uint32_t bit = 0u;
-      if (r < a.n_prime) {
-        const int c = a.inv[r];
-        bit = (uint32_t)(a.rows_init[c >> 6] >> (c & 63)) & 1u;
+    for (int r = t; r < a.n_prime; r += blockDim.x) {
+      const int c = a.inv[r];
+      if ((a.rows_init[c >> 6] >> (c & 63)) & 1ull) {
+        const int q = S.q[r];
+        atomicOr(&s_x0[q >> 5], 1u << (q & 31));
       }
-      const uint32_t word = __ballot_sync(FULL, bit);
-      if (lane == 0) s_x0[w] = word;
     }
   } else {
     for (int i = t; i < a.n_facts; i += blockDim.x) {
       const int own = a.fact_owner[i];
       const bool sel = a.init ? ((a.init[own >> 6] >> (own & 63)) & 1ull) : true;
-      if (sel) atomicOr(&s_x0[a.fact_row[i] >> 5], 1u << (a.fact_row[i] & 31));
+      if (sel) atomicOr(&s_x0[S.fact_row[i] >> 5], 1u << (S.fact_row[i] & 31));
     }
     if (a.init)
       for (int i = t; i < a.n_atom_words; i += blockDim.x)
@@ -120,13 +90,37 @@ __global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArg
   for (; it < a.max_iters; ++it) {
     const uint32_t* src = (it & 1) ? s_x1 : s_x0;
     uint32_t* dst = (it & 1) ? s_x0 : s_x1;
+    if (t == 0) s_next = nwarp;
+    __syncthreads();
+    // warp w starts with group w and takes further groups from the counter
     bool changed = false;
-    for (int w = warp; w < a.n_words; w += nwarp) {
-      const uint32_t u = block_theta_word(s_rp, s_col, s_any, src, w, lane);
-      if (lane == 0) {
-        dst[w] = u;
-        changed |= u != src[w];
+    int g = warp;
+    while (g < S.n_groups) {  // uniform in the warp
+      const int4 h0 = s_hdr[3 * g], h1 = s_hdr[3 * g + 1], h2 = s_hdr[3 * g + 2];
+      const int K = h0.y & ~(int)kStagedFlag;
+      const uint32_t inv0 = ((uint32_t)h1.x >> lane) & 1u ? FULL : 0u, inv1 = ((uint32_t)h1.y >> lane) & 1u ? FULL : 0u;
+      const uint32_t inv2 = ((uint32_t)h1.z >> lane) & 1u ? FULL : 0u, inv3 = ((uint32_t)h1.w >> lane) & 1u ? FULL : 0u;
+      uint32_t a0 = FULL, a1 = FULL, a2 = FULL, a3 = FULL;
+      const int4* e = s_col + h0.x / 4 + lane;
+      for (int k = 0; k < K; k++) {
+        const int4 c = e[32 * k];
+        a0 &= rot(src[c.x >> 5], c.x) ^ inv0;
+        a1 &= rot(src[c.y >> 5], c.y) ^ inv1;
+        a2 &= rot(src[c.z >> 5], c.z) ^ inv2;
+        a3 &= rot(src[c.w >> 5], c.w) ^ inv3;
       }
+      const uint32_t u0 = __ballot_sync(FULL, ((a0 ^ inv0) & ~((uint32_t)h2.x >> lane)) & 1u);
+      const uint32_t u1 = __ballot_sync(FULL, ((a1 ^ inv1) & ~((uint32_t)h2.y >> lane)) & 1u);
+      const uint32_t u2 = __ballot_sync(FULL, ((a2 ^ inv2) & ~((uint32_t)h2.z >> lane)) & 1u);
+      const uint32_t u3 = __ballot_sync(FULL, ((a3 ^ inv3) & ~((uint32_t)h2.w >> lane)) & 1u);
+      const int w0 = g * (kGroupRows / 32);
+      if (lane < 4 && w0 + lane < a.n_words) {
+        const uint32_t word = lane == 0 ? u0 : lane == 1 ? u1 : lane == 2 ? u2 : u3;
+        changed |= word != src[w0 + lane];
+        dst[w0 + lane] = word;
+      }
+      if (lane == 0) g = atomicAdd(&s_next, 1);
+      g = __shfl_sync(FULL, g, 0);
     }
     fin = dst;
     if (!__syncthreads_or(changed)) {
@@ -140,17 +134,16 @@ __global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArg
     if (!converged) atomicCAS(&a.ctl->status, 0, 4 /* LP_ERR_NO_FIXPOINT */);
   }
 
-  // ---- output: bit a of out = fixpoint bit of internal row perm[a]
+  // ---- output: bit a of out = fixpoint bit of row q[perm[a]]
   if (a.out) {
-    const uint32_t* x = fin;
     uint32_t* out32 = reinterpret_cast<uint32_t*>(a.out);
     const int n32 = 2 * ((a.n_out + 63) >> 6);
     for (int u = warp; u < n32; u += nwarp) {
       const int i = (u << 5) + lane;
       uint32_t bit = 0u;
       if (i < a.n_out) {
-        const int r = a.perm[i];
-        bit = (x[r >> 5] >> (r & 31)) & 1u;
+        const int r = S.perm[i];
+        bit = (fin[r >> 5] >> (r & 31)) & 1u;
       }
       const uint32_t word = __ballot_sync(FULL, bit);
       if (lane == 0) out32[u] = word;
@@ -160,13 +153,15 @@ __global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArg
 
 }  // namespace
 
-long long block_kernel_smem_bytes(int n_words, long long nnz) { return 4ll * block_layout(n_words, nnz).total; }
+long long block_kernel_smem_bytes(int n_words, int n_groups, long long entries) {
+  return 16ll * block_layout(n_words, n_groups, entries).total;
+}
 
-cudaError_t launch_fixpoint_block(const FixArgs& a, long long nnz, cudaStream_t s) {
-  const long long bytes = block_kernel_smem_bytes(a.n_words, nnz);
+cudaError_t launch_fixpoint_block(const FixArgs& a, const SlicedLayout& S, cudaStream_t s) {
+  const long long bytes = block_kernel_smem_bytes(a.n_words, S.n_groups, S.total_entries);
   cudaError_t e = set_kernel_smem((const void*)fixpoint_block_kernel, (int)bytes, -1);
   if (e != cudaSuccess) return e;
-  fixpoint_block_kernel<<<1, kBlockThreads, (size_t)bytes, s>>>(a, nnz);
+  fixpoint_block_kernel<<<1, kBlockThreads, (size_t)bytes, s>>>(a, S);
   return cudaGetLastError();
 }
 

@@ -95,11 +95,12 @@ cudaError_t build_sliced_pass2(const int32_t* row_ptr, const int32_t* col, const
 cudaError_t launch_fixpoint_sliced(const FixArgs& a, const SlicedLayout& L, bool stage, int grid, cudaStream_t s);
 int fixpoint_sliced_blocks_per_sm(bool stage, int stage_words);
 
-// The same loop in one block with the matrix in shared memory (fixpoint_block.cu), for programs
-// whose CSR fits: block_kernel_smem_bytes of the program at most the device's per-block limit.
+// The same loop in one block with kernel 2's sliced layout and both vectors in shared memory
+// (fixpoint_block.cu), for programs whose layout fits: block_kernel_smem_bytes at most the
+// device's per-block limit.
 constexpr int kBlockThreads = 1024;
-long long block_kernel_smem_bytes(int n_words, long long nnz);
-cudaError_t launch_fixpoint_block(const FixArgs& a, long long nnz, cudaStream_t s);
+long long block_kernel_smem_bytes(int n_words, int n_groups, long long entries);
+cudaError_t launch_fixpoint_block(const FixArgs& a, const SlicedLayout& S, cudaStream_t s);
 
 // Algorithms 2 + 3 over tiles of 64-bit guess words (persistent cooperative kernel).
 struct StableArgs {

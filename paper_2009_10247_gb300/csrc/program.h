@@ -100,8 +100,10 @@ extern const char* const sliced_unsupported_msg;
 // Shared memory that kernel 2 uses at most for the staged vector prefix (the rest of the
 // unified L1 / shared array stays L1).
 constexpr int kSlicedStageBytesMax = 160 * 1024;
-// Least-model kernel 3 (one block, matrix in shared memory): whether the program's CSR fits.
-bool block_kernel_fits(const lp_program* p);
+// Least-model kernel 3 (one block, sliced layout in shared memory): whether the program's layout
+// fits (builds the sliced layout on stream s if it is not built yet).
+lp_status block_kernel_fits(lp_program* p, cudaStream_t s, bool* fits);
+lp_status ensure_sliced_layout(lp_program* p, cudaStream_t s);
 
 // NVTX range for the duration of a scope (shows liblp's calls in a profiler's timeline; free
 // when no tool is attached).

@@ -98,7 +98,9 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     for (int m : {1, 2, 3}) cands.push_back(least(0, 0, 1, 1, m));
     for (int b : {0, 1})
       if (occ1 > 0 && (b == 0 || b < occ1)) cands.push_back(least(1, b, 1, 1, 0));
-    if (block_kernel_fits(p)) cands.push_back(least(3, 0, 1, 1, 0));
+    bool fits3 = false;
+    if ((st = block_kernel_fits(p, s, &fits3)) != LP_OK) return st;
+    if (fits3) cands.push_back(least(3, 0, 1, 1, 0));
     if (sliced_supported(p))
       for (int stage : {0, 1}) {
         lp_schedule c = least(2, 0, 1, 1, 0);

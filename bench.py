@@ -101,6 +101,15 @@ def measured_traffic(kernel, sched=None, workload_key=None):
     return None
 
 
+LEAST_KERNELS = {0: "fixpoint_kernel", 1: "fixpoint_stream_kernel", 2: "fixpoint_sliced_kernel",
+                 3: "fixpoint_block_kernel"}
+
+
+def least_kernel(sched):
+    """Name of the least-model kernel a schedule launches."""
+    return LEAST_KERNELS.get(sched["fixpoint_kernel"], "fixpoint_kernel")
+
+
 def alg_bytes_per_iter(n_prime, nnz):
     # row_ptr + col read once, x read once, y written once (bits)
     return 4 * (n_prime + 1) + 4 * nnz + 2 * ((n_prime + 7) // 8)
@@ -390,8 +399,9 @@ def main():
                        "l2": "flushed before every step (256 MiB write)", "wall_s": round(wall, 3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "frac_of_nominal_7900": achieved / 7900.0,
-                         "traffic": measured_traffic("fixpoint_kernel", P.schedule),
-                         "peak_kind": peak_kind, "kernel": "fixpoint_kernel", "kernel_ms": k_ms, "bytes_per_launch": per_launch_bytes,
+                         "traffic": measured_traffic(least_kernel(P.schedule), P.schedule),
+                         "peak_kind": peak_kind, "kernel": least_kernel(P.schedule), "kernel_ms": k_ms,
+                         "bytes_per_launch": per_launch_bytes,
                          "bytes_per_iter": alg_bytes_per_iter(n_prime, nnz)},
             "e2e": e2e,
             "gpu_launches": launches,
@@ -533,8 +543,8 @@ def bench_closure(lp, torch, dev, flush, steps=20, tune=True):
              "n_rules": int(prog.n_rules), "n_prime": n_prime, "nnz": nnz, "schedule": P.schedule,
              "tuned_candidates": len(tuned), "l2": "flushed before every step (256 MiB write)",
              "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                          "traffic": measured_traffic("fixpoint_kernel", P.schedule, "transitive_closure_500"),
-                          "peak_kind": peak_kind, "kernel": "fixpoint_kernel", "kernel_ms": k_ms,
+                          "traffic": measured_traffic(least_kernel(P.schedule), P.schedule, "transitive_closure_500"),
+                          "peak_kind": peak_kind, "kernel": least_kernel(P.schedule), "kernel_ms": k_ms,
                           "bytes_per_launch": per_launch, "bytes_per_iter": alg_bytes_per_iter(n_prime, nnz),
                           "note": "the 17 MB matrix stays in L2 across iterations"},
              "e2e": {"value": nnz * iters / (e2e_ms / 1e3), "unit": UNIT, **e2e},
@@ -682,13 +692,13 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
         ts.append(a.elapsed_time(b))
     ms = statistics.median(ts)
     guesses = sum(1 << k for k in B.k)
-    # algorithmic bytes: per program and iteration, row_ptr (8 B) + col (4 B) read once, the
-    # iterate (W words per row) read once and written once
+    # algorithmic bytes: per program and iteration, row pointers (4 B) and column ids (4 B) read
+    # once, the iterate row (2^k guess bits, at least 2 bytes) read once and written once
     by = 0
     for p in range(n):
         inf = B.info[p]
-        W = max(1, (1 << inf["k"]) // 64)
-        by += int(iters[p]) * (8 * (inf["n_prime"] + 1) + 4 * inf["nnz"] + 16 * inf["n_prime"] * W)
+        rb = max(2, (1 << inf["k"]) // 8)
+        by += int(iters[p]) * (4 * (inf["n_prime"] + 1) + 4 * inf["nnz"] + 2 * inf["n_prime"] * rb)
     peak, peak_kind = peaks()
     achieved = by / (ms / 1e3) / 1e9
     # baseline: one lp_stable_models launch per program, same GPU, programs resident
@@ -720,7 +730,7 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
                         "bytes_per_launch": by,
                         "note": "the iterate buffers and the CSR exceed L2: every lock-step iteration streams them"}}
     if iter_profile:
-        cells = np.array([((inf["n_prime"] + 63) // 64 * 64) * max(1, (1 << inf["k"]) // 64) for inf in B.info])
+        cells = np.array([((inf["n_prime"] + 63) // 64 * 64) * max(2, (1 << inf["k"]) // 8) for inf in B.info])
         prof = []
         for t in range(1, int(iters.max()) + 1):
             tt = []
@@ -738,7 +748,7 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
                 tt.append(a.elapsed_time(b))
             act = iters >= t
             prof.append({"max_iters": t, "ms": round(min(tt), 4), "active_programs": int(act.sum()),
-                         "active_cells": int(cells[act].sum())})
+                         "active_iterate_bytes": int(cells[act].sum())})
         out["iteration_profile"] = prof
     B.close()
     return out

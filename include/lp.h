@@ -221,10 +221,10 @@ lp_status lp_batch_program_info(const lp_batch* batch, int32_t program, lp_info*
  * stable_mask (device or host, total_mask_words): program p's bit g (at its mask_word_offset) is
  * set iff guess g gives a stable model. n_stable (device or host, n_programs, nullable): stable
  * guesses per program; iters (device or host, n_programs, nullable): theta applications until
- * the program's fixpoint (0 if it had none within max_iters). The programs run in lock step, up
- * to 4096 per cooperative launch (the environment variable LP_BATCH_GROUP_BYTES, read by
- * lp_compile_batch, also caps a launch's matrix + iterate bytes); a program stops being
- * updated once an application changes none of its words. A host buffer or a non-NULL n_stable / iters makes the call wait;
+ * the program's fixpoint (0 if it had none within max_iters). One cooperative launch runs every
+ * program as an independent job (the largest on several blocks, the rest on one block each),
+ * each iterated until an application changes none of its words. A host buffer or a non-NULL
+ * n_stable / iters makes the call wait;
  * LP_ERR_NO_FIXPOINT if a program reaches max_iters (its mask is then zero); LP_ERR_TIMEOUT if a
  * grid barrier wait gave up (2 s).
  */
@@ -250,10 +250,10 @@ typedef struct {
                                      windows, 128-row groups padded to their longest row and
                                      stored column-major, a lane per row, blocks given equal
                                      shares of the work (built on the device from the CSR on
-                                     first use); 3 = one block with the
-                                     whole CSR and both vectors in shared memory, a block barrier
-                                     per iteration (small programs only: LP_ERR_INVALID if the
-                                     matrix does not fit one block's shared memory)              */
+                                     first use); 3 = one block with kernel 2's layout and both
+                                     vectors in shared memory, a block barrier per iteration
+                                     (small programs only: lp_set_schedule builds the layout and
+                                     returns LP_ERR_INVALID if it does not fit one block)        */
   int32_t fixpoint_blocks_per_sm; /* least model: resident CTAs per SM; 0 = all that fit        */
   int32_t fixpoint_row_split;     /* least model, kernel 0: warps sharing one 32-row output word
                                      (1, 2, 4 or 8; 0 = 1): more for programs with long rows    */

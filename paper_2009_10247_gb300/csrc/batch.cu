@@ -1,21 +1,19 @@
 // batch.cu -- Algorithms 2 and 3 for many independent normal programs in one launch
 // (lp_compile_batch / lp_batch_stable_models in include/lp.h).
 //
-// Each program is compiled on the host exactly as lp_compile does (compile_host), and the
-// programs are laid end to end: one block-diagonal CSR (every program's rows and columns
-// shifted by its row offset, a multiple of 64), one row-tag array (Def. 8 initial column), the
-// negated / barred row pairs of every program, and one iterate region per program of
-// n_pad x W 64-bit words, W = ceil(2^k / 64) guess words (all 2^k guesses of the program).
+// Each program is compiled on the host exactly as lp_compile does (compile_host) and laid out
+// as the sliced layout of the least-model kernel 2: rows renumbered by length within windows,
+// 128-row groups padded to their longest row, entries column-major (program-local row ids), a
+// 48-byte header per group. A row of a program's iterate holds its 2^k guess columns (Def. 8)
+// in max(2, 2^k / 8) bytes, so programs with few guesses move few bytes.
 //
-// One cooperative persistent kernel runs all programs in lock step: iteration t applies
-// M_{t+1} = theta(M_P M_t) (rule row: AND of the body words; OR row / self-loop: OR) to every
-// program that changed in iteration t-1, and skips the others, whose iterates are final (both
-// buffers hold the fixpoint). The work unit is a warp task of 32 consecutive 64-bit words of
-// one program's iterate (row-major, W words per row); warps walk the tasks grid-stride, so a
-// large program is spread over the whole GPU and small ones share it. A per-program change flag
-// (four rotating slots) records which programs stay active; one grid barrier per iteration.
-// After the last iteration Algorithm 3 runs on every program's W words: stable word = AND over
-// its negated atoms q of word(q) XOR word(q-bar).
+// One cooperative persistent kernel takes the programs as jobs from a queue, largest first. A
+// job runs its program's iteration M_{t+1} = theta(M_P M_t) (rule row: AND of its entries'
+// rows; OR row / self-loop: OR; both one AND with an XOR mask) to the fixpoint on one block, or
+// for the largest programs on several blocks that meet at the job's own barrier, then applies
+// Algorithm 3: stable word = AND over the negated atoms q of word(q) XOR word(q-bar). Programs
+// progress independently: no grid-wide barrier, and the data of the programs in flight stays
+// in L2 across their iterations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,20 +31,20 @@
 namespace lp {
 
 struct BatchProgram {       // device table entry
-  int64_t row0;             // first global row (multiple of 64)
-  int64_t state0;           // first 64-bit word of the program's iterate region (per buffer)
+  int64_t state0;           // first byte of the program's iterate region (per buffer), 16-byte aligned
   int64_t mask0;            // first 64-bit word of the program's stable mask
+  int64_t neg0;             // first entry of the program's negated / barred row pairs
+  int64_t row0;             // first row of the program in the row-tag array
+  int32_t g0;               // first group of the program (global group index)
+  int32_t n_groups;         // 128-row groups of the program
   int32_t n_pad;            // rows (multiple of 64)
-  int32_t W;                // guess words per row (a power of two)
-  int32_t log2W;
+  int32_t rb;               // bytes per row of an iterate: max(2, 2^k / 8)
   int32_t k;                // guessed barred atoms
   int32_t n_neg;            // negated atoms (barred rows)
-  int32_t pad_;
-  int64_t neg0;             // first entry of the program's negated / barred row pairs
 };
 
 constexpr int kBatchBlock = 512;
-constexpr int kSlots = 4;  // rotating change-flag slots per program
+constexpr int kGroupRows = 128;
 
 __device__ __forceinline__ uint64_t batch_m0(int tag, int w) {
   if (tag == -2) return ~0ull;  // fact row (Def. 8 item 2)
@@ -62,222 +60,311 @@ __device__ __forceinline__ uint64_t batch_m0(int tag, int w) {
   }
 }
 
-constexpr int kBatchGroup = 4096;  // programs per launch (their task counts live in shared memory)
-// Matrix + iterate bytes per launch. Unlimited by default: launches of L2-sized groups (so a
-// group's data stays in L2 across its iterations) were measured slower on the 1000-program
-// workload (6.3 ms at 64 MB, 10.8 ms at 16 MB, against 5.4 ms for one launch): the extra
-// grid barriers cost more than the DRAM traffic they save. LP_BATCH_GROUP_BYTES overrides it.
-constexpr int64_t kGroupBytes = int64_t(1) << 62;
-constexpr int kPerThread = kBatchGroup / kBatchBlock;
-static_assert(kBatchGroup % kBatchBlock == 0, "group must be a multiple of the block");
+// A job: one program, run by n_ctas co-resident blocks (ranks 0 .. n_ctas - 1) that meet at
+// the job's own barrier once per iteration; a block takes the job's slot `first_slot + rank`.
+struct BatchJob {
+  int32_t program;
+  int32_t n_ctas;
+  int32_t first_slot;
+  int32_t pad_;
+};
 
 struct BatchArgs {
-  const BatchProgram* progs;  // all programs of the batch
-  const int64_t* cell_off;    // n_total + 1: first iterate word of each program (ascending)
-  const int64_t* mask_off;    // n_total + 1: first stable-mask word of each program
-  int p0, n;                  // this launch runs programs [p0, p0 + n), n <= kBatchGroup
-  const int64_t* row_ptr;
-  const int32_t* col;
-  const uint32_t* any_mask;
-  const int32_t* row_tag;
+  const BatchProgram* progs;
+  const BatchJob* jobs;
+  const int32_t* slot_job;    // n_slots: the job of each slot, multi-block jobs first
+  int32_t n_slots;
+  const int4* hdr;            // 3 per group: {first entry, width, 0, 0}, OR masks, empty masks
+  const int32_t* col;         // entries: program-local row ids in the program's sliced numbering
+  const int32_t* row_tag;     // per row (sliced numbering): -1 zero, -2 fact, -3 barred atom of a fact, j guess bit
   const int32_t* neg_row;
   const int32_t* bar_row;
-  uint64_t* X0;
-  uint64_t* X1;
+  unsigned char* X0;
+  unsigned char* X1;
   uint64_t* stable_mask;
   long long* n_stable;        // zeroed before the launch
   int32_t* iters;             // zeroed before the launch; 0 = no fixpoint within max_iters
-  unsigned* pflag;            // kSlots per program, zeroed before the launch
-  unsigned* gflag;            // kSlots: some program of this launch changed, zeroed before the launch
-  DeviceCtl* ctl;             // one per launch, zeroed before it
+  unsigned long long* job_bar;  // 4 per job: three rotating barrier counters, zeroed before the launch
+  unsigned* queue;            // next slot, zeroed before the launch
+  DeviceCtl* ctl;             // status and abort flag, zeroed before the launch
   int max_iters;
 };
 
-// largest p in [0, n) with off[p] <= x (off ascending, off[0] <= x)
-template <typename T>
-__device__ __forceinline__ int last_le(const T* off, int n, long long x) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if ((long long)off[mid] <= x) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// s_pre[q] = number of tasks of the active programs before program q (q = 0..n); every block
-// computes the same array. A program is active in iteration `it` if it == 0 or it changed in
-// iteration it - 1 (flag slot `prev`).
-__device__ __forceinline__ void active_prefix(const BatchArgs& a, int it, int prev, const int* s_cnt, int* s_pre,
-                                              int* s_wsum) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kBatchBlock / 32;
-  const int q0 = threadIdx.x * kPerThread;
-  int v[kPerThread];
-  int sum = 0;
+// ---- one row of an iterate: 8 RB bits (RB = 2, 4, 8, 16 or 32 bytes), as NW 64-bit words
+template <int RB>
+struct RowT {
+  static constexpr int NW = RB >= 8 ? RB / 8 : 1;
+  static constexpr uint64_t MASK = RB >= 8 ? ~0ull : ((1ull << (8 * RB)) - 1ull);
+  uint64_t v[NW];
+  __device__ __forceinline__ void load(const unsigned char* base, int r) {
+    if constexpr (RB == 2) v[0] = *reinterpret_cast<const uint16_t*>(base + 2ll * r);
+    else if constexpr (RB == 4) v[0] = *reinterpret_cast<const uint32_t*>(base + 4ll * r);
+    else if constexpr (RB == 8) v[0] = *reinterpret_cast<const uint64_t*>(base + 8ll * r);
+    else {
+      const ulonglong2* q = reinterpret_cast<const ulonglong2*>(base + (long long)RB * r);
 #pragma unroll
-  for (int j = 0; j < kPerThread; j++) {
-    const int q = q0 + j;
-    int cnt = 0;
-    if (q < a.n && (it == 0 || ld_volatile(a.pflag + (long long)(a.p0 + q) * kSlots + prev) != 0u)) cnt = s_cnt[q];
-    v[j] = sum;
-    sum += cnt;
-  }
-  int incl = sum;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += y;
-  }
-  if (lane == 31) s_wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    int x = lane < nw ? s_wsum[lane] : 0;
-    const int own = x;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= d) x += y;
+      for (int i = 0; i < NW / 2; i++) {
+        const ulonglong2 t = q[i];
+        v[2 * i] = t.x;
+        v[2 * i + 1] = t.y;
+      }
     }
-    if (lane < nw) s_wsum[lane] = x - own;  // exclusive over warps
-    if (lane == nw - 1) s_pre[a.n] = x;     // total
   }
-  __syncthreads();
-  const int off = s_wsum[warp] + incl - sum;
+  __device__ __forceinline__ void store(unsigned char* base, int r) const {
+    if constexpr (RB == 2) *reinterpret_cast<uint16_t*>(base + 2ll * r) = (uint16_t)v[0];
+    else if constexpr (RB == 4) *reinterpret_cast<uint32_t*>(base + 4ll * r) = (uint32_t)v[0];
+    else if constexpr (RB == 8) *reinterpret_cast<uint64_t*>(base + 8ll * r) = v[0];
+    else {
+      ulonglong2* q = reinterpret_cast<ulonglong2*>(base + (long long)RB * r);
 #pragma unroll
-  for (int j = 0; j < kPerThread; j++)
-    if (q0 + j < a.n) s_pre[q0 + j] = off + v[j];
-  __syncthreads();
+      for (int i = 0; i < NW / 2; i++) q[i] = make_ulonglong2(v[2 * i], v[2 * i + 1]);
+    }
+  }
+};
+
+// Group of 128 rows of one program, rows of up to 32 bytes: lane l owns rows l, 32 + l,
+// 64 + l, 96 + l; slot k of the group holds their k-th entries as one int4 at entry
+// off + 4 (32 k + l). Rule rows AND their entries, OR rows OR them (an AND of the complements,
+// complemented), empty rows are 0. This pass evaluates rows U0 .. U0 + NU - 1 of the four (all
+// four for rows of up to 8 bytes, two at a time above, to bound the registers). Returns whether
+// one of them changed.
+template <int RB, int U0, int NU>
+__device__ __forceinline__ bool group_rows(const BatchArgs& a, const int4 h0, const int4 h1, const int4 h2,
+                                           const unsigned char* src, unsigned char* dst, int lg, int n_pad, int lane) {
+  using Row = RowT<RB>;
+  constexpr int NW = Row::NW;
+  const int K = h0.y;
+  const uint32_t orm[4] = {(uint32_t)h1.x, (uint32_t)h1.y, (uint32_t)h1.z, (uint32_t)h1.w};
+  uint64_t inv[NU], acc[NU][NW];
+#pragma unroll
+  for (int u = 0; u < NU; u++) {
+    inv[u] = ((orm[U0 + u] >> lane) & 1u) ? Row::MASK : 0ull;
+#pragma unroll
+    for (int i = 0; i < NW; i++) acc[u][i] = ~0ull;
+  }
+  const int4* e = reinterpret_cast<const int4*>(a.col + h0.x) + lane;
+  for (int k = 0; k < K; k++) {
+    const int4 c = __ldg(e + 32 * k);
+    const int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int u = 0; u < NU; u++) {
+      Row x;
+      x.load(src, cc[U0 + u]);
+#pragma unroll
+      for (int i = 0; i < NW; i++) acc[u][i] &= x.v[i] ^ inv[u];
+    }
+  }
+  const uint32_t emm[4] = {(uint32_t)h2.x, (uint32_t)h2.y, (uint32_t)h2.z, (uint32_t)h2.w};
+  bool changed = false;
+#pragma unroll
+  for (int u = 0; u < NU; u++) {
+    const int r = lg * kGroupRows + 32 * (U0 + u) + lane;
+    if (r >= n_pad) break;  // the last group of a program may end 64 rows early (uniform in the warp)
+    const uint64_t keep = ((emm[U0 + u] >> lane) & 1u) ? 0ull : Row::MASK;
+    Row old, nw;
+    old.load(src, r);
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+      nw.v[i] = (acc[u][i] ^ inv[u]) & keep;
+      changed |= nw.v[i] != old.v[i];
+    }
+    nw.store(dst, r);
+  }
+  return changed;
 }
 
+template <int RB>
+__device__ __forceinline__ bool group_narrow(const BatchArgs& a, const int4 h0, const int4 h1, const int4 h2,
+                                             const unsigned char* src, unsigned char* dst, int lg, int n_pad, int lane) {
+  if constexpr (RB <= 8) {
+    return group_rows<RB, 0, 4>(a, h0, h1, h2, src, dst, lg, n_pad, lane);
+  } else {
+    const bool c0 = group_rows<RB, 0, 2>(a, h0, h1, h2, src, dst, lg, n_pad, lane);
+    const bool c1 = group_rows<RB, 2, 2>(a, h0, h1, h2, src, dst, lg, n_pad, lane);
+    return c0 || c1;
+  }
+}
+
+// Group of 128 rows whose rows hold more than 32 bytes (k > 8): the rows one after another,
+// the lanes over a row's 64-bit words.
+__device__ __forceinline__ bool group_wide(const BatchArgs& a, const int4 h0, const int4 h1, const int4 h2,
+                                           const uint64_t* src, uint64_t* dst, int lg, int NW, int n_pad, int lane) {
+  const int K = h0.y;
+  bool changed = false;
+  for (int t = 0; t < kGroupRows && lg * kGroupRows + t < n_pad; t++) {
+    const int u = t >> 5, l = t & 31;
+    const uint32_t orm = u == 0 ? (uint32_t)h1.x : u == 1 ? (uint32_t)h1.y : u == 2 ? (uint32_t)h1.z : (uint32_t)h1.w;
+    const uint32_t emm = u == 0 ? (uint32_t)h2.x : u == 1 ? (uint32_t)h2.y : u == 2 ? (uint32_t)h2.z : (uint32_t)h2.w;
+    const uint64_t inv = ((orm >> l) & 1u) ? ~0ull : 0ull;
+    const uint64_t keep = ((emm >> l) & 1u) ? 0ull : ~0ull;
+    const long long r = (long long)lg * kGroupRows + t;
+    for (int w = lane; w < NW; w += 32) {
+      uint64_t acc = ~0ull;
+      for (int k = 0; k < K; k++) {
+        const int c = __ldg(a.col + h0.x + 4 * (32 * k + l) + u);
+        acc &= src[(long long)c * NW + w] ^ inv;
+      }
+      const uint64_t nw = (acc ^ inv) & keep;
+      changed |= nw != src[r * NW + w];
+      dst[r * NW + w] = nw;
+    }
+  }
+  return changed;
+}
+
+// Barrier of the c blocks of one job (c > 1), carrying an OR of one flag: as grid_barrier_or,
+// on the job's own counters. Returns false if the launch is aborting.
+__device__ __forceinline__ bool job_barrier_or(const BatchArgs& a, int job, int rank, int c, unsigned long long round,
+                                               bool flag, bool* any_flag) {
+  __shared__ unsigned s_state;
+  const int mine = __syncthreads_or(flag);
+  if (threadIdx.x == 0) {
+    unsigned long long* base = a.job_bar + 4ll * job;
+    unsigned long long* slot = base + round % 3;
+    if (rank == 0) base[(round + 1) % 3] = 0ull;
+    red_release_add64(slot, mine ? (1ull << 32) + 1ull : 1ull);
+    unsigned polls = 0;
+    unsigned long long t0 = 0, v;
+    unsigned ab = 0;
+    while (((v = ld_acquire64(slot)) & 0xffffffffull) < (unsigned long long)c) {
+      if (++polls == 1024) t0 = global_ns();
+      if (polls > 1024 && (polls & 63) == 0) {
+        if ((ab = ld_volatile(&a.ctl->abort)) != 0) break;
+        __nanosleep(32);
+        if (global_ns() - t0 > kWaitLimitNs) {
+          atomicExch(&a.ctl->abort, 1u);
+          atomicCAS(&a.ctl->status, 0, LP_ERR_TIMEOUT);
+          atomicExch(&a.ctl->timeout_site, round);
+          ab = 1;
+          break;
+        }
+      }
+    }
+    s_state = (ab ? 1u : 0u) | ((v >> 32) ? 2u : 0u);
+  }
+  __syncthreads();
+  const unsigned st = s_state;
+  *any_flag = (st & 2u) != 0;
+  return (st & 1u) == 0;
+}
+
+// Algorithms 2 and 3 for every program, one job at a time per block: a block takes the next
+// slot of the queue, runs its share of that job's program (a contiguous range of its 128-row
+// groups; the block's warps claim them from a shared counter) to the program's fixpoint, and
+// takes the next slot. Programs progress independently, so the data of the programs being
+// solved at any moment stays in L2 across their iterations.
 __global__ void __launch_bounds__(kBatchBlock, 2) batch_stable_kernel(BatchArgs a) {
   constexpr unsigned FULL = 0xffffffffu;
-  __shared__ int s_cnt[kBatchGroup];      // tasks (32-word units) of each program
-  __shared__ int s_pre[kBatchGroup + 1];  // prefix of active tasks, rebuilt every iteration
-  __shared__ int s_wsum[kBatchBlock / 32];
+  __shared__ int s_slot, s_next;
   const int lane = threadIdx.x & 31;
-  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nthreads = (long long)gridDim.x * blockDim.x;
-  const int64_t* coff = a.cell_off + a.p0;
-  const BatchProgram* progs = a.progs + a.p0;
-  DeviceCtl* ctl = a.ctl;
-  unsigned long long round = 0;
-  for (int q = threadIdx.x; q < a.n; q += blockDim.x) s_cnt[q] = (int)((__ldg(coff + q + 1) - __ldg(coff + q)) >> 5);
-  const long long cell_base = __ldg(coff);
-  const long long n_tasks = (__ldg(coff + a.n) - cell_base) >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_slot = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int slot = s_slot;
+    if (slot >= a.n_slots) return;
+    const int j = __ldg(a.slot_job + slot);
+    const BatchJob job = a.jobs[j];
+    const int rank = slot - job.first_slot, c = job.n_ctas;
+    const BatchProgram pr = a.progs[job.program];
+    const int g_lo = (int)((long long)pr.n_groups * rank / c), g_hi = (int)((long long)pr.n_groups * (rank + 1) / c);
+    const int r_lo = g_lo * kGroupRows, r_hi = min(g_hi * kGroupRows, pr.n_pad);
+    unsigned long long round = 0;
 
-  // ---- 1. M_0 of every program (Def. 8): all 2^k guesses as columns; warp w takes the
-  // contiguous task range [n_tasks w / nwarps, n_tasks (w + 1) / nwarps)
-  {
-    const long long i0 = n_tasks * gwarp / nwarps, i1 = n_tasks * (gwarp + 1) / nwarps;
-    if (i0 < i1) {
-      int p = last_le(coff, a.n, cell_base + i0 * 32);
-      BatchProgram pr = progs[p];
-      long long p_end = __ldg(coff + p + 1);
-      for (long long i = i0; i < i1; i++) {
-        const long long c0 = cell_base + i * 32;
-        while (c0 >= p_end) {
-          ++p;
-          pr = progs[p];
-          p_end = __ldg(coff + p + 1);
-        }
-        const long long lc = c0 + lane - pr.state0;
-        a.X0[c0 + lane] = batch_m0(__ldg(a.row_tag + pr.row0 + (lc >> pr.log2W)), (int)(lc & (pr.W - 1)));
+    // ---- 1. M_0 (Def. 8) of this block's rows: all 2^k guesses as columns
+    {
+      unsigned char* x0 = a.X0 + pr.state0;
+      const int nw = pr.rb >= 8 ? pr.rb / 8 : 1;
+      for (int r = r_lo + threadIdx.x; r < r_hi; r += blockDim.x) {
+        const int tag = __ldg(a.row_tag + pr.row0 + r);
+        if (pr.rb == 2) reinterpret_cast<uint16_t*>(x0)[r] = (uint16_t)batch_m0(tag, 0);
+        else if (pr.rb == 4) reinterpret_cast<uint32_t*>(x0)[r] = (uint32_t)batch_m0(tag, 0);
+        else
+          for (int w = 0; w < nw; w++) reinterpret_cast<uint64_t*>(x0)[(long long)r * nw + w] = batch_m0(tag, w);
       }
     }
-  }
-  if (!grid_barrier(ctl, ++round, LP_ERR_TIMEOUT)) return;
+    bool dummy;
+    if (c > 1) {
+      if (!job_barrier_or(a, j, rank, c, ++round, false, &dummy)) return;
+    } else {
+      __syncthreads();
+    }
 
-  // ---- 2. lock-step fixpoint over the active programs' tasks, balanced over the warps
-  bool all_done = false;
-  for (int it = 0; it < a.max_iters; ++it) {
-    const uint64_t* src = (it & 1) ? a.X1 : a.X0;
-    uint64_t* dst = (it & 1) ? a.X0 : a.X1;
-    const int slot = it % kSlots, prev = (it + kSlots - 1) % kSlots, next = (it + 1) % kSlots;
-    // slot `next` was last read at the start of iteration it - 1: clear it for iteration it + 1
-    for (long long q = gtid; q < a.n; q += nthreads) a.pflag[(a.p0 + q) * kSlots + next] = 0u;
-    if (gtid == 0) a.gflag[next] = 0u;
-    active_prefix(a, it, prev, s_cnt, s_pre, s_wsum);
-    const long long total = s_pre[a.n];
-    const long long i0 = total * gwarp / nwarps, i1 = total * (gwarp + 1) / nwarps;
-    if (i0 < i1) {
-      int p = last_le(s_pre, a.n, i0);
-      BatchProgram pr = progs[p];
-      long long p_hi = s_pre[p + 1], t_base = ((pr.state0 - cell_base) >> 5) - s_pre[p];
-      bool flagged = false;
-      for (long long i = i0; i < i1; i++) {
-        if (i >= p_hi) {  // next active program
-          do {
-            ++p;
-          } while (s_pre[p + 1] <= i);
-          pr = progs[p];
-          p_hi = s_pre[p + 1];
-          t_base = ((pr.state0 - cell_base) >> 5) - s_pre[p];
-          flagged = false;
+    // ---- 2. M_{t+1} = theta(M_P M_t) until no row of the program changes
+    int it = 0;
+    bool converged = false;
+    for (; it < a.max_iters; ++it) {
+      const unsigned char* src = ((it & 1) ? a.X1 : a.X0) + pr.state0;
+      unsigned char* dst = ((it & 1) ? a.X0 : a.X1) + pr.state0;
+      if (threadIdx.x == 0) s_next = g_lo;
+      __syncthreads();
+      bool changed = false;
+      int g = 0;
+      if (lane == 0) g = atomicAdd(&s_next, 1);
+      g = __shfl_sync(FULL, g, 0);
+      while (g < g_hi) {  // uniform in the warp
+        const int gg = pr.g0 + g;
+        const int4 h0 = __ldg(a.hdr + 3 * gg), h1 = __ldg(a.hdr + 3 * gg + 1), h2 = __ldg(a.hdr + 3 * gg + 2);
+        bool ch;
+        switch (pr.rb) {
+          case 2: ch = group_narrow<2>(a, h0, h1, h2, src, dst, g, pr.n_pad, lane); break;
+          case 4: ch = group_narrow<4>(a, h0, h1, h2, src, dst, g, pr.n_pad, lane); break;
+          case 8: ch = group_narrow<8>(a, h0, h1, h2, src, dst, g, pr.n_pad, lane); break;
+          case 16: ch = group_narrow<16>(a, h0, h1, h2, src, dst, g, pr.n_pad, lane); break;
+          case 32: ch = group_narrow<32>(a, h0, h1, h2, src, dst, g, pr.n_pad, lane); break;
+          default:
+            ch = group_wide(a, h0, h1, h2, reinterpret_cast<const uint64_t*>(src), reinterpret_cast<uint64_t*>(dst), g,
+                            pr.rb / 8, pr.n_pad, lane);
         }
-        const long long c = cell_base + (t_base + i) * 32 + lane;
-        const long long lc = c - pr.state0;
-        const long long gr = pr.row0 + (lc >> pr.log2W);
-        const int w = (int)(lc & (pr.W - 1));
-        const long long beg = __ldg(a.row_ptr + gr), end = __ldg(a.row_ptr + gr + 1);
-        const bool any = (__ldg(a.any_mask + (gr >> 5)) >> (gr & 31)) & 1u;
-        const uint64_t old = src[c];
-        const uint64_t ident = any ? 0ull : ~0ull;  // identity of the row's OR / AND
-        uint64_t acc = end > beg ? ident : 0ull;
-        const uint64_t* base = src + pr.state0 + w;
-        // four entries at a time: all column loads, then all gathers
-        for (long long e = beg; e < end; e += 4) {
-          int cc[4];
-#pragma unroll
-          for (int j = 0; j < 4; j++) cc[j] = e + j < end ? __ldg(a.col + e + j) : -1;
-          uint64_t vv[4];
-#pragma unroll
-          for (int j = 0; j < 4; j++) vv[j] = cc[j] >= 0 ? base[(long long)(cc[j] - pr.row0) << pr.log2W] : ident;
-          const uint64_t o = vv[0] | vv[1] | vv[2] | vv[3], n = vv[0] & vv[1] & vv[2] & vv[3];
-          acc = any ? (acc | o) : (acc & n);
-        }
-        dst[c] = acc;
-        if (__any_sync(FULL, acc != old) && !flagged) {
-          flagged = true;
-          if (lane == 0) {
-            a.pflag[(long long)(a.p0 + p) * kSlots + slot] = 1u;
-            a.gflag[slot] = 1u;
+        changed |= ch;
+        if (lane == 0) g = atomicAdd(&s_next, 1);
+        g = __shfl_sync(FULL, g, 0);
+      }
+      bool any;
+      if (c > 1) {
+        if (!job_barrier_or(a, j, rank, c, ++round, changed, &any)) return;
+      } else {
+        any = __syncthreads_or(changed) != 0;
+      }
+      if (!any) {
+        converged = true;
+        ++it;
+        break;
+      }
+    }
+
+    // ---- 3. Algorithm 3 (rank 0): stable word = AND over the negated atoms q of (word of q)
+    // XOR (word of q-bar); both buffers hold the fixpoint
+    if (rank == 0) {
+      if (threadIdx.x == 0) {
+        a.iters[job.program] = converged ? it : 0;
+        if (!converged) atomicCAS(&a.ctl->status, 0, LP_ERR_NO_FIXPOINT);
+      }
+      const int nw = pr.rb >= 8 ? pr.rb / 8 : 1;
+      const unsigned char* fin = a.X0 + pr.state0;
+      for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+        const long long first = 64ll * w, ng = 1ll << pr.k;
+        uint64_t st = ng - first >= 64 ? ~0ull : ((1ull << (ng - first)) - 1ull);
+        for (int q = 0; q < pr.n_neg; q++) {
+          const int r = __ldg(a.neg_row + pr.neg0 + q), rb = __ldg(a.bar_row + pr.neg0 + q);
+          uint64_t vq, vb;
+          if (pr.rb == 2) {
+            vq = reinterpret_cast<const uint16_t*>(fin)[r];
+            vb = reinterpret_cast<const uint16_t*>(fin)[rb];
+          } else if (pr.rb == 4) {
+            vq = reinterpret_cast<const uint32_t*>(fin)[r];
+            vb = reinterpret_cast<const uint32_t*>(fin)[rb];
+          } else {
+            vq = reinterpret_cast<const uint64_t*>(fin)[(long long)r * nw + w];
+            vb = reinterpret_cast<const uint64_t*>(fin)[(long long)rb * nw + w];
           }
+          st &= vq ^ vb;
         }
+        if (!converged) st = 0;
+        a.stable_mask[pr.mask0 + w] = st;
+        if (st) atomicAdd(reinterpret_cast<unsigned long long*>(a.n_stable + job.program), (unsigned long long)__popcll(st));
       }
     }
-    if (!grid_barrier(ctl, ++round, LP_ERR_TIMEOUT)) return;
-    // programs that were active in iteration it and did not change have converged
-    for (long long q = gtid; q < a.n; q += nthreads) {
-      const unsigned* f = a.pflag + (a.p0 + q) * kSlots;
-      if ((it == 0 || ld_volatile(f + prev) != 0u) && ld_volatile(f + slot) == 0u) a.iters[a.p0 + q] = it + 1;
-    }
-    if (ld_volatile(a.gflag + slot) == 0u) {
-      all_done = true;
-      break;
-    }
-  }
-  if (!all_done && gtid == 0) atomicCAS(&ctl->status, 0, LP_ERR_NO_FIXPOINT);
-  if (!grid_barrier(ctl, ++round, LP_ERR_TIMEOUT)) return;
-
-  // ---- 3. Algorithm 3 on every program's guess words (either buffer holds the fixpoint)
-  const int64_t* moff = a.mask_off + a.p0;
-  const long long m_base = __ldg(moff), n_mask = __ldg(moff + a.n) - m_base;
-  for (long long m = gtid; m < n_mask; m += nthreads) {
-    const int p = last_le(moff, a.n, m_base + m);
-    const BatchProgram pr = progs[p];
-    const int w = (int)(m_base + m - pr.mask0);
-    const long long first = 64ll * w, ng = 1ll << pr.k;
-    uint64_t st = ng - first >= 64 ? ~0ull : ((1ull << (ng - first)) - 1ull);
-    const uint64_t* fin = a.X0 + pr.state0 + w;
-    for (int j = 0; j < pr.n_neg; j++) {
-      const long long q = __ldg(a.neg_row + pr.neg0 + j), qb = __ldg(a.bar_row + pr.neg0 + j);
-      st &= fin[q << pr.log2W] ^ fin[qb << pr.log2W];
-    }
-    if (ld_volatile(reinterpret_cast<const unsigned*>(a.iters + a.p0 + p)) == 0u) st = 0;
-    a.stable_mask[m_base + m] = st;
-    if (st)
-      atomicAdd(reinterpret_cast<unsigned long long*>(a.n_stable + a.p0 + p), (unsigned long long)__popcll(st));
+    __syncthreads();  // s_slot and s_next are reused by the next job
   }
 }
 
@@ -288,25 +375,23 @@ using namespace lp;
 struct lp_batch {
   int device = 0, sm_count = 0;
   int32_t n_programs = 0;
-  int32_t n_groups = 0;             // launches: consecutive programs, at most kBatchGroup of them
-  std::vector<int32_t> group_start;  // n_groups + 1 program boundaries
+  int32_t n_jobs = 0, n_slots = 0, grid = 0;  // the launch: jobs, their block slots, resident blocks
   std::vector<lp_info> infos;           // per program
   std::vector<BatchProgram> table;      // host copy
-  int64_t total_rows = 0, total_nnz = 0, total_state = 0, total_mask_words = 0;
+  int64_t total_rows = 0, total_nnz = 0, total_state = 0, total_mask_words = 0, total_entries = 0;
   BatchProgram* d_table = nullptr;
-  int64_t* d_cell_off = nullptr;
-  int64_t* d_mask_off = nullptr;
-  int64_t* d_row_ptr = nullptr;
+  int4* d_hdr = nullptr;
   int32_t* d_col = nullptr;
-  uint32_t* d_any = nullptr;
   int32_t* d_tag = nullptr;
   int32_t* d_neg = nullptr;
   int32_t* d_bar = nullptr;
-  uint64_t* d_x0 = nullptr;
-  uint64_t* d_x1 = nullptr;
+  unsigned char* d_x0 = nullptr;
+  unsigned char* d_x1 = nullptr;
   int64_t* d_nstable = nullptr;
   int32_t* d_iters = nullptr;
-  unsigned* d_pflag = nullptr;
+  BatchJob* d_jobs = nullptr;
+  int32_t* d_slot_job = nullptr;
+  unsigned long long* d_job_bar = nullptr;  // 4 per job, then the queue counter
   DeviceCtl* d_ctl = nullptr;
   uint64_t* d_stage = nullptr;  // staging for a host stable_mask
   int64_t device_bytes = 0;
@@ -322,9 +407,8 @@ lp_status bfail(lp_status st, const std::string& msg) {
 }
 
 void batch_release(lp_batch* b) {
-  void* ptrs[] = {b->d_table, b->d_cell_off, b->d_mask_off, b->d_row_ptr, b->d_col, b->d_any, b->d_tag,
-                  b->d_neg,   b->d_bar,      b->d_x0,       b->d_x1,      b->d_nstable, b->d_iters,
-                  b->d_pflag, b->d_ctl,      b->d_stage};
+  void* ptrs[] = {b->d_table, b->d_hdr, b->d_col, b->d_tag, b->d_neg,     b->d_bar, b->d_x0,
+                  b->d_x1,    b->d_nstable, b->d_iters, b->d_jobs, b->d_slot_job, b->d_job_bar, b->d_ctl, b->d_stage};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -347,6 +431,83 @@ lp_status bupload(lp_batch* b, T** ptr, const T* src, size_t count, cudaStream_t
   return LP_OK;
 }
 
+// One program's sliced layout (the layout of the least-model kernel 2, built on the host here):
+// rows renumbered by length within windows of 1024, 128-row groups padded to their longest row,
+// entries column-major so that lane l of a warp reads the k-th entries of rows l, 32 + l,
+// 64 + l, 96 + l as one int4; a shorter row repeats its first entry, an empty row is masked.
+struct ProgSlices {
+  std::vector<int4> hdr;     // 3 per group: {first entry (program-local), width, 0, 0}, OR masks, empty masks
+  std::vector<int32_t> ent;  // entries, columns in the new numbering
+  std::vector<int32_t> tag;  // Def. 8 initial-column tag per row, new numbering
+  std::vector<int32_t> neg, bar;
+};
+
+void build_slices(const HostMatrix& hm, ProgSlices& out) {
+  constexpr int kWin = 1024;
+  const int32_t np = hm.n_pad;
+  std::vector<int32_t> q((size_t)np), qinv((size_t)np);
+  std::vector<std::pair<int32_t, int32_t>> key;
+  for (int32_t lo = 0; lo < np; lo += kWin) {
+    const int32_t hi = std::min(np, lo + kWin);
+    key.clear();
+    for (int32_t r = lo; r < hi; r++) key.emplace_back(hm.row_ptr[r + 1] - hm.row_ptr[r], r);
+    std::stable_sort(key.begin(), key.end(), [](const std::pair<int32_t, int32_t>& x, const std::pair<int32_t, int32_t>& y) {
+      return x.first < y.first;
+    });
+    for (int32_t i = 0; i < hi - lo; i++) {
+      qinv[lo + i] = key[i].second;
+      q[key[i].second] = lo + i;
+    }
+  }
+  const int32_t ng = (np + kGroupRows - 1) / kGroupRows;
+  out.hdr.assign(3 * (size_t)ng, make_int4(0, 0, 0, 0));
+  int64_t off = 0;
+  std::vector<int32_t> K((size_t)ng, 0);
+  for (int32_t g = 0; g < ng; g++) {
+    int32_t k = 0;
+    uint32_t orm[4] = {0, 0, 0, 0}, emm[4] = {0, 0, 0, 0};
+    for (int t = 0; t < kGroupRows; t++) {
+      const int32_t row = g * kGroupRows + t;
+      int32_t len = 0;
+      bool anyb = false;
+      if (row < np) {
+        const int32_t r = qinv[row];
+        len = hm.row_ptr[r + 1] - hm.row_ptr[r];
+        anyb = (hm.any_mask[r >> 5] >> (r & 31)) & 1u;
+      }
+      k = std::max(k, len);
+      if (anyb) orm[t >> 5] |= 1u << (t & 31);
+      if (len == 0) emm[t >> 5] |= 1u << (t & 31);
+    }
+    K[g] = k;
+    out.hdr[3 * (size_t)g] = make_int4((int)off, k, 0, 0);
+    out.hdr[3 * (size_t)g + 1] = make_int4((int)orm[0], (int)orm[1], (int)orm[2], (int)orm[3]);
+    out.hdr[3 * (size_t)g + 2] = make_int4((int)emm[0], (int)emm[1], (int)emm[2], (int)emm[3]);
+    off += (int64_t)kGroupRows * k;
+  }
+  out.ent.assign((size_t)off, 0);
+  for (int32_t g = 0; g < ng; g++) {
+    const int64_t base = out.hdr[3 * (size_t)g].x;
+    for (int t = 0; t < kGroupRows; t++) {
+      const int32_t row = g * kGroupRows + t;
+      if (row >= np) continue;
+      const int32_t r = qinv[row];
+      const int32_t b = hm.row_ptr[r], len = hm.row_ptr[r + 1] - b;
+      const int32_t first = len > 0 ? q[hm.col[b]] : 0;
+      const int u = t >> 5, l = t & 31;
+      for (int32_t k = 0; k < K[g]; k++) out.ent[base + 4 * (32 * k + l) + u] = k < len ? q[hm.col[b + k]] : first;
+    }
+  }
+  out.tag.assign((size_t)np, -1);
+  for (int32_t r = 0; r < np; r++) out.tag[q[r]] = hm.row_tag[r];
+  out.neg.resize(hm.neg_row.size());
+  out.bar.resize(hm.bar_row.size());
+  for (size_t j = 0; j < hm.neg_row.size(); j++) {
+    out.neg[j] = q[hm.neg_row[j]];
+    out.bar[j] = q[hm.bar_row[j]];
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -364,6 +525,7 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     if (rule_off[p + 1] < rule_off[p]) return bfail(LP_ERR_INVALID, "rule_off decreases");
   auto t0 = std::chrono::steady_clock::now();
   std::vector<HostMatrix> hms(n_programs);
+  std::vector<ProgSlices> sl(n_programs);
   std::vector<std::string> errs(n_programs);
   std::vector<int> rcs(n_programs, LP_OK);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -372,8 +534,14 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     std::vector<int64_t> off((size_t)nr + 1);
     for (int64_t r = 0; r <= nr; r++) off[r] = body_off[r0 + r] - body_off[r0];
     const int64_t b0 = body_off[r0];
-    rcs[p] = compile_host(n_atoms[p], nr, head + r0, off.data(), body_atom ? body_atom + b0 : nullptr,
-                          body_neg ? body_neg + b0 : nullptr, hms[p], errs[p]);
+    try {
+      rcs[p] = compile_host(n_atoms[p], nr, head + r0, off.data(), body_atom ? body_atom + b0 : nullptr,
+                            body_neg ? body_neg + b0 : nullptr, hms[p], errs[p]);
+      if (rcs[p] == LP_OK && hms[p].k <= 16) build_slices(hms[p], sl[p]);
+    } catch (const std::bad_alloc&) {
+      rcs[p] = LP_ERR_OOM;
+      errs[p] = "host allocation failed";
+    }
   }
   for (int32_t p = 0; p < n_programs; p++)
     if (rcs[p] != LP_OK) return bfail((lp_status)rcs[p], "program " + std::to_string(p) + ": " + errs[p]);
@@ -382,7 +550,7 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
   b->n_programs = n_programs;
   b->infos.resize(n_programs);
   b->table.resize(n_programs);
-  int64_t row = 0, state = 0, mask = 0, nnz = 0, neg = 0;
+  int64_t row = 0, state = 0, mask = 0, nnz = 0, neg = 0, ent = 0, groups = 0;
   for (int32_t p = 0; p < n_programs; p++) {
     const HostMatrix& hm = hms[p];
     if (hm.k > 16) {
@@ -392,19 +560,21 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     BatchProgram& t = b->table[p];
     t.row0 = row;
     t.n_pad = hm.n_pad;
-    t.log2W = hm.k > 6 ? hm.k - 6 : 0;
-    t.W = 1 << t.log2W;
+    t.rb = std::max(2, (1 << hm.k) / 8);
     t.k = hm.k;
-    t.pad_ = 0;
     t.state0 = state;
     t.mask0 = mask;
     t.n_neg = (int32_t)hm.neg_row.size();
     t.neg0 = neg;
+    t.g0 = (int32_t)groups;
+    t.n_groups = (int32_t)(sl[p].hdr.size() / 3);
     row += hm.n_pad;
-    state += (int64_t)hm.n_pad * t.W;
-    mask += t.W;
+    state += (int64_t)hm.n_pad * t.rb;
+    mask += t.rb >= 8 ? t.rb / 8 : 1;
     nnz += hm.nnz;
     neg += t.n_neg;
+    ent += (int64_t)sl[p].ent.size();
+    groups += t.n_groups;
     lp_info& in = b->infos[p];
     std::memset(&in, 0, sizeof(in));
     in.n_atoms = hm.n;
@@ -422,82 +592,91 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
   b->total_nnz = nnz;
   b->total_state = state;
   b->total_mask_words = mask;
-  // block-diagonal concatenation (global row = program row offset + internal row)
-  std::vector<int64_t> rp((size_t)row + 1, 0);
-  std::vector<int32_t> cl((size_t)std::max<int64_t>(nnz, 1)), tag((size_t)std::max<int64_t>(row, 1)),
-      ng((size_t)std::max<int64_t>(neg, 1)), br((size_t)std::max<int64_t>(neg, 1));
-  std::vector<uint32_t> any((size_t)std::max<int64_t>(row / 32, 1), 0u);
-  if (row >= (int64_t(1) << 31) - 64) {
+  b->total_entries = ent;
+  if (row >= (int64_t(1) << 31) - 64 || ent >= (int64_t(1) << 31) - 64 || groups >= (int64_t(1) << 29)) {
     delete b;
-    return bfail(LP_ERR_INVALID, "batch too large (rows must be < 2^31)");
+    return bfail(LP_ERR_INVALID, "batch too large (rows and stored entries must be < 2^31)");
   }
+  // concatenation: group headers with global entry offsets, entries, row tags, negated pairs
+  std::vector<int4> hdr(3 * (size_t)std::max<int64_t>(groups, 1));
+  std::vector<int32_t> cl((size_t)std::max<int64_t>(ent, 1)), tag((size_t)std::max<int64_t>(row, 1)),
+      ng((size_t)std::max<int64_t>(neg, 1)), br((size_t)std::max<int64_t>(neg, 1));
   {
-    int64_t c = 0;
+    int64_t e0 = 0;
     for (int32_t p = 0; p < n_programs; p++) {
-      const HostMatrix& hm = hms[p];
-      const int64_t r0 = b->table[p].row0;
-      for (int32_t r = 0; r < hm.n_pad; r++) {
-        rp[r0 + r] = c + hm.row_ptr[r];
-        tag[r0 + r] = hm.row_tag[r];
+      const BatchProgram& t = b->table[p];
+      const ProgSlices& ps = sl[p];
+      for (int32_t g = 0; g < t.n_groups; g++) {
+        int4 h = ps.hdr[3 * (size_t)g];
+        h.x = (int)(h.x + e0);
+        hdr[3 * ((size_t)t.g0 + g)] = h;
+        hdr[3 * ((size_t)t.g0 + g) + 1] = ps.hdr[3 * (size_t)g + 1];
+        hdr[3 * ((size_t)t.g0 + g) + 2] = ps.hdr[3 * (size_t)g + 2];
       }
-      for (int64_t e = 0; e < hm.nnz; e++) cl[c + e] = (int32_t)(hm.col[e] + r0);
-      for (size_t w = 0; w < hm.any_mask.size(); w++) any[(r0 >> 5) + w] = hm.any_mask[w];
-      for (int32_t j = 0; j < b->table[p].n_neg; j++) {
-        ng[b->table[p].neg0 + j] = (int32_t)(hm.neg_row[j] + 0);
-        br[b->table[p].neg0 + j] = (int32_t)(hm.bar_row[j] + 0);
-      }
-      c += hm.nnz;
+      std::copy(ps.ent.begin(), ps.ent.end(), cl.begin() + e0);
+      std::copy(ps.tag.begin(), ps.tag.end(), tag.begin() + t.row0);
+      std::copy(ps.neg.begin(), ps.neg.end(), ng.begin() + t.neg0);
+      std::copy(ps.bar.begin(), ps.bar.end(), br.begin() + t.neg0);
+      e0 += (int64_t)ps.ent.size();
     }
-    rp[row] = c;
   }
-  std::vector<int64_t> cell_off((size_t)n_programs + 1), mask_off((size_t)n_programs + 1);
-  for (int32_t p = 0; p < n_programs; p++) {
-    cell_off[p] = b->table[p].state0;
-    mask_off[p] = b->table[p].mask0;
-  }
-  cell_off[n_programs] = state;
-  mask_off[n_programs] = mask;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
   lp_status st = e == cudaSuccess ? LP_OK : bfail(LP_ERR_CUDA, cudaGetErrorString(e));
   if (st == LP_OK) st = bupload(b, &b->d_table, b->table.data(), b->table.size(), s);
-  if (st == LP_OK) st = bupload(b, &b->d_cell_off, cell_off.data(), cell_off.size(), s);
-  if (st == LP_OK) st = bupload(b, &b->d_mask_off, mask_off.data(), mask_off.size(), s);
-  if (st == LP_OK) st = bupload(b, &b->d_row_ptr, rp.data(), rp.size(), s);
-  if (st == LP_OK) st = bupload(b, &b->d_col, cl.data(), (size_t)nnz, s);
-  if (st == LP_OK) st = bupload(b, &b->d_any, any.data(), any.size(), s);
+  if (st == LP_OK) st = bupload(b, &b->d_hdr, hdr.data(), 3 * (size_t)groups, s);
+  if (st == LP_OK) st = bupload(b, &b->d_col, cl.data(), (size_t)ent, s);
   if (st == LP_OK) st = bupload(b, &b->d_tag, tag.data(), (size_t)row, s);
   if (st == LP_OK) st = bupload(b, &b->d_neg, ng.data(), (size_t)neg, s);
   if (st == LP_OK) st = bupload(b, &b->d_bar, br.data(), (size_t)neg, s);
-  if (st == LP_OK) st = bupload<uint64_t>(b, &b->d_x0, nullptr, (size_t)state, s);
-  if (st == LP_OK) st = bupload<uint64_t>(b, &b->d_x1, nullptr, (size_t)state, s);
+  if (st == LP_OK) st = bupload<unsigned char>(b, &b->d_x0, nullptr, (size_t)state, s);
+  if (st == LP_OK) st = bupload<unsigned char>(b, &b->d_x1, nullptr, (size_t)state, s);
   if (st == LP_OK) st = bupload<int64_t>(b, &b->d_nstable, nullptr, (size_t)n_programs, s);
   if (st == LP_OK) st = bupload<int32_t>(b, &b->d_iters, nullptr, (size_t)n_programs, s);
-  // Groups: consecutive programs whose matrix and iterates together fit the group budget (and
-  // at most kBatchGroup of them), so that a group's data stays in L2 across its iterations.
-  int64_t budget = kGroupBytes;
-  if (const char* env = std::getenv("LP_BATCH_GROUP_BYTES")) budget = std::max<int64_t>(1, std::atoll(env));
-  b->group_start.assign(1, 0);
-  {
-    int64_t bytes = 0;
+  // Jobs: one per program, largest first. A program whose share of the work exceeds one block's
+  // share of the whole batch runs on several co-resident blocks (at most 16, and all multi-block
+  // jobs together on at most half of the grid, so that every one of them is fully staffed by
+  // the first blocks to start); the others run on one block each.
+  int per_sm = 0;
+  if (st == LP_OK && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_stable_kernel, kBatchBlock, 0)) !=
+                         cudaSuccess)
+    st = bfail(LP_ERR_CUDA, cudaGetErrorString(e));
+  if (st == LP_OK && n_programs > 0 && per_sm < 1) st = bfail(LP_ERR_CUDA, "batch kernel cannot be resident");
+  std::vector<BatchJob> jobs;
+  std::vector<int32_t> slot_job;
+  if (st == LP_OK) {
+    b->grid = std::max(1, per_sm * b->sm_count);
+    std::vector<double> work((size_t)n_programs);
+    double total_work = 0;
     for (int32_t p = 0; p < n_programs; p++) {
       const BatchProgram& t = b->table[p];
-      const int64_t pb = 8 * ((int64_t)t.n_pad + 1) + 4 * hms[p].nnz + 16 * (int64_t)t.n_pad * t.W;
-      const int32_t in_group = p - b->group_start.back();
-      if (in_group > 0 && (bytes + pb > budget || in_group == kBatchGroup)) {
-        b->group_start.push_back(p);
-        bytes = 0;
-      }
-      bytes += pb;
+      work[p] = 4.0 * (double)sl[p].ent.size() + 3.0 * (double)t.n_pad * t.rb + 48.0 * t.n_groups;
+      total_work += work[p];
     }
-    b->group_start.push_back(n_programs);
-    if (n_programs == 0) b->group_start.assign(1, 0);
+    std::vector<int32_t> order((size_t)n_programs);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return work[x] > work[y]; });
+    const double share = total_work / b->grid;
+    const int multi_cap = std::max(1, b->grid / 2);
+    int multi = 0;
+    for (int32_t p : order) {
+      int c = 1;
+      if (share > 0 && work[p] > share) c = (int)std::min<double>(16.0, std::ceil(work[p] / share));
+      c = std::min(c, std::max(1, b->table[p].n_groups));
+      if (c > 1 && multi + c > multi_cap) c = 1;
+      if (c > 1) multi += c;
+      BatchJob jb{p, c, (int32_t)slot_job.size(), 0};
+      jobs.push_back(jb);
+      for (int r = 0; r < c; r++) slot_job.push_back((int32_t)jobs.size() - 1);
+    }
+    b->n_jobs = (int32_t)jobs.size();
+    b->n_slots = (int32_t)slot_job.size();
   }
-  b->n_groups = (int32_t)b->group_start.size() - 1;
-  if (st == LP_OK)
-    st = bupload<unsigned>(b, &b->d_pflag, nullptr, ((size_t)n_programs + (size_t)b->n_groups) * kSlots, s);
-  if (st == LP_OK) st = bupload<DeviceCtl>(b, &b->d_ctl, nullptr, (size_t)b->n_groups, s);
+  if (st == LP_OK) st = bupload(b, &b->d_jobs, jobs.data(), jobs.size(), s);
+  if (st == LP_OK) st = bupload(b, &b->d_slot_job, slot_job.data(), slot_job.size(), s);
+  if (st == LP_OK) st = bupload<unsigned long long>(b, &b->d_job_bar, nullptr, 4 * (size_t)b->n_jobs + 1, s);
+  if (st == LP_OK) st = bupload<DeviceCtl>(b, &b->d_ctl, nullptr, 1, s);
   if (st == LP_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = bfail(LP_ERR_CUDA, cudaGetErrorString(e));
   if (st != LP_OK) {
     batch_release(b);
@@ -543,27 +722,19 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
     }
     d_mask = b->d_stage;
   }
-  cudaError_t e = cudaMemsetAsync(b->d_ctl, 0, std::max<size_t>(b->n_groups, 1) * sizeof(DeviceCtl), s);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(b->d_pflag, 0, ((size_t)b->n_programs + (size_t)b->n_groups) * kSlots * 4, s);
+  cudaError_t e = cudaMemsetAsync(b->d_ctl, 0, sizeof(DeviceCtl), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_job_bar, 0, (4 * (size_t)b->n_jobs + 1) * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nstable, 0, std::max<size_t>(b->n_programs, 1) * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_iters, 0, std::max<size_t>(b->n_programs, 1) * 4, s);
   if (e != cudaSuccess) return bfail(LP_ERR_CUDA, cudaGetErrorString(e));
-  int per_sm = 0;
-  if (b->n_programs > 0 &&
-      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_stable_kernel, kBatchBlock, 0) != cudaSuccess ||
-       per_sm < 1))
-    return bfail(LP_ERR_CUDA, "batch kernel cannot be resident");
-  for (int32_t g = 0; g < b->n_groups; g++) {
+  if (b->n_programs > 0) {
     BatchArgs a{};
     a.progs = b->d_table;
-    a.cell_off = b->d_cell_off;
-    a.mask_off = b->d_mask_off;
-    a.p0 = b->group_start[g];
-    a.n = b->group_start[g + 1] - a.p0;
-    a.row_ptr = b->d_row_ptr;
+    a.jobs = b->d_jobs;
+    a.slot_job = b->d_slot_job;
+    a.n_slots = b->n_slots;
+    a.hdr = b->d_hdr;
     a.col = b->d_col;
-    a.any_mask = b->d_any;
     a.row_tag = b->d_tag;
     a.neg_row = b->d_neg;
     a.bar_row = b->d_bar;
@@ -572,17 +743,12 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
     a.stable_mask = d_mask;
     a.n_stable = reinterpret_cast<long long*>(b->d_nstable);
     a.iters = b->d_iters;
-    a.pflag = b->d_pflag;
-    a.gflag = b->d_pflag + ((size_t)b->n_programs + g) * kSlots;
-    a.ctl = b->d_ctl + g;
+    a.job_bar = b->d_job_bar;
+    a.queue = reinterpret_cast<unsigned*>(b->d_job_bar + 4 * (size_t)b->n_jobs);
+    a.ctl = b->d_ctl;
     a.max_iters = max_iters;
-    // resident blocks only (grid barrier); fewer blocks make the barrier cheaper, and a grid
-    // larger than the group's work gains nothing
-    const int64_t words = b->table[a.p0 + a.n - 1].state0 + (int64_t)b->table[a.p0 + a.n - 1].n_pad *
-                                                                b->table[a.p0 + a.n - 1].W -
-                          b->table[a.p0].state0;
-    const long long want = std::max<long long>(1, (words + kBatchBlock - 1) / kBatchBlock);
-    const int grid = (int)std::min<long long>((long long)per_sm * b->sm_count, want);
+    // every block resident (multi-block jobs meet at their own barriers); no more blocks than slots
+    const int grid = std::max(1, std::min(b->grid, b->n_slots));
     void* params[] = {&a};
     e = cudaLaunchCooperativeKernel((const void*)batch_stable_kernel, dim3(grid), dim3(kBatchBlock), params, 0, s);
     if (e != cudaSuccess) {
@@ -605,14 +771,12 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
   if (iters && b->n_programs)
     if ((e = cudaMemcpyAsync(iters, b->d_iters, (size_t)b->n_programs * 4, cudaMemcpyDefault, s)) != cudaSuccess)
       return bfail(LP_ERR_CUDA, cudaGetErrorString(e));
-  std::vector<DeviceCtl> ctls((size_t)std::max(b->n_groups, 1));
-  if (b->n_groups &&
-      (e = cudaMemcpyAsync(ctls.data(), b->d_ctl, (size_t)b->n_groups * sizeof(DeviceCtl), cudaMemcpyDeviceToHost,
-                           s)) != cudaSuccess)
+  DeviceCtl ctl;
+  std::memset(&ctl, 0, sizeof(ctl));
+  if (b->n_programs && (e = cudaMemcpyAsync(&ctl, b->d_ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return bfail(LP_ERR_CUDA, cudaGetErrorString(e));
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bfail(LP_ERR_CUDA, cudaGetErrorString(e));
-  for (int32_t g = 0; g < b->n_groups; g++)
-    if (ctls[g].status != 0 && (status == 0 || status == LP_ERR_NO_FIXPOINT)) status = ctls[g].status;
+  status = ctl.status;
   if (status == LP_ERR_NO_FIXPOINT) return bfail(LP_ERR_NO_FIXPOINT, "a program reached max_iters");
   if (status != 0) return bfail((lp_status)status, "batch kernel gave up waiting at a grid barrier");
   return LP_OK;

@@ -10,7 +10,7 @@ import pytest
 import oracle
 import paper_2009_10247_gb300 as lp
 from tests.helpers import bits_to_bool
-from workloads import Program, parse, program_batch, small_definite, tiny_random
+from workloads import Program, normal_program, parse, program_batch, small_definite, tiny_random
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -128,10 +128,13 @@ def test_more_programs_than_one_launch():
     assert np.all(it >= 1)
 
 
-def test_many_small_launches(monkeypatch):
-    # a 2 MB group budget splits the uneven-size batch into many cooperative launches
-    monkeypatch.setenv("LP_BATCH_GROUP_BYTES", str(2_000_000))
-    progs = program_batch(seed=12, count=60, n_lo=100, n_hi=4000)
-    got, ns, it, B = _run_batch(progs)
-    _check_oracle(progs, got, ns)
+def test_single_and_few_large_programs():
+    # one program alone takes the whole batch's work: it runs as one job on many blocks that
+    # meet at the job's barrier; two programs of very different sizes split the blocks
+    one = [normal_program(seed=21, n=4000, n_rules=12000, k=7, per_atom=2)]
+    got, ns, it, _ = _run_batch(one)
+    _check_oracle(one, got, ns)
+    two = [normal_program(seed=22, n=6000, n_rules=18000, k=8, per_atom=2), parse("p :- not q. q :- not p.")]
+    got, ns, it, _ = _run_batch(two)
+    _check_oracle(two, got, ns)
     assert np.all(it >= 1)

@@ -645,6 +645,48 @@ def bench_stable(lp, torch, dev, flush, steps=5, tune=True):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": measured_traffic("stable_kernel"), "peak_kind": peak_kind, "kernel": "stable_kernel",
                         "note": "tiles are sized to stay L2 resident, so this fraction can exceed 1"}}
+    # the frontier schedule on the same tile width: after each tile's first (full) iteration only
+    # the rows that changed and the rows that refer to them are evaluated. Its own byte count:
+    # the full first iteration of every tile by the formula above, then per evaluated row its row
+    # pointers (8 B), its entries (4 B each) and their gathered words (8 W B each), its old words
+    # read and new words written (16 W B), and per changed row the transposed row pointers (8 B)
+    # and its dependents (4 B each).
+    sched = P.schedule
+    P.set_schedule(stable_frontier=1)
+    P.stable_models(mask)
+    ns_f = None
+    for _ in range(2):
+        flush.zero_()
+        P.stable_models(mask, sync=False)
+    tf = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.stable_models(mask, sync=False)
+        b.record(stream)
+        b.synchronize()
+        tf.append(a.elapsed_time(b))
+    sf = P.last_stats()
+    ns_f = int(sum(bin(int(w)).count("1") for w in mask.cpu().numpy().view(np.uint64)))
+    msf = sum(tf) / len(tf)
+    fbytes = (sf["tiles"] * bytes_tile_iter + 8 * sf["frontier_rows"] + 4 * sf["frontier_entries"]
+              + 8 * W * sf["frontier_entries"] + 16 * W * sf["frontier_rows"] + 8 * sf["frontier_list"]
+              + 4 * sf["frontier_deps"])
+    fach = fbytes / (msf / 1e3) / 1e9
+    out["frontier"] = {
+        "metric": "stable-model guesses/sec, frontier schedule", "value": ng / (msf / 1e3), "unit": "guesses/s",
+        "ms_per_step": msf, "n_stable": ns_f, "tile_words": W, "tile_iters_sum": sf["sum_tile_iters"],
+        "rows_reevaluated": sf["frontier_rows"], "rows_of_full_sweeps": info["n_prime"] * (sf["sum_tile_iters"] - sf["tiles"]),
+        "over_full_sweep": ms / msf,
+        "roofline": {"bound": "hbm", "achieved": fach, "peak": peak, "unit": "GB/s", "frac": fach / peak,
+                     "bytes_per_launch": fbytes, "peak_kind": peak_kind,
+                     "note": "bytes the schedule touches: each tile's first full iteration, then only the "
+                             "re-evaluated rows (their entries, gathered words, old and new words) and the "
+                             "changed rows' dependents; never the full-sweep formula"}}
+    if ns_f != ns:
+        raise RuntimeError("frontier schedule found another number of stable models")
+    P.set_schedule(**sched)
     # the baseline: one launch per guess (lp_stable_models on a one-guess list), sampled
     n_one = 128
     one = torch.zeros(1, dtype=torch.int64, device=dev)

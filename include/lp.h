@@ -79,6 +79,11 @@ typedef struct {
   int64_t tile_words;    /* stable models: 64-bit guess words per tile                       */
   int64_t max_tile_iters;/* stable models: largest per-tile iteration count                  */
   int64_t sum_tile_iters;/* stable models: sum of per-tile iteration counts                  */
+  int64_t frontier_rows;   /* stable models, frontier schedule: rows re-evaluated after each
+                              tile's first iteration (summed over iterations and tiles)          */
+  int64_t frontier_entries;/* ... their matrix entries                                           */
+  int64_t frontier_list;   /* ... changed rows whose dependents were visited                    */
+  int64_t frontier_deps;   /* ... dependents visited (entries of the transposed matrix)         */
 } lp_solve_stats;
 
 /*
@@ -270,6 +275,11 @@ typedef struct {
   int32_t stable_blocks_per_sm;   /* stable models: resident CTAs per SM; 0 = all that fit      */
   int32_t stable_row_split;       /* stable models: 1 = one row per warp, its entries split over
                                      the warp's lane groups (long rows); 0 = 32 / W rows per warp */
+  int32_t stable_frontier;        /* stable models: 1 = after each tile's first iteration evaluate
+                                     only the rows that changed and the rows that refer to them
+                                     (same iterates and iteration counts; the transposed matrix is
+                                     built on the device on first use); needs stable_row_split 0;
+                                     the autotuner leaves it as it is                            */
   int32_t fixpoint_stage;         /* least model, kernel 2: 0 = copy the vector prefix that rule
                                      rows gather into shared memory every iteration when it fits
                                      (160 KB); 1 = gather from global memory (through L1)         */

@@ -111,6 +111,7 @@ void release(lp_program* p) {
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
                   p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
                   p->sl_q, p->sl_qinv, p->sl_hdr, p->sl_col, p->sl_fact_row, p->sl_perm,
+                  p->fr_tptr, p->fr_tidx, p->fr_mark, p->fr_list, p->fr_eval, p->fr_cnt,
                   p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p,
                   p->tune_out.p, p->tune_in.p};
   for (void* q : ptrs)
@@ -323,6 +324,50 @@ lp_status lp_program_info(const lp_program* p, lp_info* out) {
 }
 
 namespace {
+
+// The frontier schedule's transposed matrix and work lists, built on the device on first use.
+lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
+  if (p->fr_cnt) return LP_OK;
+  const HostMatrix& hm = p->hm;
+  lp_status st;
+  int32_t* cnt = nullptr;
+  auto fail_clean = [&](lp_status code) {
+    if (cnt) cudaFree(cnt);
+    void** ptrs[] = {(void**)&p->fr_tptr, (void**)&p->fr_tidx, (void**)&p->fr_mark, (void**)&p->fr_list,
+                     (void**)&p->fr_eval, (void**)&p->fr_cnt};
+    for (void** q : ptrs)
+      if (*q) {
+        cudaFree(*q);
+        *q = nullptr;
+      }
+    return code;
+  };
+  if ((st = dalloc(p, &p->fr_tptr, (size_t)hm.n_pad + 1)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->fr_tidx, (size_t)std::max<int64_t>(hm.nnz, 1))) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->fr_mark, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->fr_list, 2 * (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->fr_eval, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
+  unsigned* counters = nullptr;
+  if ((st = dalloc(p, &counters, 8)) != LP_OK) return fail_clean(st);
+  if (device_malloc((void**)&cnt, ((size_t)hm.n_pad + 1) * 4) != cudaSuccess) {
+    cnt = nullptr;
+    cudaGetLastError();
+    cudaFree(counters);
+    return fail_clean(fail(LP_ERR_OOM, "frontier scratch"));
+  }
+  cudaError_t e = cudaMemsetAsync(cnt, 0, ((size_t)hm.n_pad + 1) * 4, s);
+  if (e == cudaSuccess) e = build_transpose(p->row_ptr, p->col, hm.n_pad, p->fr_tptr, p->fr_tidx, cnt, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(cnt);
+  cnt = nullptr;
+  if (e != cudaSuccess) {
+    cudaFree(counters);
+    return fail_clean(cuda_fail(e, "frontier transpose"));
+  }
+  count_launches(hm.n_pad > 0 ? 3 : 0);
+  p->fr_cnt = counters;
+  return LP_OK;
+}
 
 // The streamed kernel's layout, built on its first use from the device CSR.
 lp_status ensure_stream_layout(lp_program* p, cudaStream_t s) {
@@ -602,14 +647,24 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   a.max_iters = max_iters;
   a.ctl = p->ctl;
   const bool split = p->sched.stable_row_split == 1;
-  static int occ_by_split[2] = {-1, -1};
-  int& occ = occ_by_split[split];
-  if (occ < 0) occ = stable_blocks_per_sm(split);
+  const bool frontier = p->sched.stable_frontier == 1 && !split;
+  if (frontier) {
+    if ((st = ensure_frontier(p, s)) != LP_OK) return st;
+    a.t_ptr = p->fr_tptr;
+    a.t_idx = p->fr_tidx;
+    a.mark = p->fr_mark;
+    a.fr_list = p->fr_list;
+    a.fr_eval = p->fr_eval;
+    a.fr_cnt = p->fr_cnt;
+  }
+  static int occ_by_split[3] = {-1, -1, -1};
+  int& occ = occ_by_split[frontier ? 2 : (int)split];
+  if (occ < 0) occ = stable_blocks_per_sm(split, frontier);
   if (occ <= 0) return fail(LP_ERR_CUDA, "stable kernel cannot be resident");
   const int per_sm = p->sched.stable_blocks_per_sm > 0 ? std::min(occ, p->sched.stable_blocks_per_sm) : occ;
   const int64_t rows_per_block = (int64_t)(kStableBlock / 32) * (32 / W);
   int grid = (int)std::min<int64_t>(max_coresident(p, per_sm), std::max<int64_t>(1, hm.n_pad / rows_per_block));
-  if ((st = launch_count_and_check(launch_stable(a, grid, split, s), "launch stable kernel", p)) != LP_OK) return st;
+  if ((st = launch_count_and_check(launch_stable(a, grid, split, frontier, s), "launch stable kernel", p)) != LP_OK) return st;
   LP_CUDA(cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s));
   if (host_mask) LP_CUDA(cudaMemcpyAsync(stable_mask, d_mask, (size_t)n_gwords * 8, cudaMemcpyDeviceToHost, s));
   if (host_models) LP_CUDA(cudaMemcpyAsync(models, d_models, (size_t)max_models * atom_words * 8, cudaMemcpyDeviceToHost, s));
@@ -653,6 +708,9 @@ lp_status lp_set_schedule(lp_program* p, const lp_schedule* in) {
   if (R > 0 && (in->fixpoint_kernel != 0 || G > 1 || X == 4))
     return fail(LP_ERR_INVALID, "a thread-per-row map needs fixpoint_kernel 0, no row split and no chunk batch");
   if (in->stable_row_split != 0 && in->stable_row_split != 1) return fail(LP_ERR_INVALID, "stable_row_split must be 0 or 1");
+  if (in->stable_frontier != 0 && in->stable_frontier != 1) return fail(LP_ERR_INVALID, "stable_frontier must be 0 or 1");
+  if (in->stable_frontier == 1 && in->stable_row_split == 1)
+    return fail(LP_ERR_INVALID, "the frontier schedule needs stable_row_split 0");
   if (W < 0 || W > 32 || (W & (W - 1)) != 0) return fail(LP_ERR_INVALID, "stable_tile_words must be 0 or 1, 2, 4, 8, 16, 32");
   p->sched = *in;
   return LP_OK;
@@ -677,6 +735,10 @@ lp_status lp_last_solve_stats(lp_program* p, lp_solve_stats* out, void* cuda_str
   out->tile_words = p->tile_words;
   out->max_tile_iters = p->h_ctl->max_tile_iters;
   out->sum_tile_iters = p->h_ctl->sum_tile_iters;
+  out->frontier_rows = (int64_t)p->h_ctl->fr_rows;
+  out->frontier_entries = (int64_t)p->h_ctl->fr_entries;
+  out->frontier_list = (int64_t)p->h_ctl->fr_list;
+  out->frontier_deps = (int64_t)p->h_ctl->fr_deps;
   return LP_OK;
 }
 

@@ -22,6 +22,9 @@ struct DeviceCtl {
   unsigned long long timeout_site;  // where a wait gave up (diagnostics)
   unsigned long long count[3];      // true rows per iteration, rotating (monotone runs)
   unsigned long long init_count;    // true rows of the initial vector
+  // stable models, frontier schedule: rows re-evaluated, their entries, changed-row list
+  // items expanded, and dependents visited, summed over the launch's iterations after the first
+  unsigned long long fr_rows, fr_entries, fr_list, fr_deps;
 };
 
 // Upper bound of one barrier wait. A healthy wait takes microseconds; after this the waiting

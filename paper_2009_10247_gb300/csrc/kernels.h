@@ -129,11 +129,26 @@ struct StableArgs {
   int32_t n_atom_words;
   int32_t max_iters;
   DeviceCtl* ctl;
+  // frontier schedule (after a tile's first iteration only the rows with a changed input are
+  // evaluated): the transposed matrix, a per-row stamp, two changed-row lists, the list of rows
+  // to evaluate, and six counters (changed-list sizes, rotating; to-evaluate sizes, rotating)
+  const int32_t* t_ptr;     // n_pad + 1: rows referring to column j are t_idx[t_ptr[j] .. t_ptr[j + 1])
+  const int32_t* t_idx;     // nnz
+  int32_t* mark;            // n_pad
+  int32_t* fr_list;         // 2 x n_pad
+  int32_t* fr_eval;         // n_pad
+  unsigned* fr_cnt;         // 6
 };
 
 constexpr int kStableBlock = 256;
-// row_split: one row per warp, its entries split over the warp's 32 / W lane groups
-cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, cudaStream_t s);
-int stable_blocks_per_sm(bool row_split);
+// row_split: one row per warp, its entries split over the warp's 32 / W lane groups; frontier:
+// after each tile's first iteration, only rows with an input that changed are evaluated (needs
+// the t_ptr / t_idx / mark / fr_* fields; not with row_split)
+cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, bool frontier, cudaStream_t s);
+int stable_blocks_per_sm(bool row_split, bool frontier);
+// Transposed matrix for the frontier schedule, built on the device: cnt (n_pad + 1 ints of
+// scratch, zeroed by the caller) becomes the cursor of the fill.
+cudaError_t build_transpose(const int32_t* row_ptr, const int32_t* col, int32_t n_pad, int32_t* t_ptr, int32_t* t_idx,
+                            int32_t* cnt, cudaStream_t s);
 
 }  // namespace lp

@@ -45,6 +45,13 @@ struct lp_program {
   int32_t* sl_fact_row = nullptr;
   int32_t* sl_perm = nullptr;
   int64_t sl_entries = -1;        // stored entries; -1 = not built
+  // frontier schedule of the stable models: transposed matrix and work lists (built on first use)
+  int32_t* fr_tptr = nullptr;
+  int32_t* fr_tidx = nullptr;
+  int32_t* fr_mark = nullptr;
+  int32_t* fr_list = nullptr;
+  int32_t* fr_eval = nullptr;
+  unsigned* fr_cnt = nullptr;
   // scratch
   uint32_t* x[2] = {nullptr, nullptr};
   lp::DeviceCtl* ctl = nullptr;

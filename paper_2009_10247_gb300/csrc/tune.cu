@@ -151,7 +151,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     }
     if ((st = ensure(p, p->tune_out, (size_t)n_gwords * 8)) != LP_OK) return st;
     uint64_t* mask = (uint64_t*)p->tune_out.p;
-    const int occ = stable_blocks_per_sm(false);
+    const int occ = stable_blocks_per_sm(false, base.stable_frontier == 1);
     auto stable = [&](int W, int blocks, int split) {
       lp_schedule c = best_least;  // least-model fields as chosen above
       c.stable_tile_words = W;

@@ -33,7 +33,9 @@ class _Info(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
                 ("launches", ctypes.c_int64), ("tiles", ctypes.c_int64), ("tile_words", ctypes.c_int64),
-                ("max_tile_iters", ctypes.c_int64), ("sum_tile_iters", ctypes.c_int64)]
+                ("max_tile_iters", ctypes.c_int64), ("sum_tile_iters", ctypes.c_int64),
+                ("frontier_rows", ctypes.c_int64), ("frontier_entries", ctypes.c_int64),
+                ("frontier_list", ctypes.c_int64), ("frontier_deps", ctypes.c_int64)]
 
 
 EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models", "lp_last_solve_stats",
@@ -46,7 +48,7 @@ LP_TUNE_LEAST = 1
 LP_TUNE_STABLE = 2
 SCHEDULE_FIELDS = ("fixpoint_kernel", "fixpoint_blocks_per_sm", "fixpoint_row_split", "fixpoint_chunk_batch",
                    "fixpoint_row_map", "stable_tile_words", "stable_blocks_per_sm", "stable_row_split",
-                   "fixpoint_stage")
+                   "stable_frontier", "fixpoint_stage")
 
 
 class _Schedule(ctypes.Structure):
@@ -58,7 +60,7 @@ class _TuneRecord(ctypes.Structure):
 
 # Version of the schedule fields and their meaning (row maps, kernels); part of the key of
 # autotune_cached, so a cache written by another build is not applied.
-SCHEDULE_FORMAT = 2
+SCHEDULE_FORMAT = 3
 
 _lib = None
 

@@ -141,7 +141,8 @@ def test_schedule_get_set_validates(lib):
     with lp.Program.from_program(small_definite(1), host_only=True) as P:
         assert P.schedule == {"fixpoint_kernel": 0, "fixpoint_blocks_per_sm": 0, "fixpoint_row_split": 0,
                               "fixpoint_chunk_batch": 0, "fixpoint_row_map": 0, "stable_tile_words": 0,
-                              "stable_blocks_per_sm": 0, "stable_row_split": 0, "fixpoint_stage": 0}
+                              "stable_blocks_per_sm": 0, "stable_row_split": 0, "stable_frontier": 0,
+                              "fixpoint_stage": 0}
         for m in (1, 2, 3):
             P.set_schedule(fixpoint_row_map=m)
             assert P.schedule["fixpoint_row_map"] == m
@@ -151,7 +152,8 @@ def test_schedule_get_set_validates(lib):
         P.set_schedule(fixpoint_row_map=0)
         P.set_schedule(fixpoint_kernel=1, fixpoint_blocks_per_sm=2, stable_tile_words=8, stable_blocks_per_sm=1)
         assert P.schedule["stable_tile_words"] == 8 and P.schedule["fixpoint_kernel"] == 1
-        for bad in ({"fixpoint_kernel": 4}, {"fixpoint_stage": 2}, {"stable_tile_words": 3}, {"stable_tile_words": 64},
+        for bad in ({"fixpoint_kernel": 4}, {"fixpoint_stage": 2}, {"stable_frontier": 2},
+                    {"stable_frontier": 1, "stable_row_split": 1}, {"stable_tile_words": 3}, {"stable_tile_words": 64},
                     {"fixpoint_row_split": 3}, {"fixpoint_row_split": 2},  # the second: kernel 1 is set
                     {"fixpoint_chunk_batch": 2}, {"fixpoint_chunk_batch": 4}, {"stable_row_split": 2},
                     {"fixpoint_blocks_per_sm": -1}, {"stable_blocks_per_sm": -2}, {"fixpoint_row_map": 4},

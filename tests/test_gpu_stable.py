@@ -136,17 +136,19 @@ def _full_size_expected(prog):
 
 
 def test_full_size_2_16_guesses_every_bit():
-    # all 65,536 guesses in one call, default and tuned schedules: every stable bit equals the
-    # oracle's, and every tile's iteration count is the largest of its columns' counts
+    # all 65,536 guesses in one call, default, tuned and frontier schedules: every stable bit
+    # equals the oracle's, and every tile's iteration count is the largest of its columns' counts
     p = normal_program(seed=1)
     want, word_iters = _full_size_expected(p)
     assert len(want) == 1 << 16
     with lp.Program.from_program(p) as P:
-        for tuned in (False, True):
-            if tuned:
+        for variant in ("default", "tuned", "frontier"):
+            if variant == "tuned":
                 P.autotune(lp.LP_TUNE_STABLE, reps=1)  # the schedule the benchmark times
+            if variant == "frontier":
+                P.set_schedule(stable_frontier=1)  # on the tuned tile width
             st, _, ns = gpu_stable(P)
-            assert np.array_equal(st, want), f"tuned={tuned}: {np.count_nonzero(st != want)} guesses differ"
+            assert np.array_equal(st, want), f"{variant}: {np.count_nonzero(st != want)} guesses differ"
             assert ns == int(want.sum())
             stats = P.last_stats()
             W = stats["tile_words"]
@@ -154,3 +156,38 @@ def test_full_size_2_16_guesses_every_bit():
             assert stats["tiles"] == len(per_tile)
             assert stats["max_tile_iters"] == per_tile.max()
             assert stats["sum_tile_iters"] == per_tile.sum()
+            if variant == "frontier":  # re-evaluated rows: a few per cent of the full sweeps
+                assert 0 < stats["frontier_rows"] < 0.2 * P.info["n_prime"] * per_tile.sum()
+
+
+@pytest.mark.parametrize("W", [1, 2, 8, 32])
+def test_frontier_schedule_matches_oracle(W):
+    # the frontier schedule (after a tile's first iteration only rows with a changed input are
+    # evaluated) gives the oracle's stable bits and models, and the full sweep's tile iterations
+    progs = [normal_program(seed=4, n=3000, n_rules=9000, k=12, per_atom=2), parse("p :- not q. q :- not p."),
+             parse("a :- not b. b :- not a. c :- a. c :- b."), small_definite(2)]
+    rng = np.random.default_rng(9)
+    progs += [tiny_random(7000 + s, n_atoms=int(rng.integers(2, 60)), n_rules=int(rng.integers(1, 120)), max_body=4,
+                          p_fact=0.15, p_neg=0.1) for s in range(12)]
+    for prog in progs:
+        st4, m4, _ = oracle.stable_models_alg23(prog)
+        with lp.Program.from_program(prog) as P:
+            P.set_schedule(stable_tile_words=W)
+            _, _, _ = gpu_stable(P)
+            full = P.last_stats()
+            P.set_schedule(stable_frontier=1)
+            st, models, ns = gpu_stable(P, max_models=16)
+            fr = P.last_stats()
+        assert np.array_equal(st, st4) and ns == int(st4.sum())
+        assert np.array_equal(models, m4[st4][:16])
+        assert (fr["max_tile_iters"], fr["sum_tile_iters"]) == (full["max_tile_iters"], full["sum_tile_iters"])
+
+
+def test_frontier_schedule_explicit_guesses():
+    p = normal_program(seed=6, n=2000, n_rules=6000, k=12, per_atom=3)
+    g = np.random.default_rng(2).integers(0, 1 << 12, 500).astype(np.uint64)
+    st4, _, _ = oracle.stable_models_alg23(p, guesses=g)
+    with lp.Program.from_program(p) as P:
+        P.set_schedule(stable_frontier=1)
+        st, _, ns = gpu_stable(P, guesses=g)
+    assert np.array_equal(st, st4) and ns == int(st4.sum())

@@ -254,6 +254,9 @@ def main():
     ap.add_argument("--seed", type=int, default=1, help="seed of the least-model workload (default 1)")
     ap.add_argument("--n-atoms", type=int, default=1_000_000,
                     help="atoms of the least-model workload (5 rules per atom); smaller for profiler captures")
+    ap.add_argument("--stable-atoms", type=int, default=100_000,
+                    help="atoms of the stable-model workload (3 rules per atom); smaller for profiler captures")
+    ap.add_argument("--stable-k", type=int, default=16, help="negated atoms of the stable-model workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -370,7 +373,8 @@ def main():
     if not args.no_closure and rank == 0:
         closure = bench_closure(lp, torch, dev, flush, tune=not args.no_tune)
     if not args.no_stable and rank == 0:
-        secondary = bench_stable(lp, torch, dev, flush, tune=not args.no_tune)
+        secondary = bench_stable(lp, torch, dev, flush, tune=not args.no_tune, n_atoms=args.stable_atoms,
+                                 k=args.stable_k)
     if not args.no_batch and rank == 0:
         batch = bench_batch(lp, torch, dev, flush, iter_profile=args.batch_iter_profile)
     if not args.no_relaxed and rank == 0:
@@ -605,17 +609,10 @@ def bench_stable_sharded(lp, torch, dev, flush, dist, world, steps=5):
                     "to the host), max over ranks; explicit guess lists per range"}
 
 
-def bench_stable(lp, torch, dev, flush, steps=5, tune=True):
-    """Batched stable models (Algorithms 2 + 3): all 2^16 guesses of the normal program."""
-    prog = normal_program(seed=1)
-    P = lp.Program.from_program(prog)
-    k = P.info["k"]
-    ng = 1 << k
-    mask = torch.zeros(lp.words(ng), dtype=torch.int64, device=dev)
-    if tune:
-        P.autotune(lp.LP_TUNE_STABLE, reps=2)
-    ns = P.stable_models(mask)
-    stream = torch.cuda.current_stream()
+def _time_stable(P, mask, flush, stream, torch, steps):
+    """Mean CUDA-event time of one all-guess solve on the handle's schedule (L2 flushed before
+    each), its stats and its number of stable guesses."""
+    P.stable_models(mask)  # first solve: buffers (and the frontier buffers' rest state)
     for _ in range(2):
         flush.zero_()
         P.stable_models(mask, sync=False)
@@ -628,64 +625,77 @@ def bench_stable(lp, torch, dev, flush, steps=5, tune=True):
         b.record(stream)
         b.synchronize()
         ts.append(a.elapsed_time(b))
-    st = P.last_stats()
-    ms = sum(ts) / len(ts)
-    info = P.info
+    ns = int(sum(bin(int(w)).count("1") for w in mask.cpu().numpy().view(np.uint64)))
+    return sum(ts) / len(ts), P.last_stats(), ns
+
+
+def _stable_line(info, st, ms, ng, frontier):
+    """Throughput and roofline of one stable-model schedule, each with its own byte count.
+    Full sweep: every tile iteration reads the row pointers and column ids once and the tile's
+    iterate words once and writes them once (4(n'+1) + 4 nnz + 16 n' W bytes). Frontier: only
+    what it touches -- per evaluated row its row pointers (8 B), its entries (4 B each) and their
+    gathered words (8 W B each), its old words read and new words written (16 W B); per changed
+    row the transposed row pointers (8 B) and its dependents (4 B each)."""
     W = st["tile_words"]
-    bytes_tile_iter = 4 * (info["n_prime"] + 1) + 4 * info["nnz"] + 16 * info["n_prime"] * W
-    achieved = bytes_tile_iter * st["sum_tile_iters"] / (ms / 1e3) / 1e9
+    if frontier:
+        by = (8 * st["frontier_rows"] + 4 * st["frontier_entries"] + 8 * W * st["frontier_entries"]
+              + 16 * W * st["frontier_rows"] + 8 * st["frontier_list"] + 4 * st["frontier_deps"])
+        evals = st["frontier_entries"] * 64 * W
+        kernel = "stable_frontier_kernel"
+        note = ("bytes the schedule touches (evaluated rows, their entries and gathered words, changed rows' "
+                "dependents), not the full-sweep formula; the buffers' reset and the first list are not counted")
+    else:
+        by = (4 * (info["n_prime"] + 1) + 4 * info["nnz"] + 16 * info["n_prime"] * W) * st["sum_tile_iters"]
+        evals = info["nnz"] * st["sum_tile_iters"] * 64 * W
+        kernel = "stable_kernel"
+        note = "tiles are sized to stay L2 resident, so this fraction can exceed 1"
     peak, peak_kind = peaks()
-    # rule evaluations of the batch: every tile iteration evaluates every entry for 64 W guesses
-    rule_evals = info["nnz"] * st["sum_tile_iters"] * 64 * W
-    out = {"metric": "stable-model guesses/sec", "value": ng / (ms / 1e3), "unit": "guesses/s",
-           "rule_evals_per_s": rule_evals / (ms / 1e3),
-           "ms_per_step": ms, "workload": WORKLOAD_STABLE, "n_prime": info["n_prime"], "nnz": info["nnz"], "k": k,
-           "n_stable": ns, "tiles": st["tiles"], "tile_words": W, "tile_iters_max": st["max_tile_iters"],
-           "schedule": P.schedule,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": measured_traffic("stable_kernel"), "peak_kind": peak_kind, "kernel": "stable_kernel",
-                        "note": "tiles are sized to stay L2 resident, so this fraction can exceed 1"}}
-    # the frontier schedule on the same tile width: after each tile's first (full) iteration only
-    # the rows that changed and the rows that refer to them are evaluated. Its own byte count:
-    # the full first iteration of every tile by the formula above, then per evaluated row its row
-    # pointers (8 B), its entries (4 B each) and their gathered words (8 W B each), its old words
-    # read and new words written (16 W B), and per changed row the transposed row pointers (8 B)
-    # and its dependents (4 B each).
+    achieved = by / (ms / 1e3) / 1e9
+    return {"value": ng / (ms / 1e3), "unit": "guesses/s", "ms_per_step": ms, "rule_evals_per_s": evals / (ms / 1e3),
+            "tiles": st["tiles"], "tile_words": W, "tile_iters_max": st["max_tile_iters"],
+            "tile_iters_sum": st["sum_tile_iters"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": measured_traffic(kernel), "peak_kind": peak_kind, "kernel": kernel,
+                         "bytes_per_launch": by, "note": note}}
+
+
+def stable_workload(n_atoms, k):
+    if (n_atoms, k) == (100_000, 16):
+        return WORKLOAD_STABLE
+    return (f"normal program: {n_atoms} atoms, {3 * n_atoms} rules, bodies U{{1..6}}, 1% facts, k={k} negated "
+            f"atoms x 4 (seed 1), all {1 << k} guesses")
+
+
+def bench_stable(lp, torch, dev, flush, steps=5, tune=True, n_atoms=100_000, k=16):
+    """Batched stable models (Algorithms 2 + 3): all 2^k guesses of the normal program (1e5 atoms,
+    k = 16 unless scaled for a profiler capture), on the tuned schedule, with the other schedule
+    (full sweep or frontier) on the same tile width."""
+    prog = normal_program(seed=1, n=n_atoms, n_rules=3 * n_atoms, k=k)
+    P = lp.Program.from_program(prog)
+    k = P.info["k"]
+    ng = 1 << k
+    mask = torch.zeros(lp.words(ng), dtype=torch.int64, device=dev)
+    if tune:
+        P.autotune(lp.LP_TUNE_STABLE, reps=2)
+    stream = torch.cuda.current_stream()
+    info = P.info
     sched = P.schedule
-    P.set_schedule(stable_frontier=1)
-    P.stable_models(mask)
-    ns_f = None
-    for _ in range(2):
-        flush.zero_()
-        P.stable_models(mask, sync=False)
-    tf = []
-    for _ in range(steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        P.stable_models(mask, sync=False)
-        b.record(stream)
-        b.synchronize()
-        tf.append(a.elapsed_time(b))
-    sf = P.last_stats()
-    ns_f = int(sum(bin(int(w)).count("1") for w in mask.cpu().numpy().view(np.uint64)))
-    msf = sum(tf) / len(tf)
-    fbytes = (sf["tiles"] * bytes_tile_iter + 8 * sf["frontier_rows"] + 4 * sf["frontier_entries"]
-              + 8 * W * sf["frontier_entries"] + 16 * W * sf["frontier_rows"] + 8 * sf["frontier_list"]
-              + 4 * sf["frontier_deps"])
-    fach = fbytes / (msf / 1e3) / 1e9
-    out["frontier"] = {
-        "metric": "stable-model guesses/sec, frontier schedule", "value": ng / (msf / 1e3), "unit": "guesses/s",
-        "ms_per_step": msf, "n_stable": ns_f, "tile_words": W, "tile_iters_sum": sf["sum_tile_iters"],
-        "rows_reevaluated": sf["frontier_rows"], "rows_of_full_sweeps": info["n_prime"] * (sf["sum_tile_iters"] - sf["tiles"]),
-        "over_full_sweep": ms / msf,
-        "roofline": {"bound": "hbm", "achieved": fach, "peak": peak, "unit": "GB/s", "frac": fach / peak,
-                     "bytes_per_launch": fbytes, "peak_kind": peak_kind,
-                     "note": "bytes the schedule touches: each tile's first full iteration, then only the "
-                             "re-evaluated rows (their entries, gathered words, old and new words) and the "
-                             "changed rows' dependents; never the full-sweep formula"}}
-    if ns_f != ns:
-        raise RuntimeError("frontier schedule found another number of stable models")
+    main_frontier = sched["stable_frontier"] == 1
+    ms, st, ns = _time_stable(P, mask, flush, stream, torch, steps)
+    out = {"metric": "stable-model guesses/sec", **_stable_line(info, st, ms, ng, main_frontier),
+           "workload": stable_workload(n_atoms, k), "n_prime": info["n_prime"], "nnz": info["nnz"], "k": k, "n_stable": ns,
+           "schedule": sched}
+    P.set_schedule(stable_frontier=0 if main_frontier else 1)
+    ms2, st2, ns2 = _time_stable(P, mask, flush, stream, torch, steps)
+    other = "full_sweep" if main_frontier else "frontier"
+    out[other] = {"metric": f"stable-model guesses/sec, {other.replace('_', ' ')} schedule",
+                  **_stable_line(info, st2, ms2, ng, not main_frontier), "n_stable": ns2,
+                  "over_main": ms / ms2}
+    fr_st = st if main_frontier else st2
+    out["frontier_rows_reevaluated"] = fr_st["frontier_rows"]
+    out["rows_of_full_sweeps"] = info["n_prime"] * (st2 if main_frontier else st)["sum_tile_iters"]
+    if ns2 != ns:
+        raise RuntimeError("the stable-model schedules found other numbers of stable models")
     P.set_schedule(**sched)
     # the baseline: one launch per guess (lp_stable_models on a one-guess list), sampled
     n_one = 128

@@ -49,6 +49,9 @@ typedef enum {
 /* lp_compile flags */
 #define LP_COMPILE_HOST_ONLY 1u /* build M_P on the host only (no GPU needed): the handle then
                                    serves lp_program_info and lp_export_matrix only          */
+#define LP_COMPILE_ON_HOST 2u   /* standardize on the host's threads and upload the matrix
+                                   (default: the rules are uploaded and standardized on the
+                                   GPU; both give the same matrix, array for array)          */
 
 /* lp_least_model flags */
 #define LP_ROWS 1u   /* init/out are over all n' rows of M_P in canonical order (see below)   */
@@ -107,10 +110,13 @@ typedef struct {
  * head[r] in [0, n_atoms) and body literals body_atom[body_off[r] .. body_off[r+1]) with
  * body_off[0] = 0 and body_off non-decreasing; body_neg (nullable) marks negated literals with
  * a non-zero byte. An empty body is a fact. n_rules, the body literals, n_prime and nnz must
- * stay below 2^31. The host work runs on OpenMP threads; the matrix does not depend on their
- * number.
- * flags: 0, or LP_COMPILE_HOST_ONLY (no device memory is touched; solves on such a handle return
- * LP_ERR_INVALID). cuda_stream: stream of the uploads. On success *out receives a new
+ * stay below 2^31. By default the rules are copied to the device as given and standardized
+ * there by kernels on cuda_stream; with LP_COMPILE_ON_HOST (or LP_COMPILE_HOST_ONLY) the host
+ * compiler runs on OpenMP threads. Both build the same arrays, and neither depends on the number
+ * of threads.
+ * flags: 0, LP_COMPILE_ON_HOST, or LP_COMPILE_HOST_ONLY (no device memory is touched; solves on
+ * such a handle return LP_ERR_INVALID). cuda_stream: stream of the uploads and the device
+ * compile; the call returns after it has finished. On success *out receives a new
  * handle (free it with lp_free). Errors: LP_ERR_INVALID (malformed program), LP_ERR_OOM,
  * LP_ERR_CUDA; *out is then NULL.
  */
@@ -405,6 +411,16 @@ void lp_free(lp_program* prog);
  * (a small kernel; waits for cuda_stream) or, for an LP_COMPILE_HOST_ONLY handle, on the host
  * copy. *n_bad (host) receives the number of violations (0 for every matrix lp_compile builds). */
 lp_status lp_check_matrix(const lp_program* prog, int64_t* n_bad, void* cuda_stream);
+
+/* Diagnostics, no counterpart in the paper: copies internal array `which` of a device handle
+ * to host memory `out` (the two compilers are compared with it). which: 0 row_ptr (n_pad + 1
+ * int32), 1 col (nnz int32), 2 perm (canonical -> internal, n' int32), 3 any_mask (n_pad / 32
+ * uint32), 4 row_tag (n_pad int32), 5 fact_row (fact rows int32), 6 fact_owner (same), 7
+ * fact_mask (ceil(n / 64) uint64), 8 neg_row (n_barred int32), 9 bar_row (same). *bytes (host)
+ * receives the array's size; out may be NULL to ask for it, else it must hold that many bytes.
+ * Waits for cuda_stream. Errors: LP_ERR_INVALID (NULL handle or bytes, unknown which, a
+ * host-only handle). */
+lp_status lp_debug_internal(const lp_program* prog, int32_t which, void* out, int64_t* bytes, void* cuda_stream);
 
 /* Test hook, no counterpart in the paper: after `after` more successful device allocations by
  * liblp, the next one fails (once) as if the device were out of memory, so that the

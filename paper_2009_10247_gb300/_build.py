@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "liblp.so")
-SOURCES = ["api.cu", "fixpoint.cu", "fixpoint_stream.cu", "fixpoint_sliced.cu", "fixpoint_block.cu", "stable.cu", "static_scratch.cu", "relaxed.cu", "batch.cu", "tune.cu", "search.cu", "diag.cu", "compile.cpp"]
+SOURCES = ["api.cu", "fixpoint.cu", "fixpoint_stream.cu", "fixpoint_sliced.cu", "fixpoint_block.cu", "stable.cu", "stable_frontier.cu", "static_scratch.cu", "compile_device.cu", "relaxed.cu", "batch.cu", "tune.cu", "search.cu", "diag.cu", "compile.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -62,6 +62,39 @@ cudaError_t device_malloc(void** ptr, size_t bytes) {
   return cudaMalloc(ptr, bytes);
 }
 
+cudaError_t device_malloc_async(void** ptr, size_t bytes, cudaStream_t s) {
+  int64_t left = g_fail_alloc_after.load();
+  while (left >= 0) {
+    if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+      if (left == 0) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  static std::mutex mu;
+  static std::vector<int> pools_set;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(pools_set.begin(), pools_set.end(), dev) == pools_set.end()) {
+      // this process's stream-ordered pool keeps up to 8 GiB between compiles instead of
+      // returning it at every synchronization
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = 8ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      cudaGetLastError();
+      pools_set.push_back(dev);
+    }
+  }
+  return cudaMallocAsync(ptr, bytes, s);
+}
+
 lp_status ensure(lp_program* p, DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return LP_OK;
   if (b.p) {
@@ -111,7 +144,7 @@ void release(lp_program* p) {
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
                   p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
                   p->sl_q, p->sl_qinv, p->sl_hdr, p->sl_col, p->sl_fact_row, p->sl_perm,
-                  p->fr_tptr, p->fr_tidx, p->fr_mark, p->fr_list, p->fr_eval, p->fr_cnt,
+                  p->fr_tptr, p->fr_tidx, p->fr_cnt, p->fr_buf.p, p->dc_kind, p->dc_rule,
                   p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p,
                   p->tune_out.p, p->tune_in.p};
   for (void* q : ptrs)
@@ -232,6 +265,71 @@ const char* const sliced_unsupported_msg = "fixpoint_kernel 2 needs fewer than 2
 
 }  // namespace lp
 
+// What every device handle gets after its matrix is on the device: the iterate vectors, the
+// scratch, the default schedule. Frees the handle on failure.
+lp_status finish_handle(lp_program* p, cudaStream_t s, std::chrono::steady_clock::time_point t0,
+                        std::chrono::steady_clock::time_point t_host, std::chrono::steady_clock::time_point t_upload,
+                        lp_program** out) {
+  auto cleanup = [&](lp_status code) {
+    release(p);
+    delete p;
+    return code;
+  };
+  const HostMatrix& hm = p->hm;
+  lp_status st;
+  // iterate vectors, padded so 16-byte vector loads of a staged prefix stay inside
+  if ((st = dalloc(p, &p->x[0], (size_t)hm.n_pad / 32 + 4)) != LP_OK) return cleanup(st);
+  if ((st = dalloc(p, &p->x[1], (size_t)hm.n_pad / 32 + 4)) != LP_OK) return cleanup(st);
+  if ((st = ensure_scratch(p)) != LP_OK) return cleanup(st);
+  // default least-model schedule: the one-block kernel 3 where the program fits one block's
+  // shared memory, else the sliced kernel 2 with the vector gathered through L1 (the autotuner's
+  // picks on small and on large programs); kernel 0 where the sliced layout's indices overflow
+  if (p->sched.fixpoint_kernel == 0 && sliced_supported(p)) {
+    bool fits = false;
+    if ((st = block_kernel_fits(p, s, &fits)) != LP_OK) return cleanup(st);
+    p->sched.fixpoint_kernel = fits ? 3 : 2;
+    p->sched.fixpoint_stage = fits ? 0 : 1;
+  }
+  p->sched.stable_frontier = 1;  // stable models: the frontier schedule over all tiles at once
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "lp_compile"));
+  const auto t_end = std::chrono::steady_clock::now();
+  p->compile_ms = std::chrono::duration<double, std::milli>(t_end - t0).count();
+  if (std::getenv("LP_COMPILE_TRACE")) {
+    auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+    std::fprintf(stderr, "lp_compile (ms): standardize=%.2f upload=%.2f schedule=%.2f total=%.2f\n", ms(t0, t_host),
+                 ms(t_host, t_upload), ms(t_upload, t_end), p->compile_ms);
+  }
+  *out = p;
+  return LP_OK;
+}
+
+// lp_compile without LP_COMPILE_ON_HOST: the rules go to the device and are standardized there.
+lp_status compile_device_handle(lp_program* p, int32_t n_atoms, int64_t n_rules, const int32_t* head,
+                                const int64_t* body_off, const int32_t* body_atom, const uint8_t* body_neg,
+                                cudaStream_t s, std::chrono::steady_clock::time_point t0, lp_program** out) {
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice/attribute");
+  }
+  lp_status st;
+  {
+    NvtxRange nvtx_dev("lp_compile: standardize on the device");
+    st = compile_on_device(p, n_atoms, n_rules, head, body_off, body_atom, body_neg, s);
+  }
+  if (st != LP_OK) {
+    const std::string msg = g_err;  // release() may not touch it, but keep the compile's message
+    cudaStreamSynchronize(s);       // the scratch frees are stream-ordered
+    release(p);
+    delete p;
+    return fail(st, msg);
+  }
+  const auto t = std::chrono::steady_clock::now();
+  return finish_handle(p, s, t0, t, t, out);
+}
+
 extern "C" {
 
 const char* lp_last_error(void) { return g_err.c_str(); }
@@ -246,7 +344,7 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   NvtxRange nvtx("lp_compile");
   if (!out) return fail(LP_ERR_INVALID, "out must not be NULL");
   *out = nullptr;
-  if (flags & ~LP_COMPILE_HOST_ONLY) return fail(LP_ERR_INVALID, "unknown flags");
+  if (flags & ~(LP_COMPILE_HOST_ONLY | LP_COMPILE_ON_HOST)) return fail(LP_ERR_INVALID, "unknown flags");
   auto t0 = std::chrono::steady_clock::now();
   lp_program* p = new (std::nothrow) lp_program();
   if (p) {
@@ -256,6 +354,9 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   if (!p) return fail(LP_ERR_OOM, "host allocation failed");
   std::string err;
   lp_status st;
+  const bool on_host = (flags & (LP_COMPILE_HOST_ONLY | LP_COMPILE_ON_HOST)) != 0;
+  if (!on_host) return compile_device_handle(p, n_atoms, n_rules, head, body_off, body_atom, body_neg,
+                                             (cudaStream_t)cuda_stream, t0, out);
   {
     NvtxRange nvtx_host("lp_compile: standardize");
     st = compile_host(n_atoms, n_rules, head, body_off, body_atom, body_neg, p->hm, err);
@@ -271,6 +372,7 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
     return LP_OK;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  const auto t_host = std::chrono::steady_clock::now();
   auto cleanup = [&](lp_status code) {
     release(p);
     delete p;
@@ -290,18 +392,13 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   if ((st = upload(p, &p->neg_row, hm.neg_row, s)) != LP_OK) return cleanup(st);
   if ((st = upload(p, &p->bar_row, hm.bar_row, s)) != LP_OK) return cleanup(st);
   if ((st = upload(p, &p->row_tag, hm.row_tag, s)) != LP_OK) return cleanup(st);
-  // iterate vectors, padded so 16-byte vector loads of a staged prefix stay inside
-  if ((st = dalloc(p, &p->x[0], (size_t)hm.n_pad / 32 + 4)) != LP_OK) return cleanup(st);
-  if ((st = dalloc(p, &p->x[1], (size_t)hm.n_pad / 32 + 4)) != LP_OK) return cleanup(st);
-  if ((st = ensure_scratch(p)) != LP_OK) return cleanup(st);
   e = cudaStreamSynchronize(s);  // host vectors are pageable and about to be released
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "upload"));
   free_vec(hm.row_ptr);
   free_vec(hm.col);
   free_vec(hm.row_tag);
-  p->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  *out = p;
-  return LP_OK;
+  p->host_tables = true;
+  return finish_handle(p, s, t0, t_host, std::chrono::steady_clock::now(), out);
 }
 
 lp_status lp_program_info(const lp_program* p, lp_info* out) {
@@ -325,53 +422,70 @@ lp_status lp_program_info(const lp_program* p, lp_info* out) {
 
 namespace {
 
-// The frontier schedule's transposed matrix and work lists, built on the device on first use.
+// The frontier schedule's transposed matrix and counters, built on the device on first use.
 lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
   if (p->fr_cnt) return LP_OK;
   const HostMatrix& hm = p->hm;
   lp_status st;
   int32_t* cnt = nullptr;
+  unsigned* counters = nullptr;
   auto fail_clean = [&](lp_status code) {
     if (cnt) cudaFree(cnt);
-    void** ptrs[] = {(void**)&p->fr_tptr, (void**)&p->fr_tidx, (void**)&p->fr_mark, (void**)&p->fr_list,
-                     (void**)&p->fr_eval, (void**)&p->fr_cnt};
-    for (void** q : ptrs)
-      if (*q) {
-        cudaFree(*q);
-        *q = nullptr;
-      }
+    void* ptrs[] = {p->fr_tptr, p->fr_tidx, counters};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+    p->fr_tptr = p->fr_tidx = nullptr;
     return code;
   };
   if ((st = dalloc(p, &p->fr_tptr, (size_t)hm.n_pad + 1)) != LP_OK) return fail_clean(st);
   if ((st = dalloc(p, &p->fr_tidx, (size_t)std::max<int64_t>(hm.nnz, 1))) != LP_OK) return fail_clean(st);
-  if ((st = dalloc(p, &p->fr_mark, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
-  if ((st = dalloc(p, &p->fr_list, 2 * (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
-  if ((st = dalloc(p, &p->fr_eval, (size_t)hm.n_pad)) != LP_OK) return fail_clean(st);
-  unsigned* counters = nullptr;
   if ((st = dalloc(p, &counters, 8)) != LP_OK) return fail_clean(st);
   if (device_malloc((void**)&cnt, ((size_t)hm.n_pad + 1) * 4) != cudaSuccess) {
     cnt = nullptr;
     cudaGetLastError();
-    cudaFree(counters);
     return fail_clean(fail(LP_ERR_OOM, "frontier scratch"));
   }
-  cudaError_t e = cudaMemsetAsync(cnt, 0, ((size_t)hm.n_pad + 1) * 4, s);
+  cudaError_t e = cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, ((size_t)hm.n_pad + 1) * 4, s);
   if (e == cudaSuccess) e = build_transpose(p->row_ptr, p->col, hm.n_pad, p->fr_tptr, p->fr_tidx, cnt, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(cnt);
   cnt = nullptr;
-  if (e != cudaSuccess) {
-    cudaFree(counters);
-    return fail_clean(cuda_fail(e, "frontier transpose"));
-  }
+  if (e != cudaSuccess) return fail_clean(cuda_fail(e, "frontier transpose"));
   count_launches(hm.n_pad > 0 ? 3 : 0);
   p->fr_cnt = counters;
+  return LP_OK;
+}
+
+// Bytes of the frontier buffers for `tiles` tiles of W words: two iterate buffers, a stamp and two
+// list slots per item, the changed-item bitmap, a counter per tile.
+int64_t frontier_bytes(int64_t n_pad, int W, int64_t tiles) {
+  const int64_t items = tiles * n_pad;
+  return 2 * items * W * 8 + items * 4 + 2 * items * 4 + ((items + 31) / 32) * 4 + tiles * 4 + 64;
+}
+
+// The wave buffers for `tiles` tiles of W words; a new allocation voids the rest-state record.
+lp_status ensure_frontier_buffers(lp_program* p, int W, int32_t tiles, cudaStream_t s) {
+  if (p->fr_buf.p && p->fr_W == W && p->fr_tiles == tiles) return LP_OK;
+  const size_t bytes = (size_t)frontier_bytes(p->hm.n_pad, W, tiles);
+  if (p->fr_buf.p && p->fr_buf.bytes < bytes) {
+    cudaFree(p->fr_buf.p);
+    p->device_bytes -= (int64_t)p->fr_buf.bytes;
+    p->fr_buf = DevBuf{};
+  }
+  lp_status st = ensure(p, p->fr_buf, bytes);
+  if (st != LP_OK) return st;
+  p->fr_W = W;
+  p->fr_tiles = tiles;
+  LP_CUDA(cudaMemsetAsync(p->fr_cnt, 0, 8 * sizeof(unsigned), s));
   return LP_OK;
 }
 
 // The streamed kernel's layout, built on its first use from the device CSR.
 lp_status ensure_stream_layout(lp_program* p, cudaStream_t s) {
   if (p->desc) return LP_OK;
+  lp_status ht = ensure_host_tables(p, s);  // the layout is built on the host from perm and kinds
+  if (ht != LP_OK) return ht;
   HostMatrix& hm = p->hm;
   hm.row_ptr.resize((size_t)hm.n_pad + 1);
   hm.col.resize((size_t)std::max<int64_t>(hm.nnz, 1));
@@ -419,6 +533,7 @@ lp_status lp_least_model(lp_program* p, const uint64_t* init, uint64_t* out, int
   const size_t out_words = in_words;
 
   if (rows && !p->inv) {
+    if ((st = ensure_host_tables(p, s)) != LP_OK) return st;
     std::vector<int32_t> inv(std::max(hm.n_pad, 1), 0);
     for (int32_t c = 0; c < hm.n_prime; c++) inv[hm.perm[c]] = c;
     if ((st = upload(p, &p->inv, inv, s)) != LP_OK) return st;
@@ -596,7 +711,24 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   }
   const int W = 1 << log2W;
   const int64_t n_tiles = (n_gwords + W - 1) / W;
-  if ((st = ensure(p, p->tiles, (size_t)2 * hm.n_pad * W * 8)) != LP_OK) return st;
+  const bool split = p->sched.stable_row_split == 1;
+  const bool frontier = p->sched.stable_frontier == 1 && !split;
+  int32_t wave_tiles = 0;
+  if (frontier) {
+    // tiles in flight at once: as many as the budget holds (8 GiB by default), item ids in int32
+    int64_t fr_budget = 8ll << 30;
+    if (const char* env = std::getenv("LP_FRONTIER_BYTES")) fr_budget = std::max<int64_t>(1, std::atoll(env));
+    int64_t c = std::min<int64_t>(n_tiles, fr_budget / frontier_bytes(hm.n_pad, W, 1));
+    c = std::min<int64_t>(c, (int64_t)(INT32_MAX - 64) / std::max<int64_t>(hm.n_pad, 1));
+    wave_tiles = (int32_t)std::max<int64_t>(c, 1);
+    if ((st = ensure_frontier(p, s)) != LP_OK) return st;
+    // a handle keeps the largest wave it has run unless a wider tile needs another layout
+    const int32_t keep = p->fr_W == W ? std::max(p->fr_tiles, wave_tiles) : wave_tiles;
+    if (frontier_bytes(hm.n_pad, W, keep) <= fr_budget) wave_tiles = keep;
+    if ((st = ensure_frontier_buffers(p, W, wave_tiles, s)) != LP_OK) return st;
+  } else if ((st = ensure(p, p->tiles, (size_t)2 * hm.n_pad * W * 8)) != LP_OK) {
+    return st;
+  }
   p->tile_words = W;
 
   const bool host_g = guesses && !is_device_ptr(guesses);
@@ -626,8 +758,6 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   a.any_mask = p->any_mask;
   a.row_tag = p->row_tag;
   a.n_pad = hm.n_pad;
-  a.X0 = (uint64_t*)p->tiles.p;
-  a.X1 = (uint64_t*)p->tiles.p + (size_t)hm.n_pad * W;
   a.W = W;
   a.log2W = log2W;
   a.n_guesses = n_guesses;
@@ -646,25 +776,41 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   a.n_atom_words = atom_words;
   a.max_iters = max_iters;
   a.ctl = p->ctl;
-  const bool split = p->sched.stable_row_split == 1;
-  const bool frontier = p->sched.stable_frontier == 1 && !split;
+  int grid = 0;
   if (frontier) {
-    if ((st = ensure_frontier(p, s)) != LP_OK) return st;
+    const int64_t items = (int64_t)wave_tiles * hm.n_pad;
+    char* b = (char*)p->fr_buf.p;
+    a.X0 = (uint64_t*)b;
+    a.X1 = a.X0 + items * W;
+    a.mark = (unsigned*)(a.X1 + items * W);
+    a.fr_list = (int32_t*)(a.mark + items);
+    a.fr_dirty = (unsigned*)(a.fr_list + 2 * items);
+    a.fr_last = (int32_t*)(a.fr_dirty + (items + 31) / 32);
     a.t_ptr = p->fr_tptr;
     a.t_idx = p->fr_tidx;
-    a.mark = p->fr_mark;
-    a.fr_list = p->fr_list;
-    a.fr_eval = p->fr_eval;
     a.fr_cnt = p->fr_cnt;
+    a.fr_tiles = wave_tiles;
+    a.fr_key = 1u | ((unsigned)W << 1) | ((unsigned)wave_tiles << 7);
+    static int occ_frontier = -1;
+    if (occ_frontier < 0) occ_frontier = stable_frontier_blocks_per_sm();
+    if (occ_frontier <= 0) return fail(LP_ERR_CUDA, "stable frontier kernel cannot be resident");
+    const int per_sm =
+        p->sched.stable_blocks_per_sm > 0 ? std::min(occ_frontier, p->sched.stable_blocks_per_sm) : occ_frontier;
+    grid = (int)max_coresident(p, per_sm);
+    if ((st = launch_count_and_check(launch_stable_frontier(a, grid, s), "launch stable frontier kernel", p)) != LP_OK)
+      return st;
+  } else {
+    a.X0 = (uint64_t*)p->tiles.p;
+    a.X1 = (uint64_t*)p->tiles.p + (size_t)hm.n_pad * W;
+    static int occ_by_split[2] = {-1, -1};
+    int& occ = occ_by_split[(int)split];
+    if (occ < 0) occ = stable_blocks_per_sm(split);
+    if (occ <= 0) return fail(LP_ERR_CUDA, "stable kernel cannot be resident");
+    const int per_sm = p->sched.stable_blocks_per_sm > 0 ? std::min(occ, p->sched.stable_blocks_per_sm) : occ;
+    const int64_t rows_per_block = (int64_t)(kStableBlock / 32) * (32 / W);
+    grid = (int)std::min<int64_t>(max_coresident(p, per_sm), std::max<int64_t>(1, hm.n_pad / rows_per_block));
+    if ((st = launch_count_and_check(launch_stable(a, grid, split, s), "launch stable kernel", p)) != LP_OK) return st;
   }
-  static int occ_by_split[3] = {-1, -1, -1};
-  int& occ = occ_by_split[frontier ? 2 : (int)split];
-  if (occ < 0) occ = stable_blocks_per_sm(split, frontier);
-  if (occ <= 0) return fail(LP_ERR_CUDA, "stable kernel cannot be resident");
-  const int per_sm = p->sched.stable_blocks_per_sm > 0 ? std::min(occ, p->sched.stable_blocks_per_sm) : occ;
-  const int64_t rows_per_block = (int64_t)(kStableBlock / 32) * (32 / W);
-  int grid = (int)std::min<int64_t>(max_coresident(p, per_sm), std::max<int64_t>(1, hm.n_pad / rows_per_block));
-  if ((st = launch_count_and_check(launch_stable(a, grid, split, frontier, s), "launch stable kernel", p)) != LP_OK) return st;
   LP_CUDA(cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s));
   if (host_mask) LP_CUDA(cudaMemcpyAsync(stable_mask, d_mask, (size_t)n_gwords * 8, cudaMemcpyDeviceToHost, s));
   if (host_models) LP_CUDA(cudaMemcpyAsync(models, d_models, (size_t)max_models * atom_words * 8, cudaMemcpyDeviceToHost, s));
@@ -747,6 +893,8 @@ lp_status lp_export_matrix(const lp_program* p, int64_t* row_ptr, int64_t* col, 
   if (!p || !row_ptr || !col || !threshold) return fail(LP_ERR_INVALID, "NULL argument");
   const HostMatrix& hm = p->hm;
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  lp_status st = ensure_host_tables(const_cast<lp_program*>(p), s);
+  if (st != LP_OK) return st;
   std::vector<int32_t> rp, cl;
   if (p->host_only) {
     rp.assign(hm.row_ptr.begin(), hm.row_ptr.end());

@@ -13,8 +13,12 @@
 //              of that row, then rule order), so that an OR row gathers one contiguous range;
 //   padding:   empty rows up to a multiple of 64.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
+#include <string>
 
 #include "internal.h"
 
@@ -28,6 +32,24 @@
 namespace lp {
 
 namespace {
+
+// Wall time of each compile phase, printed to stderr at the end when LP_COMPILE_TRACE is set.
+struct PhaseTrace {
+  bool on = std::getenv("LP_COMPILE_TRACE") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  std::string line;
+  void mark(const char* name) {
+    if (!on) return;
+    const auto now = std::chrono::steady_clock::now();
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "%s=%.2f ", name, std::chrono::duration<double, std::milli>(now - t).count());
+    line += buf;
+    t = now;
+  }
+  ~PhaseTrace() {
+    if (on && !line.empty()) std::fprintf(stderr, "lp_compile phases (ms): %s\n", line.c_str());
+  }
+};
 
 inline void sort_small(int32_t* a, int64_t m) {
   if (m > 24) {
@@ -107,6 +129,7 @@ int64_t blocked_scan(int64_t m, Count count, Prepare prepare, Emit emit) {
 
 lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const int64_t* body_off,
                        const int32_t* body_atom, const uint8_t* body_neg, HostMatrix& hm, std::string& err) {
+  PhaseTrace trace;
   // ---- validation
   if (n < 0 || n_rules < 0) {
     err = "negative atom or rule count";
@@ -153,6 +176,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
   }
 
   try {
+    trace.mark("validate");
     // ---- rules per head, negated atoms, barred ids (canonical: n + rank of q)
     hvec<int32_t> cnt, bar_id;
     par_fill(cnt, (size_t)n, 0);
@@ -218,6 +242,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       return LP_ERR_INVALID;
     }
     const int32_t np = (int32_t)n_prime64;
+    trace.mark("heads");
 
     // ---- body sets in canonical columns (sorted, duplicates removed), in place per rule
     hvec<int32_t> rb(total);  // every rule writes its whole range
@@ -237,6 +262,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       setlen[r] = (int32_t)u;
     }
 
+    trace.mark("bodies");
     // ---- canonical rows: kind, defining rule, rules of each head (in rule order)
     // hr_off: first position of each head's rules in the grouped order (a scan of the counts).
     hvec<int64_t> hr_off((size_t)n + 1);
@@ -296,6 +322,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
         }
       }
     }
+    trace.mark("group");
     auto rule_at = [&](int64_t t) -> int32_t { return by_head[t]; };
     hvec<int8_t> kind;
     hvec<int32_t> row_rule;  // rule defining a RULE/FACT row
@@ -331,6 +358,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       }
     };
 
+    trace.mark("kinds");
     // ---- references per canonical column (for the internal order)
     int64_t nnz = 0;
 #pragma omp parallel for reduction(+ : nnz) schedule(static)
@@ -374,6 +402,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       }
     }
 
+    trace.mark("refs");
     // ---- internal order
     hvec<int32_t> inv(np);  // internal -> canonical (a permutation: every entry is written)
     // bpos[i]: first section-B position (relative to nA) of the new atoms of the OR row at
@@ -426,6 +455,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       hm.perm[inv[i]] = i;
     }
     const int32_t npad = (int32_t)(((int64_t)np + 63) / 64 * 64);
+    trace.mark("order");
 
     // ---- internal CSR
     // Row lengths and kinds moved to internal order (sequential reads, one scattered write per
@@ -458,6 +488,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
           }
         });
     for (int32_t i = np; i < npad; i++) hm.row_ptr[i + 1] = hm.row_ptr[i];  // empty padding rows
+    trace.mark("row_ptr");
     hm.col.resize((size_t)nnz);  // the passes below write every entry of every row
     // rule rows: walk the rules in order (sequential reads of the body sets) and scatter each
     // body, mapped to internal ids and sorted, into its row
@@ -476,6 +507,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       for (int32_t t = 0; t < setlen[r]; t++) d[t] = hm.perm[sb[t]];
       sort_small(d, setlen[r]);
     }
+    trace.mark("scatter");
     // self-loop rows (facts, barred atoms) hold their own column; OR rows list their new
     // atoms, which sit consecutively in section B in rule order
 #pragma omp parallel for schedule(dynamic, 4096)
@@ -498,6 +530,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
       hm.any_mask[w] = bits;
     }
 
+    trace.mark("or_rows");
     // ---- facts, negated atoms, guesses (Def. 4 and Def. 8)
     hvec<int32_t> owner_of_row(np);
 #pragma omp parallel for schedule(static)
@@ -578,6 +611,7 @@ lp_status compile_host(int32_t n, int64_t n_rules, const int32_t* head, const in
     for (int32_t c = 0; c < np; c++)
       if (kind[c] == K_RULE) hm.canon_rule[c] = row_rule[c];
     hm.canon_kind.swap(kind);
+    trace.mark("facts");
   } catch (const std::bad_alloc&) {
     err = "host allocation failed in lp_compile";
     return LP_ERR_OOM;

@@ -127,3 +127,32 @@ extern "C" lp_status lp_check_matrix(const lp_program* p, int64_t* n_bad, void* 
   *n_bad = (int64_t)h_bad;
   return LP_OK;
 }
+
+extern "C" lp_status lp_debug_internal(const lp_program* p, int32_t which, void* out, int64_t* bytes,
+                                       void* cuda_stream) {
+  if (!p || !bytes) return fail(LP_ERR_INVALID, "NULL argument");
+  if (p->host_only) return fail(LP_ERR_INVALID, "program was compiled with LP_COMPILE_HOST_ONLY");
+  const HostMatrix& hm = p->hm;
+  const void* src = nullptr;
+  int64_t size = 0;
+  switch (which) {
+    case 0: src = p->row_ptr; size = 4 * ((int64_t)hm.n_pad + 1); break;
+    case 1: src = p->col; size = 4 * hm.nnz; break;
+    case 2: src = p->perm; size = 4 * (int64_t)hm.n_prime; break;
+    case 3: src = p->any_mask; size = 4 * ((int64_t)hm.n_pad / 32); break;
+    case 4: src = p->row_tag; size = 4 * (int64_t)hm.n_pad; break;
+    case 5: src = p->fact_row; size = 4 * (int64_t)hm.n_fact_rows; break;
+    case 6: src = p->fact_owner; size = 4 * (int64_t)hm.n_fact_rows; break;
+    case 7: src = p->fact_mask; size = 8 * (((int64_t)hm.n + 63) / 64); break;
+    case 8: src = p->neg_row; size = 4 * (int64_t)hm.n_barred; break;
+    case 9: src = p->bar_row; size = 4 * (int64_t)hm.n_barred; break;
+    default: return fail(LP_ERR_INVALID, "unknown internal array");
+  }
+  *bytes = size;
+  if (!out || size == 0) return LP_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMemcpyAsync(out, src, (size_t)size, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(LP_ERR_CUDA, cudaGetErrorString(e));
+  return LP_OK;
+}

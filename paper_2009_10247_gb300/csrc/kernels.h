@@ -129,23 +129,27 @@ struct StableArgs {
   int32_t n_atom_words;
   int32_t max_iters;
   DeviceCtl* ctl;
-  // frontier schedule (after a tile's first iteration only the rows with a changed input are
-  // evaluated): the transposed matrix, a per-row stamp, two changed-row lists, the list of rows
-  // to evaluate, and six counters (changed-list sizes, rotating; to-evaluate sizes, rotating)
+  // frontier schedule (stable_frontier.cu): the transposed matrix, and per wave of fr_tiles
+  // tiles (item = tile * n_pad + row; X0 / X1 above then hold fr_tiles tiles each) a stamp per
+  // item, two work lists, a changed-item bitmap and each tile's last changing iteration
   const int32_t* t_ptr;     // n_pad + 1: rows referring to column j are t_idx[t_ptr[j] .. t_ptr[j + 1])
   const int32_t* t_idx;     // nnz
-  int32_t* mark;            // n_pad
-  int32_t* fr_list;         // 2 x n_pad
-  int32_t* fr_eval;         // n_pad
-  unsigned* fr_cnt;         // 6
+  unsigned* mark;           // fr_tiles * n_pad
+  int32_t* fr_list;         // 2 x fr_tiles * n_pad
+  unsigned* fr_dirty;       // ceil(fr_tiles * n_pad / 32)
+  int32_t* fr_last;         // fr_tiles
+  unsigned* fr_cnt;         // 8: list sizes (3, rotating), rest-state record (slots 3 to 7)
+  int32_t fr_tiles;         // tiles per wave (the buffers' capacity)
+  unsigned fr_key;          // nonzero tag of the buffers' layout
 };
 
 constexpr int kStableBlock = 256;
-// row_split: one row per warp, its entries split over the warp's 32 / W lane groups; frontier:
-// after each tile's first iteration, only rows with an input that changed are evaluated (needs
-// the t_ptr / t_idx / mark / fr_* fields; not with row_split)
-cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, bool frontier, cudaStream_t s);
-int stable_blocks_per_sm(bool row_split, bool frontier);
+// row_split: one row per warp, its entries split over the warp's 32 / W lane groups
+cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, cudaStream_t s);
+int stable_blocks_per_sm(bool row_split);
+// Frontier schedule (needs the t_ptr ... fr_key fields)
+cudaError_t launch_stable_frontier(const StableArgs& a, int grid, cudaStream_t s);
+int stable_frontier_blocks_per_sm();
 // Transposed matrix for the frontier schedule, built on the device: cnt (n_pad + 1 ints of
 // scratch, zeroed by the caller) becomes the cursor of the fill.
 cudaError_t build_transpose(const int32_t* row_ptr, const int32_t* col, int32_t n_pad, int32_t* t_ptr, int32_t* t_idx,

@@ -32,6 +32,11 @@ struct lp_program {
   int32_t* neg_row = nullptr;
   int32_t* bar_row = nullptr;
   int32_t* row_tag = nullptr;
+  // a device compile keeps the canonical kinds and rules here until a host-side user downloads
+  // them with perm (ensure_host_tables); a host compile has them in hm from the start
+  int8_t* dc_kind = nullptr;
+  int32_t* dc_rule = nullptr;
+  bool host_tables = true;
   // streamed layout of the least-model kernel
   uint32_t* desc = nullptr;
   int32_t* word_hdr = nullptr;
@@ -45,13 +50,13 @@ struct lp_program {
   int32_t* sl_fact_row = nullptr;
   int32_t* sl_perm = nullptr;
   int64_t sl_entries = -1;        // stored entries; -1 = not built
-  // frontier schedule of the stable models: transposed matrix and work lists (built on first use)
+  // frontier schedule of the stable models: transposed matrix and counters (built on first use),
+  // and the buffers of one wave of fr_tiles tiles of fr_W words (iterates, stamps, lists, bitmap)
   int32_t* fr_tptr = nullptr;
   int32_t* fr_tidx = nullptr;
-  int32_t* fr_mark = nullptr;
-  int32_t* fr_list = nullptr;
-  int32_t* fr_eval = nullptr;
   unsigned* fr_cnt = nullptr;
+  DevBuf fr_buf;
+  int32_t fr_W = 0, fr_tiles = 0;
   // scratch
   uint32_t* x[2] = {nullptr, nullptr};
   lp::DeviceCtl* ctl = nullptr;
@@ -99,6 +104,15 @@ void count_launches(int64_t n);  // add to lp_launch_count()
 // cudaMalloc behind the allocation-failure hook (lp_debug_fail_alloc): every device allocation
 // of liblp's handles goes through here.
 cudaError_t device_malloc(void** ptr, size_t bytes);
+// The standardization of lp_compile on the device (compile_device.cu): fills the device arrays
+// of the handle and hm's sizes and small tables; perm, canon_kind and canon_rule reach hm on
+// demand through ensure_host_tables.
+lp_status compile_on_device(lp_program* p, int32_t n, int64_t n_rules, const int32_t* head, const int64_t* body_off,
+                            const int32_t* body_atom, const uint8_t* body_neg, cudaStream_t s);
+lp_status ensure_host_tables(lp_program* p, cudaStream_t s);
+// Stream-ordered allocation (freed with cudaFreeAsync on the same stream), with the same
+// injected failures as device_malloc.
+cudaError_t device_malloc_async(void** ptr, size_t bytes, cudaStream_t s);
 
 // Least-model kernel 2 (sliced layout): whether the program fits its index widths, and the
 // message of LP_ERR_INVALID when it does not.

@@ -281,6 +281,8 @@ int rx_grid(lp_program* p, int64_t warps_needed) {
 // Builds the per-row kinds, rule ids and the transposed copy on first use.
 lp_status ensure_relaxed(lp_program* p, cudaStream_t s) {
   if (p->rx_ready) return LP_OK;
+  const lp_status ht = ensure_host_tables(p, s);
+  if (ht != LP_OK) return ht;
   const HostMatrix& hm = p->hm;
   std::vector<int32_t> rp((size_t)hm.n_pad + 1), cl(std::max<int64_t>(hm.nnz, 1));
   LP_CUDA(cudaMemcpyAsync(rp.data(), p->row_ptr, rp.size() * 4, cudaMemcpyDeviceToHost, s));

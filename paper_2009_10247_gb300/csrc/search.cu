@@ -124,6 +124,7 @@ extern "C" lp_status lp_stable_search(lp_program* p, int32_t population, int32_t
 
   const lp_schedule saved = p->sched;
   p->sched.stable_tile_words = W;
+  p->sched.stable_frontier = 0;  // the update reads the fixpoint from the full sweep's one tile
   for (int r = 0; r < rounds; r++) {
     st = lp_stable_models(p, d_guess, P, d_mask, nullptr, 0, nullptr, 1 << 30, cuda_stream);
     if (st != LP_OK) break;

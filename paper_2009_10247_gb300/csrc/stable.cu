@@ -23,167 +23,14 @@
 
 #include "device.cuh"
 #include "kernels.h"
+#include "stable_common.cuh"
 
 namespace lp {
-
-__device__ __forceinline__ uint64_t m0_word(int tag, long long gw, const StableArgs& a) {
-  if (tag == -2) return ~0ull;  // fact row (Def. 8 item 2)
-  if (tag < 0) return 0ull;     // other original rows, barred atoms of facts (item 3)
-  if (a.guesses == nullptr) {
-    // guess g = 64*gw + b, bit tag of g
-    switch (tag) {  // bit b of the word is bit tag of b
-      case 0: return 0xAAAAAAAAAAAAAAAAull;
-      case 1: return 0xCCCCCCCCCCCCCCCCull;
-      case 2: return 0xF0F0F0F0F0F0F0F0ull;
-      case 3: return 0xFF00FF00FF00FF00ull;
-      case 4: return 0xFFFF0000FFFF0000ull;
-      case 5: return 0xFFFFFFFF00000000ull;
-      default: break;
-    }
-    return ((gw >> (tag - 6)) & 1ll) ? ~0ull : 0ull;
-  }
-  uint64_t w = 0;
-  const long long g0 = gw * 64;
-  for (int b = 0; b < 64; b++) {
-    const long long g = g0 + b;
-    if (g < a.n_guesses) w |= ((a.guesses[g] >> tag) & 1ull) << b;
-  }
-  return w;
-}
-
-// The words of `row` in a tile of W words (lane word wl): AND of its entries' words for a rule
-// row, OR for an OR row or a self-loop, 0 for an empty row. Four entries per step: their column
-// loads, then their gathers. *n_entries grows by the row's length.
-__device__ __forceinline__ uint64_t eval_row(const StableArgs& a, const uint64_t* src, int row, int wl,
-                                             unsigned* n_entries) {
-  const int beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
-  const bool any = (__ldg(a.any_mask + (row >> 5)) >> (row & 31)) & 1u;
-  const uint64_t ident = any ? 0ull : ~0ull;
-  uint64_t acc = (end > beg) ? ident : 0ull;
-  for (int e = beg; e < end; e += 4) {
-    int cc[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) cc[j] = e + j < end ? __ldg(a.col + e + j) : -1;
-    uint64_t vv[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) vv[j] = cc[j] >= 0 ? src[((long long)cc[j] << a.log2W) + wl] : ident;
-    const uint64_t orv = vv[0] | vv[1] | vv[2] | vv[3], andv = vv[0] & vv[1] & vv[2] & vv[3];
-    acc = any ? (acc | orv) : (acc & andv);
-  }
-  *n_entries += (unsigned)(end - beg);
-  return acc;
-}
-
-// Appends `value` of every lane whose flag is set to list[*cnt ...] (one atomic per warp; all
-// lanes of the warp call it).
-__device__ __forceinline__ void warp_append(int32_t* list, unsigned* cnt, bool flag, int value, int lane) {
-  const unsigned m = __ballot_sync(FULL, flag);
-  if (m == 0u) return;
-  const int leader = __ffs(m) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
-  base = __shfl_sync(FULL, base, leader);
-  if (flag) list[base + __popc(m & ((1u << lane) - 1u))] = value;
-}
-
-// Algorithm 2 on one tile, frontier schedule. The iteration and its result are those of the full
-// sweep: M_{t+1}[i] = theta(M_P M_t)[i] depends only on the rows i refers to, so a row none of
-// whose inputs changed in iteration t - 1 keeps its value, and the buffer being written already
-// holds it (it held M_{t-1}[i] = M_t[i]). Iteration 0 evaluates every row and lists the rows that
-// changed; iteration t >= 1 evaluates the rows of that list and the rows that refer to them (the
-// transposed matrix; each row once, by a per-row stamp), writes them, and lists those that
-// changed. The tile has converged when the list is empty. Returns false if the grid is aborting.
-__device__ __noinline__ bool frontier_iterate(const StableArgs& a, const uint64_t*& fin, int& it, bool& converged,
-                                              unsigned long long& round, int lane, int gwarp, int nwarps,
-                                              long long gtid, long long nthreads) {
-  DeviceCtl* ctl = a.ctl;
-  const int W = a.W, rpw = 32 >> a.log2W, sub = lane >> a.log2W, wl = lane & (W - 1);
-  const unsigned subm = W == 32 ? FULL : (((1u << W) - 1u) << (sub * W));
-  unsigned n_rows = 0, n_ent = 0, n_list = 0, n_deps = 0;
-  for (; it < a.max_iters; ++it) {
-    const uint64_t* src = (it & 1) ? a.X1 : a.X0;
-    uint64_t* dst = (it & 1) ? a.X0 : a.X1;
-    // counters of iteration it + 1 were last read in iteration it - 1, before the last barrier
-    if (gtid == 0) {
-      a.fr_cnt[(it + 1) % 3] = 0u;
-      a.fr_cnt[3 + (it + 1) % 3] = 0u;
-    }
-    int32_t* changed = a.fr_list + (size_t)(it & 1) * a.n_pad;
-    unsigned* changed_cnt = a.fr_cnt + it % 3;
-    if (it == 0) {
-      const int n_groups = a.n_pad / rpw;
-      for (int g = gwarp; g < n_groups; g += nwarps) {
-        const int row = g * rpw + sub;
-        unsigned ne = 0;
-        const uint64_t acc = eval_row(a, src, row, wl, &ne);
-        const long long o = ((long long)row << a.log2W) + wl;
-        const uint64_t old = src[o];
-        dst[o] = acc;
-        const bool ch = (__ballot_sync(FULL, acc != old) & subm) != 0u;
-        warp_append(changed, changed_cnt, ch && wl == 0, row, lane);
-      }
-    } else {
-      const unsigned n_prev = ld_volatile(a.fr_cnt + (it - 1) % 3);
-      const int32_t* prev = a.fr_list + (size_t)((it - 1) & 1) * a.n_pad;
-      unsigned* eval_cnt = a.fr_cnt + 3 + it % 3;
-      for (long long i = gtid; i < (long long)n_prev; i += nthreads) {
-        const int j = prev[i];
-        if (atomicExch(a.mark + j, it) != it) a.fr_eval[atomicAdd(eval_cnt, 1u)] = j;
-        const int tb = __ldg(a.t_ptr + j), te = __ldg(a.t_ptr + j + 1);
-        for (int e = tb; e < te; e++) {
-          const int r = __ldg(a.t_idx + e);
-          if (atomicExch(a.mark + r, it) != it) a.fr_eval[atomicAdd(eval_cnt, 1u)] = r;
-        }
-        n_list++;
-        n_deps += (unsigned)(te - tb);
-      }
-      if (!grid_barrier(ctl, ++round, 6)) return false;
-      const long long n_eval = ld_volatile(eval_cnt);
-      for (long long g = gwarp; g * rpw < n_eval; g += nwarps) {
-        const long long item = g * rpw + sub;
-        const int row = item < n_eval ? a.fr_eval[item] : -1;
-        uint64_t acc = 0ull, old = 0ull;
-        if (row >= 0) {
-          unsigned ne = 0;
-          acc = eval_row(a, src, row, wl, &ne);
-          const long long o = ((long long)row << a.log2W) + wl;
-          old = src[o];
-          dst[o] = acc;
-          if (wl == 0) {
-            n_rows++;
-            n_ent += ne;
-          }
-        }
-        const bool ch = (__ballot_sync(FULL, acc != old) & subm) != 0u;
-        warp_append(changed, changed_cnt, ch && wl == 0 && row >= 0, row, lane);
-      }
-    }
-    if (!grid_barrier(ctl, ++round, 6)) return false;
-    const unsigned n_changed = ld_volatile(changed_cnt);
-    fin = dst;
-    if (n_changed == 0u) {
-      converged = true;
-      ++it;
-      break;
-    }
-  }
-  n_rows = __reduce_add_sync(FULL, n_rows);
-  n_ent = __reduce_add_sync(FULL, n_ent);
-  n_list = __reduce_add_sync(FULL, n_list);
-  n_deps = __reduce_add_sync(FULL, n_deps);
-  if (lane == 0) {
-    if (n_rows) atomicAdd(&ctl->fr_rows, (unsigned long long)n_rows);
-    if (n_ent) atomicAdd(&ctl->fr_entries, (unsigned long long)n_ent);
-    if (n_list) atomicAdd(&ctl->fr_list, (unsigned long long)n_list);
-    if (n_deps) atomicAdd(&ctl->fr_deps, (unsigned long long)n_deps);
-  }
-  return true;
-}
 
 // SPLIT: a warp takes one row at a time and its 32 / W lane groups split the row's entries
 // (each group one word per lane), combining their partial AND / OR with shuffles; for long rows
 // (dense programs) this replaces one lane walking a whole row. With W = 32 both are the same.
-template <bool SPLIT, bool FRONTIER>
+template <bool SPLIT>
 __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
   __shared__ unsigned long long s_cnt;
   __shared__ long long s_base;
@@ -205,10 +52,6 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
     const long long gw0 = t * W;  // first guess word of the tile
     // The previous tile's readers of the change flags are all past its last barrier.
     if (threadIdx.x == 0) s_cnt = 0ull;
-    if (FRONTIER) {  // stamps and list counters start over with every tile
-      for (long long r = gtid; r < a.n_pad; r += nthreads) a.mark[r] = 0;
-      if (gtid < 6) a.fr_cnt[gtid] = 0u;
-    }
     __syncthreads();
     // ---- 1. M_0
     unsigned cnt0 = 0;
@@ -233,9 +76,6 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
     const uint64_t* fin = a.X0;
     int it = 0;
     bool converged = false;
-    if (FRONTIER) {
-      if (!frontier_iterate(a, fin, it, converged, round, lane, gwarp, nwarps, gtid, nthreads)) return;
-    } else
     for (; it < a.max_iters; ++it) {
       const uint64_t* src = (it & 1) ? a.X1 : a.X0;
       uint64_t* dst = (it & 1) ? a.X0 : a.X1;
@@ -383,9 +223,8 @@ __global__ void __launch_bounds__(kStableBlock) stable_kernel(StableArgs a) {
 }
 
 namespace {
-const void* stable_entry(bool row_split, bool frontier) {
-  if (frontier) return (const void*)stable_kernel<false, true>;
-  return row_split ? (const void*)stable_kernel<true, false> : (const void*)stable_kernel<false, false>;
+const void* stable_entry(bool row_split) {
+  return row_split ? (const void*)stable_kernel<true> : (const void*)stable_kernel<false>;
 }
 
 // Transposed matrix: per column the rows that refer to it (order within a column is arbitrary).
@@ -442,15 +281,15 @@ cudaError_t build_transpose(const int32_t* row_ptr, const int32_t* col, int32_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, bool frontier, cudaStream_t s) {
+cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, cudaStream_t s) {
   StableArgs copy = a;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(stable_entry(row_split, frontier), dim3(grid), dim3(kStableBlock), params, 0, s);
+  return cudaLaunchCooperativeKernel(stable_entry(row_split), dim3(grid), dim3(kStableBlock), params, 0, s);
 }
 
-int stable_blocks_per_sm(bool row_split, bool frontier) {
+int stable_blocks_per_sm(bool row_split) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stable_entry(row_split, frontier), kStableBlock, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stable_entry(row_split), kStableBlock, 0) !=
       cudaSuccess)
     return 0;
   return nb;

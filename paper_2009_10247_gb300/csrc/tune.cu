@@ -151,20 +151,22 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     }
     if ((st = ensure(p, p->tune_out, (size_t)n_gwords * 8)) != LP_OK) return st;
     uint64_t* mask = (uint64_t*)p->tune_out.p;
-    const int occ = stable_blocks_per_sm(false, base.stable_frontier == 1);
-    auto stable = [&](int W, int blocks, int split) {
+    const int occ = stable_blocks_per_sm(false);
+    auto stable = [&](int W, int blocks, int split, int frontier) {
       lp_schedule c = best_least;  // least-model fields as chosen above
       c.stable_tile_words = W;
       c.stable_blocks_per_sm = blocks;
       c.stable_row_split = split;
+      c.stable_frontier = frontier;
       return c;
     };
     std::vector<lp_schedule> cands;
     for (int W = 1; W <= 32; W *= 2) {
       if (W > 1 && W / 2 >= n_gwords) break;  // wider tiles than the guesses only repeat
       for (int b : {0, occ / 2})
-        if (b == 0 || (b > 0 && b < occ)) cands.push_back(stable(W, b, 0));
-      if (W < 32) cands.push_back(stable(W, 0, 1));  // with 32-word tiles the row split is the same mapping
+        if (b == 0 || (b > 0 && b < occ)) cands.push_back(stable(W, b, 0, 0));
+      if (W < 32) cands.push_back(stable(W, 0, 1, 0));  // with 32-word tiles the row split is the same mapping
+      if (W >= 8 || W >= n_gwords) cands.push_back(stable(W, 0, 0, 1));
     }
     std::vector<uint8_t> ref, bits;
     float best = -1.f;
@@ -208,6 +210,7 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
     chosen.stable_tile_words = best_stable.stable_tile_words;
     chosen.stable_blocks_per_sm = best_stable.stable_blocks_per_sm;
     chosen.stable_row_split = best_stable.stable_row_split;
+    chosen.stable_frontier = best_stable.stable_frontier;
   }
   p->sched = chosen;
   for (int32_t i = 0; i < max_records && i < (int32_t)recs.size(); i++) records[i] = recs[i];

@@ -16,6 +16,7 @@ STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_OOM", "LP_ERR_CUDA", "LP_ERR_
                 "LP_ERR_TOO_MANY_GUESSES", "LP_ERR_TIMEOUT"]
 LP_ROWS, LP_TIMING = 1, 2
 LP_COMPILE_HOST_ONLY = 1
+LP_COMPILE_ON_HOST = 2
 
 
 class LPError(RuntimeError):
@@ -42,7 +43,8 @@ EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models"
            "lp_export_matrix", "lp_free", "lp_last_error", "lp_launch_count", "lp_least_model_static",
            "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward", "lp_compile_batch", "lp_batch_info",
            "lp_batch_program_info", "lp_batch_stable_models", "lp_batch_free", "lp_get_schedule", "lp_set_schedule",
-           "lp_autotune", "lp_stable_search", "lp_check_grid_barrier", "lp_check_matrix", "lp_debug_fail_alloc"]
+           "lp_autotune", "lp_stable_search", "lp_check_grid_barrier", "lp_check_matrix", "lp_debug_fail_alloc",
+           "lp_debug_internal"]
 
 LP_TUNE_LEAST = 1
 LP_TUNE_STABLE = 2
@@ -120,8 +122,9 @@ def load(build_if_missing: bool = False):
     L.lp_check_matrix.argtypes = [P, ctypes.POINTER(i64), P]
     L.lp_debug_fail_alloc.argtypes = [i64]
     L.lp_debug_fail_alloc.restype = None
+    L.lp_debug_internal.argtypes = [P, i32, P, ctypes.POINTER(i64), P]
     for name in ("lp_get_schedule", "lp_set_schedule", "lp_autotune", "lp_stable_search", "lp_check_grid_barrier",
-                 "lp_check_matrix"):
+                 "lp_check_matrix", "lp_debug_internal"):
         getattr(L, name).restype = ctypes.c_int
     L.lp_least_model_static.argtypes = [i32, P, P, P, P, P, i32, ctypes.POINTER(i32), P]
     L.lp_least_model_static.restype = ctypes.c_int
@@ -204,23 +207,43 @@ def words(n_bits: int) -> int:
 class Program:
     """A compiled program (owns the liblp handle)."""
 
-    def __init__(self, n_atoms, head, body_off, body_atom, body_neg=None, stream=None, host_only=False):
+    def __init__(self, n_atoms, head, body_off, body_atom, body_neg=None, stream=None, host_only=False,
+                 on_host=False):
+        """host_only: the host compiler alone, no device memory; on_host: the host compiler, then
+        the matrix uploaded (default: the rules uploaded and standardized on the device)."""
         L = load()
         self._keep = [np.ascontiguousarray(head, dtype=np.int32), np.ascontiguousarray(body_off, dtype=np.int64),
                       np.ascontiguousarray(body_atom, dtype=np.int32),
                       None if body_neg is None else np.ascontiguousarray(body_neg, dtype=np.uint8)]
         h, off, atom, neg = self._keep
         self._h = ctypes.c_void_p()
-        _check(L.lp_compile(int(n_atoms), len(h), _ptr(h), _ptr(off), _ptr(atom), _ptr(neg), LP_COMPILE_HOST_ONLY if host_only else 0,
+        flags = LP_COMPILE_HOST_ONLY if host_only else (LP_COMPILE_ON_HOST if on_host else 0)
+        _check(L.lp_compile(int(n_atoms), len(h), _ptr(h), _ptr(off), _ptr(atom), _ptr(neg), flags,
                             None if host_only else _stream(stream),
                             ctypes.byref(self._h)))
         self._keep = None
         self.info = self._info()
 
     @classmethod
-    def from_program(cls, prog, stream=None, host_only=False):
+    def from_program(cls, prog, stream=None, host_only=False, on_host=False):
         return cls(prog.n_atoms, prog.head, prog.body_off, prog.body_atom, getattr(prog, "body_neg", None), stream,
-                   host_only)
+                   host_only, on_host)
+
+    INTERNAL = {"row_ptr": (0, np.int32), "col": (1, np.int32), "perm": (2, np.int32), "any_mask": (3, np.uint32),
+                "row_tag": (4, np.int32), "fact_row": (5, np.int32), "fact_owner": (6, np.int32),
+                "fact_mask": (7, np.uint64), "neg_row": (8, np.int32), "bar_row": (9, np.int32)}
+
+    def debug_internal(self, name, stream=None):
+        """An internal device array of the handle (lp_debug_internal) as a numpy array."""
+        which, dt = self.INTERNAL[name]
+        L = load()
+        nbytes = ctypes.c_int64()
+        _check(L.lp_debug_internal(self._h, which, None, ctypes.byref(nbytes), _stream(stream)))
+        out = np.zeros(nbytes.value // np.dtype(dt).itemsize, dtype=dt)
+        if nbytes.value:
+            _check(L.lp_debug_internal(self._h, which, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nbytes),
+                                       _stream(stream)))
+        return out
 
     def _info(self):
         i = _Info()

@@ -19,17 +19,20 @@ from workloads import normal_program, parse, small_definite, tiny_random
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from tests.gpu_util import gpu_stable  # noqa: E402
+from tests.gpu_util import dev_words, gpu_stable  # noqa: E402
 
 
 def _parity(prog, guesses=None, max_models=64):
+    # both schedules: the full sweep per tile and the frontier over all tiles (the default)
     st4, m4, _ = oracle.stable_models_alg23(prog, guesses=guesses)
-    with lp.Program.from_program(prog) as P:
-        st, models, ns = gpu_stable(P, guesses=guesses, max_models=max_models)
-    assert np.array_equal(st, st4)
-    assert ns == int(st4.sum())
     want_models = m4[st4]
-    assert np.array_equal(models, want_models[:max_models])
+    with lp.Program.from_program(prog) as P:
+        for frontier in (0, 1):
+            P.set_schedule(stable_frontier=frontier)
+            st, models, ns = gpu_stable(P, guesses=guesses, max_models=max_models)
+            assert np.array_equal(st, st4), f"frontier={frontier}"
+            assert ns == int(st4.sum()), f"frontier={frontier}"
+            assert np.array_equal(models, want_models[:max_models]), f"frontier={frontier}"
     return st, models
 
 
@@ -136,13 +139,16 @@ def _full_size_expected(prog):
 
 
 def test_full_size_2_16_guesses_every_bit():
-    # all 65,536 guesses in one call, default, tuned and frontier schedules: every stable bit
-    # equals the oracle's, and every tile's iteration count is the largest of its columns' counts
+    # all 65,536 guesses in one call, default (frontier), full-sweep, tuned and frontier-on-the-
+    # tuned-width schedules: every stable bit equals the oracle's, and every tile's iteration
+    # count is the largest of its columns' counts
     p = normal_program(seed=1)
     want, word_iters = _full_size_expected(p)
     assert len(want) == 1 << 16
     with lp.Program.from_program(p) as P:
-        for variant in ("default", "tuned", "frontier"):
+        for variant in ("default", "full", "tuned", "frontier"):
+            if variant == "full":
+                P.set_schedule(stable_frontier=0)
             if variant == "tuned":
                 P.autotune(lp.LP_TUNE_STABLE, reps=1)  # the schedule the benchmark times
             if variant == "frontier":
@@ -156,7 +162,7 @@ def test_full_size_2_16_guesses_every_bit():
             assert stats["tiles"] == len(per_tile)
             assert stats["max_tile_iters"] == per_tile.max()
             assert stats["sum_tile_iters"] == per_tile.sum()
-            if variant == "frontier":  # re-evaluated rows: a few per cent of the full sweeps
+            if variant in ("default", "frontier"):  # re-evaluated rows: a few per cent of the full sweeps
                 assert 0 < stats["frontier_rows"] < 0.2 * P.info["n_prime"] * per_tile.sum()
 
 
@@ -172,7 +178,7 @@ def test_frontier_schedule_matches_oracle(W):
     for prog in progs:
         st4, m4, _ = oracle.stable_models_alg23(prog)
         with lp.Program.from_program(prog) as P:
-            P.set_schedule(stable_tile_words=W)
+            P.set_schedule(stable_tile_words=W, stable_frontier=0)
             _, _, _ = gpu_stable(P)
             full = P.last_stats()
             P.set_schedule(stable_frontier=1)
@@ -191,3 +197,48 @@ def test_frontier_schedule_explicit_guesses():
         P.set_schedule(stable_frontier=1)
         st, _, ns = gpu_stable(P, guesses=g)
     assert np.array_equal(st, st4) and ns == int(st4.sum())
+
+
+def _frontier_tile_bytes(P, W):
+    # one tile's share of the frontier buffers: two iterate buffers of W words per row, a stamp
+    # and two list slots per row, the changed-row bitmap, a per-tile counter (and 64 spare bytes)
+    n_pad = (P.info["n_prime"] + 63) // 64 * 64
+    return 2 * n_pad * W * 8 + 12 * n_pad + (n_pad + 31) // 32 * 4 + 4 + 64
+
+
+def test_frontier_waves_and_rest_state(monkeypatch):
+    # One handle, many solves: all tiles in one wave, repeated (the buffers' rest state reused),
+    # explicit guesses, waves of 1 and 3 tiles, a solve stopped by max_iters, another tile width.
+    # Every solve gives the oracle's stable bits and models.
+    prog = normal_program(seed=4, n=3000, n_rules=9000, k=12, per_atom=2)
+    st_all, m_all, _ = oracle.stable_models_alg23(prog)
+    g = np.random.default_rng(5).integers(0, 1 << 12, 700).astype(np.uint64)
+    st_g, _, _ = oracle.stable_models_alg23(prog, guesses=g)
+
+    def check_all(P, label):
+        st, models, ns = gpu_stable(P, max_models=16)
+        assert np.array_equal(st, st_all), label
+        assert ns == int(st_all.sum()) and np.array_equal(models, m_all[st_all][:16]), label
+
+    with lp.Program.from_program(prog) as P:
+        P.set_schedule(stable_tile_words=2, stable_frontier=1)  # 4096 guesses: 32 tiles of 2 words
+        for rep in range(3):
+            check_all(P, f"one wave, solve {rep}")
+            assert P.last_stats()["tiles"] == 32
+        st, _, ns = gpu_stable(P, guesses=g)
+        assert np.array_equal(st, st_g) and ns == int(st_g.sum())
+        check_all(P, "after explicit guesses")
+        for c in (1, 3):
+            monkeypatch.setenv("LP_FRONTIER_BYTES", str(c * _frontier_tile_bytes(P, 2)))
+            check_all(P, f"waves of {c}")
+            check_all(P, f"waves of {c}, again")
+        monkeypatch.delenv("LP_FRONTIER_BYTES")
+        mask = dev_words(1 << 12)
+        with pytest.raises(lp.LPError) as e:
+            P.stable_models(mask, max_iters=2)
+        assert e.value.status == lp.ERR_NO_FIXPOINT
+        check_all(P, "after a solve stopped by max_iters")
+        P.set_schedule(stable_tile_words=8)
+        check_all(P, "8-word tiles")
+        P.set_schedule(stable_tile_words=2)
+        check_all(P, "back to 2-word tiles")

@@ -43,7 +43,8 @@ def test_stable_models_every_tile_width(W, split):
     for prog in progs:
         st4, _, _ = oracle.stable_models_alg23(prog)
         with lp.Program.from_program(prog) as P:
-            P.set_schedule(stable_tile_words=W, stable_blocks_per_sm=0 if W < 8 else 1, stable_row_split=split)
+            P.set_schedule(stable_tile_words=W, stable_blocks_per_sm=0 if W < 8 else 1, stable_row_split=split,
+                           stable_frontier=0)
             st, _, ns = gpu_stable(P)
         assert np.array_equal(st, st4) and ns == int(st4.sum())
 

@@ -791,8 +791,9 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
     a.fr_cnt = p->fr_cnt;
     a.fr_tiles = wave_tiles;
     a.fr_key = 1u | ((unsigned)W << 1) | ((unsigned)wave_tiles << 7);
-    static int occ_frontier = -1;
-    if (occ_frontier < 0) occ_frontier = stable_frontier_blocks_per_sm();
+    static int occ_by_w[6] = {-1, -1, -1, -1, -1, -1};
+    int& occ_frontier = occ_by_w[log2W];
+    if (occ_frontier < 0) occ_frontier = stable_frontier_blocks_per_sm(W);
     if (occ_frontier <= 0) return fail(LP_ERR_CUDA, "stable frontier kernel cannot be resident");
     const int per_sm =
         p->sched.stable_blocks_per_sm > 0 ? std::min(occ_frontier, p->sched.stable_blocks_per_sm) : occ_frontier;

@@ -474,12 +474,23 @@ struct RowLen {
   }
 };
 
-// References of each section-A column by rule-row entries (facts define self-loops).
+// References of each section-A column by rule-row entries (facts define self-loops). A warp
+// takes 32 rules and walks their entries in step; lanes holding the same column add once (the
+// most referenced atoms of a skewed program would otherwise serialize on one counter).
 __global__ void deg_kernel(const int64_t* off, const int32_t* setlen, int64_t n_rules, const int32_t* rb,
                            int32_t* deg) {
-  for (int64_t r = gtid(); r < n_rules; r += gstride()) {
-    const int32_t* sb = rb + off[r];
-    for (int32_t i = 0; i < setlen[r]; i++) atomicAdd(deg + sb[i], 1);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t base = gtid() - lane; base < n_rules; base += gstride()) {  // uniform in the warp
+    const int64_t r = base + lane;
+    const int m = r < n_rules ? setlen[r] : 0;
+    const int32_t* sb = rb + (r < n_rules ? off[r] : 0);
+    const int steps = (int)__reduce_max_sync(FULL, (unsigned)m);
+    for (int i = 0; i < steps; i++) {
+      const int c = i < m ? sb[i] : -1;
+      const unsigned peers = __match_any_sync(FULL, c);
+      if (c >= 0 && (peers & lt) == 0u) atomicAdd(deg + c, __popc(peers));
+    }
   }
 }
 __global__ void max_kernel(const int32_t* v, int64_t n, unsigned* out) {

@@ -71,32 +71,48 @@ __device__ __forceinline__ void window_range(int i, int n_sec_a, int n_pad, int*
 }
 
 // Pass 1: the renumbering. One block per window: sort key = class << 20 | min(length, 2^20 - 1),
-// class 1 if some entry lies outside the leading n_sec_a rows; rank = number of rows of the window
-// with a smaller key, or the same key and a smaller row id (a stable sort).
+// class 1 if some entry lies outside the leading n_sec_a rows; a row's rank is its place in the
+// window sorted by (key, row id), a stable sort: a bitonic sort of key << 10 | i (unique) in
+// shared memory, padded with all-ones keys to the window size.
+static_assert(kWindow == 1024, "the composite key keeps 10 bits of row id");
 __global__ void __launch_bounds__(256) sliced_order_kernel(const int32_t* __restrict__ row_ptr,
                                                            const int32_t* __restrict__ col, int n_sec_a, int n_pad,
                                                            int32_t* __restrict__ q, int32_t* __restrict__ qinv) {
-  __shared__ int s_key[kWindow];
+  __shared__ uint32_t s_key[kWindow];
   int lo, hi;
   window_range(blockIdx.x, n_sec_a, n_pad, &lo, &hi);
   const int n = hi - lo;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int r = lo + i;
-    const int b = row_ptr[r], e = row_ptr[r + 1];
-    int cls = n_sec_a > 0 ? 0 : 1;
-    for (int t = b; t < e && cls == 0; t++) cls = (unsigned)col[t] >= (unsigned)n_sec_a;
-    s_key[i] = (cls << 20) | min(e - b, (1 << 20) - 1);
+  for (int i = threadIdx.x; i < kWindow; i += blockDim.x) {
+    uint32_t key = 0xFFFFFFFFu;
+    if (i < n) {
+      const int r = lo + i;
+      const int b = row_ptr[r], e = row_ptr[r + 1];
+      int cls = n_sec_a > 0 ? 0 : 1;
+      for (int t = b; t < e && cls == 0; t++) cls = (unsigned)col[t] >= (unsigned)n_sec_a;
+      key = ((uint32_t)((cls << 20) | min(e - b, (1 << 20) - 1)) << 10) | (uint32_t)i;
+    }
+    s_key[i] = key;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int k = s_key[i];
-    int rank = 0;
-    for (int j = 0; j < n; j++) {
-      const int kj = s_key[j];
-      rank += (kj < k) || (kj == k && j < i);
+  for (int k = 2; k <= kWindow; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < kWindow; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t x = s_key[i], y = s_key[ixj];
+          if ((x > y) == ((i & k) == 0)) {
+            s_key[i] = y;
+            s_key[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
     }
-    q[lo + i] = lo + rank;
-    qinv[lo + rank] = lo + i;
+  }
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int i = (int)(s_key[p] & (kWindow - 1));
+    q[lo + i] = lo + p;
+    qinv[lo + p] = lo + i;
   }
 }
 

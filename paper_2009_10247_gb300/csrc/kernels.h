@@ -149,7 +149,7 @@ cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, cudaStr
 int stable_blocks_per_sm(bool row_split);
 // Frontier schedule (needs the t_ptr ... fr_key fields)
 cudaError_t launch_stable_frontier(const StableArgs& a, int grid, cudaStream_t s);
-int stable_frontier_blocks_per_sm();
+int stable_frontier_blocks_per_sm(int W);
 // Transposed matrix for the frontier schedule, built on the device: cnt (n_pad + 1 ints of
 // scratch, zeroed by the caller) becomes the cursor of the fill.
 cudaError_t build_transpose(const int32_t* row_ptr, const int32_t* col, int32_t n_pad, int32_t* t_ptr, int32_t* t_idx,

@@ -43,6 +43,65 @@ constexpr unsigned kStampLimit = 0xF0000000u;
 
 __device__ __forceinline__ uint64_t rest_word(int tag) { return tag == -2 ? ~0ull : 0ull; }
 
+// WPL consecutive 64-bit words at p (16-byte aligned when WPL > 1).
+template <int WPL>
+__device__ __forceinline__ void load_words(const uint64_t* p, uint64_t (&v)[WPL]) {
+  if constexpr (WPL == 1) {
+    v[0] = *p;
+  } else {
+#pragma unroll
+    for (int j = 0; j < WPL; j += 2) {
+      const ulonglong2 q = *reinterpret_cast<const ulonglong2*>(p + j);
+      v[j] = q.x;
+      v[j + 1] = q.y;
+    }
+  }
+}
+
+// Words w0 .. w0 + WPL - 1 of `row` in a tile (src is the tile's buffer), as eval_row: AND of the
+// entries' words for a rule row, OR for an OR row or a self-loop, 0 for an empty row; E entries
+// per step (their column loads, then their gathers: four entries, two with four words per lane).
+// *n_entries grows by the row's length.
+template <int WPL>
+__device__ __forceinline__ void eval_row_words(const StableArgs& a, const uint64_t* src, int row, int w0,
+                                               uint64_t (&acc)[WPL], unsigned* n_entries) {
+  constexpr int E = WPL >= 4 ? 2 : 4;
+  const int beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
+  const bool any = (__ldg(a.any_mask + (row >> 5)) >> (row & 31)) & 1u;
+  const uint64_t ident = any ? 0ull : ~0ull;
+#pragma unroll
+  for (int j = 0; j < WPL; j++) acc[j] = end > beg ? ident : 0ull;
+  for (int e = beg; e < end; e += E) {
+    int cc[E];
+#pragma unroll
+    for (int q = 0; q < E; q++) cc[q] = e + q < end ? __ldg(a.col + e + q) : -1;
+    uint64_t v[E][WPL];
+#pragma unroll
+    for (int q = 0; q < E; q++) {
+      if (cc[q] >= 0) {
+        load_words<WPL>(src + ((long long)cc[q] << a.log2W) + w0, v[q]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < WPL; j++) v[q][j] = ident;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < WPL; j++) {
+      uint64_t orv = 0ull, andv = ~0ull;
+#pragma unroll
+      for (int q = 0; q < E; q++) {
+        orv |= v[q][j];
+        andv &= v[q][j];
+      }
+      acc[j] = any ? (acc[j] | orv) : (acc[j] & andv);
+    }
+  }
+  *n_entries += (unsigned)(end - beg);
+}
+
+// WPL: words per lane in the iterations. An item (W words) takes W / WPL lanes, so a warp
+// evaluates 32 WPL / W items at once: with W = 32, four items of eight lanes, four words each.
+template <int WPL>
 __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(StableArgs a) {
   __shared__ long long s_base;
   const int lane = threadIdx.x & 31;
@@ -58,6 +117,11 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
   const int sub = lane >> log2W;  // item within the warp's group
   const int wl = lane & (W - 1);  // word within the tile
   const unsigned subm = W == 32 ? FULL : (((1u << W) - 1u) << (sub * W));
+  const int lpi = W / WPL;           // lanes per item in the iterations
+  const int ipw = 32 / lpi;          // items per warp
+  const int isub = lane / lpi;       // item within the warp
+  const int il = lane - isub * lpi;  // lane within the item
+  const unsigned imask = lpi == 32 ? FULL : (((1u << lpi) - 1u) << (isub * lpi));
   const int n_pad = a.n_pad;
   const long long tile_words = (long long)n_pad * W;
   const int c_wave = (int)min((long long)a.fr_tiles, (long long)a.n_tiles);  // tiles per wave
@@ -147,44 +211,49 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
       // slot (t + 2) % 3 was last read as iteration t - 1's list size, before the last barrier
       if (gtid == 0) st[(t + 2) % 3] = 0u;
       const long long n_cur = ld_volatile(st + t % 3);
-      for (long long g = gwarp; g * rpw < n_cur; g += nwarps) {
-        const long long idx = g * rpw + sub;
+      for (long long g = gwarp; g * ipw < n_cur; g += nwarps) {
+        const long long idx = g * ipw + isub;
         const int item = idx < n_cur ? cur[idx] : -1;
-        uint64_t acc = 0ull, old = 0ull;
+        uint64_t acc[WPL], old[WPL];
+        bool differs = false;
         int c = 0, row = 0, tb = 0, te = 0;
         if (item >= 0) {
           c = item / n_pad;
           row = item - c * n_pad;
-          const long long o = (long long)item * W + wl;
+          const long long o = (long long)item * W + il * WPL;
           // loads that do not wait on the row's entries go first: the old words and the
           // transposed row's range (used if the row changes)
-          old = src[o];
+          load_words<WPL>(src + o, old);
           tb = __ldg(a.t_ptr + row);
           te = __ldg(a.t_ptr + row + 1);
           unsigned ne = 0;
-          acc = eval_row(a, src + (size_t)c * tile_words, row, wl, &ne);
-          dst[o] = acc;
-          if (wl == 0) {
+          eval_row_words<WPL>(a, src + (size_t)c * tile_words, row, il * WPL, acc, &ne);
+#pragma unroll
+          for (int j = 0; j < WPL; j++) {
+            dst[o + j] = acc[j];
+            differs |= acc[j] != old[j];
+          }
+          if (il == 0) {
             n_rows++;
             n_ent += ne;
           }
         }
-        const unsigned diff = __ballot_sync(FULL, acc != old);
-        const bool ch = item >= 0 && (diff & subm) != 0u;
+        const unsigned diff = __ballot_sync(FULL, differs);
+        const bool ch = item >= 0 && (diff & imask) != 0u;
         int per = 0;
         if (ch) {
           per = 1 + te - tb;
-          if (wl == 0) {
+          if (il == 0) {
             atomicOr(a.fr_dirty + (item >> 5), 1u << (item & 31));
             atomicMax(a.fr_last + c, t);
             n_list++;
             n_deps += (unsigned)(per - 1);
           }
         }
-        // the item and the rows referring to it, W lanes at a time
-        const int steps = __reduce_max_sync(FULL, (unsigned)((per + W - 1) >> log2W));
+        // the item and the rows referring to it, lpi lanes at a time
+        const int steps = __reduce_max_sync(FULL, (unsigned)((per + lpi - 1) / lpi));
         for (int s = 0; s < steps; s++) {
-          const int d = (s << log2W) + wl;
+          const int d = s * lpi + il;
           bool win = false;
           int it2 = 0;
           if (d < per) {
@@ -366,18 +435,24 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
 
 }  // namespace
 
+namespace {
+// words per lane: W <= 8 one (W lanes per item), W = 16 two, W = 32 four (eight lanes per item)
+const void* frontier_entry(int W) {
+  if (W >= 32) return (const void*)stable_frontier_kernel<4>;
+  if (W == 16) return (const void*)stable_frontier_kernel<2>;
+  return (const void*)stable_frontier_kernel<1>;
+}
+}  // namespace
+
 cudaError_t launch_stable_frontier(const StableArgs& a, int grid, cudaStream_t s) {
   StableArgs copy = a;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)stable_frontier_kernel, dim3(grid), dim3(kStableBlock), params, 0,
-                                     s);
+  return cudaLaunchCooperativeKernel(frontier_entry(a.W), dim3(grid), dim3(kStableBlock), params, 0, s);
 }
 
-int stable_frontier_blocks_per_sm() {
+int stable_frontier_blocks_per_sm(int W) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)stable_frontier_kernel, kStableBlock, 0) !=
-      cudaSuccess)
-    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, frontier_entry(W), kStableBlock, 0) != cudaSuccess) return 0;
   return nb;
 }
 

@@ -144,7 +144,7 @@ void release(lp_program* p) {
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
                   p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
                   p->sl_q, p->sl_qinv, p->sl_hdr, p->sl_col, p->sl_fact_row, p->sl_perm,
-                  p->fr_tptr, p->fr_tidx, p->fr_cnt, p->fr_buf.p, p->dc_kind, p->dc_rule,
+                  p->fr_tptr, p->fr_tidx, p->fr_cnt, p->fr_buf.p, p->dc_kind, p->dc_rule, p->fr_seed,
                   p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p,
                   p->tune_out.p, p->tune_in.p};
   for (void* q : ptrs)
@@ -431,12 +431,20 @@ lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
   unsigned* counters = nullptr;
   auto fail_clean = [&](lp_status code) {
     if (cnt) cudaFree(cnt);
-    void* ptrs[] = {p->fr_tptr, p->fr_tidx, counters};
+    void* ptrs[] = {p->fr_tptr, p->fr_tidx, p->fr_seed, counters};
     for (void* q : ptrs)
       if (q) cudaFree(q);
-    p->fr_tptr = p->fr_tidx = nullptr;
+    p->fr_tptr = p->fr_tidx = p->fr_seed = nullptr;
     return code;
   };
+  const int32_t n_seed = hm.n_fact_rows + (int32_t)hm.guess_row.size();
+  if ((st = dalloc(p, &p->fr_seed, (size_t)n_seed)) != LP_OK) return fail_clean(st);
+  if (hm.n_fact_rows > 0 &&
+      cudaMemcpyAsync(p->fr_seed, p->fact_row, (size_t)hm.n_fact_rows * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return fail_clean(cuda_fail(cudaGetLastError(), "frontier seed rows"));
+  if (!hm.guess_row.empty() && cudaMemcpyAsync(p->fr_seed + hm.n_fact_rows, hm.guess_row.data(),
+                                               hm.guess_row.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail_clean(cuda_fail(cudaGetLastError(), "frontier seed rows"));
   if ((st = dalloc(p, &p->fr_tptr, (size_t)hm.n_pad + 1)) != LP_OK) return fail_clean(st);
   if ((st = dalloc(p, &p->fr_tidx, (size_t)std::max<int64_t>(hm.nnz, 1))) != LP_OK) return fail_clean(st);
   if ((st = dalloc(p, &counters, 8)) != LP_OK) return fail_clean(st);
@@ -453,6 +461,7 @@ lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
   cnt = nullptr;
   if (e != cudaSuccess) return fail_clean(cuda_fail(e, "frontier transpose"));
   count_launches(hm.n_pad > 0 ? 3 : 0);
+  p->fr_nseed = n_seed;
   p->fr_cnt = counters;
   return LP_OK;
 }
@@ -786,6 +795,8 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
     a.fr_list = (int32_t*)(a.mark + items);
     a.fr_dirty = (unsigned*)(a.fr_list + 2 * items);
     a.fr_last = (int32_t*)(a.fr_dirty + (items + 31) / 32);
+    a.fr_seed = p->fr_seed;
+    a.n_seed = p->fr_nseed;
     a.t_ptr = p->fr_tptr;
     a.t_idx = p->fr_tidx;
     a.fr_cnt = p->fr_cnt;

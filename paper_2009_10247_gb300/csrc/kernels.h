@@ -141,6 +141,8 @@ struct StableArgs {
   unsigned* fr_cnt;         // 8: list sizes (3, rotating), rest-state record (slots 3 to 7)
   int32_t fr_tiles;         // tiles per wave (the buffers' capacity)
   unsigned fr_key;          // nonzero tag of the buffers' layout
+  const int32_t* fr_seed;   // n_seed rows nonzero in M_0: the fact rows, then the guessed rows
+  int32_t n_seed;
 };
 
 constexpr int kStableBlock = 256;

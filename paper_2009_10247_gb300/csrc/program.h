@@ -53,6 +53,8 @@ struct lp_program {
   // frontier schedule of the stable models: transposed matrix and counters (built on first use),
   // and the buffers of one wave of fr_tiles tiles of fr_W words (iterates, stamps, lists, bitmap)
   int32_t* fr_tptr = nullptr;
+  int32_t* fr_seed = nullptr;  // fact rows, then guessed rows (the first list's sources)
+  int32_t fr_nseed = 0;
   int32_t* fr_tidx = nullptr;
   unsigned* fr_cnt = nullptr;
   DevBuf fr_buf;

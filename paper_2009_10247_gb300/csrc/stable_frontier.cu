@@ -43,6 +43,40 @@ constexpr unsigned kStampLimit = 0xF0000000u;
 
 __device__ __forceinline__ uint64_t rest_word(int tag) { return tag == -2 ? ~0ull : 0ull; }
 
+// Appends to a work list staged per warp in shared memory: the winners of a step go to the
+// warp's 64-slot buffer, and the list gets them 32 at a time with one atomic on its counter (all
+// warps of the grid append to the same counter; one atomic per step serialized on it). All lanes
+// call both functions with the same n.
+__device__ __forceinline__ void staged_append(int* buf, int& n, bool flag, int value, int32_t* list, unsigned* cnt,
+                                              int lane) {
+  const unsigned m = __ballot_sync(FULL, flag);
+  if (flag) buf[n + __popc(m & ((1u << lane) - 1u))] = value;
+  n += __popc(m);
+  __syncwarp();
+  if (n >= 32) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(cnt, 32u);
+    base = __shfl_sync(FULL, base, 0);
+    list[base + lane] = buf[lane];
+    const int rest = n - 32;
+    const int moved = lane < rest ? buf[32 + lane] : 0;
+    __syncwarp();
+    if (lane < rest) buf[lane] = moved;
+    n = rest;
+    __syncwarp();
+  }
+}
+__device__ __forceinline__ void staged_flush(int* buf, int& n, int32_t* list, unsigned* cnt, int lane) {
+  if (n > 0) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(cnt, (unsigned)n);
+    base = __shfl_sync(FULL, base, 0);
+    if (lane < n) list[base + lane] = buf[lane];
+    n = 0;
+  }
+  __syncwarp();
+}
+
 // WPL consecutive 64-bit words at p (16-byte aligned when WPL > 1).
 template <int WPL>
 __device__ __forceinline__ void load_words(const uint64_t* p, uint64_t (&v)[WPL]) {
@@ -104,6 +138,7 @@ __device__ __forceinline__ void eval_row_words(const StableArgs& a, const uint64
 template <int WPL>
 __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(StableArgs a) {
   __shared__ long long s_base;
+  __shared__ int s_stage[kStableBlock / 32][64];  // per-warp list staging
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -167,33 +202,39 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
     }
 
     // ---- 1. M_0 of the guessed rows, and the first list: fact and guessed rows and the rows
-    // referring to them, in every tile of the wave
-    for (long long rb = (long long)gwarp * 32; rb < n_pad; rb += (long long)nwarps * 32) {
-      const long long r = rb + lane;
-      const int tag = r < n_pad ? __ldg(a.row_tag + r) : -1;
-      unsigned m = __ballot_sync(FULL, tag == -2 || tag >= 0);
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const int row = (int)rb + b;
-        const int tg = __shfl_sync(FULL, tag, b);
-        if (tg >= 0)
-          for (int k = lane; k < cw * W; k += 32)
-            a.X0[((long long)(k >> log2W) * n_pad + row) * W + (k & (W - 1))] = m0_word(tg, gw0 + k, a);
-        const int tb = __ldg(a.t_ptr + row), per = 1 + __ldg(a.t_ptr + row + 1) - tb;
-        const int total = cw * per;
-        for (int k0 = 0; k0 < total; k0 += 32) {
-          const int k = k0 + lane;
+    // referring to them, in every tile of the wave. A (seed row, tile) pair per eight lanes,
+    // four pairs per warp.
+    {
+      int* const buf = s_stage[threadIdx.x >> 5];
+      int n_staged = 0;
+      const int gsub = lane >> 3, gl = lane & 7;
+      const long long n_pairs = (long long)a.n_seed * cw;
+      for (long long base = (long long)gwarp * 4; base < n_pairs; base += (long long)nwarps * 4) {
+        const long long pi = base + gsub;
+        int row = 0, c = 0, tb = 0, per = 0, tg = -1;
+        if (pi < n_pairs) {
+          row = __ldg(a.fr_seed + (int)(pi % a.n_seed));
+          c = (int)(pi / a.n_seed);
+          tg = __ldg(a.row_tag + row);
+          tb = __ldg(a.t_ptr + row);
+          per = 1 + __ldg(a.t_ptr + row + 1) - tb;
+        }
+        if (tg >= 0)  // a guessed row: its words of M_0 in this tile
+          for (int w = gl; w < W; w += 8)
+            a.X0[((long long)c * n_pad + row) * W + w] = m0_word(tg, gw0 + (long long)c * W + w, a);
+        const int steps = (int)__reduce_max_sync(FULL, (unsigned)((per + 7) >> 3));
+        for (int s2 = 0; s2 < steps; s2++) {
+          const int d = 8 * s2 + gl;
           bool win = false;
           int item = 0;
-          if (k < total) {
-            const int c = k / per, d = k - c * per;
+          if (d < per) {
             item = c * n_pad + (d == 0 ? row : __ldg(a.t_idx + tb + d - 1));
             win = atomicExch(a.mark + item, stamp) != stamp;
           }
-          warp_append(a.fr_list, st + 0, win, item, lane);
+          staged_append(buf, n_staged, win, item, a.fr_list, st + 0, lane);
         }
       }
+      staged_flush(buf, n_staged, a.fr_list, st + 0, lane);
     }
     if (!grid_barrier(ctl, ++round, 6)) return;
 
@@ -211,6 +252,8 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
       // slot (t + 2) % 3 was last read as iteration t - 1's list size, before the last barrier
       if (gtid == 0) st[(t + 2) % 3] = 0u;
       const long long n_cur = ld_volatile(st + t % 3);
+      int* const buf = s_stage[threadIdx.x >> 5];
+      int n_staged = 0;
       for (long long g = gwarp; g * ipw < n_cur; g += nwarps) {
         const long long idx = g * ipw + isub;
         const int item = idx < n_cur ? cur[idx] : -1;
@@ -260,9 +303,10 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
             it2 = c * n_pad + (d == 0 ? row : __ldg(a.t_idx + tb + d - 1));
             win = atomicExch(a.mark + it2, nstamp) != nstamp;
           }
-          warp_append(nxt, nxt_cnt, win, it2, lane);
+          staged_append(buf, n_staged, win, it2, nxt, nxt_cnt, lane);
         }
       }
+      staged_flush(buf, n_staged, nxt, nxt_cnt, lane);
       if (!grid_barrier(ctl, ++round, 6)) return;
       fin = dst;
       if (ld_volatile(nxt_cnt) == 0u) {

@@ -717,19 +717,8 @@ def bench_stable(lp, torch, dev, flush, steps=5, tune=True, n_atoms=100_000, k=1
     return out
 
 
-def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
-    """Many programs in one launch (lp_batch_stable_models) against one launch per program.
-    iter_profile: also time the launch with every program cut off after t iterations
-    (max_iters = t), for every t, with the programs and iterate bytes still active at t."""
-    progs = program_batch(seed=1)
-    B = lp.Batch(progs)
-    n = B.n_programs
-    mask = torch.zeros(B.total_mask_words, dtype=torch.int64, device=dev)
-    ns = torch.zeros(n, dtype=torch.int64, device=dev)
-    it = torch.zeros(n, dtype=torch.int32, device=dev)
-    B.stable_models(mask, ns, it)
-    n_stable, iters = ns.cpu().numpy(), it.cpu().numpy()
-    stream = torch.cuda.current_stream()
+def _time_batch(B, mask, flush, stream, torch, steps):
+    """Median CUDA-event time of one lp_batch_stable_models call (L2 flushed before each)."""
     for _ in range(2):
         flush.zero_()
         B.stable_models(mask)
@@ -742,17 +731,46 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
         b.record(stream)
         b.synchronize()
         ts.append(a.elapsed_time(b))
-    ms = statistics.median(ts)
+    return statistics.median(ts)
+
+
+def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
+    """Many programs in one launch (lp_batch_stable_models) against one launch per program, under
+    the default schedule (the frontier for programs with k <= 8) and the full sweep.
+    iter_profile: also time the full-sweep launch with every program cut off after t iterations
+    (max_iters = t), for every t, with the programs and iterate bytes still active at t."""
+    progs = program_batch(seed=1)
+    B = lp.Batch(progs)
+    n = B.n_programs
+    mask = torch.zeros(B.total_mask_words, dtype=torch.int64, device=dev)
+    ns = torch.zeros(n, dtype=torch.int64, device=dev)
+    it = torch.zeros(n, dtype=torch.int32, device=dev)
+    B.stable_models(mask, ns, it)
+    n_stable, iters = ns.cpu().numpy(), it.cpu().numpy()
+    first_mask = mask.cpu().numpy().copy()
+    stream = torch.cuda.current_stream()
+    ms = _time_batch(B, mask, flush, stream, torch, steps)
+    fr = B.last_stats()
     guesses = sum(1 << k for k in B.k)
-    # algorithmic bytes: per program and iteration, row pointers (4 B) and column ids (4 B) read
-    # once, the iterate row (2^k guess bits, at least 2 bytes) read once and written once
+    peak, peak_kind = peaks()
+    # the full sweep on the same programs: per program and iteration, row pointers (4 B) and
+    # column ids (4 B) read once, the iterate row (2^k guess bits, at least 2 bytes) read once and
+    # written once
+    Bf = lp.Batch(progs, full_sweep=True)
+    mf = torch.zeros(Bf.total_mask_words, dtype=torch.int64, device=dev)
+    itf = torch.zeros(n, dtype=torch.int32, device=dev)
+    Bf.stable_models(mf, None, itf)
+    if not (np.array_equal(mf.cpu().numpy(), first_mask) and np.array_equal(itf.cpu().numpy(), iters)):
+        raise RuntimeError("batch schedules disagree")
+    ms_f = _time_batch(Bf, mf, flush, stream, torch, steps)
     by = 0
     for p in range(n):
         inf = B.info[p]
         rb = max(2, (1 << inf["k"]) // 8)
         by += int(iters[p]) * (4 * (inf["n_prime"] + 1) + 4 * inf["nnz"] + 2 * inf["n_prime"] * rb)
-    peak, peak_kind = peaks()
-    achieved = by / (ms / 1e3) / 1e9
+    ach_f = by / (ms_f / 1e3) / 1e9
+    full_rows = sum(int(i) * inf["n_prime"] for i, inf in zip(iters, B.info))
+    ach = fr["bytes_touched"] / (ms / 1e3) / 1e9
     # baseline: one lp_stable_models launch per program, same GPU, programs resident
     Ps = [lp.Program.from_program(pr) for pr in progs]
     ms_k = [torch.zeros(lp.words(1 << P.info["k"]), dtype=torch.int64, device=dev) for P in Ps]
@@ -772,16 +790,25 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
     out = {"metric": "stable-model guesses/sec, many programs in one launch", "value": guesses / (ms / 1e3),
            "unit": "guesses/s", "ms_per_step": ms, "workload": WORKLOAD_BATCH, "programs": n, "guesses": guesses,
            "rows": B.total_rows, "nnz": B.total_nnz, "n_stable": int(n_stable.sum()), "iters_max": int(iters.max()),
-           "iters_mean": float(iters.mean()), "launches_per_step": 1 if n else 0,
+           "iters_mean": float(iters.mean()), "launches_per_step": 1 if n else 0, "schedule": "frontier",
+           "rows_evaluated": fr["rows_evaluated"], "rows_of_full_sweeps": full_rows,
            "per_program_launches": {"ms_per_step": per_prog_ms, "value": guesses / (per_prog_ms / 1e3),
                                     "unit": "guesses/s", "launches_per_step": n},
            "batched_over_per_program": per_prog_ms / ms,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": measured_traffic("batch_stable_kernel"), "peak_kind": peak_kind,
-                        "kernel": "batch_stable_kernel",
-                        "bytes_per_launch": by,
-                        "note": "programs run as independent jobs; the data of all programs exceeds L2, "
-                                "the data of the programs in flight mostly does not"}}
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "peak_kind": peak_kind, "kernel": "batch_stable_kernel",
+                        "bytes_per_launch": fr["bytes_touched"],
+                        "note": "bytes the frontier touches (lp_batch_last_stats), not the full-sweep formula; "
+                                "latency-bound: each iteration of a program is a chain of dependent loads"},
+           "full_sweep": {"metric": "stable-model guesses/sec, many programs in one launch, full sweep",
+                          "value": guesses / (ms_f / 1e3), "unit": "guesses/s", "ms_per_step": ms_f,
+                          "over_main": ms / ms_f,
+                          "roofline": {"bound": "hbm", "achieved": ach_f, "peak": peak, "unit": "GB/s",
+                                       "frac": ach_f / peak, "traffic": measured_traffic("batch_stable_kernel"),
+                                       "peak_kind": peak_kind, "kernel": "batch_stable_kernel",
+                                       "bytes_per_launch": by,
+                                       "note": "programs run as independent jobs; the data of all programs "
+                                               "exceeds L2, the data of the programs in flight mostly does not"}}}
     if iter_profile:
         cells = np.array([((inf["n_prime"] + 63) // 64 * 64) * max(2, (1 << inf["k"]) // 8) for inf in B.info])
         prof = []
@@ -792,7 +819,7 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 try:
-                    B.stable_models(mask, max_iters=t)
+                    Bf.stable_models(mf, max_iters=t)
                 except lp.LPError as e:  # programs still changing after t iterations
                     if e.status != 4:
                         raise
@@ -804,6 +831,7 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
                          "active_iterate_bytes": int(cells[act].sum())})
         out["iteration_profile"] = prof
     B.close()
+    Bf.close()
     return out
 
 

@@ -210,9 +210,17 @@ lp_status lp_relaxed_backward(lp_program* prog, const float* weights, const floa
  * lp_compile_batch: programs p in [0, n_programs); program p has n_atoms[p] atoms (ids local to
  * the program) and the rules [rule_off[p], rule_off[p+1]) of the concatenated rule arrays head,
  * body_off (over all rules, body_off[0] = 0), body_atom, body_neg (nullable), in the format of
- * lp_compile. Each program is compiled exactly as lp_compile would; every program needs k <= 16.
- * flags: 0. On success *out receives a handle (lp_batch_free).
+ * lp_compile. Each program is compiled exactly as lp_compile would (on the host's threads);
+ * every program needs k <= 16.
+ * flags: 0, or LP_BATCH_FULL_SWEEP. By default the programs whose iterate rows hold at most 32
+ * bytes (k <= 8) run the frontier schedule: after a first list of the rows nonzero in M_0 and
+ * the rows referring to them, each iteration evaluates only the rows one of whose inputs changed
+ * in the last one (the compile builds each program's transposed matrix for it); the others, and
+ * every program under LP_BATCH_FULL_SWEEP, evaluate every row in every iteration. Both give the
+ * same iterates, iteration counts and stable masks. On success *out receives a handle
+ * (lp_batch_free).
  */
+#define LP_BATCH_FULL_SWEEP 1u
 typedef struct lp_batch lp_batch;
 lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int64_t* rule_off, const int32_t* head,
                            const int64_t* body_off, const int32_t* body_atom, const uint8_t* body_neg,
@@ -242,6 +250,14 @@ lp_status lp_batch_program_info(const lp_batch* batch, int32_t program, lp_info*
 lp_status lp_batch_stable_models(lp_batch* batch, uint64_t* stable_mask, int64_t* n_stable, int32_t* iters,
                                  int32_t max_iters, void* cuda_stream);
 
+/* Work of the last lp_batch_stable_models call under the frontier schedule (host outputs,
+ * nullable): rows evaluated and their stored entries, summed over programs and iterations, and
+ * the bytes those evaluations touch (per evaluated row its list slot, group header, entries,
+ * gathered rows, old and new row; per changed row its transposed row pointers and per pushed
+ * row its id, stamp and list slot); 0 for full-sweep programs. Waits for cuda_stream. */
+lp_status lp_batch_last_stats(const lp_batch* batch, int64_t* rows_evaluated, int64_t* entries_evaluated,
+                              int64_t* bytes_touched, void* cuda_stream);
+
 /* Release a batch and its device memory (NULL is a no-op). */
 void lp_batch_free(lp_batch* batch);
 
@@ -249,8 +265,11 @@ void lp_batch_free(lp_batch* batch);
  * Schedules and the autotuner. A schedule fixes how the solves of one handle map onto the GPU:
  * which least-model kernel runs and with how many resident CTAs per SM, and how wide the
  * stable-model column tiles are (Algorithm 2 processes the 2^k columns of M_0 a tile at a
- * time). Every schedule computes the same result; only the time differs. A new handle starts
- * with all fields 0 (LP_FIXPOINT=stream in the environment makes fixpoint_kernel default to 1).
+ * time). Every schedule computes the same result; only the time differs. A host-only handle
+ * starts with all fields 0. A device handle starts with fixpoint_kernel 3 if the program fits
+ * one block's shared memory, else 2 with fixpoint_stage 1 (0 where the sliced layout's indices
+ * would overflow), and stable_frontier 1; the other fields are 0 (LP_FIXPOINT=stream in the
+ * environment makes fixpoint_kernel default to 1).
  */
 typedef struct {
   int32_t fixpoint_kernel;        /* least model: 0 = warps over 32-row output words, the words'
@@ -281,11 +300,14 @@ typedef struct {
   int32_t stable_blocks_per_sm;   /* stable models: resident CTAs per SM; 0 = all that fit      */
   int32_t stable_row_split;       /* stable models: 1 = one row per warp, its entries split over
                                      the warp's lane groups (long rows); 0 = 32 / W rows per warp */
-  int32_t stable_frontier;        /* stable models: 1 = after each tile's first iteration evaluate
-                                     only the rows that changed and the rows that refer to them
-                                     (same iterates and iteration counts; the transposed matrix is
-                                     built on the device on first use); needs stable_row_split 0;
-                                     the autotuner leaves it as it is                            */
+  int32_t stable_frontier;        /* stable models: 1 = all tiles at once, each iteration
+                                     evaluating only the rows that changed and the rows that refer
+                                     to them, starting from the rows nonzero in M_0 (same iterates
+                                     and iteration counts; the transposed matrix is built on the
+                                     device on first use; the iterate buffers of up to 8 GiB,
+                                     LP_FRONTIER_BYTES, stay allocated and are restored to their
+                                     rest state after each solve); 0 = a full sweep per tile;
+                                     needs stable_row_split 0; the autotuner tries both         */
   int32_t fixpoint_stage;         /* least model, kernel 2: 0 = copy the vector prefix that rule
                                      rows gather into shared memory every iteration when it fits
                                      (160 KB); 1 = gather from global memory (through L1)         */

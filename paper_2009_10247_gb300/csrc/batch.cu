@@ -41,9 +41,14 @@ struct BatchProgram {       // device table entry
   int32_t rb;               // bytes per row of an iterate: max(2, 2^k / 8)
   int32_t k;                // guessed barred atoms
   int32_t n_neg;            // negated atoms (barred rows)
+  int64_t tp0;              // frontier: first entry of the program's transposed row pointers
+  int64_t seed0;            // frontier: first entry of the program's seed rows
+  int32_t n_seed;           // frontier: rows nonzero in M_0 (fact rows, guessed rows)
+  int32_t pad_;
 };
 
-constexpr int kBatchBlock = 512;
+constexpr int kBatchBlock = 512;          // full sweep: 512 threads, 2 blocks per SM
+constexpr int kBatchFrontierBlock = 512;  // frontier: as many threads per program (its M_0 writes and lists)
 constexpr int kGroupRows = 128;
 
 __device__ __forceinline__ uint64_t batch_m0(int tag, int w) {
@@ -88,6 +93,18 @@ struct BatchArgs {
   unsigned* queue;            // next slot, zeroed before the launch
   DeviceCtl* ctl;             // status and abort flag, zeroed before the launch
   int max_iters;
+  // frontier schedule (programs with rows of at most 32 bytes): per program its transposed
+  // matrix (tptr: global offsets into tidx, which holds program-local rows) and seed rows; per
+  // row a stamp; two lists of program-local rows per program (list + row0 and
+  // list + total_rows + row0); three rotating list sizes per program
+  bool frontier;
+  const int32_t* tptr;
+  const int32_t* tidx;
+  const int32_t* seed;
+  unsigned* mark;
+  int32_t* list;
+  unsigned* fcnt;
+  int64_t total_rows;
 };
 
 // ---- one row of an iterate: 8 RB bits (RB = 2, 4, 8, 16 or 32 bytes), as NW 64-bit words
@@ -248,14 +265,205 @@ __device__ __forceinline__ bool job_barrier_or(const BatchArgs& a, int job, int 
   return (st & 1u) == 0;
 }
 
+// Frontier schedule of one job (rows of RB <= 32 bytes: a lane per row). Row i of M_{t+1} depends
+// only on the rows that row i of M_P refers to, so iteration t evaluates only the rows of a list:
+// those that changed in iteration t - 1 and the rows that refer to them (the transposed matrix,
+// deduplicated by a per-row stamp); with two buffers an unevaluated row keeps the right value
+// (dst held M_{t-1}, equal to M_t and M_{t+1} on it). Iteration 0 starts from the rows nonzero in
+// M_0 (fact rows, guessed rows) and the rows that refer to them: theta of a row whose inputs are
+// all zero is zero. The iterates, the iteration count and the fixpoint are the full sweep's.
+// Returns false if the launch is aborting; *it and *converged as the full sweep's.
+template <int RB>
+__device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int program, int j, int rank, int c,
+                             int r_lo, int r_hi, unsigned long long& round, int* it_out, bool* converged_out,
+                             int (*s_push)[3][32]) {
+  using Row = RowT<RB>;
+  constexpr int NW = Row::NW;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* const s_incl = s_push[warp][0];  // this warp's prefix sums, transposed row starts, rows
+  int* const s_tb = s_push[warp][1];
+  int* const s_row = s_push[warp][2];
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned char* const xs[2] = {a.X0 + pr.state0, a.X1 + pr.state0};
+  unsigned* const mark = a.mark + pr.row0;
+  unsigned* const cnt = a.fcnt + 3ll * program;
+  int32_t* const lists[2] = {a.list + pr.row0, a.list + a.total_rows + pr.row0};
+  const int32_t* const tptr = a.tptr + pr.tp0;
+  const long long tid = (long long)rank * blockDim.x + threadIdx.x, nth = (long long)c * blockDim.x;
+  const long long warp0 = tid - lane;  // first item index of this warp in each round
+  unsigned n_rows = 0, n_ent = 0;
+  unsigned long long n_bytes = 0;  // bytes the schedule touches (lp_batch_last_stats)
+  bool dummy;
+  auto barrier = [&]() -> bool {
+    if (c > 1) return job_barrier_or(a, j, rank, c, ++round, false, &dummy);
+    __syncthreads();
+    return true;
+  };
+  // appends `value` of every lane whose flag is set to the list (one atomic per warp)
+  auto append = [&](int32_t* list, unsigned* counter, bool flag, int value) {
+    const unsigned m = __ballot_sync(FULL, flag);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(m));
+    base = __shfl_sync(FULL, base, leader);
+    if (flag) list[base + __popc(m & lt)] = value;
+  };
+  // Every lane with `ch` pushes its row and the rows referring to it (stamp `stamp`): the
+  // warp's (row, dependent) pairs are spread over its lanes, 32 per round, a lane finding its
+  // pair's row by binary search over the warp's prefix sums.
+  auto push = [&](bool ch, int row, unsigned stamp, int32_t* list, unsigned* counter) {
+    int tb = 0, per = 0;
+    if (ch) {
+      tb = __ldg(tptr + row);
+      per = 1 + __ldg(tptr + row + 1) - tb;
+      n_bytes += 8ull + 12ull * (unsigned)per;  // row pointers; per item its id, stamp, list slot
+    }
+    int incl = per;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) return;
+    s_incl[lane] = incl;
+    s_tb[lane] = tb;
+    s_row[lane] = row;
+    __syncwarp();
+    for (int q0 = 0; q0 < total; q0 += 32) {
+      const int q = q0 + lane;
+      bool win = false;
+      int item = 0;
+      if (q < total) {
+        int lo = 0, hi = 31;  // first lane whose inclusive sum exceeds q
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (s_incl[mid] > q) hi = mid;
+          else lo = mid + 1;
+        }
+        const int first = lo == 0 ? 0 : s_incl[lo - 1];
+        const int d = q - first;
+        item = d == 0 ? s_row[lo] : __ldg(a.tidx + s_tb[lo] + d - 1);
+        win = atomicExch(mark + item, stamp) != stamp;
+      }
+      append(list, counter, win, item);
+    }
+    __syncwarp();
+  };
+
+  // ---- 1. M_0 (Def. 8) of this block's rows in both buffers; stamps cleared; four rows per
+  // thread (rows come in 128-row groups, so a thread's four are whole)
+  for (int r = r_lo + 4 * threadIdx.x; r < r_hi; r += 4 * blockDim.x) {
+    const int4 tag4 = *reinterpret_cast<const int4*>(a.row_tag + pr.row0 + r);
+    const int tags[4] = {tag4.x, tag4.y, tag4.z, tag4.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      Row m0;
+#pragma unroll
+      for (int w = 0; w < NW; w++) m0.v[w] = batch_m0(tags[i], w) & Row::MASK;
+      m0.store(xs[0], r + i);
+      m0.store(xs[1], r + i);
+    }
+    *reinterpret_cast<uint4*>(mark + r) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (rank == 0 && threadIdx.x < 3) cnt[threadIdx.x] = 0u;
+  if (!barrier()) return false;
+  // ---- 2. the first list: seed rows and the rows referring to them
+  for (long long base = warp0; base < pr.n_seed; base += nth) {  // uniform in the warp
+    const long long i = base + lane;
+    const bool ok = i < pr.n_seed;
+    const int row = ok ? __ldg(a.seed + pr.seed0 + i) : 0;
+    push(ok, row, 1u, lists[0], cnt);
+  }
+  if (!barrier()) return false;
+  // ---- 3. the iterations
+  int t = 0;
+  bool converged = false;
+  for (; t < a.max_iters; ++t) {
+    const unsigned char* src = xs[t & 1];
+    unsigned char* dst = xs[(t + 1) & 1];
+    const int32_t* cur = lists[t & 1];
+    int32_t* nxt = lists[(t + 1) & 1];
+    unsigned* nxt_cnt = cnt + (t + 1) % 3;
+    if (rank == 0 && threadIdx.x == 0) cnt[(t + 2) % 3] = 0u;  // last read as iteration t - 1's size
+    const long long n_cur = ld_volatile(cnt + t % 3);
+    for (long long base = warp0; base < n_cur; base += nth) {  // uniform in the warp
+      const long long i = base + lane;
+      bool ch = false;
+      int r = 0;
+      if (i < n_cur) {
+        r = cur[i];
+        const int gg = pr.g0 + (r >> 7), tt = r & 127, u = tt >> 5, l = tt & 31;
+        Row old;
+        old.load(src, r);  // independent of the header: in flight with it
+        const int4 h0 = __ldg(a.hdr + 3 * gg), h1 = __ldg(a.hdr + 3 * gg + 1), h2 = __ldg(a.hdr + 3 * gg + 2);
+        const uint32_t orm = u == 0 ? (uint32_t)h1.x : u == 1 ? (uint32_t)h1.y : u == 2 ? (uint32_t)h1.z : (uint32_t)h1.w;
+        const uint32_t emm = u == 0 ? (uint32_t)h2.x : u == 1 ? (uint32_t)h2.y : u == 2 ? (uint32_t)h2.z : (uint32_t)h2.w;
+        const uint64_t inv = ((orm >> l) & 1u) ? Row::MASK : 0ull, keep = ((emm >> l) & 1u) ? 0ull : Row::MASK;
+        const int K = h0.y;
+        uint64_t acc[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) acc[w] = ~0ull;
+        const int32_t* e = a.col + h0.x + 4 * l + u;
+        for (int k = 0; k < K; k += 4) {  // four entries' ids, then their rows
+          int cc[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) cc[q] = k + q < K ? __ldg(e + 128 * (k + q)) : -1;
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            if (cc[q] >= 0) {
+              Row x;
+              x.load(src, cc[q]);
+#pragma unroll
+              for (int w = 0; w < NW; w++) acc[w] &= x.v[w] ^ inv;
+            }
+          }
+        }
+        Row nw;
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+          nw.v[w] = (acc[w] ^ inv) & keep;
+          ch |= nw.v[w] != old.v[w];
+        }
+        nw.store(dst, r);
+        n_rows++;
+        n_ent += (unsigned)K;
+        // list slot, header, entries and their gathered rows, the row's old and new words
+        n_bytes += 4ull + 48ull + (unsigned long long)K * (4 + RB) + 2ull * RB;
+      }
+      push(ch, r, (unsigned)t + 2u, nxt, nxt_cnt);
+    }
+    if (!barrier()) return false;
+    if (ld_volatile(nxt_cnt) == 0u) {
+      converged = true;
+      ++t;
+      break;
+    }
+  }
+  n_rows = __reduce_add_sync(FULL, n_rows);
+  n_ent = __reduce_add_sync(FULL, n_ent);
+  for (int o = 16; o > 0; o >>= 1) n_bytes += __shfl_xor_sync(FULL, n_bytes, o);
+  if (lane == 0) {
+    if (n_rows) atomicAdd(&a.ctl->fr_rows, (unsigned long long)n_rows);
+    if (n_ent) atomicAdd(&a.ctl->fr_entries, (unsigned long long)n_ent);
+    if (n_bytes) atomicAdd(&a.ctl->fr_list, n_bytes);  // the batch keeps its byte count here
+  }
+  *it_out = t;
+  *converged_out = converged;
+  return true;
+}
+
 // Algorithms 2 and 3 for every program, one job at a time per block: a block takes the next
 // slot of the queue, runs its share of that job's program (a contiguous range of its 128-row
 // groups; the block's warps claim them from a shared counter) to the program's fixpoint, and
 // takes the next slot. Programs progress independently, so the data of the programs being
 // solved at any moment stays in L2 across their iterations.
-__global__ void __launch_bounds__(kBatchBlock, 2) batch_stable_kernel(BatchArgs a) {
+template <int BLOCK, bool FRONTIER>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_stable_kernel(BatchArgs a) {
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ int s_slot, s_next;
+  __shared__ int s_push[FRONTIER ? BLOCK / 32 : 1][3][32];  // frontier pushes: per-warp scratch
   const int lane = threadIdx.x & 31;
   for (;;) {
     if (threadIdx.x == 0) s_slot = (int)atomicAdd(a.queue, 1u);
@@ -269,7 +477,19 @@ __global__ void __launch_bounds__(kBatchBlock, 2) batch_stable_kernel(BatchArgs 
     const int g_lo = (int)((long long)pr.n_groups * rank / c), g_hi = (int)((long long)pr.n_groups * (rank + 1) / c);
     const int r_lo = g_lo * kGroupRows, r_hi = min(g_hi * kGroupRows, pr.n_pad);
     unsigned long long round = 0;
-
+    int it = 0;
+    bool converged = false;
+    if (FRONTIER && pr.rb <= 32) {  // phases 1 and 2 under the frontier schedule
+      bool ok = false;
+      switch (pr.rb) {
+        case 2: ok = frontier_job<2>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
+        case 4: ok = frontier_job<4>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
+        case 8: ok = frontier_job<8>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
+        case 16: ok = frontier_job<16>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
+        default: ok = frontier_job<32>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
+      }
+      if (!ok) return;
+    } else {
     // ---- 1. M_0 (Def. 8) of this block's rows: all 2^k guesses as columns
     {
       unsigned char* x0 = a.X0 + pr.state0;
@@ -290,8 +510,6 @@ __global__ void __launch_bounds__(kBatchBlock, 2) batch_stable_kernel(BatchArgs 
     }
 
     // ---- 2. M_{t+1} = theta(M_P M_t) until no row of the program changes
-    int it = 0;
-    bool converged = false;
     for (; it < a.max_iters; ++it) {
       const unsigned char* src = ((it & 1) ? a.X1 : a.X0) + pr.state0;
       unsigned char* dst = ((it & 1) ? a.X0 : a.X1) + pr.state0;
@@ -331,6 +549,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) batch_stable_kernel(BatchArgs 
         break;
       }
     }
+    }  // full sweep
 
     // ---- 3. Algorithm 3 (rank 0): stable word = AND over the negated atoms q of (word of q)
     // XOR (word of q-bar); both buffers hold the fixpoint
@@ -394,12 +613,25 @@ struct lp_batch {
   unsigned long long* d_job_bar = nullptr;  // 4 per job, then the queue counter
   DeviceCtl* d_ctl = nullptr;
   uint64_t* d_stage = nullptr;  // staging for a host stable_mask
+  bool frontier = false;         // frontier schedule for the programs with rows of <= 32 bytes
+  int block = 512;               // threads per block of the launch
+  int32_t* d_tptr = nullptr;     // frontier: transposed row pointers (global offsets into d_tidx)
+  int32_t* d_tidx = nullptr;
+  int32_t* d_seed = nullptr;
+  unsigned* d_mark = nullptr;
+  int32_t* d_list = nullptr;     // 2 x total_rows
+  unsigned* d_fcnt = nullptr;    // 3 per program
   int64_t device_bytes = 0;
   double compile_ms = 0;
   int64_t launches = 0;
 };
 
 namespace {
+
+const void* batch_entry(bool frontier) {
+  return frontier ? (const void*)batch_stable_kernel<kBatchFrontierBlock, true>
+                  : (const void*)batch_stable_kernel<kBatchBlock, false>;
+}
 
 lp_status bfail(lp_status st, const std::string& msg) {
   set_error(msg);
@@ -408,7 +640,8 @@ lp_status bfail(lp_status st, const std::string& msg) {
 
 void batch_release(lp_batch* b) {
   void* ptrs[] = {b->d_table, b->d_hdr, b->d_col, b->d_tag, b->d_neg,     b->d_bar, b->d_x0,
-                  b->d_x1,    b->d_nstable, b->d_iters, b->d_jobs, b->d_slot_job, b->d_job_bar, b->d_ctl, b->d_stage};
+                  b->d_x1,    b->d_nstable, b->d_iters, b->d_jobs, b->d_slot_job, b->d_job_bar, b->d_ctl, b->d_stage,
+                  b->d_tptr,  b->d_tidx, b->d_seed, b->d_mark, b->d_list, b->d_fcnt};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -440,9 +673,12 @@ struct ProgSlices {
   std::vector<int32_t> ent;  // entries, columns in the new numbering
   std::vector<int32_t> tag;  // Def. 8 initial-column tag per row, new numbering
   std::vector<int32_t> neg, bar;
+  // frontier schedule: per row (new numbering) the rows that refer to it, and the rows nonzero in
+  // M_0 (fact rows, guessed rows)
+  std::vector<int32_t> tptr, tidx, seed;
 };
 
-void build_slices(const HostMatrix& hm, ProgSlices& out) {
+void build_slices(const HostMatrix& hm, ProgSlices& out, bool frontier) {
   constexpr int kWin = 1024;
   const int32_t np = hm.n_pad;
   std::vector<int32_t> q((size_t)np), qinv((size_t)np);
@@ -506,6 +742,18 @@ void build_slices(const HostMatrix& hm, ProgSlices& out) {
     out.neg[j] = q[hm.neg_row[j]];
     out.bar[j] = q[hm.bar_row[j]];
   }
+  if (!frontier) return;
+  out.tptr.assign((size_t)np + 1, 0);
+  for (int32_t r = 0; r < np; r++)
+    for (int32_t e = hm.row_ptr[r]; e < hm.row_ptr[r + 1]; e++) out.tptr[q[hm.col[e]] + 1]++;
+  for (int32_t j = 0; j < np; j++) out.tptr[j + 1] += out.tptr[j];
+  out.tidx.assign((size_t)out.tptr[np], 0);
+  std::vector<int32_t> cur(out.tptr.begin(), out.tptr.end() - 1);
+  for (int32_t r = 0; r < np; r++)
+    for (int32_t e = hm.row_ptr[r]; e < hm.row_ptr[r + 1]; e++) out.tidx[cur[q[hm.col[e]]]++] = q[r];
+  out.seed.clear();
+  for (int32_t j = 0; j < np; j++)
+    if (out.tag[j] == -2 || out.tag[j] >= 0) out.seed.push_back(j);
 }
 
 }  // namespace
@@ -518,7 +766,8 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
   NvtxRange nvtx("lp_compile_batch");
   if (!out) return bfail(LP_ERR_INVALID, "out must not be NULL");
   *out = nullptr;
-  if (flags != 0) return bfail(LP_ERR_INVALID, "flags must be 0");
+  if (flags & ~LP_BATCH_FULL_SWEEP) return bfail(LP_ERR_INVALID, "unknown flags");
+  const bool frontier = !(flags & LP_BATCH_FULL_SWEEP);
   if (n_programs < 0 || (n_programs > 0 && (!n_atoms || !rule_off))) return bfail(LP_ERR_INVALID, "bad program list");
   if (n_programs > 0 && rule_off[0] != 0) return bfail(LP_ERR_INVALID, "rule_off[0] must be 0");
   for (int32_t p = 0; p < n_programs; p++)
@@ -537,7 +786,7 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     try {
       rcs[p] = compile_host(n_atoms[p], nr, head + r0, off.data(), body_atom ? body_atom + b0 : nullptr,
                             body_neg ? body_neg + b0 : nullptr, hms[p], errs[p]);
-      if (rcs[p] == LP_OK && hms[p].k <= 16) build_slices(hms[p], sl[p]);
+      if (rcs[p] == LP_OK && hms[p].k <= 16) build_slices(hms[p], sl[p], frontier);
     } catch (const std::bad_alloc&) {
       rcs[p] = LP_ERR_OOM;
       errs[p] = "host allocation failed";
@@ -548,9 +797,10 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
   lp_batch* b = new (std::nothrow) lp_batch();
   if (!b) return bfail(LP_ERR_OOM, "host allocation failed");
   b->n_programs = n_programs;
+  b->frontier = frontier;
   b->infos.resize(n_programs);
   b->table.resize(n_programs);
-  int64_t row = 0, state = 0, mask = 0, nnz = 0, neg = 0, ent = 0, groups = 0;
+  int64_t row = 0, state = 0, mask = 0, nnz = 0, neg = 0, ent = 0, groups = 0, tp = 0, ti = 0, seeds = 0;
   for (int32_t p = 0; p < n_programs; p++) {
     const HostMatrix& hm = hms[p];
     if (hm.k > 16) {
@@ -568,6 +818,12 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     t.neg0 = neg;
     t.g0 = (int32_t)groups;
     t.n_groups = (int32_t)(sl[p].hdr.size() / 3);
+    t.tp0 = tp;
+    t.seed0 = seeds;
+    t.n_seed = (int32_t)sl[p].seed.size();
+    tp += (int64_t)sl[p].tptr.size();
+    ti += (int64_t)sl[p].tidx.size();
+    seeds += (int64_t)sl[p].seed.size();
     row += hm.n_pad;
     state += (int64_t)hm.n_pad * t.rb;
     mask += t.rb >= 8 ? t.rb / 8 : 1;
@@ -593,7 +849,8 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
   b->total_state = state;
   b->total_mask_words = mask;
   b->total_entries = ent;
-  if (row >= (int64_t(1) << 31) - 64 || ent >= (int64_t(1) << 31) - 64 || groups >= (int64_t(1) << 29)) {
+  if (row >= (int64_t(1) << 31) - 64 || ent >= (int64_t(1) << 31) - 64 || groups >= (int64_t(1) << 29) ||
+      ti >= (int64_t(1) << 31) - 64) {
     delete b;
     return bfail(LP_ERR_INVALID, "batch too large (rows and stored entries must be < 2^31)");
   }
@@ -620,6 +877,20 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
       e0 += (int64_t)ps.ent.size();
     }
   }
+  // frontier: transposed matrices (row pointers made global), seed rows
+  std::vector<int32_t> tptr((size_t)std::max<int64_t>(tp, 1)), tidx((size_t)std::max<int64_t>(ti, 1)),
+      seed((size_t)std::max<int64_t>(seeds, 1));
+  if (frontier) {
+    int64_t i0 = 0;
+    for (int32_t p = 0; p < n_programs; p++) {
+      const BatchProgram& t = b->table[p];
+      const ProgSlices& ps = sl[p];
+      for (size_t x = 0; x < ps.tptr.size(); x++) tptr[t.tp0 + x] = (int32_t)(ps.tptr[x] + i0);
+      std::copy(ps.tidx.begin(), ps.tidx.end(), tidx.begin() + i0);
+      std::copy(ps.seed.begin(), ps.seed.end(), seed.begin() + t.seed0);
+      i0 += (int64_t)ps.tidx.size();
+    }
+  }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
@@ -634,12 +905,21 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
   if (st == LP_OK) st = bupload<unsigned char>(b, &b->d_x1, nullptr, (size_t)state, s);
   if (st == LP_OK) st = bupload<int64_t>(b, &b->d_nstable, nullptr, (size_t)n_programs, s);
   if (st == LP_OK) st = bupload<int32_t>(b, &b->d_iters, nullptr, (size_t)n_programs, s);
+  if (frontier) {
+    if (st == LP_OK) st = bupload(b, &b->d_tptr, tptr.data(), (size_t)tp, s);
+    if (st == LP_OK) st = bupload(b, &b->d_tidx, tidx.data(), (size_t)ti, s);
+    if (st == LP_OK) st = bupload(b, &b->d_seed, seed.data(), (size_t)seeds, s);
+    if (st == LP_OK) st = bupload<unsigned>(b, &b->d_mark, nullptr, (size_t)row, s);
+    if (st == LP_OK) st = bupload<int32_t>(b, &b->d_list, nullptr, 2 * (size_t)row, s);
+    if (st == LP_OK) st = bupload<unsigned>(b, &b->d_fcnt, nullptr, 3 * (size_t)n_programs, s);
+  }
   // Jobs: one per program, largest first. A program whose share of the work exceeds one block's
   // share of the whole batch runs on several co-resident blocks (at most 16, and all multi-block
   // jobs together on at most half of the grid, so that every one of them is fully staffed by
   // the first blocks to start); the others run on one block each.
   int per_sm = 0;
-  if (st == LP_OK && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_stable_kernel, kBatchBlock, 0)) !=
+  b->block = frontier ? kBatchFrontierBlock : kBatchBlock;
+  if (st == LP_OK && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_entry(frontier), b->block, 0)) !=
                          cudaSuccess)
     st = bfail(LP_ERR_CUDA, cudaGetErrorString(e));
   if (st == LP_OK && n_programs > 0 && per_sm < 1) st = bfail(LP_ERR_CUDA, "batch kernel cannot be resident");
@@ -662,7 +942,9 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     int multi = 0;
     for (int32_t p : order) {
       int c = 1;
-      if (share > 0 && work[p] > share) c = (int)std::min<double>(16.0, std::ceil(work[p] / share));
+      // a frontier program evaluates a small share of its rows: one block (no job barriers)
+      const bool fr_prog = frontier && b->table[p].rb <= 32;
+      if (!fr_prog && share > 0 && work[p] > share) c = (int)std::min<double>(16.0, std::ceil(work[p] / share));
       c = std::min(c, std::max(1, b->table[p].n_groups));
       if (c > 1 && multi + c > multi_cap) c = 1;
       if (c > 1) multi += c;
@@ -703,6 +985,23 @@ lp_status lp_batch_program_info(const lp_batch* b, int32_t program, lp_info* inf
   if (!b || program < 0 || program >= b->n_programs) return bfail(LP_ERR_INVALID, "bad program index");
   if (info) *info = b->infos[program];
   if (mask_word_offset) *mask_word_offset = b->table[program].mask0;
+  return LP_OK;
+}
+
+lp_status lp_batch_last_stats(const lp_batch* b, int64_t* rows_evaluated, int64_t* entries_evaluated,
+                              int64_t* bytes_touched, void* cuda_stream) {
+  if (!b) return bfail(LP_ERR_INVALID, "NULL batch");
+  DeviceCtl ctl;
+  std::memset(&ctl, 0, sizeof(ctl));
+  if (b->n_programs > 0) {
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemcpyAsync(&ctl, b->d_ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bfail(LP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (rows_evaluated) *rows_evaluated = (int64_t)ctl.fr_rows;
+  if (entries_evaluated) *entries_evaluated = (int64_t)ctl.fr_entries;
+  if (bytes_touched) *bytes_touched = (int64_t)ctl.fr_list;
   return LP_OK;
 }
 
@@ -747,10 +1046,18 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
     a.queue = reinterpret_cast<unsigned*>(b->d_job_bar + 4 * (size_t)b->n_jobs);
     a.ctl = b->d_ctl;
     a.max_iters = max_iters;
+    a.frontier = b->frontier;
+    a.tptr = b->d_tptr;
+    a.tidx = b->d_tidx;
+    a.seed = b->d_seed;
+    a.mark = b->d_mark;
+    a.list = b->d_list;
+    a.fcnt = b->d_fcnt;
+    a.total_rows = b->total_rows;
     // every block resident (multi-block jobs meet at their own barriers); no more blocks than slots
     const int grid = std::max(1, std::min(b->grid, b->n_slots));
     void* params[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void*)batch_stable_kernel, dim3(grid), dim3(kBatchBlock), params, 0, s);
+    e = cudaLaunchCooperativeKernel(batch_entry(b->frontier), dim3(grid), dim3(b->block), params, 0, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return bfail(LP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));

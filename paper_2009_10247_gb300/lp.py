@@ -17,6 +17,7 @@ STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_OOM", "LP_ERR_CUDA", "LP_ERR_
 LP_ROWS, LP_TIMING = 1, 2
 LP_COMPILE_HOST_ONLY = 1
 LP_COMPILE_ON_HOST = 2
+LP_BATCH_FULL_SWEEP = 1
 
 
 class LPError(RuntimeError):
@@ -44,7 +45,7 @@ EXPORTS = ["lp_compile", "lp_program_info", "lp_least_model", "lp_stable_models"
            "lp_relaxed_workspace", "lp_relaxed_forward", "lp_relaxed_backward", "lp_compile_batch", "lp_batch_info",
            "lp_batch_program_info", "lp_batch_stable_models", "lp_batch_free", "lp_get_schedule", "lp_set_schedule",
            "lp_autotune", "lp_stable_search", "lp_check_grid_barrier", "lp_check_matrix", "lp_debug_fail_alloc",
-           "lp_debug_internal"]
+           "lp_debug_internal", "lp_batch_last_stats"]
 
 LP_TUNE_LEAST = 1
 LP_TUNE_STABLE = 2
@@ -112,6 +113,8 @@ def load(build_if_missing: bool = False):
     L.lp_batch_stable_models.argtypes = [P, P, P, P, i32, P]
     for name in ("lp_compile_batch", "lp_batch_info", "lp_batch_program_info", "lp_batch_stable_models"):
         getattr(L, name).restype = ctypes.c_int
+    L.lp_batch_last_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64), P]
+    L.lp_batch_last_stats.restype = ctypes.c_int
     L.lp_batch_free.argtypes = [P]
     L.lp_batch_free.restype = None
     L.lp_get_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
@@ -403,7 +406,9 @@ class Program:
 class Batch:
     """Many independent normal programs compiled for one launch (lp_compile_batch)."""
 
-    def __init__(self, programs, stream=None):
+    def __init__(self, programs, stream=None, full_sweep=False):
+        """full_sweep: every program evaluates every row in every iteration (LP_BATCH_FULL_SWEEP);
+        by default programs with k <= 8 run the frontier schedule."""
         L = load()
         n = len(programs)
         n_atoms = np.array([p.n_atoms for p in programs], dtype=np.int32)
@@ -421,7 +426,7 @@ class Batch:
                                   else np.zeros(len(p.body_atom), np.uint8) for p in programs])
         self._h = ctypes.c_void_p()
         _check(L.lp_compile_batch(n, _ptr(n_atoms), _ptr(rule_off), _ptr(head), _ptr(body_off), _ptr(atom), _ptr(neg),
-                                  0, _stream(stream), ctypes.byref(self._h)))
+                                  LP_BATCH_FULL_SWEEP if full_sweep else 0, _stream(stream), ctypes.byref(self._h)))
         vals = [ctypes.c_int64() for _ in range(5)]
         _check(L.lp_batch_info(self._h, *[ctypes.byref(v) for v in vals]))
         self.n_programs, self.total_rows, self.total_nnz, self.total_mask_words, self.device_bytes = [v.value for v in vals]
@@ -437,6 +442,13 @@ class Batch:
     def stable_models(self, stable_mask, n_stable=None, iters=None, max_iters=1 << 30, stream=None):
         _check(load().lp_batch_stable_models(self._h, _ptr(stable_mask), _ptr(n_stable), _ptr(iters), int(max_iters),
                                              _stream(stream)))
+
+    def last_stats(self, stream=None):
+        """Rows and entries the last solve evaluated under the frontier schedule."""
+        rows, ents, byts = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().lp_batch_last_stats(self._h, ctypes.byref(rows), ctypes.byref(ents), ctypes.byref(byts),
+                                          _stream(stream)))
+        return {"rows_evaluated": rows.value, "entries_evaluated": ents.value, "bytes_touched": byts.value}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

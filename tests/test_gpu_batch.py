@@ -18,8 +18,8 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_util import DEV, gpu_stable  # noqa: E402
 
 
-def _run_batch(progs, host=False, max_iters=1 << 30):
-    with lp.Batch(progs) as B:
+def _run_batch(progs, host=False, max_iters=1 << 30, full_sweep=False):
+    with lp.Batch(progs, full_sweep=full_sweep) as B:
         n = B.n_programs
         if host:
             mask = np.zeros(max(B.total_mask_words, 1), dtype=np.uint64)
@@ -48,7 +48,8 @@ def _check_oracle(progs, got, ns):
         assert ns[p] == int(st4.sum())
 
 
-def test_tiny_random_programs():
+@pytest.mark.parametrize("full_sweep", [False, True])
+def test_tiny_random_programs(full_sweep):
     rng = np.random.default_rng(77)
     progs = []
     for s in range(60):
@@ -56,15 +57,16 @@ def test_tiny_random_programs():
                                  max_body=4, p_fact=0.15, p_neg=0.12))
     progs += [parse("p :- not q. q :- not p."), parse("p :- not p."), small_definite(1),
               parse("a :- not b. b :- not a. c :- a. c :- b.")]
-    got, ns, _, _ = _run_batch(progs)
+    got, ns, _, _ = _run_batch(progs, full_sweep=full_sweep)
     _check_oracle(progs, got, ns)
 
 
-def test_degenerate_programs():
+@pytest.mark.parametrize("full_sweep", [False, True])
+def test_degenerate_programs(full_sweep):
     empty = Program(n_atoms=3, head=np.zeros(0, np.int64), body_off=np.zeros(1, np.int64),
                     body_atom=np.zeros(0, np.int64), body_neg=None)
     progs = [empty, parse("p."), parse("p :- not q. q :- not p."), empty]
-    got, ns, it, _ = _run_batch(progs)
+    got, ns, it, _ = _run_batch(progs, full_sweep=full_sweep)
     _check_oracle(progs, got, ns)
     assert all(i >= 1 for i in it)
 
@@ -83,10 +85,11 @@ def test_host_buffers_match_device():
     _check_oracle(progs, a, na)
 
 
-def test_reduced_uneven_batch_against_oracle():
+@pytest.mark.parametrize("full_sweep", [False, True])
+def test_reduced_uneven_batch_against_oracle(full_sweep):
     # the uneven-size workload's generator with smaller programs (oracle cost)
     progs = program_batch(seed=11, count=40, n_lo=100, n_hi=3000)
-    got, ns, _, _ = _run_batch(progs)
+    got, ns, _, _ = _run_batch(progs, full_sweep=full_sweep)
     _check_oracle(progs, got, ns)
 
 
@@ -128,13 +131,41 @@ def test_more_programs_than_one_launch():
     assert np.all(it >= 1)
 
 
-def test_single_and_few_large_programs():
+@pytest.mark.parametrize("full_sweep", [False, True])
+def test_single_and_few_large_programs(full_sweep):
     # one program alone takes the whole batch's work: it runs as one job on many blocks that
     # meet at the job's barrier; two programs of very different sizes split the blocks
     one = [normal_program(seed=21, n=4000, n_rules=12000, k=7, per_atom=2)]
-    got, ns, it, _ = _run_batch(one)
+    got, ns, it, _ = _run_batch(one, full_sweep=full_sweep)
     _check_oracle(one, got, ns)
     two = [normal_program(seed=22, n=6000, n_rules=18000, k=8, per_atom=2), parse("p :- not q. q :- not p.")]
-    got, ns, it, _ = _run_batch(two)
+    got, ns, it, _ = _run_batch(two, full_sweep=full_sweep)
     _check_oracle(two, got, ns)
     assert np.all(it >= 1)
+
+
+def test_frontier_equals_full_sweep():
+    # the frontier schedule (programs with k <= 8) against the full sweep on the same programs:
+    # the same stable masks and the same per-program iteration counts, with programs of k = 9 and
+    # 10 (rows wider than 32 bytes, full sweep in both) mixed in; and the frontier evaluates far
+    # fewer rows than the full sweeps would
+    progs = program_batch(seed=13, count=60, n_lo=100, n_hi=4000)
+    progs += [normal_program(seed=31, n=2000, n_rules=6000, k=9, per_atom=2),
+              normal_program(seed=32, n=1500, n_rules=4500, k=10, per_atom=2)]
+    a, na, ia, _ = _run_batch(progs)
+    b, nb, ib, _ = _run_batch(progs, full_sweep=True)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert np.array_equal(na, nb) and np.array_equal(ia, ib)
+    _check_oracle(progs[-2:], a[-2:], na[-2:])
+    with lp.Batch(progs[:60]) as B:
+        m = torch.zeros(max(B.total_mask_words, 1), dtype=torch.int64, device=DEV)
+        B.stable_models(m)
+        torch.cuda.synchronize()
+        rows = B.last_stats()["rows_evaluated"]
+    full_rows = sum(int(i) * inf["n_prime"] for i, inf in zip(ib[:60], B.info))
+    assert 0 < rows < full_rows
+
+
+def test_frontier_no_fixpoint_reports_error():
+    with pytest.raises(lp.LPError):
+        _run_batch([normal_program(seed=21, n=400, n_rules=1200, k=5, per_atom=2)], max_iters=1)

@@ -105,6 +105,12 @@ struct BatchArgs {
   int32_t* list;
   unsigned* fcnt;
   int64_t total_rows;
+  // the iterate buffers of a frontier program rest between solves in M_0's guess-independent
+  // part (fact rows all ones, other rows zero); a bit per row that changed in this solve; per
+  // program 1 while its rest state is valid, and its next unused stamp
+  unsigned* dirty;
+  unsigned* clean;
+  unsigned* epoch;
 };
 
 // ---- one row of an iterate: 8 RB bits (RB = 2, 4, 8, 16 or 32 bytes), as NW 64-bit words
@@ -276,7 +282,7 @@ __device__ __forceinline__ bool job_barrier_or(const BatchArgs& a, int job, int 
 template <int RB>
 __device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int program, int j, int rank, int c,
                              int r_lo, int r_hi, unsigned long long& round, int* it_out, bool* converged_out,
-                             int (*s_push)[3][32]) {
+                             int (*s_push)[3][32], unsigned* epoch_out) {
   using Row = RowT<RB>;
   constexpr int NW = Row::NW;
   constexpr unsigned FULL = 0xffffffffu;
@@ -352,29 +358,50 @@ __device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int pro
     __syncwarp();
   };
 
-  // ---- 1. M_0 (Def. 8) of this block's rows in both buffers; stamps cleared; four rows per
-  // thread (rows come in 128-row groups, so a thread's four are whole)
-  for (int r = r_lo + 4 * threadIdx.x; r < r_hi; r += 4 * blockDim.x) {
-    const int4 tag4 = *reinterpret_cast<const int4*>(a.row_tag + pr.row0 + r);
-    const int tags[4] = {tag4.x, tag4.y, tag4.z, tag4.w};
+  // ---- 1. M_0 (Def. 8). In the rest state only the guessed rows differ from it: write those into
+  // X0 (iteration 0 evaluates them, so X1 need not hold them). Otherwise (first solve, a solve
+  // that did not finish, stamps about to wrap) the block writes M_0 for its rows into both
+  // buffers, four rows per thread (rows come in 128-row groups, so a thread's four are whole),
+  // and clears their stamps and changed bits.
+  unsigned e = ld_volatile(a.epoch + program);
+  const bool clean = ld_volatile(a.clean + program) != 0u && e < 0xF0000000u - (unsigned)a.max_iters;
+  if (!clean) e = 0u;
+  if (clean) {
+    for (long long i = tid; i < pr.n_seed; i += nth) {
+      const int row = __ldg(a.seed + pr.seed0 + i);
+      const int tag = __ldg(a.row_tag + pr.row0 + row);
+      if (tag >= 0) {
+        Row m0;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-      Row m0;
-#pragma unroll
-      for (int w = 0; w < NW; w++) m0.v[w] = batch_m0(tags[i], w) & Row::MASK;
-      m0.store(xs[0], r + i);
-      m0.store(xs[1], r + i);
+        for (int w = 0; w < NW; w++) m0.v[w] = batch_m0(tag, w) & Row::MASK;
+        m0.store(xs[0], row);
+      }
     }
-    *reinterpret_cast<uint4*>(mark + r) = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    for (int r = r_lo + 4 * threadIdx.x; r < r_hi; r += 4 * blockDim.x) {
+      const int4 tag4 = *reinterpret_cast<const int4*>(a.row_tag + pr.row0 + r);
+      const int tags[4] = {tag4.x, tag4.y, tag4.z, tag4.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        Row m0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) m0.v[w] = batch_m0(tags[i], w) & Row::MASK;
+        m0.store(xs[0], r + i);
+        m0.store(xs[1], r + i);
+      }
+      *reinterpret_cast<uint4*>(mark + r) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int w = r_lo / 32 + threadIdx.x; w < r_hi / 32; w += blockDim.x) a.dirty[pr.row0 / 32 + w] = 0u;
   }
   if (rank == 0 && threadIdx.x < 3) cnt[threadIdx.x] = 0u;
   if (!barrier()) return false;
+  if (rank == 0 && threadIdx.x == 0) a.clean[program] = 0u;  // every block has read it: in use
   // ---- 2. the first list: seed rows and the rows referring to them
   for (long long base = warp0; base < pr.n_seed; base += nth) {  // uniform in the warp
     const long long i = base + lane;
     const bool ok = i < pr.n_seed;
     const int row = ok ? __ldg(a.seed + pr.seed0 + i) : 0;
-    push(ok, row, 1u, lists[0], cnt);
+    push(ok, row, e + 1u, lists[0], cnt);
   }
   if (!barrier()) return false;
   // ---- 3. the iterations
@@ -427,12 +454,13 @@ __device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int pro
           ch |= nw.v[w] != old.v[w];
         }
         nw.store(dst, r);
+        if (ch) atomicOr(a.dirty + ((pr.row0 + r) >> 5), 1u << ((pr.row0 + r) & 31));
         n_rows++;
         n_ent += (unsigned)K;
         // list slot, header, entries and their gathered rows, the row's old and new words
         n_bytes += 4ull + 48ull + (unsigned long long)K * (4 + RB) + 2ull * RB;
       }
-      push(ch, r, (unsigned)t + 2u, nxt, nxt_cnt);
+      push(ch, r, e + (unsigned)t + 2u, nxt, nxt_cnt);
     }
     if (!barrier()) return false;
     if (ld_volatile(nxt_cnt) == 0u) {
@@ -451,7 +479,44 @@ __device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int pro
   }
   *it_out = t;
   *converged_out = converged;
+  *epoch_out = e + (unsigned)t + 2u;  // the next solve's first stamp
   return true;
+}
+
+// After Algorithm 3: the rows of [r_lo, r_hi) that changed in this solve, and (rank 0) the
+// guessed rows, back to the rest state in both buffers; their changed bits cleared.
+template <int RB>
+__device__ void frontier_reset(const BatchArgs& a, const BatchProgram& pr, int rank, int c, int r_lo, int r_hi) {
+  using Row = RowT<RB>;
+  constexpr int NW = Row::NW;
+  unsigned char* const xs[2] = {a.X0 + pr.state0, a.X1 + pr.state0};
+  for (int w = r_lo / 32 + threadIdx.x; w < r_hi / 32; w += blockDim.x) {
+    unsigned bits = a.dirty[pr.row0 / 32 + w];
+    if (bits == 0u) continue;
+    a.dirty[pr.row0 / 32 + w] = 0u;
+    while (bits) {
+      const int r = 32 * w + __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int tag = __ldg(a.row_tag + pr.row0 + r);
+      Row v;
+#pragma unroll
+      for (int i = 0; i < NW; i++) v.v[i] = tag == -2 ? Row::MASK : 0ull;
+      v.store(xs[0], r);
+      v.store(xs[1], r);
+    }
+  }
+  if (rank == 0)
+    for (int i = threadIdx.x; i < pr.n_seed; i += blockDim.x) {
+      const int row = __ldg(a.seed + pr.seed0 + i);
+      if (__ldg(a.row_tag + pr.row0 + row) >= 0) {
+        Row z;
+#pragma unroll
+        for (int k = 0; k < NW; k++) z.v[k] = 0ull;
+        z.store(xs[0], row);
+        z.store(xs[1], row);
+      }
+    }
+  (void)c;
 }
 
 // Algorithms 2 and 3 for every program, one job at a time per block: a block takes the next
@@ -479,14 +544,15 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_stable_kernel(Batch
     unsigned long long round = 0;
     int it = 0;
     bool converged = false;
+    unsigned next_epoch = 0u;
     if (FRONTIER && pr.rb <= 32) {  // phases 1 and 2 under the frontier schedule
       bool ok = false;
       switch (pr.rb) {
-        case 2: ok = frontier_job<2>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
-        case 4: ok = frontier_job<4>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
-        case 8: ok = frontier_job<8>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
-        case 16: ok = frontier_job<16>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
-        default: ok = frontier_job<32>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push); break;
+        case 2: ok = frontier_job<2>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push, &next_epoch); break;
+        case 4: ok = frontier_job<4>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push, &next_epoch); break;
+        case 8: ok = frontier_job<8>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push, &next_epoch); break;
+        case 16: ok = frontier_job<16>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push, &next_epoch); break;
+        default: ok = frontier_job<32>(a, pr, job.program, j, rank, c, r_lo, r_hi, round, &it, &converged, s_push, &next_epoch); break;
       }
       if (!ok) return;
     } else {
@@ -583,6 +649,27 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_stable_kernel(Batch
         if (st) atomicAdd(reinterpret_cast<unsigned long long*>(a.n_stable + job.program), (unsigned long long)__popcll(st));
       }
     }
+    if (FRONTIER && pr.rb <= 32) {
+      // the rest state again, once Algorithm 3 has read the fixpoint; no wait follows, so every
+      // block of the job finishes its share once it passes this barrier
+      if (c > 1) {
+        bool dummy2;
+        if (!job_barrier_or(a, j, rank, c, ++round, false, &dummy2)) return;
+      } else {
+        __syncthreads();
+      }
+      switch (pr.rb) {
+        case 2: frontier_reset<2>(a, pr, rank, c, r_lo, r_hi); break;
+        case 4: frontier_reset<4>(a, pr, rank, c, r_lo, r_hi); break;
+        case 8: frontier_reset<8>(a, pr, rank, c, r_lo, r_hi); break;
+        case 16: frontier_reset<16>(a, pr, rank, c, r_lo, r_hi); break;
+        default: frontier_reset<32>(a, pr, rank, c, r_lo, r_hi); break;
+      }
+      if (rank == 0 && threadIdx.x == 0) {
+        a.epoch[job.program] = next_epoch;
+        a.clean[job.program] = 1u;
+      }
+    }
     __syncthreads();  // s_slot and s_next are reused by the next job
   }
 }
@@ -621,6 +708,9 @@ struct lp_batch {
   unsigned* d_mark = nullptr;
   int32_t* d_list = nullptr;     // 2 x total_rows
   unsigned* d_fcnt = nullptr;    // 3 per program
+  unsigned* d_dirty = nullptr;   // a bit per row
+  unsigned* d_clean = nullptr;   // per program: rest state valid (zeroed at compile)
+  unsigned* d_epoch = nullptr;   // per program: next unused stamp
   int64_t device_bytes = 0;
   double compile_ms = 0;
   int64_t launches = 0;
@@ -641,7 +731,8 @@ lp_status bfail(lp_status st, const std::string& msg) {
 void batch_release(lp_batch* b) {
   void* ptrs[] = {b->d_table, b->d_hdr, b->d_col, b->d_tag, b->d_neg,     b->d_bar, b->d_x0,
                   b->d_x1,    b->d_nstable, b->d_iters, b->d_jobs, b->d_slot_job, b->d_job_bar, b->d_ctl, b->d_stage,
-                  b->d_tptr,  b->d_tidx, b->d_seed, b->d_mark, b->d_list, b->d_fcnt};
+                  b->d_tptr,  b->d_tidx, b->d_seed, b->d_mark, b->d_list, b->d_fcnt, b->d_dirty, b->d_clean,
+                  b->d_epoch};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -912,6 +1003,11 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     if (st == LP_OK) st = bupload<unsigned>(b, &b->d_mark, nullptr, (size_t)row, s);
     if (st == LP_OK) st = bupload<int32_t>(b, &b->d_list, nullptr, 2 * (size_t)row, s);
     if (st == LP_OK) st = bupload<unsigned>(b, &b->d_fcnt, nullptr, 3 * (size_t)n_programs, s);
+    if (st == LP_OK) st = bupload<unsigned>(b, &b->d_dirty, nullptr, (size_t)row / 32 + 1, s);
+    if (st == LP_OK) st = bupload<unsigned>(b, &b->d_clean, nullptr, (size_t)n_programs, s);
+    if (st == LP_OK) st = bupload<unsigned>(b, &b->d_epoch, nullptr, (size_t)n_programs, s);
+    if (st == LP_OK && (e = cudaMemsetAsync(b->d_clean, 0, std::max<size_t>(n_programs, 1) * 4, s)) != cudaSuccess)
+      st = bfail(LP_ERR_CUDA, cudaGetErrorString(e));
   }
   // Jobs: one per program, largest first. A program whose share of the work exceeds one block's
   // share of the whole batch runs on several co-resident blocks (at most 16, and all multi-block
@@ -942,9 +1038,9 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     int multi = 0;
     for (int32_t p : order) {
       int c = 1;
-      // a frontier program evaluates a small share of its rows: one block (no job barriers)
+      // a frontier program evaluates a small share of its rows: at most two blocks
       const bool fr_prog = frontier && b->table[p].rb <= 32;
-      if (!fr_prog && share > 0 && work[p] > share) c = (int)std::min<double>(16.0, std::ceil(work[p] / share));
+      if (share > 0 && work[p] > share) c = (int)std::min<double>(fr_prog ? 2.0 : 16.0, std::ceil(work[p] / share));
       c = std::min(c, std::max(1, b->table[p].n_groups));
       if (c > 1 && multi + c > multi_cap) c = 1;
       if (c > 1) multi += c;
@@ -1054,6 +1150,9 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
     a.list = b->d_list;
     a.fcnt = b->d_fcnt;
     a.total_rows = b->total_rows;
+    a.dirty = b->d_dirty;
+    a.clean = b->d_clean;
+    a.epoch = b->d_epoch;
     // every block resident (multi-block jobs meet at their own barriers); no more blocks than slots
     const int grid = std::max(1, std::min(b->grid, b->n_slots));
     void* params[] = {&a};

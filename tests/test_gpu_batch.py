@@ -169,3 +169,31 @@ def test_frontier_equals_full_sweep():
 def test_frontier_no_fixpoint_reports_error():
     with pytest.raises(lp.LPError):
         _run_batch([normal_program(seed=21, n=400, n_rules=1200, k=5, per_atom=2)], max_iters=1)
+
+
+def _solve(B, max_iters=1 << 30):
+    n = B.n_programs
+    mask_t = torch.zeros(max(B.total_mask_words, 1), dtype=torch.int64, device=DEV)
+    ns_t = torch.zeros(max(n, 1), dtype=torch.int64, device=DEV)
+    it_t = torch.zeros(max(n, 1), dtype=torch.int32, device=DEV)
+    B.stable_models(mask_t, ns_t, it_t, max_iters=max_iters)
+    torch.cuda.synchronize()
+    return mask_t.cpu().numpy().copy(), ns_t.cpu().numpy()[:n].copy(), it_t.cpu().numpy()[:n].copy()
+
+
+def test_frontier_repeated_solves_keep_rest_state():
+    # one handle, several solves: the frontier's buffers rest between solves and each solve
+    # restores the rows it changed; a solve stopped by max_iters leaves the handle usable
+    progs = program_batch(seed=17, count=30, n_lo=100, n_hi=3000)
+    with lp.Batch(progs, full_sweep=True) as F:
+        ref = _solve(F)
+    assert ref[2].max() > 2
+    with lp.Batch(progs) as B:
+        for _ in range(3):
+            got = _solve(B)
+            assert all(np.array_equal(x, y) for x, y in zip(got, ref))
+        with pytest.raises(lp.LPError):
+            _solve(B, max_iters=2)
+        for _ in range(2):
+            got = _solve(B)
+            assert all(np.array_equal(x, y) for x, y in zip(got, ref))

@@ -71,10 +71,11 @@ def _least_fields(sched):
     return f
 
 
-def measured_traffic(kernel, sched=None, workload_key=None):
+def measured_traffic(kernel, sched=None, workload_key=None, variant=None):
     """DRAM bytes per launch from the committed ncu summaries: the record of `kernel` taken on
     the kernel sources as they are now and, for the least-model kernel, under the same schedule
-    and on the same workload (`workload_key`; records without one are the headline workload's).
+    and on the same workload (`workload_key`; records without one are the headline workload's);
+    `variant` tells apart the instantiations of one kernel (the batch's frontier and full sweep).
     None if there is none: the counters are stale or belong to another variant."""
     import hashlib
     try:
@@ -87,7 +88,7 @@ def measured_traffic(kernel, sched=None, workload_key=None):
             continue
         if sched is not None and rec.get("schedule_fields") != _least_fields(sched):
             continue
-        if rec.get("workload_key") != workload_key:
+        if rec.get("workload_key") != workload_key or rec.get("variant") != variant:
             continue
         try:
             h = hashlib.sha256()
@@ -796,7 +797,8 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
                                     "unit": "guesses/s", "launches_per_step": n},
            "batched_over_per_program": per_prog_ms / ms,
            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                        "traffic": None, "peak_kind": peak_kind, "kernel": "batch_stable_kernel",
+                        "traffic": measured_traffic("batch_stable_kernel", variant="frontier"),
+                        "peak_kind": peak_kind, "kernel": "batch_stable_kernel",
                         "bytes_per_launch": fr["bytes_touched"],
                         "note": "bytes the frontier touches (lp_batch_last_stats), not the full-sweep formula; "
                                 "latency-bound: each iteration of a program is a chain of dependent loads"},
@@ -804,7 +806,8 @@ def bench_batch(lp, torch, dev, flush, steps=5, iter_profile=False):
                           "value": guesses / (ms_f / 1e3), "unit": "guesses/s", "ms_per_step": ms_f,
                           "over_main": ms / ms_f,
                           "roofline": {"bound": "hbm", "achieved": ach_f, "peak": peak, "unit": "GB/s",
-                                       "frac": ach_f / peak, "traffic": measured_traffic("batch_stable_kernel"),
+                                       "frac": ach_f / peak,
+                                       "traffic": measured_traffic("batch_stable_kernel", variant="full_sweep"),
                                        "peak_kind": peak_kind, "kernel": "batch_stable_kernel",
                                        "bytes_per_launch": by,
                                        "note": "programs run as independent jobs; the data of all programs "

@@ -144,7 +144,7 @@ void release(lp_program* p) {
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
                   p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
                   p->sl_q, p->sl_qinv, p->sl_hdr, p->sl_col, p->sl_fact_row, p->sl_perm,
-                  p->fr_tptr, p->fr_tidx, p->fr_cnt, p->fr_buf.p, p->dc_kind, p->dc_rule, p->fr_seed,
+                  p->fr_tptr, p->fr_tidx, p->fr_cnt, p->fr_long, p->fr_buf.p, p->dc_kind, p->dc_rule, p->fr_seed,
                   p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p,
                   p->tune_out.p, p->tune_in.p};
   for (void* q : ptrs)
@@ -431,10 +431,11 @@ lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
   unsigned* counters = nullptr;
   auto fail_clean = [&](lp_status code) {
     if (cnt) cudaFree(cnt);
-    void* ptrs[] = {p->fr_tptr, p->fr_tidx, p->fr_seed, counters};
+    void* ptrs[] = {p->fr_tptr, p->fr_tidx, p->fr_seed, p->fr_long, counters};
     for (void* q : ptrs)
       if (q) cudaFree(q);
     p->fr_tptr = p->fr_tidx = p->fr_seed = nullptr;
+    p->fr_long = nullptr;
     return code;
   };
   const int32_t n_seed = hm.n_fact_rows + (int32_t)hm.guess_row.size();
@@ -447,30 +448,42 @@ lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
     return fail_clean(cuda_fail(cudaGetLastError(), "frontier seed rows"));
   if ((st = dalloc(p, &p->fr_tptr, (size_t)hm.n_pad + 1)) != LP_OK) return fail_clean(st);
   if ((st = dalloc(p, &p->fr_tidx, (size_t)std::max<int64_t>(hm.nnz, 1))) != LP_OK) return fail_clean(st);
-  if ((st = dalloc(p, &counters, 8)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &p->fr_long, (size_t)hm.n_pad / 32 + 1)) != LP_OK) return fail_clean(st);
+  if ((st = dalloc(p, &counters, kFrontierCounters)) != LP_OK) return fail_clean(st);
   if (device_malloc((void**)&cnt, ((size_t)hm.n_pad + 1) * 4) != cudaSuccess) {
     cnt = nullptr;
     cudaGetLastError();
     return fail_clean(fail(LP_ERR_OOM, "frontier scratch"));
   }
-  cudaError_t e = cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(counters, 0, kFrontierCounters * sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, ((size_t)hm.n_pad + 1) * 4, s);
   if (e == cudaSuccess) e = build_transpose(p->row_ptr, p->col, hm.n_pad, p->fr_tptr, p->fr_tidx, cnt, s);
+  // counters[kFrontierCounters - 1] (zeroed above, unused by the kernel): whether a row is long
+  unsigned any_long = 0;
+  if (e == cudaSuccess) e = build_long_rows(p->row_ptr, hm.n_pad, p->fr_long, counters + kFrontierCounters - 1, s);
+  if (e == cudaSuccess && hm.n_pad > 0)
+    e = cudaMemcpyAsync(&any_long, counters + kFrontierCounters - 1, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(cnt);
   cnt = nullptr;
   if (e != cudaSuccess) return fail_clean(cuda_fail(e, "frontier transpose"));
-  count_launches(hm.n_pad > 0 ? 3 : 0);
+  count_launches(hm.n_pad > 0 ? 4 : 0);
   p->fr_nseed = n_seed;
+  p->fr_any_long = any_long != 0;
   p->fr_cnt = counters;
   return LP_OK;
 }
 
+// Room for wide items (more dependents than the grid-push threshold) per wave of `items`; past it
+// the warps push the rest themselves.
+int64_t frontier_wide_cap(int64_t items) { return items / 16 + 64; }
+
 // Bytes of the frontier buffers for `tiles` tiles of W words: two iterate buffers, a stamp and two
-// list slots per item, the changed-item bitmap, a counter per tile.
+// list slots per item, the changed-item bitmap, a counter per tile, the wide-item list.
 int64_t frontier_bytes(int64_t n_pad, int W, int64_t tiles) {
   const int64_t items = tiles * n_pad;
-  return 2 * items * W * 8 + items * 4 + 2 * items * 4 + ((items + 31) / 32) * 4 + tiles * 4 + 64;
+  return 2 * items * W * 8 + items * 4 + 2 * items * 4 + ((items + 31) / 32) * 4 + tiles * 4 +
+         frontier_wide_cap(items) * 4 + 64;
 }
 
 // The wave buffers for `tiles` tiles of W words; a new allocation voids the rest-state record.
@@ -486,7 +499,7 @@ lp_status ensure_frontier_buffers(lp_program* p, int W, int32_t tiles, cudaStrea
   if (st != LP_OK) return st;
   p->fr_W = W;
   p->fr_tiles = tiles;
-  LP_CUDA(cudaMemsetAsync(p->fr_cnt, 0, 8 * sizeof(unsigned), s));
+  LP_CUDA(cudaMemsetAsync(p->fr_cnt, 0, kFrontierCounters * sizeof(unsigned), s));
   return LP_OK;
 }
 
@@ -797,6 +810,11 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
     a.fr_last = (int32_t*)(a.fr_dirty + (items + 31) / 32);
     a.fr_seed = p->fr_seed;
     a.n_seed = p->fr_nseed;
+    a.fr_wide = a.fr_last + wave_tiles;
+    a.wide_cap = (int32_t)frontier_wide_cap(items);
+    if (const char* env = std::getenv("LP_FRONTIER_WIDE_ITEMS"))  // a smaller wide list (tests its overflow)
+      a.wide_cap = (int32_t)std::max<int64_t>(0, std::min<int64_t>(a.wide_cap, std::atoll(env)));
+    a.long_mask = p->fr_any_long ? p->fr_long : nullptr;
     a.t_ptr = p->fr_tptr;
     a.t_idx = p->fr_tidx;
     a.fr_cnt = p->fr_cnt;

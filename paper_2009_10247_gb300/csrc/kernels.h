@@ -138,7 +138,12 @@ struct StableArgs {
   int32_t* fr_list;         // 2 x fr_tiles * n_pad
   unsigned* fr_dirty;       // ceil(fr_tiles * n_pad / 32)
   int32_t* fr_last;         // fr_tiles
-  unsigned* fr_cnt;         // 8: list sizes (3, rotating), rest-state record (slots 3 to 7)
+  unsigned* fr_cnt;         // kFrontierCounters: rest-state record (slots 3 to 7), per iteration the
+                            // list sizes and wide-item count (16 to 27, rotating)
+  const unsigned* long_mask;  // ceil(n_pad / 32): rows of at least kLongRow entries (a warp evaluates
+                              // them); NULL if there are none
+  int32_t* fr_wide;         // wide_cap: items whose dependents the whole grid pushes
+  int32_t wide_cap;
   int32_t fr_tiles;         // tiles per wave (the buffers' capacity)
   unsigned fr_key;          // nonzero tag of the buffers' layout
   const int32_t* fr_seed;   // n_seed rows nonzero in M_0: the fact rows, then the guessed rows
@@ -149,9 +154,16 @@ constexpr int kStableBlock = 256;
 // row_split: one row per warp, its entries split over the warp's 32 / W lane groups
 cudaError_t launch_stable(const StableArgs& a, int grid, bool row_split, cudaStream_t s);
 int stable_blocks_per_sm(bool row_split);
-// Frontier schedule (needs the t_ptr ... fr_key fields)
+// Frontier schedule (needs the t_ptr ... wide_cap fields)
 cudaError_t launch_stable_frontier(const StableArgs& a, int grid, cudaStream_t s);
 int stable_frontier_blocks_per_sm(int W);
+// rows with at least this many entries are evaluated by a whole warp under the frontier schedule
+constexpr int kLongRow = 64;
+// counters of the frontier schedule (StableArgs::fr_cnt)
+constexpr int kFrontierCounters = 32;
+// mask (ceil(n_pad / 32) words): bit r set iff row r has at least kLongRow entries; *any (zeroed
+// by the caller) becomes nonzero if one is
+cudaError_t build_long_rows(const int32_t* row_ptr, int32_t n_pad, unsigned* mask, unsigned* any, cudaStream_t s);
 // Transposed matrix for the frontier schedule, built on the device: cnt (n_pad + 1 ints of
 // scratch, zeroed by the caller) becomes the cursor of the fill.
 cudaError_t build_transpose(const int32_t* row_ptr, const int32_t* col, int32_t n_pad, int32_t* t_ptr, int32_t* t_idx,

@@ -57,6 +57,8 @@ struct lp_program {
   int32_t fr_nseed = 0;
   int32_t* fr_tidx = nullptr;
   unsigned* fr_cnt = nullptr;
+  unsigned* fr_long = nullptr;  // rows the frontier evaluates a warp at a time
+  bool fr_any_long = false;
   DevBuf fr_buf;
   int32_t fr_W = 0, fr_tiles = 0;
   // scratch

@@ -23,6 +23,14 @@
 // after a launch that did not finish, or after the layout changed) writes the rest state in full.
 // A record in fr_cnt tells the next launch whether it can trust the buffers: the layout tag, the
 // grid size, and how many blocks of the last launch finished.
+//
+// Dense programs (rows of hundreds of entries, atoms in thousands of bodies) get two more paths.
+// A row with at least kLongRow entries goes to a long list whose items a whole warp evaluates, its
+// lane groups splitting the entries and combining their partial AND / OR with shuffles. An item
+// whose row has more than kWideDeps dependents lists itself as wide, and after the iteration's
+// barrier the whole grid pushes those dependents (one more barrier in such an iteration) instead
+// of one lane group pushing them in sequence. Where an item takes fewer than eight lanes, a
+// warp's pushes are numbered across its items and spread over all 32 lanes.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -39,25 +47,60 @@ constexpr int kCntKey = 4;    // layout tag of the rest state
 constexpr int kCntStamp = 5;  // next unused stamp
 constexpr int kCntClean = 6;  // tiles of the buffers in the rest state
 constexpr int kCntDone = 7;   // blocks of the last launch that finished
+// Three groups of four (16-byte aligned), rotating: group t % 3 holds what iteration t produces
+// -- the sizes of the next short and long lists and the number of its wide items -- read by
+// every thread with one load after the barrier that ends the iteration. The first list is
+// iteration -1's (group 2).
+constexpr int kCntGroups = 16;
 constexpr unsigned kStampLimit = 0xF0000000u;
+// an item whose row has more dependents than this has them pushed by the whole grid
+constexpr int kWideDeps = 128;
 
 __device__ __forceinline__ uint64_t rest_word(int tag) { return tag == -2 ? ~0ull : 0ull; }
 
-// Appends to a work list staged per warp in shared memory: the winners of a step go to the
-// warp's 64-slot buffer, and the list gets them 32 at a time with one atomic on its counter (all
-// warps of the grid append to the same counter; one atomic per step serialized on it). All lanes
-// call both functions with the same n.
-__device__ __forceinline__ void staged_append(int* buf, int& n, bool flag, int value, int32_t* list, unsigned* cnt,
+__device__ __forceinline__ uint4 ld_volatile4(const unsigned* p) {
+  uint4 v;
+  asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+
+// Per-warp staging of list appends in shared memory: the winners of a step go to the warp's
+// 64-slot buffer, and the list gets them 32 at a time with one atomic on its counter (all warps
+// of the grid append to the same counter; one atomic per step serialized on it).
+__shared__ int s_stage[2][kStableBlock / 32][64];  // [short, long][warp of the block]
+
+// The two lists an iteration appends to share one buffer of cap = fr_tiles * n_pad slots: the
+// short list from the front, the long list from the back (slot cap - 1 - i holds entry i).
+// Their sizes are cnt[0] and cnt[1]. Both never hold more than cap items together, as an item
+// enters them at most once per stamp.
+struct Lists {
+  int32_t* list;
+  unsigned* cnt;
+  int n_s, n_l;  // entries staged in this warp's two buffers
+};
+
+__device__ __forceinline__ void stage_out(const StableArgs& a, int32_t* list, unsigned base, int i, int v, bool back) {
+  const long long pos = (long long)base + i;
+  list[back ? (long long)a.fr_tiles * a.n_pad - 1 - pos : pos] = v;
+}
+// One staged append; all lanes call it with the same state.
+__device__ __forceinline__ void staged_append(const StableArgs& a, Lists& L, bool back, bool flag, int value,
                                               int lane) {
   const unsigned m = __ballot_sync(FULL, flag);
+  if (m == 0u) return;
+  int* buf = s_stage[back][threadIdx.x >> 5];
+  int& n = back ? L.n_l : L.n_s;
   if (flag) buf[n + __popc(m & ((1u << lane) - 1u))] = value;
   n += __popc(m);
   __syncwarp();
   if (n >= 32) {
     unsigned base = 0;
-    if (lane == 0) base = atomicAdd(cnt, 32u);
+    if (lane == 0) base = atomicAdd(L.cnt + (back ? 1 : 0), 32u);
     base = __shfl_sync(FULL, base, 0);
-    list[base + lane] = buf[lane];
+    stage_out(a, L.list, base, lane, buf[lane], back);
     const int rest = n - 32;
     const int moved = lane < rest ? buf[32 + lane] : 0;
     __syncwarp();
@@ -66,15 +109,67 @@ __device__ __forceinline__ void staged_append(int* buf, int& n, bool flag, int v
     __syncwarp();
   }
 }
-__device__ __forceinline__ void staged_flush(int* buf, int& n, int32_t* list, unsigned* cnt, int lane) {
-  if (n > 0) {
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(cnt, (unsigned)n);
-    base = __shfl_sync(FULL, base, 0);
-    if (lane < n) list[base + lane] = buf[lane];
-    n = 0;
+__device__ __forceinline__ void staged_flush(const StableArgs& a, Lists& L, int lane) {
+#pragma unroll
+  for (int back = 0; back < 2; back++) {
+    int& n = back ? L.n_l : L.n_s;
+    if (n > 0) {
+      const int* buf = s_stage[back][threadIdx.x >> 5];
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(L.cnt + (back ? 1 : 0), (unsigned)n);
+      base = __shfl_sync(FULL, base, 0);
+      if (lane < n) stage_out(a, L.list, base, lane, buf[lane], back);
+      n = 0;
+    }
+    __syncwarp();
   }
-  __syncwarp();
+}
+
+// One push of item (tile c, row): the first push under `stamp` wins, and the winner goes to the
+// long list if the row is long, else to the short one (long_mask is NULL when no row is long).
+// All lanes call it; `valid` marks a push.
+__device__ __forceinline__ void push_item(const StableArgs& a, bool valid, int c, int row, unsigned stamp, Lists& L,
+                                          int lane) {
+  bool win = false, lg = false;
+  int item = 0;
+  if (valid) {
+    item = c * a.n_pad + row;
+    win = atomicExch(a.mark + item, stamp) != stamp;
+    if (a.long_mask) lg = (__ldg(a.long_mask + (row >> 5)) >> (row & 31)) & 1u;
+  }
+  staged_append(a, L, false, win && !lg, item, lane);
+  if (a.long_mask) staged_append(a, L, true, win && lg, item, lane);
+}
+
+// The dependents of the wide items (items whose rows have more than kWideDeps dependents, set
+// aside while the grid evaluated): with n_wide <= nwarps each item gets a run of nwarps / n_wide
+// warps whose lanes split its dependents, else each warp takes whole items.
+__device__ __forceinline__ void expand_wide(const StableArgs& a, unsigned n_wide, unsigned stamp, Lists& L, int gwarp,
+                                            int nwarps, int lane) {
+  const long long nw = n_wide;
+  long long i0, di, k, nk;
+  if (nw <= nwarps) {
+    i0 = (long long)gwarp * nw / nwarps;
+    const long long f0 = (i0 * nwarps + nw - 1) / nw, f1 = ((i0 + 1) * nwarps + nw - 1) / nw;
+    k = gwarp - f0;
+    nk = f1 - f0;
+    di = nw;  // one item
+  } else {
+    i0 = gwarp;
+    di = nwarps;
+    k = 0;
+    nk = 1;
+  }
+  for (long long i = i0; i < nw; i += di) {
+    const int item = a.fr_wide[i];
+    const int c = item / a.n_pad, row = item - c * a.n_pad;
+    const int tb = __ldg(a.t_ptr + row), nd = __ldg(a.t_ptr + row + 1) - tb;
+    for (long long d0 = k * 32; d0 < nd; d0 += nk * 32) {
+      const long long d = d0 + lane;
+      const int dep = d < nd ? __ldg(a.t_idx + tb + d) : 0;
+      push_item(a, d < nd, c, dep, stamp, L, lane);
+    }
+  }
 }
 
 // WPL consecutive 64-bit words at p (16-byte aligned when WPL > 1).
@@ -93,22 +188,23 @@ __device__ __forceinline__ void load_words(const uint64_t* p, uint64_t (&v)[WPL]
 }
 
 // Words w0 .. w0 + WPL - 1 of `row` in a tile (src is the tile's buffer), as eval_row: AND of the
-// entries' words for a rule row, OR for an OR row or a self-loop, 0 for an empty row; E entries
-// per step (their column loads, then their gathers: four entries, two with four words per lane).
-// *n_entries grows by the row's length.
+// entries' words for a rule row, OR for an OR row or a self-loop, 0 for an empty row; over the
+// entries beg + s0, beg + s0 + S, ... (S = 1: all of them; lane groups that split a long row
+// take one residue each and combine afterwards), E per step (their column loads, then their
+// gathers: four entries, two with four words per lane). Returns the row's length.
 template <int WPL>
-__device__ __forceinline__ void eval_row_words(const StableArgs& a, const uint64_t* src, int row, int w0,
-                                               uint64_t (&acc)[WPL], unsigned* n_entries) {
+__device__ __forceinline__ int eval_row_words(const StableArgs& a, const uint64_t* src, int row, int w0, int s0,
+                                              int S, uint64_t (&acc)[WPL]) {
   constexpr int E = WPL >= 4 ? 2 : 4;
   const int beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
   const bool any = (__ldg(a.any_mask + (row >> 5)) >> (row & 31)) & 1u;
   const uint64_t ident = any ? 0ull : ~0ull;
 #pragma unroll
   for (int j = 0; j < WPL; j++) acc[j] = end > beg ? ident : 0ull;
-  for (int e = beg; e < end; e += E) {
+  for (int e = beg + s0; e < end; e += E * S) {
     int cc[E];
 #pragma unroll
-    for (int q = 0; q < E; q++) cc[q] = e + q < end ? __ldg(a.col + e + q) : -1;
+    for (int q = 0; q < E; q++) cc[q] = e + q * S < end ? __ldg(a.col + e + q * S) : -1;
     uint64_t v[E][WPL];
 #pragma unroll
     for (int q = 0; q < E; q++) {
@@ -130,7 +226,7 @@ __device__ __forceinline__ void eval_row_words(const StableArgs& a, const uint64
       acc[j] = any ? (acc[j] | orv) : (acc[j] & andv);
     }
   }
-  *n_entries += (unsigned)(end - beg);
+  return end - beg;
 }
 
 // WPL: words per lane in the iterations. An item (W words) takes W / WPL lanes, so a warp
@@ -138,7 +234,6 @@ __device__ __forceinline__ void eval_row_words(const StableArgs& a, const uint64
 template <int WPL>
 __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(StableArgs a) {
   __shared__ long long s_base;
-  __shared__ int s_stage[kStableBlock / 32][64];  // per-warp list staging
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -151,7 +246,6 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
   const int rpw = 32 >> log2W;   // items per warp
   const int sub = lane >> log2W;  // item within the warp's group
   const int wl = lane & (W - 1);  // word within the tile
-  const unsigned subm = W == 32 ? FULL : (((1u << W) - 1u) << (sub * W));
   const int lpi = W / WPL;           // lanes per item in the iterations
   const int ipw = 32 / lpi;          // items per warp
   const int isub = lane / lpi;       // item within the warp
@@ -171,7 +265,7 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
     st[kCntKey] = a.fr_key;
     st[kCntGrid] = gridDim.x;
     st[kCntDone] = 0u;
-    st[0] = st[1] = st[2] = 0u;
+    for (int q = kCntGroups; q < kCntGroups + 12; q++) st[q] = 0u;
   }
   for (long long c = gtid; c < a.fr_tiles; c += nthreads) a.fr_last[c] = -1;
   if (clean < c_wave) {  // tiles clean .. c_wave - 1 into the rest state
@@ -201,12 +295,13 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
       if (!grid_barrier(ctl, ++round, 6)) return;
     }
 
+    uint4 cnt4;  // the sizes of the list an iteration works on (x: short, y: long)
+
     // ---- 1. M_0 of the guessed rows, and the first list: fact and guessed rows and the rows
     // referring to them, in every tile of the wave. A (seed row, tile) pair per eight lanes,
-    // four pairs per warp.
+    // four pairs per warp; a seed row with many dependents has them pushed by the whole grid.
     {
-      int* const buf = s_stage[threadIdx.x >> 5];
-      int n_staged = 0;
+      Lists L{a.fr_list, st + kCntGroups + 8, 0, 0};
       const int gsub = lane >> 3, gl = lane & 7;
       const long long n_pairs = (long long)a.n_seed * cw;
       for (long long base = (long long)gwarp * 4; base < n_pairs; base += (long long)nwarps * 4) {
@@ -218,6 +313,15 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
           tg = __ldg(a.row_tag + row);
           tb = __ldg(a.t_ptr + row);
           per = 1 + __ldg(a.t_ptr + row + 1) - tb;
+          if (per - 1 > kWideDeps) {  // its dependents go to the grid (if the wide list has room)
+            unsigned slot = 0;
+            if (gl == 0) {
+              slot = atomicAdd(L.cnt + 2, 1u);
+              if (slot < (unsigned)a.wide_cap) a.fr_wide[slot] = c * n_pad + row;
+            }
+            slot = __shfl_sync(0xFFu << (8 * gsub), slot, 8 * gsub);
+            if (slot < (unsigned)a.wide_cap) per = 1;
+          }
         }
         if (tg >= 0)  // a guessed row: its words of M_0 in this tile
           for (int w = gl; w < W; w += 8)
@@ -225,20 +329,24 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
         const int steps = (int)__reduce_max_sync(FULL, (unsigned)((per + 7) >> 3));
         for (int s2 = 0; s2 < steps; s2++) {
           const int d = 8 * s2 + gl;
-          bool win = false;
-          int item = 0;
-          if (d < per) {
-            item = c * n_pad + (d == 0 ? row : __ldg(a.t_idx + tb + d - 1));
-            win = atomicExch(a.mark + item, stamp) != stamp;
-          }
-          staged_append(buf, n_staged, win, item, a.fr_list, st + 0, lane);
+          const int dep = d < per ? (d == 0 ? row : __ldg(a.t_idx + tb + d - 1)) : 0;
+          push_item(a, d < per, c, dep, stamp, L, lane);
         }
       }
-      staged_flush(buf, n_staged, a.fr_list, st + 0, lane);
+      staged_flush(a, L, lane);
+      if (!grid_barrier(ctl, ++round, 6)) return;  // the first list and its wide seeds are listed
+      cnt4 = ld_volatile4(L.cnt);
+      const unsigned n_wide = min(cnt4.z, (unsigned)a.wide_cap);
+      if (n_wide > 0u) {
+        expand_wide(a, n_wide, stamp, L, gwarp, nwarps, lane);
+        staged_flush(a, L, lane);
+        if (!grid_barrier(ctl, ++round, 6)) return;
+        cnt4 = ld_volatile4(L.cnt);
+      }
     }
-    if (!grid_barrier(ctl, ++round, 6)) return;
 
-    // ---- 2. the iterations
+    // ---- 2. the iterations: the long list (rows of at least kLongRow entries, a warp per item,
+    // the warp's lane groups splitting the entries), then the short list (a lane group per item)
     const uint64_t* fin = a.X0;
     int t = 0;
     bool converged = false;
@@ -247,14 +355,71 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
       uint64_t* dst = (t & 1) ? a.X0 : a.X1;
       const int32_t* cur = a.fr_list + (size_t)(t & 1) * cap_items;
       int32_t* nxt = a.fr_list + (size_t)((t + 1) & 1) * cap_items;
-      unsigned* nxt_cnt = st + (t + 1) % 3;
+      unsigned* const grp = st + kCntGroups + 4 * (t % 3);  // what this iteration produces
+      unsigned* const wide_cnt = grp + 2;
       const unsigned nstamp = stamp + (unsigned)t + 1u;
-      // slot (t + 2) % 3 was last read as iteration t - 1's list size, before the last barrier
-      if (gtid == 0) st[(t + 2) % 3] = 0u;
-      const long long n_cur = ld_volatile(st + t % 3);
-      int* const buf = s_stage[threadIdx.x >> 5];
-      int n_staged = 0;
-      for (long long g = gwarp; g * ipw < n_cur; g += nwarps) {
+      // group (t + 1) % 3 was last read after iteration t - 2, before the last barrier
+      if (gtid == 0) {
+        unsigned* g1 = st + kCntGroups + 4 * ((t + 1) % 3);
+        g1[0] = g1[1] = g1[2] = 0u;
+      }
+      const long long n_cur = cnt4.x, n_long = cnt4.y;
+      Lists L{nxt, grp, 0, 0};
+
+      // (a) long items, one per warp
+      for (long long g = gwarp; g < n_long; g += nwarps) {
+        const int item = cur[cap_items - 1 - g];
+        const int c = item / n_pad, row = item - c * n_pad;
+        const long long o = (long long)item * W + il * WPL;
+        uint64_t acc[WPL], old[WPL];
+        load_words<WPL>(src + o, old);
+        const int tb = __ldg(a.t_ptr + row), te = __ldg(a.t_ptr + row + 1);
+        const bool any = (__ldg(a.any_mask + (row >> 5)) >> (row & 31)) & 1u;
+        const int len = eval_row_words<WPL>(a, src + (size_t)c * tile_words, row, il * WPL, isub, ipw, acc);
+        for (int off = lpi; off < 32; off <<= 1) {  // combine the lane groups
+#pragma unroll
+          for (int j = 0; j < WPL; j++) {
+            const uint64_t other = __shfl_xor_sync(FULL, acc[j], off);
+            acc[j] = any ? (acc[j] | other) : (acc[j] & other);
+          }
+        }
+        bool differs = false;
+#pragma unroll
+        for (int j = 0; j < WPL; j++) differs |= acc[j] != old[j];
+        if (isub == 0) {
+#pragma unroll
+          for (int j = 0; j < WPL; j++) dst[o + j] = acc[j];
+        }
+        if (lane == 0) {
+          n_rows++;
+          n_ent += (unsigned)len;
+        }
+        if (__ballot_sync(FULL, differs) == 0u) continue;
+        int per = 1 + te - tb;
+        if (lane == 0) {
+          atomicOr(a.fr_dirty + (item >> 5), 1u << (item & 31));
+          atomicMax(a.fr_last + c, t);
+          n_list++;
+          n_deps += (unsigned)(per - 1);
+          if (per - 1 > kWideDeps) {
+            const unsigned slot = atomicAdd(wide_cnt, 1u);
+            if (slot < (unsigned)a.wide_cap) {
+              a.fr_wide[slot] = item;
+              per = 1;
+            }
+          }
+        }
+        per = __shfl_sync(FULL, per, 0);
+        for (int d0 = 0; d0 < per; d0 += 32) {
+          const int d = d0 + lane;
+          const int dep = d < per ? (d == 0 ? row : __ldg(a.t_idx + tb + d - 1)) : 0;
+          push_item(a, d < per, c, dep, nstamp, L, lane);
+        }
+      }
+
+      // (b) short items, ipw per warp; the chunks start after the warps that took long items
+      const long long g0 = ((gwarp - n_long) % nwarps + nwarps) % nwarps;
+      for (long long g = g0; g * ipw < n_cur; g += nwarps) {
         const long long idx = g * ipw + isub;
         const int item = idx < n_cur ? cur[idx] : -1;
         uint64_t acc[WPL], old[WPL];
@@ -269,8 +434,7 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
           load_words<WPL>(src + o, old);
           tb = __ldg(a.t_ptr + row);
           te = __ldg(a.t_ptr + row + 1);
-          unsigned ne = 0;
-          eval_row_words<WPL>(a, src + (size_t)c * tile_words, row, il * WPL, acc, &ne);
+          const int len = eval_row_words<WPL>(a, src + (size_t)c * tile_words, row, il * WPL, 0, 1, acc);
 #pragma unroll
           for (int j = 0; j < WPL; j++) {
             dst[o + j] = acc[j];
@@ -278,38 +442,77 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
           }
           if (il == 0) {
             n_rows++;
-            n_ent += ne;
+            n_ent += (unsigned)len;
           }
         }
         const unsigned diff = __ballot_sync(FULL, differs);
         const bool ch = item >= 0 && (diff & imask) != 0u;
+        // pushes of the warp's changed items (each: itself and the rows referring to it), numbered
+        // across the warp and spread over all 32 lanes
         int per = 0;
-        if (ch) {
+        if (ch && il == 0) {
           per = 1 + te - tb;
-          if (il == 0) {
-            atomicOr(a.fr_dirty + (item >> 5), 1u << (item & 31));
-            atomicMax(a.fr_last + c, t);
-            n_list++;
-            n_deps += (unsigned)(per - 1);
+          atomicOr(a.fr_dirty + (item >> 5), 1u << (item & 31));
+          atomicMax(a.fr_last + c, t);
+          n_list++;
+          n_deps += (unsigned)(per - 1);
+          if (per - 1 > kWideDeps) {
+            const unsigned slot = atomicAdd(wide_cnt, 1u);
+            if (slot < (unsigned)a.wide_cap) {
+              a.fr_wide[slot] = item;
+              per = 1;
+            }
           }
         }
-        // the item and the rows referring to it, lpi lanes at a time
-        const int steps = __reduce_max_sync(FULL, (unsigned)((per + lpi - 1) / lpi));
-        for (int s = 0; s < steps; s++) {
-          const int d = s * lpi + il;
-          bool win = false;
-          int it2 = 0;
-          if (d < per) {
-            it2 = c * n_pad + (d == 0 ? row : __ldg(a.t_idx + tb + d - 1));
-            win = atomicExch(a.mark + it2, nstamp) != nstamp;
+        if (WPL >= 2 || lpi >= 8) {
+          // eight lanes per item: each item pushes itself and its dependents, eight at a time
+          per = __shfl_sync(FULL, per, isub * lpi);
+          const int steps = __reduce_max_sync(FULL, (unsigned)((per + lpi - 1) / lpi));
+          for (int s2 = 0; s2 < steps; s2++) {
+            const int d = s2 * lpi + il;
+            const int dep = d < per ? (d == 0 ? row : __ldg(a.t_idx + tb + d - 1)) : 0;
+            push_item(a, d < per, c, dep, nstamp, L, lane);
           }
-          staged_append(buf, n_staged, win, it2, nxt, nxt_cnt, lane);
+        } else {
+          // one to four lanes per item: the warp's pushes are numbered across its items and
+          // spread over all 32 lanes
+          int incl = per;  // inclusive scan (only each item's first lane is nonzero)
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += u;
+          }
+          const int total = __shfl_sync(FULL, incl, 31);
+          const int first = incl - per;  // this item's first push (valid on its first lane)
+          for (int f0 = 0; f0 < total; f0 += 32) {
+            const int f = f0 + lane;
+            int pos = 0;  // the last item whose first push is <= f
+            for (int step = ipw >> 1; step > 0; step >>= 1) {
+              const int b = __shfl_sync(FULL, first, (pos + step) * lpi);
+              if (b <= f) pos += step;
+            }
+            const int src_lane = pos * lpi;
+            const int p_item = __shfl_sync(FULL, item, src_lane);
+            const int p_tb = __shfl_sync(FULL, tb, src_lane);
+            const int d = f - __shfl_sync(FULL, first, src_lane);
+            const int pc = p_item / n_pad, prow = p_item - pc * n_pad;
+            const int dep = f < total ? (d == 0 ? prow : __ldg(a.t_idx + p_tb + d - 1)) : 0;
+            push_item(a, f < total, pc, dep, nstamp, L, lane);
+          }
         }
       }
-      staged_flush(buf, n_staged, nxt, nxt_cnt, lane);
-      if (!grid_barrier(ctl, ++round, 6)) return;
+      staged_flush(a, L, lane);
+      if (!grid_barrier(ctl, ++round, 6)) return;  // the next lists and this iteration's wide items
+      cnt4 = ld_volatile4(grp);
+      const unsigned n_wide = min(cnt4.z, (unsigned)a.wide_cap);
+      if (n_wide > 0u) {  // the wide items' dependents join the next lists
+        expand_wide(a, n_wide, nstamp, L, gwarp, nwarps, lane);
+        staged_flush(a, L, lane);
+        if (!grid_barrier(ctl, ++round, 6)) return;
+        cnt4 = ld_volatile4(grp);
+      }
       fin = dst;
-      if (ld_volatile(nxt_cnt) == 0u) {
+      if (cnt4.x == 0u && cnt4.y == 0u) {
         converged = true;
         ++t;
         break;
@@ -453,7 +656,8 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
         }
       }
     }
-    if (gtid < 3) st[gtid] = 0u;  // every read of the list sizes was before the last barrier
+    // every read of the list sizes and wide counts was before the last barrier
+    if (gtid < 12) st[kCntGroups + gtid] = 0u;
     for (long long c = gtid; c < cw; c += nthreads) a.fr_last[c] = -1;
     if (!converged) break;  // every block takes this branch
     if (w0 + c_wave < a.n_tiles && !grid_barrier(ctl, ++round, 6)) return;
@@ -480,6 +684,17 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
 }  // namespace
 
 namespace {
+__global__ void long_rows_kernel(const int32_t* __restrict__ row_ptr, int32_t n_pad, unsigned* __restrict__ mask,
+                                 unsigned* __restrict__ any) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool lg = r < n_pad && row_ptr[r + 1] - row_ptr[r] >= kLongRow;
+  const unsigned m = __ballot_sync(FULL, lg);
+  if ((threadIdx.x & 31) == 0 && r < n_pad) {
+    mask[r >> 5] = m;
+    if (m) atomicOr(any, 1u);
+  }
+}
+
 // words per lane: W <= 8 one (W lanes per item), W = 16 two, W = 32 four (eight lanes per item)
 const void* frontier_entry(int W) {
   if (W >= 32) return (const void*)stable_frontier_kernel<4>;
@@ -492,6 +707,12 @@ cudaError_t launch_stable_frontier(const StableArgs& a, int grid, cudaStream_t s
   StableArgs copy = a;
   void* params[] = {&copy};
   return cudaLaunchCooperativeKernel(frontier_entry(a.W), dim3(grid), dim3(kStableBlock), params, 0, s);
+}
+
+cudaError_t build_long_rows(const int32_t* row_ptr, int32_t n_pad, unsigned* mask, unsigned* any, cudaStream_t s) {
+  if (n_pad <= 0) return cudaSuccess;
+  long_rows_kernel<<<(n_pad + 255) / 256, 256, 0, s>>>(row_ptr, n_pad, mask, any);
+  return cudaGetLastError();
 }
 
 int stable_frontier_blocks_per_sm(int W) {

@@ -14,7 +14,7 @@ import pytest
 import oracle
 import paper_2009_10247_gb300 as lp
 from tests.helpers import golden, program_fingerprint
-from workloads import normal_program, parse, small_definite, tiny_random
+from workloads import normal_program, parse, small_definite, table1_program, tiny_random
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -189,6 +189,65 @@ def test_frontier_schedule_matches_oracle(W):
         assert (fr["max_tile_iters"], fr["sum_tile_iters"]) == (full["max_tile_iters"], full["sum_tile_iters"])
 
 
+def _hub_program(seed, n=400, n_rules=1500, k=6):
+    # normal program with hot atoms and long bodies: atoms 0-3 sit in every rule body (thousands of
+    # dependents each), a third of the rules have 70-200 body atoms (rows a warp evaluates), the
+    # rest 1-3; facts 10-39; k negated atoms as in the Table 5/6 programs
+    rng = np.random.default_rng(seed)
+    heads, bodies = [], []
+    for a in range(10, 40):
+        heads.append(a)
+        bodies.append([])
+    for r in range(n_rules):
+        ln = int(rng.integers(70, 200)) if r % 3 == 0 else int(rng.integers(1, 4))
+        body = set(rng.choice(np.arange(4, n), size=ln, replace=False).tolist()) | {r % 4}
+        heads.append(int(rng.integers(0, n)))
+        bodies.append(sorted(body))
+    for a in range(4):  # the hubs become true early
+        heads.append(a)
+        bodies.append([10 + a])
+    neg = rng.choice(np.arange(40, n), size=k, replace=False)
+    text = []
+    negated = set()
+    for h, b in zip(heads, bodies):
+        lits = []
+        for x in b:
+            if x in neg and x not in negated and len(b) > 1:
+                negated.add(x)
+                lits.append(f"not a{x}")
+            else:
+                lits.append(f"a{x}")
+        text.append(f"a{h}." if not lits else f"a{h} :- {', '.join(lits)}.")
+    return parse(" ".join(text), atoms=[f"a{i}" for i in range(n)])
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+@pytest.mark.parametrize("wide_items", [None, "0", "3"])
+def test_frontier_dense_rows_and_hot_atoms(W, wide_items, monkeypatch):
+    # programs whose rows have up to ~200 entries (the long list: a warp per row) and whose atoms
+    # have hundreds to thousands of dependents (pushed by the whole grid; with a wide list of 0 or
+    # 3 slots the warps push what does not fit): the oracle's stable bits and models, and the full
+    # sweep's tile iterations
+    if wide_items is not None:
+        monkeypatch.setenv("LP_FRONTIER_WIDE_ITEMS", wide_items)
+    progs = [table1_program(61, 600, 1500, dense=True, k=6), table1_program(62, 1600, 4000, dense=True, k=8),
+             _hub_program(63), _hub_program(64, k=8)]
+    for prog in progs:
+        st4, m4, _ = oracle.stable_models_alg23(prog)
+        with lp.Program.from_program(prog) as P:
+            P.set_schedule(stable_tile_words=W, stable_frontier=0)
+            gpu_stable(P)
+            full = P.last_stats()
+            P.set_schedule(stable_frontier=1)
+            for rep in range(2):  # the second solve starts from the rest state the first left
+                st, models, ns = gpu_stable(P, max_models=16)
+                fr = P.last_stats()
+                assert np.array_equal(st, st4) and ns == int(st4.sum()), rep
+                assert np.array_equal(models, m4[st4][:16]), rep
+                assert (fr["max_tile_iters"], fr["sum_tile_iters"]) == (full["max_tile_iters"],
+                                                                        full["sum_tile_iters"]), rep
+
+
 def test_frontier_schedule_explicit_guesses():
     p = normal_program(seed=6, n=2000, n_rules=6000, k=12, per_atom=3)
     g = np.random.default_rng(2).integers(0, 1 << 12, 500).astype(np.uint64)
@@ -201,9 +260,10 @@ def test_frontier_schedule_explicit_guesses():
 
 def _frontier_tile_bytes(P, W):
     # one tile's share of the frontier buffers: two iterate buffers of W words per row, a stamp
-    # and two list slots per row, the changed-row bitmap, a per-tile counter (and 64 spare bytes)
+    # and two list slots per row, the changed-row bitmap, a per-tile counter, the wide-item list
+    # (n_pad / 16 + 64 slots) and 64 spare bytes
     n_pad = (P.info["n_prime"] + 63) // 64 * 64
-    return 2 * n_pad * W * 8 + 12 * n_pad + (n_pad + 31) // 32 * 4 + 4 + 64
+    return 2 * n_pad * W * 8 + 12 * n_pad + (n_pad + 31) // 32 * 4 + 4 + (n_pad // 16 + 64) * 4 + 64
 
 
 def test_frontier_waves_and_rest_state(monkeypatch):

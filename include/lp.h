@@ -52,6 +52,9 @@ typedef enum {
 #define LP_COMPILE_ON_HOST 2u   /* standardize on the host's threads and upload the matrix
                                    (default: the rules are uploaded and standardized on the
                                    GPU; both give the same matrix, array for array)          */
+#define LP_COMPILE_ON_DEVICE 4u /* standardize on the GPU even a small program (by default
+                                   programs of at most 16,384 rules plus body literals are
+                                   standardized on one host thread, which is faster there)   */
 
 /* lp_least_model flags */
 #define LP_ROWS 1u   /* init/out are over all n' rows of M_P in canonical order (see below)   */
@@ -111,11 +114,14 @@ typedef struct {
  * body_off[0] = 0 and body_off non-decreasing; body_neg (nullable) marks negated literals with
  * a non-zero byte. An empty body is a fact. n_rules, the body literals, n_prime and nnz must
  * stay below 2^31. By default the rules are copied to the device as given and standardized
- * there by kernels on cuda_stream; with LP_COMPILE_ON_HOST (or LP_COMPILE_HOST_ONLY) the host
- * compiler runs on OpenMP threads. Both build the same arrays, and neither depends on the number
- * of threads.
- * flags: 0, LP_COMPILE_ON_HOST, or LP_COMPILE_HOST_ONLY (no device memory is touched; solves on
- * such a handle return LP_ERR_INVALID). cuda_stream: stream of the uploads and the device
+ * there by kernels on cuda_stream, except that a program of at most 16,384 rules plus body
+ * literals is standardized on one host thread and uploaded; with LP_COMPILE_ON_HOST (or
+ * LP_COMPILE_HOST_ONLY) the host compiler runs on OpenMP threads (one for such a small
+ * program), with LP_COMPILE_ON_DEVICE always on the device. All build the same arrays, and none
+ * depends on the number of threads.
+ * flags: 0, LP_COMPILE_ON_HOST, LP_COMPILE_ON_DEVICE, or LP_COMPILE_HOST_ONLY (no device memory
+ * is touched; solves on such a handle return LP_ERR_INVALID); LP_COMPILE_ON_DEVICE with another
+ * flag is LP_ERR_INVALID. cuda_stream: stream of the uploads and the device
  * compile; the call returns after it has finished. On success *out receives a new
  * handle (free it with lp_free). Errors: LP_ERR_INVALID (malformed program), LP_ERR_OOM,
  * LP_ERR_CUDA; *out is then NULL.

@@ -48,6 +48,41 @@ namespace {
 std::atomic<int64_t> g_fail_alloc_after{-1};  // lp_debug_fail_alloc: -1 = off
 }
 
+namespace {
+// Small device buffers of the handles are kept for reuse instead of freed: a program compiled,
+// solved and freed in a loop would otherwise spend most of its time in cudaMalloc and cudaFree
+// (each a driver call; cudaFree waits for the device). Requests up to 4 MiB are rounded up to a
+// power of two and served from per-device free lists; freed blocks go back to those lists while
+// they hold at most 32 MiB in all, and are never returned to the driver before the process
+// exits. LP_ALLOC_CACHE=0 turns the cache off.
+constexpr int kCacheMinLog2 = 9;   // 512 B
+constexpr int kCacheMaxLog2 = 22;  // 4 MiB
+constexpr size_t kCacheCapBytes = 32ull << 20;
+struct AllocCache {
+  std::mutex mu;
+  std::map<void*, std::pair<int, int>> live;           // cached-size blocks in use: (device, log2 size)
+  std::map<std::pair<int, int>, std::vector<void*>> free;  // (device, log2 size) -> blocks
+  size_t held = 0;                                      // bytes on the free lists
+  std::vector<DeviceCtl*> pinned;                       // host control blocks (pinned)
+};
+AllocCache& alloc_cache() {
+  static AllocCache* c = new AllocCache;  // outlives every handle, never destroyed
+  return *c;
+}
+bool alloc_cache_on() {
+  static const bool on = [] {
+    const char* env = std::getenv("LP_ALLOC_CACHE");
+    return !(env && env[0] == '0');
+  }();
+  return on;
+}
+int ceil_log2(size_t x) {
+  int l = 0;
+  while ((size_t(1) << l) < x) l++;
+  return l;
+}
+}  // namespace
+
 cudaError_t device_malloc(void** ptr, size_t bytes) {
   int64_t left = g_fail_alloc_after.load();
   while (left >= 0) {
@@ -59,7 +94,97 @@ cudaError_t device_malloc(void** ptr, size_t bytes) {
       break;
     }
   }
-  return cudaMalloc(ptr, bytes);
+  if (!alloc_cache_on() || bytes > (size_t(1) << kCacheMaxLog2)) return cudaMalloc(ptr, bytes);
+  const int l = std::max(kCacheMinLog2, ceil_log2(bytes));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  AllocCache& c = alloc_cache();
+  {
+    std::lock_guard<std::mutex> g(c.mu);
+    auto it = c.free.find({dev, l});
+    if (it != c.free.end() && !it->second.empty()) {
+      *ptr = it->second.back();
+      it->second.pop_back();
+      c.held -= size_t(1) << l;
+      c.live[*ptr] = {dev, l};
+      return cudaSuccess;
+    }
+  }
+  e = cudaMalloc(ptr, size_t(1) << l);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(c.mu);
+  c.live[*ptr] = {dev, l};
+  return cudaSuccess;
+}
+
+// Frees device_malloc's buffers: once the device is idle (what cudaFree would wait for), cached
+// sizes go back to the free lists, the rest to the driver.
+void device_free_all(void* const* ptrs, size_t n) {
+  AllocCache& c = alloc_cache();
+  std::vector<std::pair<void*, std::pair<int, int>>> keep;
+  std::vector<void*> release;
+  {
+    std::lock_guard<std::mutex> g(c.mu);
+    for (size_t i = 0; i < n; i++) {
+      if (!ptrs[i]) continue;
+      auto it = c.live.find(ptrs[i]);
+      if (it == c.live.end()) {
+        release.push_back(ptrs[i]);
+      } else {
+        keep.push_back({ptrs[i], it->second});
+        c.live.erase(it);
+      }
+    }
+  }
+  if (!keep.empty()) {
+    // the blocks' devices finish their work (all blocks of a handle share its device)
+    int cur = 0;
+    bool ok = cudaGetDevice(&cur) == cudaSuccess;
+    const int dev = keep[0].second.first;
+    if (ok && dev != cur) ok = cudaSetDevice(dev) == cudaSuccess;
+    ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+    if (dev != cur) cudaSetDevice(cur);
+    cudaGetLastError();
+    std::lock_guard<std::mutex> g(c.mu);
+    for (auto& [q, dl] : keep) {
+      const size_t sz = size_t(1) << dl.second;
+      if (ok && dl.first == dev && c.held + sz <= kCacheCapBytes) {
+        c.free[dl].push_back(q);
+        c.held += sz;
+      } else {
+        release.push_back(q);
+      }
+    }
+  }
+  for (void* q : release) cudaFree(q);
+}
+void device_free(void* ptr) { device_free_all(&ptr, 1); }
+
+// Pinned host control block of a handle (reused across handles like the device buffers).
+cudaError_t pinned_ctl_alloc(DeviceCtl** out) {
+  if (alloc_cache_on()) {
+    AllocCache& c = alloc_cache();
+    std::lock_guard<std::mutex> g(c.mu);
+    if (!c.pinned.empty()) {
+      *out = c.pinned.back();
+      c.pinned.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaMallocHost((void**)out, sizeof(DeviceCtl));
+}
+void pinned_ctl_free(DeviceCtl* q) {
+  if (!q) return;
+  if (alloc_cache_on()) {
+    AllocCache& c = alloc_cache();
+    std::lock_guard<std::mutex> g(c.mu);
+    if (c.pinned.size() < 64) {
+      c.pinned.push_back(q);
+      return;
+    }
+  }
+  cudaFreeHost(q);
 }
 
 cudaError_t device_malloc_async(void** ptr, size_t bytes, cudaStream_t s) {
@@ -98,7 +223,7 @@ cudaError_t device_malloc_async(void** ptr, size_t bytes, cudaStream_t s) {
 lp_status ensure(lp_program* p, DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return LP_OK;
   if (b.p) {
-    cudaFree(b.p);
+    device_free(b.p);
     p->device_bytes -= (int64_t)b.bytes;
     b.p = nullptr;
     b.bytes = 0;
@@ -129,7 +254,7 @@ lp_status ensure_scratch(lp_program* p) {
   if (!p->ctl) {
     lp_status st = dalloc(p, &p->ctl, 1);
     if (st != LP_OK) return st;
-    LP_CUDA(cudaMallocHost((void**)&p->h_ctl, sizeof(DeviceCtl)));
+    LP_CUDA(pinned_ctl_alloc(&p->h_ctl));
     std::memset(p->h_ctl, 0, sizeof(DeviceCtl));
   }
   if (!p->ev0) {
@@ -147,9 +272,8 @@ void release(lp_program* p) {
                   p->fr_tptr, p->fr_tidx, p->fr_cnt, p->fr_long, p->fr_buf.p, p->dc_kind, p->dc_rule, p->fr_seed,
                   p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p,
                   p->tune_out.p, p->tune_in.p};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
-  if (p->h_ctl) cudaFreeHost(p->h_ctl);
+  device_free_all(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
+  pinned_ctl_free(p->h_ctl);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
 }
@@ -205,12 +329,12 @@ lp_status ensure_sliced_layout(lp_program* p, cudaStream_t s) {
   lp_status st;
   int32_t* cnt = nullptr;
   auto fail_clean = [&](lp_status code) {
-    if (cnt) cudaFree(cnt);
+    if (cnt) device_free(cnt);
     void** ptrs[] = {(void**)&p->sl_q, (void**)&p->sl_qinv, (void**)&p->sl_hdr, (void**)&p->sl_col,
                      (void**)&p->sl_fact_row, (void**)&p->sl_perm};
     for (void** q : ptrs)
       if (*q) {
-        cudaFree(*q);
+        device_free(*q);
         *q = nullptr;
       }
     return code;
@@ -240,7 +364,7 @@ lp_status ensure_sliced_layout(lp_program* p, cudaStream_t s) {
   e = build_sliced_pass2(p->row_ptr, p->col, p->sl_q, p->sl_qinv, p->sl_hdr, hm.n_pad, p->sl_col, p->fact_row,
                          hm.n_fact_rows, p->sl_fact_row, p->perm, hm.n_prime, p->sl_perm, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(cnt);
+  device_free(cnt);
   cnt = nullptr;
   if (e != cudaSuccess) return fail_clean(cuda_fail(e, "sliced layout pass 2"));
   count_launches(n_words > 0 ? 6 : 0);
@@ -344,7 +468,10 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   NvtxRange nvtx("lp_compile");
   if (!out) return fail(LP_ERR_INVALID, "out must not be NULL");
   *out = nullptr;
-  if (flags & ~(LP_COMPILE_HOST_ONLY | LP_COMPILE_ON_HOST)) return fail(LP_ERR_INVALID, "unknown flags");
+  if (flags & ~(LP_COMPILE_HOST_ONLY | LP_COMPILE_ON_HOST | LP_COMPILE_ON_DEVICE))
+    return fail(LP_ERR_INVALID, "unknown flags");
+  if ((flags & LP_COMPILE_ON_DEVICE) && (flags & (LP_COMPILE_HOST_ONLY | LP_COMPILE_ON_HOST)))
+    return fail(LP_ERR_INVALID, "LP_COMPILE_ON_DEVICE excludes the host flags");
   auto t0 = std::chrono::steady_clock::now();
   lp_program* p = new (std::nothrow) lp_program();
   if (p) {
@@ -354,12 +481,17 @@ lp_status lp_compile(int32_t n_atoms, int64_t n_rules, const int32_t* head, cons
   if (!p) return fail(LP_ERR_OOM, "host allocation failed");
   std::string err;
   lp_status st;
-  const bool on_host = (flags & (LP_COMPILE_HOST_ONLY | LP_COMPILE_ON_HOST)) != 0;
+  // rules plus body literals (a malformed body_off is left to the compilers to reject)
+  const int64_t size = n_rules > 0 && body_off ? n_rules + body_off[n_rules] : std::max<int64_t>(n_rules, 0);
+  const bool small = size >= 0 && size <= kSmallCompile;
+  const bool on_host = (flags & (LP_COMPILE_HOST_ONLY | LP_COMPILE_ON_HOST)) != 0 ||
+                       (small && !(flags & LP_COMPILE_ON_DEVICE));
   if (!on_host) return compile_device_handle(p, n_atoms, n_rules, head, body_off, body_atom, body_neg,
                                              (cudaStream_t)cuda_stream, t0, out);
   {
     NvtxRange nvtx_host("lp_compile: standardize");
-    st = compile_host(n_atoms, n_rules, head, body_off, body_atom, body_neg, p->hm, err);
+    st = small ? compile_host_serial(n_atoms, n_rules, head, body_off, body_atom, body_neg, p->hm, err)
+               : compile_host(n_atoms, n_rules, head, body_off, body_atom, body_neg, p->hm, err);
   }
   if (st != LP_OK) {
     delete p;
@@ -430,10 +562,9 @@ lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
   int32_t* cnt = nullptr;
   unsigned* counters = nullptr;
   auto fail_clean = [&](lp_status code) {
-    if (cnt) cudaFree(cnt);
+    if (cnt) device_free(cnt);
     void* ptrs[] = {p->fr_tptr, p->fr_tidx, p->fr_seed, p->fr_long, counters};
-    for (void* q : ptrs)
-      if (q) cudaFree(q);
+    device_free_all(ptrs, 5);
     p->fr_tptr = p->fr_tidx = p->fr_seed = nullptr;
     p->fr_long = nullptr;
     return code;
@@ -464,7 +595,7 @@ lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
   if (e == cudaSuccess && hm.n_pad > 0)
     e = cudaMemcpyAsync(&any_long, counters + kFrontierCounters - 1, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(cnt);
+  device_free(cnt);
   cnt = nullptr;
   if (e != cudaSuccess) return fail_clean(cuda_fail(e, "frontier transpose"));
   count_launches(hm.n_pad > 0 ? 4 : 0);
@@ -491,7 +622,7 @@ lp_status ensure_frontier_buffers(lp_program* p, int W, int32_t tiles, cudaStrea
   if (p->fr_buf.p && p->fr_W == W && p->fr_tiles == tiles) return LP_OK;
   const size_t bytes = (size_t)frontier_bytes(p->hm.n_pad, W, tiles);
   if (p->fr_buf.p && p->fr_buf.bytes < bytes) {
-    cudaFree(p->fr_buf.p);
+    device_free(p->fr_buf.p);
     p->device_bytes -= (int64_t)p->fr_buf.bytes;
     p->fr_buf = DevBuf{};
   }

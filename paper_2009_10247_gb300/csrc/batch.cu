@@ -733,8 +733,7 @@ void batch_release(lp_batch* b) {
                   b->d_x1,    b->d_nstable, b->d_iters, b->d_jobs, b->d_slot_job, b->d_job_bar, b->d_ctl, b->d_stage,
                   b->d_tptr,  b->d_tidx, b->d_seed, b->d_mark, b->d_list, b->d_fcnt, b->d_dirty, b->d_clean,
                   b->d_epoch};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  device_free_all(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
 }
 
 template <typename T>

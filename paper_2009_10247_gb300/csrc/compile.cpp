@@ -744,4 +744,19 @@ lp_status build_stream_layout(HostMatrix& hm, std::string& err) {
   return LP_OK;
 }
 
+lp_status compile_host_serial(int32_t n, int64_t n_rules, const int32_t* head, const int64_t* body_off,
+                              const int32_t* body_atom, const uint8_t* body_neg, HostMatrix& hm, std::string& err) {
+  lp_status st = LP_OK;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(1)
+  {
+    omp_set_num_threads(1);  // this task's regions (and the parallel sort) run on one thread
+    st = compile_host(n, n_rules, head, body_off, body_atom, body_neg, hm, err);
+  }
+#else
+  st = compile_host(n, n_rules, head, body_off, body_atom, body_neg, hm, err);
+#endif
+  return st;
+}
+
 }  // namespace lp

@@ -8,7 +8,9 @@
 // stored column-major at their width, a row's entries reduced as one AND with an XOR mask for OR
 // rows) into shared memory once, keeps both iterate vectors there, and meets at a block barrier
 // per iteration, so the loop touches global memory only to load the layout, read the initial
-// facts and write the projected fixpoint. Warps take groups from a shared counter.
+// facts and write the projected fixpoint. Warps take groups round-robin (the groups are
+// ordered by width, so each warp gets a similar mix; a shared work counter cost one more block
+// barrier and an atomic per iteration).
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -42,7 +44,7 @@ __device__ __forceinline__ uint32_t rot(uint32_t x, int j) { return __funnelshif
 
 __global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArgs a, SlicedLayout S) {
   extern __shared__ int4 s_raw[];
-  __shared__ int s_bad, s_next;
+  __shared__ int s_bad;
   const BlockLayout B = block_layout(a.n_words, S.n_groups, S.total_entries);
   uint32_t* const s_x0 = reinterpret_cast<uint32_t*>(s_raw + B.x0);
   uint32_t* const s_x1 = reinterpret_cast<uint32_t*>(s_raw + B.x1);
@@ -90,9 +92,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArg
   for (; it < a.max_iters; ++it) {
     const uint32_t* src = (it & 1) ? s_x1 : s_x0;
     uint32_t* dst = (it & 1) ? s_x0 : s_x1;
-    if (t == 0) s_next = nwarp;
-    __syncthreads();
-    // warp w starts with group w and takes further groups from the counter
+    // warp w takes groups w, w + nwarp, ...
     bool changed = false;
     int g = warp;
     while (g < S.n_groups) {  // uniform in the warp
@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArg
       const uint32_t inv2 = ((uint32_t)h1.z >> lane) & 1u ? FULL : 0u, inv3 = ((uint32_t)h1.w >> lane) & 1u ? FULL : 0u;
       uint32_t a0 = FULL, a1 = FULL, a2 = FULL, a3 = FULL;
       const int4* e = s_col + h0.x / 4 + lane;
+#pragma unroll 4  // the entries' loads of four steps in flight at once
       for (int k = 0; k < K; k++) {
         const int4 c = e[32 * k];
         a0 &= rot(src[c.x >> 5], c.x) ^ inv0;
@@ -119,8 +120,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) fixpoint_block_kernel(FixArg
         changed |= word != src[w0 + lane];
         dst[w0 + lane] = word;
       }
-      if (lane == 0) g = atomicAdd(&s_next, 1);
-      g = __shfl_sync(FULL, g, 0);
+      g += nwarp;
     }
     fin = dst;
     if (!__syncthreads_or(changed)) {

@@ -112,6 +112,13 @@ constexpr uint32_t kHasSelf = 0x40000000u;   // header (first int) flag: the wor
 // Builds the matrix; returns LP_OK or LP_ERR_INVALID / LP_ERR_OOM with a message in err.
 lp_status compile_host(int32_t n_atoms, int64_t n_rules, const int32_t* head, const int64_t* body_off,
                        const int32_t* body_atom, const uint8_t* body_neg, HostMatrix& hm, std::string& err);
+// compile_host on the calling thread alone (its parallel regions get teams of one): for small
+// programs, where waking a thread team costs more than the work. Same result.
+lp_status compile_host_serial(int32_t n_atoms, int64_t n_rules, const int32_t* head, const int64_t* body_off,
+                              const int32_t* body_atom, const uint8_t* body_neg, HostMatrix& hm, std::string& err);
+// Programs with at most this many rules plus body literals are standardized by
+// compile_host_serial unless lp_compile is asked for the device.
+constexpr int64_t kSmallCompile = 1 << 14;
 // The streamed layout (desc, word_hdr, and_col, groups) from hm.row_ptr / hm.col, which the
 // caller fills with the internal CSR first.
 lp_status build_stream_layout(HostMatrix& hm, std::string& err);

@@ -106,8 +106,12 @@ void count_launches(int64_t n);  // add to lp_launch_count()
   } while (0)
 
 // cudaMalloc behind the allocation-failure hook (lp_debug_fail_alloc): every device allocation
-// of liblp's handles goes through here.
+// of liblp's handles goes through here, and small ones are reused across handles (api.cu).
 cudaError_t device_malloc(void** ptr, size_t bytes);
+// Frees what device_malloc returned (NULL entries are skipped); waits for the device first, as
+// cudaFree does.
+void device_free_all(void* const* ptrs, size_t n);
+void device_free(void* ptr);
 // The standardization of lp_compile on the device (compile_device.cu): fills the device arrays
 // of the handle and hm's sizes and small tables; perm, canon_kind and canon_rule reach hm on
 // demand through ensure_host_tables.

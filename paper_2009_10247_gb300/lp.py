@@ -17,6 +17,7 @@ STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_OOM", "LP_ERR_CUDA", "LP_ERR_
 LP_ROWS, LP_TIMING = 1, 2
 LP_COMPILE_HOST_ONLY = 1
 LP_COMPILE_ON_HOST = 2
+LP_COMPILE_ON_DEVICE = 4
 LP_BATCH_FULL_SWEEP = 1
 
 
@@ -211,9 +212,11 @@ class Program:
     """A compiled program (owns the liblp handle)."""
 
     def __init__(self, n_atoms, head, body_off, body_atom, body_neg=None, stream=None, host_only=False,
-                 on_host=False):
+                 on_host=False, on_device=False):
         """host_only: the host compiler alone, no device memory; on_host: the host compiler, then
-        the matrix uploaded (default: the rules uploaded and standardized on the device)."""
+        the matrix uploaded; on_device: the rules uploaded and standardized on the device (the
+        default, except for programs of at most 16,384 rules plus body literals, which one host
+        thread standardizes)."""
         L = load()
         self._keep = [np.ascontiguousarray(head, dtype=np.int32), np.ascontiguousarray(body_off, dtype=np.int64),
                       np.ascontiguousarray(body_atom, dtype=np.int32),
@@ -221,6 +224,8 @@ class Program:
         h, off, atom, neg = self._keep
         self._h = ctypes.c_void_p()
         flags = LP_COMPILE_HOST_ONLY if host_only else (LP_COMPILE_ON_HOST if on_host else 0)
+        if on_device:
+            flags |= LP_COMPILE_ON_DEVICE
         _check(L.lp_compile(int(n_atoms), len(h), _ptr(h), _ptr(off), _ptr(atom), _ptr(neg), flags,
                             None if host_only else _stream(stream),
                             ctypes.byref(self._h)))
@@ -228,9 +233,9 @@ class Program:
         self.info = self._info()
 
     @classmethod
-    def from_program(cls, prog, stream=None, host_only=False, on_host=False):
+    def from_program(cls, prog, stream=None, host_only=False, on_host=False, on_device=False):
         return cls(prog.n_atoms, prog.head, prog.body_off, prog.body_atom, getattr(prog, "body_neg", None), stream,
-                   host_only, on_host)
+                   host_only, on_host, on_device)
 
     INTERNAL = {"row_ptr": (0, np.int32), "col": (1, np.int32), "perm": (2, np.int32), "any_mask": (3, np.uint32),
                 "row_tag": (4, np.int32), "fact_row": (5, np.int32), "fact_owner": (6, np.int32),

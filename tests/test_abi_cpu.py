@@ -165,6 +165,25 @@ def test_schedule_get_set_validates(lib):
             P.autotune()  # a host-only handle cannot run solves
 
 
+def test_compile_flags_validate_without_gpu(lib):
+    # LP_COMPILE_ON_DEVICE with a host flag and unknown flags fail before any device use; a small
+    # program compiled on the host (one thread) gives the oracle's matrix
+    out = ctypes.c_void_p()
+    head = np.array([0, 1], np.int32)
+    off = np.array([0, 0, 1], np.int64)
+    atom = np.array([0], np.int32)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    for flags in (lp.LP_COMPILE_ON_DEVICE | lp.LP_COMPILE_HOST_ONLY, lp.LP_COMPILE_ON_DEVICE | lp.LP_COMPILE_ON_HOST,
+                  8, 16):
+        assert lib.lp_compile(2, 2, ptr(head), ptr(off), ptr(atom), None, flags, None, ctypes.byref(out)) == 1
+        assert not out.value
+    prog = small_definite(3)
+    with lp.Program.from_program(prog, host_only=True) as P:
+        m = P.export_matrix()
+    s = oracle.standardize(prog)
+    assert np.array_equal(m["row_ptr"], s.row_ptr) and np.array_equal(m["col"], s.col)
+
+
 def test_batch_entry_points_validate_without_gpu(lib):
     out = ctypes.c_void_p()
     one = np.array([2], np.int32)

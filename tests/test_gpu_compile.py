@@ -1,5 +1,5 @@
-"""The standardization on the GPU (the default of lp_compile) against the host compiler
-(LP_COMPILE_ON_HOST): the same matrix of Sec. 2.1-2.2 (Eq. 4 barred atoms, bodies as sets, OR
+"""The standardization on the GPU (LP_COMPILE_ON_DEVICE, the default of lp_compile above 65,536
+rules plus body literals) against the host compiler (LP_COMPILE_ON_HOST): the same matrix of Sec. 2.1-2.2 (Eq. 4 barred atoms, bodies as sets, OR
 rules for heads with several rules, Def. 2 / Def. 7 rows) in the same internal order, array for
 array, on programs that reach every branch: negation, facts, duplicate body atoms, multi-rule
 heads, bodies long enough for the sorted-segment path, atoms that head nothing, empty programs;
@@ -23,7 +23,7 @@ INFO_KEYS = ("n_atoms", "n_rules", "n_prime", "nnz", "n_barred", "n_aux", "k", "
 
 
 def _same_compile(prog):
-    with lp.Program.from_program(prog) as D, lp.Program.from_program(prog, on_host=True) as H:
+    with lp.Program.from_program(prog, on_device=True) as D, lp.Program.from_program(prog, on_host=True) as H:
         for key in INFO_KEYS:
             assert D.info[key] == H.info[key], key
         for name in lp.Program.INTERNAL:
@@ -85,12 +85,12 @@ def test_solves_on_a_device_compiled_handle():
     # the least model and the stable set of programs compiled on the device, against the oracle
     for prog in (PROGRAMS["long_bodies"](), PROGRAMS["dense_table3"](), small_definite(3)):
         want, want_it = oracle.least_model(prog)
-        with lp.Program.from_program(prog) as P:
+        with lp.Program.from_program(prog, on_device=True) as P:
             got, it = gpu_least_model(P)
         assert it == want_it and np.array_equal(got, want)
     prog = PROGRAMS["normal"]()
     st4, _, _ = oracle.stable_models_alg23(prog)
-    with lp.Program.from_program(prog) as P:
+    with lp.Program.from_program(prog, on_device=True) as P:
         st, _, ns = gpu_stable(P)
     assert np.array_equal(st, st4) and ns == int(st4.sum())
 
@@ -107,12 +107,12 @@ def test_malformed_program_same_error(bad):
     else:
         off[2] = 0
     msgs = []
-    for on_host in (False, True):
+    for kw in ({"on_device": True}, {"on_host": True}, {}):
         with pytest.raises(lp.LPError) as e:
-            lp.Program(3, head, off, atom, on_host=on_host)
+            lp.Program(3, head, off, atom, **kw)
         assert e.value.status == lp.ERR_INVALID
         msgs.append(str(e.value))
-    assert msgs[0] == msgs[1]
+    assert msgs[0] == msgs[1] == msgs[2]
 
 
 def test_host_side_users_of_a_device_compile():
@@ -121,7 +121,7 @@ def test_host_side_users_of_a_device_compile():
     prog = small_definite(5)
     want, want_it = oracle.least_model(prog)
     s = oracle.standardize(prog)
-    with lp.Program.from_program(prog) as P, lp.Program.from_program(prog, on_host=True) as H:
+    with lp.Program.from_program(prog, on_device=True) as P, lp.Program.from_program(prog, on_host=True) as H:
         P.set_schedule(fixpoint_kernel=1, fixpoint_stage=0)
         got, it = gpu_least_model(P)
         assert it == want_it and np.array_equal(got, want)
@@ -132,3 +132,17 @@ def test_host_side_users_of_a_device_compile():
             assert it_r == want_it_r and np.array_equal(rows, want_rows.astype(bool))
         md, mh = P.export_matrix(), H.export_matrix()
         assert all(np.array_equal(md[k], mh[k]) for k in md)
+
+
+def test_small_program_default_compile():
+    # a program of at most 16,384 rules plus body literals is standardized on one host thread by
+    # default; the handle equals the device-compiled one and solves as the oracle does
+    prog = small_definite(4)
+    assert prog.n_rules + int(prog.body_off[-1]) <= 1 << 14
+    want, want_it = oracle.least_model(prog)
+    with lp.Program.from_program(prog) as P, lp.Program.from_program(prog, on_device=True) as D:
+        for name in lp.Program.INTERNAL:
+            assert np.array_equal(P.debug_internal(name), D.debug_internal(name)), name
+        assert P.schedule == D.schedule
+        got, it = gpu_least_model(P)
+    assert it == want_it and np.array_equal(got, want)

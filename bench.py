@@ -681,22 +681,29 @@ def bench_stable(lp, torch, dev, flush, steps=5, tune=True, n_atoms=100_000, k=1
     stream = torch.cuda.current_stream()
     info = P.info
     sched = P.schedule
-    main_frontier = sched["stable_frontier"] == 1
+    main_frontier = sched["stable_frontier"] >= 1
     ms, st, ns = _time_stable(P, mask, flush, stream, torch, steps)
     out = {"metric": "stable-model guesses/sec", **_stable_line(info, st, ms, ng, main_frontier),
            "workload": stable_workload(n_atoms, k), "n_prime": info["n_prime"], "nnz": info["nnz"], "k": k, "n_stable": ns,
            "schedule": sched}
-    P.set_schedule(stable_frontier=0 if main_frontier else 1)
-    ms2, st2, ns2 = _time_stable(P, mask, flush, stream, torch, steps)
-    other = "full_sweep" if main_frontier else "frontier"
-    out[other] = {"metric": f"stable-model guesses/sec, {other.replace('_', ' ')} schedule",
-                  **_stable_line(info, st2, ms2, ng, not main_frontier), "n_stable": ns2,
-                  "over_main": ms / ms2}
-    fr_st = st if main_frontier else st2
-    out["frontier_rows_reevaluated"] = fr_st["frontier_rows"]
-    out["rows_of_full_sweeps"] = info["n_prime"] * (st2 if main_frontier else st)["sum_tile_iters"]
-    if ns2 != ns:
-        raise RuntimeError("the stable-model schedules found other numbers of stable models")
+    # the other schedules on the same tile width: the full sweep, and the frontier from M_0 (the
+    # iterates and iteration counts of Algorithm 2) or from F (the guess-independent fixpoint)
+    others = {"full_sweep": 0, "frontier_from_m0": 1, "frontier_from_f": 2}
+    full_st = st if not main_frontier else None
+    for other, mode in others.items():
+        if mode == sched["stable_frontier"]:
+            continue
+        P.set_schedule(stable_frontier=mode)
+        ms2, st2, ns2 = _time_stable(P, mask, flush, stream, torch, steps)
+        out[other] = {"metric": f"stable-model guesses/sec, {other.replace('_', ' ')} schedule",
+                      **_stable_line(info, st2, ms2, ng, mode >= 1), "n_stable": ns2, "over_main": ms / ms2}
+        if mode == 0:
+            full_st = st2
+        if ns2 != ns:
+            raise RuntimeError("the stable-model schedules found other numbers of stable models")
+    if main_frontier:
+        out["frontier_rows_reevaluated"] = st["frontier_rows"]
+    out["rows_of_full_sweeps"] = info["n_prime"] * full_st["sum_tile_iters"]
     P.set_schedule(**sched)
     # the baseline: one launch per guess (lp_stable_models on a one-guess list), sampled
     n_one = 128

@@ -83,7 +83,8 @@ typedef struct {
   int64_t launches;      /* kernels launched by the last call                                 */
   int64_t tiles;         /* stable models: column tiles processed                            */
   int64_t tile_words;    /* stable models: 64-bit guess words per tile                       */
-  int64_t max_tile_iters;/* stable models: largest per-tile iteration count                  */
+  int64_t max_tile_iters;/* stable models: largest per-tile iteration count (Algorithm 2's
+                            from M_0; from F under stable_frontier 2)                        */
   int64_t sum_tile_iters;/* stable models: sum of per-tile iteration counts                  */
   int64_t frontier_rows;   /* stable models, frontier schedule: rows re-evaluated after each
                               tile's first iteration (summed over iterations and tiles)          */
@@ -274,7 +275,7 @@ void lp_batch_free(lp_batch* batch);
  * time). Every schedule computes the same result; only the time differs. A host-only handle
  * starts with all fields 0. A device handle starts with fixpoint_kernel 3 if the program fits
  * one block's shared memory, else 2 with fixpoint_stage 1 (0 where the sliced layout's indices
- * would overflow), and stable_frontier 1; the other fields are 0 (LP_FIXPOINT=stream in the
+ * would overflow), and stable_frontier 2; the other fields are 0 (LP_FIXPOINT=stream in the
  * environment makes fixpoint_kernel default to 1).
  */
 typedef struct {
@@ -312,8 +313,13 @@ typedef struct {
                                      and iteration counts; the transposed matrix is built on the
                                      device on first use; the iterate buffers of up to 8 GiB,
                                      LP_FRONTIER_BYTES, stay allocated and are restored to their
-                                     rest state after each solve); 0 = a full sweep per tile;
-                                     needs stable_row_split 0; the autotuner tries both         */
+                                     rest state after each solve); 2 = the same from F, the
+                                     fixpoint reached from the fact rows with every guessed row 0
+                                     (the part of every column's fixpoint no guess changes;
+                                     computed once per handle by a least-model solve): the same
+                                     stable bits and models in fewer iterations, and the reported
+                                     iteration counts are those from F; 0 = a full sweep per tile;
+                                     1 and 2 need stable_row_split 0; the autotuner tries all   */
   int32_t fixpoint_stage;         /* least model, kernel 2: 0 = copy the vector prefix that rule
                                      rows gather into shared memory every iteration when it fits
                                      (160 KB); 1 = gather from global memory (through L1)         */

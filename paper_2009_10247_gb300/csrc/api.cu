@@ -269,7 +269,7 @@ void release(lp_program* p) {
                   p->neg_row, p->bar_row, p->row_tag, p->x[0], p->x[1], p->ctl, p->tiles.p, p->stage_in.p,
                   p->stage_out.p, p->stage_out2.p, p->desc, p->word_hdr, p->and_col, p->groups,
                   p->sl_q, p->sl_qinv, p->sl_hdr, p->sl_col, p->sl_fact_row, p->sl_perm,
-                  p->fr_tptr, p->fr_tidx, p->fr_cnt, p->fr_long, p->fr_buf.p, p->dc_kind, p->dc_rule, p->fr_seed,
+                  p->fr_tptr, p->fr_tidx, p->fr_cnt, p->fr_long, p->fr_F, p->fr_buf.p, p->dc_kind, p->dc_rule, p->fr_seed,
                   p->rx_info, p->rx_rule, p->rx_colptr, p->rx_rowidx, p->rx_dw.p, p->rx_units, p->rx_part.p,
                   p->tune_out.p, p->tune_in.p};
   device_free_all(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
@@ -414,7 +414,7 @@ lp_status finish_handle(lp_program* p, cudaStream_t s, std::chrono::steady_clock
     p->sched.fixpoint_kernel = fits ? 3 : 2;
     p->sched.fixpoint_stage = fits ? 0 : 1;
   }
-  p->sched.stable_frontier = 1;  // stable models: the frontier schedule over all tiles at once
+  p->sched.stable_frontier = 2;  // stable models: the frontier over all tiles, from F
   const cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "lp_compile"));
   const auto t_end = std::chrono::steady_clock::now();
@@ -608,6 +608,56 @@ lp_status ensure_frontier(lp_program* p, cudaStream_t s) {
 // Room for wide items (more dependents than the grid-push threshold) per wave of `items`; past it
 // the warps push the rest themselves.
 int64_t frontier_wide_cap(int64_t items) { return items / 16 + 64; }
+
+// F for the frontier from F (stable_frontier 2): Algorithm 1 on the internal matrix from every
+// fact row with every barred row zero (kernel 0; its loop ends when an iteration changes
+// nothing, so both iterate vectors hold the fixpoint), kept per handle.
+lp_status ensure_frontier_F(lp_program* p, cudaStream_t s) {
+  if (p->fr_F) return LP_OK;
+  const HostMatrix& hm = p->hm;
+  lp_status st = ensure_scratch(p);
+  if (st != LP_OK) return st;
+  uint32_t* F = nullptr;
+  if ((st = dalloc(p, &F, (size_t)hm.n_pad / 32 + 1)) != LP_OK) return st;
+  auto fail_clean = [&](lp_status code) {
+    device_free(F);
+    return code;
+  };
+  FixArgs a{};
+  a.row_ptr = p->row_ptr;
+  a.col = p->col;
+  a.any_mask = p->any_mask;
+  a.x0 = p->x[0];
+  a.x1 = p->x[1];
+  a.n_words = hm.n_pad / 32;
+  a.max_iters = (int32_t)std::min<int64_t>(INT32_MAX, (int64_t)hm.n_prime + 2);
+  a.ctl = p->ctl;
+  a.fact_row = p->fact_row;
+  a.fact_owner = p->fact_owner;
+  a.n_facts = hm.n_fact_rows;
+  a.fact_mask = p->fact_mask;
+  a.n_atom_words = (hm.n + 63) / 64;
+  a.n_prime = hm.n_prime;
+  a.perm = p->perm;
+  a.n_sec_a = hm.n_sec_a;
+  static int occ = -1;
+  if (occ < 0) occ = fixpoint_blocks_per_sm(1, 1, 0);
+  if (occ <= 0) return fail_clean(fail(LP_ERR_CUDA, "fixpoint kernel cannot be resident"));
+  const int words_per_block = fix_block(0) / 32;
+  const int grid = std::min(max_coresident(p, occ), std::max(1, (a.n_words + words_per_block - 1) / words_per_block));
+  cudaError_t e = cudaMemsetAsync(p->ctl, 0, sizeof(DeviceCtl), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->x[0], 0, (size_t)hm.n_pad / 8, s);
+  if (e == cudaSuccess) e = launch_fixpoint(a, grid, 1, 1, 0, s);
+  if (e == cudaSuccess) count_launches(1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(F, p->x[0], (size_t)hm.n_pad / 8, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_clean(cuda_fail(e, "guess-independent fixpoint"));
+  if (p->h_ctl->status != 0)
+    return fail_clean(fail((lp_status)p->h_ctl->status, "guess-independent fixpoint: the solve did not finish"));
+  p->fr_F = F;
+  return LP_OK;
+}
 
 // Bytes of the frontier buffers for `tiles` tiles of W words: two iterate buffers, a stamp and two
 // list slots per item, the changed-item bitmap, a counter per tile, the wide-item list.
@@ -865,7 +915,8 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
   const int W = 1 << log2W;
   const int64_t n_tiles = (n_gwords + W - 1) / W;
   const bool split = p->sched.stable_row_split == 1;
-  const bool frontier = p->sched.stable_frontier == 1 && !split;
+  const bool frontier = p->sched.stable_frontier >= 1 && !split;
+  const bool from_F = frontier && p->sched.stable_frontier == 2;
   int32_t wave_tiles = 0;
   if (frontier) {
     // tiles in flight at once: as many as the budget holds (8 GiB by default), item ids in int32
@@ -875,6 +926,7 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
     c = std::min<int64_t>(c, (int64_t)(INT32_MAX - 64) / std::max<int64_t>(hm.n_pad, 1));
     wave_tiles = (int32_t)std::max<int64_t>(c, 1);
     if ((st = ensure_frontier(p, s)) != LP_OK) return st;
+    if (from_F && (st = ensure_frontier_F(p, s)) != LP_OK) return st;
     // a handle keeps the largest wave it has run unless a wider tile needs another layout
     const int32_t keep = p->fr_W == W ? std::max(p->fr_tiles, wave_tiles) : wave_tiles;
     if (frontier_bytes(hm.n_pad, W, keep) <= fr_budget) wave_tiles = keep;
@@ -939,8 +991,10 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
     a.fr_list = (int32_t*)(a.mark + items);
     a.fr_dirty = (unsigned*)(a.fr_list + 2 * items);
     a.fr_last = (int32_t*)(a.fr_dirty + (items + 31) / 32);
-    a.fr_seed = p->fr_seed;
-    a.n_seed = p->fr_nseed;
+    // from F the fact rows and their consequences are already in place: the guessed rows seed
+    a.fr_F = from_F ? p->fr_F : nullptr;
+    a.fr_seed = from_F ? p->fr_seed + hm.n_fact_rows : p->fr_seed;
+    a.n_seed = from_F ? p->fr_nseed - hm.n_fact_rows : p->fr_nseed;
     a.fr_wide = a.fr_last + wave_tiles;
     a.wide_cap = (int32_t)frontier_wide_cap(items);
     if (const char* env = std::getenv("LP_FRONTIER_WIDE_ITEMS"))  // a smaller wide list (tests its overflow)
@@ -950,7 +1004,7 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
     a.t_idx = p->fr_tidx;
     a.fr_cnt = p->fr_cnt;
     a.fr_tiles = wave_tiles;
-    a.fr_key = 1u | ((unsigned)W << 1) | ((unsigned)wave_tiles << 7);
+    a.fr_key = 1u | ((unsigned)W << 1) | (from_F ? 0x80u : 0u) | ((unsigned)wave_tiles << 8);
     static int occ_by_w[6] = {-1, -1, -1, -1, -1, -1};
     int& occ_frontier = occ_by_w[log2W];
     if (occ_frontier < 0) occ_frontier = stable_frontier_blocks_per_sm(W);
@@ -1015,8 +1069,8 @@ lp_status lp_set_schedule(lp_program* p, const lp_schedule* in) {
   if (R > 0 && (in->fixpoint_kernel != 0 || G > 1 || X == 4))
     return fail(LP_ERR_INVALID, "a thread-per-row map needs fixpoint_kernel 0, no row split and no chunk batch");
   if (in->stable_row_split != 0 && in->stable_row_split != 1) return fail(LP_ERR_INVALID, "stable_row_split must be 0 or 1");
-  if (in->stable_frontier != 0 && in->stable_frontier != 1) return fail(LP_ERR_INVALID, "stable_frontier must be 0 or 1");
-  if (in->stable_frontier == 1 && in->stable_row_split == 1)
+  if (in->stable_frontier < 0 || in->stable_frontier > 2) return fail(LP_ERR_INVALID, "stable_frontier must be 0, 1 or 2");
+  if (in->stable_frontier >= 1 && in->stable_row_split == 1)
     return fail(LP_ERR_INVALID, "the frontier schedule needs stable_row_split 0");
   if (W < 0 || W > 32 || (W & (W - 1)) != 0) return fail(LP_ERR_INVALID, "stable_tile_words must be 0 or 1, 2, 4, 8, 16, 32");
   p->sched = *in;

@@ -146,8 +146,9 @@ struct StableArgs {
   int32_t wide_cap;
   int32_t fr_tiles;         // tiles per wave (the buffers' capacity)
   unsigned fr_key;          // nonzero tag of the buffers' layout
-  const int32_t* fr_seed;   // n_seed rows nonzero in M_0: the fact rows, then the guessed rows
-  int32_t n_seed;
+  const int32_t* fr_seed;   // n_seed rows the first list starts from: the fact rows, then the
+  int32_t n_seed;           // guessed rows (only the guessed rows when starting from fr_F)
+  const uint32_t* fr_F;     // ceil(n_pad / 32) or NULL: the guess-independent fixpoint to start from
 };
 
 constexpr int kStableBlock = 256;

@@ -59,6 +59,7 @@ struct lp_program {
   unsigned* fr_cnt = nullptr;
   unsigned* fr_long = nullptr;  // rows the frontier evaluates a warp at a time
   bool fr_any_long = false;
+  uint32_t* fr_F = nullptr;     // the guess-independent fixpoint (stable_frontier 2), internal rows
   DevBuf fr_buf;
   int32_t fr_W = 0, fr_tiles = 0;
   // scratch

@@ -17,6 +17,16 @@
 // none, an empty row never fires). So with dst = M_0 on every other row, the first list is those
 // rows and the rows referring to them.
 //
+// Starting from F (fr_F set): F is the least fixpoint reached from the fact rows with every
+// guessed row zero -- the part of every column's fixpoint that no guess can change (theta of M_P
+// is monotone and a guess only adds ones to M_0). The iteration may start from S = F with the
+// guess's bits on the guessed rows instead of from M_0: M_0 <= S <= the column's least fixpoint
+// and S <= theta(M_P S) (F is a fixpoint, a guessed row is a self-loop), so it climbs to the same
+// fixpoint, the same stable bits and models, in fewer iterations (the iteration counts are then
+// those from S, not Algorithm 2's from M_0). Rows other than the guessed rows and the rows
+// referring to them keep F's value in iteration 0, so the first list is those rows alone, and the
+// buffers rest at F.
+//
 // Between solves the buffers rest in that state -- fact rows all ones, every other row zero, in
 // both buffers -- and a solve leaves them so: a bitmap records every item that changed, and after
 // Algorithm 3 those items and the guessed rows are written back. The first solve on a handle (or
@@ -56,7 +66,13 @@ constexpr unsigned kStampLimit = 0xF0000000u;
 // an item whose row has more dependents than this has them pushed by the whole grid
 constexpr int kWideDeps = 128;
 
-__device__ __forceinline__ uint64_t rest_word(int tag) { return tag == -2 ? ~0ull : 0ull; }
+// The words a row rests at between solves (in every tile): with fr_F, its bit of the
+// guess-independent fixpoint F (all ones or all zeros across the guesses); else M_0 outside the
+// guessed rows (ones on a fact row, zeros elsewhere).
+__device__ __forceinline__ uint64_t rest_word(const StableArgs& a, int row) {
+  if (a.fr_F) return ((__ldg(a.fr_F + (row >> 5)) >> (row & 31)) & 1u) ? ~0ull : 0ull;
+  return __ldg(a.row_tag + row) == -2 ? ~0ull : 0ull;
+}
 
 __device__ __forceinline__ uint4 ld_volatile4(const unsigned* p) {
   uint4 v;
@@ -70,7 +86,11 @@ __device__ __forceinline__ uint4 ld_volatile4(const unsigned* p) {
 // Per-warp staging of list appends in shared memory: the winners of a step go to the warp's
 // 64-slot buffer, and the list gets them 32 at a time with one atomic on its counter (all warps
 // of the grid append to the same counter; one atomic per step serialized on it).
-__shared__ int s_stage[2][kStableBlock / 32][64];  // [short, long][warp of the block]
+// one 1024-thread block per SM: a quarter of the blocks (and arrivals) at each grid barrier of
+// the 256-thread blocks it replaced, with the same 32 warps per SM (2 % faster on the 2^16-guess
+// normal program)
+constexpr int kFrontierBlock = 1024;
+__shared__ int s_stage[2][kFrontierBlock / 32][64];  // [short, long][warp of the block]
 
 // The two lists an iteration appends to share one buffer of cap = fr_tiles * n_pad slots: the
 // short list from the front, the long list from the back (slot cap - 1 - i holds entry i).
@@ -232,7 +252,7 @@ __device__ __forceinline__ int eval_row_words(const StableArgs& a, const uint64_
 // WPL: words per lane in the iterations. An item (W words) takes W / WPL lanes, so a warp
 // evaluates 32 WPL / W items at once: with W = 32, four items of eight lanes, four words each.
 template <int WPL>
-__global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(StableArgs a) {
+__global__ void __launch_bounds__(kFrontierBlock, 1) stable_frontier_kernel(StableArgs a) {
   __shared__ long long s_base;
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -273,7 +293,7 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
     for (long long g = gwarp; i0 + g * rpw < i1; g += nwarps) {
       const long long item = i0 + g * rpw + sub;
       if (item < i1) {
-        const uint64_t v = rest_word(__ldg(a.row_tag + (int)(item % n_pad)));
+        const uint64_t v = rest_word(a, (int)(item % n_pad));
         a.X0[item * W + wl] = v;
         a.X1[item * W + wl] = v;
         if (wl == 0) a.mark[item] = 0u;
@@ -634,7 +654,7 @@ __global__ void __launch_bounds__(kStableBlock, 4) stable_frontier_kernel(Stable
         const int b = __ffs(bits) - 1;
         bits &= bits - 1;
         const long long item = q * 32 + b;
-        const uint64_t v = rest_word(__ldg(a.row_tag + (int)(item % n_pad)));
+        const uint64_t v = rest_word(a, (int)(item % n_pad));
         for (int w = lane; w < W; w += 32) {
           a.X0[item * W + w] = v;
           a.X1[item * W + w] = v;
@@ -706,7 +726,7 @@ const void* frontier_entry(int W) {
 cudaError_t launch_stable_frontier(const StableArgs& a, int grid, cudaStream_t s) {
   StableArgs copy = a;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(frontier_entry(a.W), dim3(grid), dim3(kStableBlock), params, 0, s);
+  return cudaLaunchCooperativeKernel(frontier_entry(a.W), dim3(grid), dim3(kFrontierBlock), params, 0, s);
 }
 
 cudaError_t build_long_rows(const int32_t* row_ptr, int32_t n_pad, unsigned* mask, unsigned* any, cudaStream_t s) {
@@ -717,7 +737,7 @@ cudaError_t build_long_rows(const int32_t* row_ptr, int32_t n_pad, unsigned* mas
 
 int stable_frontier_blocks_per_sm(int W) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, frontier_entry(W), kStableBlock, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, frontier_entry(W), kFrontierBlock, 0) != cudaSuccess) return 0;
   return nb;
 }
 

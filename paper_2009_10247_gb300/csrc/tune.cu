@@ -166,7 +166,10 @@ extern "C" lp_status lp_autotune(lp_program* p, uint32_t what, int32_t reps, lp_
       for (int b : {0, occ / 2})
         if (b == 0 || (b > 0 && b < occ)) cands.push_back(stable(W, b, 0, 0));
       if (W < 32) cands.push_back(stable(W, 0, 1, 0));  // with 32-word tiles the row split is the same mapping
-      if (W >= 8 || W >= n_gwords) cands.push_back(stable(W, 0, 0, 1));
+      if (W >= 8 || W >= n_gwords) {
+        cands.push_back(stable(W, 0, 0, 1));
+        cands.push_back(stable(W, 0, 0, 2));
+      }
     }
     std::vector<uint8_t> ref, bits;
     float best = -1.f;

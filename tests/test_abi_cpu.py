@@ -152,8 +152,8 @@ def test_schedule_get_set_validates(lib):
         P.set_schedule(fixpoint_row_map=0)
         P.set_schedule(fixpoint_kernel=1, fixpoint_blocks_per_sm=2, stable_tile_words=8, stable_blocks_per_sm=1)
         assert P.schedule["stable_tile_words"] == 8 and P.schedule["fixpoint_kernel"] == 1
-        for bad in ({"fixpoint_kernel": 4}, {"fixpoint_stage": 2}, {"stable_frontier": 2},
-                    {"stable_frontier": 1, "stable_row_split": 1}, {"stable_tile_words": 3}, {"stable_tile_words": 64},
+        for bad in ({"fixpoint_kernel": 4}, {"fixpoint_stage": 2}, {"stable_frontier": 3}, {"stable_frontier": -1},
+                    {"stable_frontier": 1, "stable_row_split": 1}, {"stable_frontier": 2, "stable_row_split": 1}, {"stable_tile_words": 3}, {"stable_tile_words": 64},
                     {"fixpoint_row_split": 3}, {"fixpoint_row_split": 2},  # the second: kernel 1 is set
                     {"fixpoint_chunk_batch": 2}, {"fixpoint_chunk_batch": 4}, {"stable_row_split": 2},
                     {"fixpoint_blocks_per_sm": -1}, {"stable_blocks_per_sm": -2}, {"fixpoint_row_map": 4},
@@ -161,6 +161,9 @@ def test_schedule_get_set_validates(lib):
             with pytest.raises(lp.LPError):
                 P.set_schedule(**bad)
         assert P.schedule["stable_tile_words"] == 8  # unchanged by the rejected calls
+        for mode in (2, 1, 0):
+            P.set_schedule(stable_frontier=mode)
+            assert P.schedule["stable_frontier"] == mode
         with pytest.raises(lp.LPError):
             P.autotune()  # a host-only handle cannot run solves
 

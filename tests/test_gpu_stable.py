@@ -23,11 +23,12 @@ from tests.gpu_util import dev_words, gpu_stable  # noqa: E402
 
 
 def _parity(prog, guesses=None, max_models=64):
-    # both schedules: the full sweep per tile and the frontier over all tiles (the default)
+    # every schedule: the full sweep per tile, the frontier over all tiles from M_0, and the
+    # frontier from the guess-independent fixpoint F (the default)
     st4, m4, _ = oracle.stable_models_alg23(prog, guesses=guesses)
     want_models = m4[st4]
     with lp.Program.from_program(prog) as P:
-        for frontier in (0, 1):
+        for frontier in (0, 1, 2):
             P.set_schedule(stable_frontier=frontier)
             st, models, ns = gpu_stable(P, guesses=guesses, max_models=max_models)
             assert np.array_equal(st, st4), f"frontier={frontier}"
@@ -139,20 +140,23 @@ def _full_size_expected(prog):
 
 
 def test_full_size_2_16_guesses_every_bit():
-    # all 65,536 guesses in one call, default (frontier), full-sweep, tuned and frontier-on-the-
-    # tuned-width schedules: every stable bit equals the oracle's, and every tile's iteration
-    # count is the largest of its columns' counts
+    # all 65,536 guesses in one call, default (frontier from F), full-sweep, tuned, frontier-from-
+    # M_0 on the tuned width and frontier-from-F schedules: every stable bit equals the oracle's;
+    # every tile's iteration count is the largest of its columns' counts (from M_0), or at most
+    # that (from F)
     p = normal_program(seed=1)
     want, word_iters = _full_size_expected(p)
     assert len(want) == 1 << 16
     with lp.Program.from_program(p) as P:
-        for variant in ("default", "full", "tuned", "frontier"):
+        for variant in ("default", "full", "tuned", "frontier", "from_F"):
             if variant == "full":
                 P.set_schedule(stable_frontier=0)
             if variant == "tuned":
                 P.autotune(lp.LP_TUNE_STABLE, reps=1)  # the schedule the benchmark times
             if variant == "frontier":
                 P.set_schedule(stable_frontier=1)  # on the tuned tile width
+            if variant == "from_F":
+                P.set_schedule(stable_frontier=2)
             st, _, ns = gpu_stable(P)
             assert np.array_equal(st, want), f"{variant}: {np.count_nonzero(st != want)} guesses differ"
             assert ns == int(want.sum())
@@ -160,9 +164,13 @@ def test_full_size_2_16_guesses_every_bit():
             W = stats["tile_words"]
             per_tile = word_iters.reshape(-1, W).max(axis=1)
             assert stats["tiles"] == len(per_tile)
-            assert stats["max_tile_iters"] == per_tile.max()
-            assert stats["sum_tile_iters"] == per_tile.sum()
-            if variant in ("default", "frontier"):  # re-evaluated rows: a few per cent of the full sweeps
+            if P.schedule["stable_frontier"] == 2:
+                assert 1 <= stats["max_tile_iters"] <= per_tile.max()
+                assert stats["sum_tile_iters"] <= per_tile.sum()
+            else:
+                assert stats["max_tile_iters"] == per_tile.max()
+                assert stats["sum_tile_iters"] == per_tile.sum()
+            if P.schedule["stable_frontier"] >= 1:  # re-evaluated rows: a few per cent of the full sweeps
                 assert 0 < stats["frontier_rows"] < 0.2 * P.info["n_prime"] * per_tile.sum()
 
 
@@ -181,12 +189,18 @@ def test_frontier_schedule_matches_oracle(W):
             P.set_schedule(stable_tile_words=W, stable_frontier=0)
             _, _, _ = gpu_stable(P)
             full = P.last_stats()
-            P.set_schedule(stable_frontier=1)
-            st, models, ns = gpu_stable(P, max_models=16)
-            fr = P.last_stats()
-        assert np.array_equal(st, st4) and ns == int(st4.sum())
-        assert np.array_equal(models, m4[st4][:16])
-        assert (fr["max_tile_iters"], fr["sum_tile_iters"]) == (full["max_tile_iters"], full["sum_tile_iters"])
+            for mode in (1, 2):
+                P.set_schedule(stable_frontier=mode)
+                st, models, ns = gpu_stable(P, max_models=16)
+                fr = P.last_stats()
+                assert np.array_equal(st, st4) and ns == int(st4.sum()), mode
+                assert np.array_equal(models, m4[st4][:16]), mode
+                if mode == 1:  # Algorithm 2's iterates: its counts
+                    assert (fr["max_tile_iters"], fr["sum_tile_iters"]) == (full["max_tile_iters"],
+                                                                            full["sum_tile_iters"])
+                else:  # from F: at most those
+                    assert fr["max_tile_iters"] <= full["max_tile_iters"]
+                    assert fr["sum_tile_iters"] <= full["sum_tile_iters"]
 
 
 def _hub_program(seed, n=400, n_rules=1500, k=6):
@@ -238,14 +252,18 @@ def test_frontier_dense_rows_and_hot_atoms(W, wide_items, monkeypatch):
             P.set_schedule(stable_tile_words=W, stable_frontier=0)
             gpu_stable(P)
             full = P.last_stats()
-            P.set_schedule(stable_frontier=1)
-            for rep in range(2):  # the second solve starts from the rest state the first left
-                st, models, ns = gpu_stable(P, max_models=16)
-                fr = P.last_stats()
-                assert np.array_equal(st, st4) and ns == int(st4.sum()), rep
-                assert np.array_equal(models, m4[st4][:16]), rep
-                assert (fr["max_tile_iters"], fr["sum_tile_iters"]) == (full["max_tile_iters"],
-                                                                        full["sum_tile_iters"]), rep
+            for mode in (1, 2, 1):  # a switch of mode rewrites the rest state in full
+                P.set_schedule(stable_frontier=mode)
+                for rep in range(2):  # the second solve starts from the rest state the first left
+                    st, models, ns = gpu_stable(P, max_models=16)
+                    fr = P.last_stats()
+                    assert np.array_equal(st, st4) and ns == int(st4.sum()), (mode, rep)
+                    assert np.array_equal(models, m4[st4][:16]), (mode, rep)
+                    its = (fr["max_tile_iters"], fr["sum_tile_iters"])
+                    if mode == 1:
+                        assert its == (full["max_tile_iters"], full["sum_tile_iters"]), (mode, rep)
+                    else:
+                        assert its[0] <= full["max_tile_iters"] and its[1] <= full["sum_tile_iters"], rep
 
 
 def test_frontier_schedule_explicit_guesses():
@@ -266,10 +284,11 @@ def _frontier_tile_bytes(P, W):
     return 2 * n_pad * W * 8 + 12 * n_pad + (n_pad + 31) // 32 * 4 + 4 + (n_pad // 16 + 64) * 4 + 64
 
 
-def test_frontier_waves_and_rest_state(monkeypatch):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_frontier_waves_and_rest_state(mode, monkeypatch):
     # One handle, many solves: all tiles in one wave, repeated (the buffers' rest state reused),
-    # explicit guesses, waves of 1 and 3 tiles, a solve stopped by max_iters, another tile width.
-    # Every solve gives the oracle's stable bits and models.
+    # explicit guesses, waves of 1 and 3 tiles, a solve stopped by max_iters, another tile width,
+    # from M_0 (mode 1) and from F (mode 2). Every solve gives the oracle's stable bits and models.
     prog = normal_program(seed=4, n=3000, n_rules=9000, k=12, per_atom=2)
     st_all, m_all, _ = oracle.stable_models_alg23(prog)
     g = np.random.default_rng(5).integers(0, 1 << 12, 700).astype(np.uint64)
@@ -281,7 +300,7 @@ def test_frontier_waves_and_rest_state(monkeypatch):
         assert ns == int(st_all.sum()) and np.array_equal(models, m_all[st_all][:16]), label
 
     with lp.Program.from_program(prog) as P:
-        P.set_schedule(stable_tile_words=2, stable_frontier=1)  # 4096 guesses: 32 tiles of 2 words
+        P.set_schedule(stable_tile_words=2, stable_frontier=mode)  # 4096 guesses: 32 tiles of 2 words
         for rep in range(3):
             check_all(P, f"one wave, solve {rep}")
             assert P.last_stats()["tiles"] == 32
@@ -295,7 +314,7 @@ def test_frontier_waves_and_rest_state(monkeypatch):
         monkeypatch.delenv("LP_FRONTIER_BYTES")
         mask = dev_words(1 << 12)
         with pytest.raises(lp.LPError) as e:
-            P.stable_models(mask, max_iters=2)
+            P.stable_models(mask, max_iters=1)
         assert e.value.status == lp.ERR_NO_FIXPOINT
         check_all(P, "after a solve stopped by max_iters")
         P.set_schedule(stable_tile_words=8)

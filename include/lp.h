@@ -219,15 +219,21 @@ lp_status lp_relaxed_backward(lp_program* prog, const float* weights, const floa
  * body_off (over all rules, body_off[0] = 0), body_atom, body_neg (nullable), in the format of
  * lp_compile. Each program is compiled exactly as lp_compile would (on the host's threads);
  * every program needs k <= 16.
- * flags: 0, or LP_BATCH_FULL_SWEEP. By default the programs whose iterate rows hold at most 32
- * bytes (k <= 8) run the frontier schedule: after a first list of the rows nonzero in M_0 and
- * the rows referring to them, each iteration evaluates only the rows one of whose inputs changed
- * in the last one (the compile builds each program's transposed matrix for it); the others, and
- * every program under LP_BATCH_FULL_SWEEP, evaluate every row in every iteration. Both give the
- * same iterates, iteration counts and stable masks. On success *out receives a handle
+ * flags: 0, LP_BATCH_FULL_SWEEP, or LP_BATCH_FROM_M0. By default the programs whose iterate rows
+ * hold at most 32 bytes (k <= 8) run the frontier schedule: after a first list of rows and the
+ * rows referring to them, each iteration evaluates only the rows one of whose inputs changed in
+ * the last one (the compile builds each program's transposed matrix for it), and every column
+ * starts from F, the fixpoint of the program from its fact rows with every guessed row zero
+ * (computed by one extra launch before the first solve, then kept): the first list is the
+ * guessed rows. Under LP_BATCH_FROM_M0 the frontier starts from M_0 (the first list: the rows
+ * nonzero in M_0), which gives Algorithm 2's iterates and iteration counts; from F the columns
+ * reach the same fixpoints in fewer iterations, and `iters` counts those. The programs with
+ * wider rows, and every program under LP_BATCH_FULL_SWEEP, evaluate every row in every
+ * iteration from M_0. All give the same stable masks. On success *out receives a handle
  * (lp_batch_free).
  */
 #define LP_BATCH_FULL_SWEEP 1u
+#define LP_BATCH_FROM_M0 2u
 typedef struct lp_batch lp_batch;
 lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int64_t* rule_off, const int32_t* head,
                            const int64_t* body_off, const int32_t* body_atom, const uint8_t* body_neg,
@@ -247,7 +253,8 @@ lp_status lp_batch_program_info(const lp_batch* batch, int32_t program, lp_info*
  * stable_mask (device or host, total_mask_words): program p's bit g (at its mask_word_offset) is
  * set iff guess g gives a stable model. n_stable (device or host, n_programs, nullable): stable
  * guesses per program; iters (device or host, n_programs, nullable): theta applications until
- * the program's fixpoint (0 if it had none within max_iters). One cooperative launch runs every
+ * the program's fixpoint (from F under the default frontier schedule; 0 if it had none within
+ * max_iters). One cooperative launch runs every
  * program as an independent job (the largest on several blocks, the rest on one block each),
  * each iterated until an application changes none of its words. A host buffer or a non-NULL
  * n_stable / iters makes the call wait;

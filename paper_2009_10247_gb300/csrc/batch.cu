@@ -111,7 +111,23 @@ struct BatchArgs {
   unsigned* dirty;
   unsigned* clean;
   unsigned* epoch;
+  // From F: the fixpoint every program reaches from its fact rows with every guessed row zero
+  // (a bit per row, fbits) is where its columns start and where its buffers rest; the F pass
+  // (f_pass) computes it once per batch, from M_0 with the guessed rows kept at zero.
+  bool from_f;
+  bool f_pass;
+  unsigned* fbits;
 };
+
+// The value of a non-guessed row at rest (every column alike): its bit of F where F is known,
+// else M_0's (ones on a fact row).
+__device__ __forceinline__ bool batch_rest_one(const BatchArgs& a, const BatchProgram& pr, int r, int tag, bool use_f) {
+  if (use_f) {
+    const long long q = pr.row0 + r;
+    return (a.fbits[q >> 5] >> (q & 31)) & 1u;
+  }
+  return tag == -2;
+}
 
 // ---- one row of an iterate: 8 RB bits (RB = 2, 4, 8, 16 or 32 bytes), as NW 64-bit words
 template <int RB>
@@ -363,20 +379,24 @@ __device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int pro
   // that did not finish, stamps about to wrap) the block writes M_0 for its rows into both
   // buffers, four rows per thread (rows come in 128-row groups, so a thread's four are whole),
   // and clears their stamps and changed bits.
+  // From F (not in the F pass) the rows rest at F and the columns start from F; the F pass keeps
+  // the guessed rows at zero and starts from M_0's other rows.
+  const bool at_f = a.from_f && !a.f_pass;
   unsigned e = ld_volatile(a.epoch + program);
   const bool clean = ld_volatile(a.clean + program) != 0u && e < 0xF0000000u - (unsigned)a.max_iters;
   if (!clean) e = 0u;
   if (clean) {
-    for (long long i = tid; i < pr.n_seed; i += nth) {
-      const int row = __ldg(a.seed + pr.seed0 + i);
-      const int tag = __ldg(a.row_tag + pr.row0 + row);
-      if (tag >= 0) {
-        Row m0;
+    if (!a.f_pass)
+      for (long long i = tid; i < pr.n_seed; i += nth) {
+        const int row = __ldg(a.seed + pr.seed0 + i);
+        const int tag = __ldg(a.row_tag + pr.row0 + row);
+        if (tag >= 0) {
+          Row m0;
 #pragma unroll
-        for (int w = 0; w < NW; w++) m0.v[w] = batch_m0(tag, w) & Row::MASK;
-        m0.store(xs[0], row);
+          for (int w = 0; w < NW; w++) m0.v[w] = batch_m0(tag, w) & Row::MASK;
+          m0.store(xs[0], row);
+        }
       }
-    }
   } else {
     for (int r = r_lo + 4 * threadIdx.x; r < r_hi; r += 4 * blockDim.x) {
       const int4 tag4 = *reinterpret_cast<const int4*>(a.row_tag + pr.row0 + r);
@@ -384,8 +404,10 @@ __device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int pro
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         Row m0;
+        const bool one = tags[i] < 0 && batch_rest_one(a, pr, r + i, tags[i], at_f);
 #pragma unroll
-        for (int w = 0; w < NW; w++) m0.v[w] = batch_m0(tags[i], w) & Row::MASK;
+        for (int w = 0; w < NW; w++)
+          m0.v[w] = (tags[i] >= 0 ? (a.f_pass ? 0ull : batch_m0(tags[i], w)) : (one ? ~0ull : 0ull)) & Row::MASK;
         m0.store(xs[0], r + i);
         m0.store(xs[1], r + i);
       }
@@ -396,11 +418,16 @@ __device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int pro
   if (rank == 0 && threadIdx.x < 3) cnt[threadIdx.x] = 0u;
   if (!barrier()) return false;
   if (rank == 0 && threadIdx.x == 0) a.clean[program] = 0u;  // every block has read it: in use
-  // ---- 2. the first list: seed rows and the rows referring to them
+  // ---- 2. the first list: seed rows and the rows referring to them (from F the guessed rows
+  // alone; in the F pass the fact rows alone, the guessed rows staying zero)
   for (long long base = warp0; base < pr.n_seed; base += nth) {  // uniform in the warp
     const long long i = base + lane;
-    const bool ok = i < pr.n_seed;
+    bool ok = i < pr.n_seed;
     const int row = ok ? __ldg(a.seed + pr.seed0 + i) : 0;
+    if (ok && a.from_f) {
+      const int tag = __ldg(a.row_tag + pr.row0 + row);
+      ok = a.f_pass ? tag < 0 : tag >= 0;
+    }
     push(ok, row, e + 1u, lists[0], cnt);
   }
   if (!barrier()) return false;
@@ -484,7 +511,8 @@ __device__ bool frontier_job(const BatchArgs& a, const BatchProgram& pr, int pro
 }
 
 // After Algorithm 3: the rows of [r_lo, r_hi) that changed in this solve, and (rank 0) the
-// guessed rows, back to the rest state in both buffers; their changed bits cleared.
+// guessed rows, back to the rest state in both buffers (from F, and after the F pass, F; else
+// M_0's guess-independent part); their changed bits cleared.
 template <int RB>
 __device__ void frontier_reset(const BatchArgs& a, const BatchProgram& pr, int rank, int c, int r_lo, int r_hi) {
   using Row = RowT<RB>;
@@ -498,9 +526,10 @@ __device__ void frontier_reset(const BatchArgs& a, const BatchProgram& pr, int r
       const int r = 32 * w + __ffs(bits) - 1;
       bits &= bits - 1;
       const int tag = __ldg(a.row_tag + pr.row0 + r);
+      const bool one = tag < 0 && batch_rest_one(a, pr, r, tag, a.from_f);  // F: known by now
       Row v;
 #pragma unroll
-      for (int i = 0; i < NW; i++) v.v[i] = tag == -2 ? Row::MASK : 0ull;
+      for (int i = 0; i < NW; i++) v.v[i] = one ? Row::MASK : 0ull;
       v.store(xs[0], r);
       v.store(xs[1], r);
     }
@@ -539,6 +568,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_stable_kernel(Batch
     const BatchJob job = a.jobs[j];
     const int rank = slot - job.first_slot, c = job.n_ctas;
     const BatchProgram pr = a.progs[job.program];
+    if (a.f_pass && !(FRONTIER && pr.rb <= 32)) {  // the F pass serves the frontier programs only
+      __syncthreads();
+      continue;
+    }
     const int g_lo = (int)((long long)pr.n_groups * rank / c), g_hi = (int)((long long)pr.n_groups * (rank + 1) / c);
     const int r_lo = g_lo * kGroupRows, r_hi = min(g_hi * kGroupRows, pr.n_pad);
     unsigned long long round = 0;
@@ -617,14 +650,23 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_stable_kernel(Batch
     }
     }  // full sweep
 
+    // ---- the F pass: F = column 0 (the all-zero guess) of each row of this block's range
+    if (a.f_pass) {
+      const unsigned char* fin = a.X0 + pr.state0;
+      for (int w32 = r_lo / 32 + (threadIdx.x >> 5); w32 < r_hi / 32; w32 += blockDim.x >> 5) {
+        const int r = 32 * w32 + lane;
+        const unsigned word = __ballot_sync(FULL, fin[(long long)pr.rb * r] & 1u);
+        if (lane == 0) a.fbits[(pr.row0 >> 5) + w32] = word;
+      }
+    }
     // ---- 3. Algorithm 3 (rank 0): stable word = AND over the negated atoms q of (word of q)
     // XOR (word of q-bar); both buffers hold the fixpoint
     if (rank == 0) {
       if (threadIdx.x == 0) {
-        a.iters[job.program] = converged ? it : 0;
+        if (!a.f_pass) a.iters[job.program] = converged ? it : 0;
         if (!converged) atomicCAS(&a.ctl->status, 0, LP_ERR_NO_FIXPOINT);
       }
-      const int nw = pr.rb >= 8 ? pr.rb / 8 : 1;
+      const int nw = a.f_pass ? 0 : (pr.rb >= 8 ? pr.rb / 8 : 1);
       const unsigned char* fin = a.X0 + pr.state0;
       for (int w = threadIdx.x; w < nw; w += blockDim.x) {
         const long long first = 64ll * w, ng = 1ll << pr.k;
@@ -667,7 +709,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_stable_kernel(Batch
       }
       if (rank == 0 && threadIdx.x == 0) {
         a.epoch[job.program] = next_epoch;
-        a.clean[job.program] = 1u;
+        a.clean[job.program] = a.f_pass && !converged ? 0u : 1u;  // an unfinished F pass leaves no F
       }
     }
     __syncthreads();  // s_slot and s_next are reused by the next job
@@ -714,6 +756,9 @@ struct lp_batch {
   int64_t device_bytes = 0;
   double compile_ms = 0;
   int64_t launches = 0;
+  bool from_f = false;           // frontier programs start from F (unless LP_BATCH_FROM_M0)
+  bool f_ready = false;          // F has been computed (the F pass ran to its end)
+  unsigned* d_fbits = nullptr;   // F: a bit per row
 };
 
 namespace {
@@ -732,7 +777,7 @@ void batch_release(lp_batch* b) {
   void* ptrs[] = {b->d_table, b->d_hdr, b->d_col, b->d_tag, b->d_neg,     b->d_bar, b->d_x0,
                   b->d_x1,    b->d_nstable, b->d_iters, b->d_jobs, b->d_slot_job, b->d_job_bar, b->d_ctl, b->d_stage,
                   b->d_tptr,  b->d_tidx, b->d_seed, b->d_mark, b->d_list, b->d_fcnt, b->d_dirty, b->d_clean,
-                  b->d_epoch};
+                  b->d_epoch, b->d_fbits};
   device_free_all(ptrs, sizeof(ptrs) / sizeof(ptrs[0]));
 }
 
@@ -856,7 +901,7 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
   NvtxRange nvtx("lp_compile_batch");
   if (!out) return bfail(LP_ERR_INVALID, "out must not be NULL");
   *out = nullptr;
-  if (flags & ~LP_BATCH_FULL_SWEEP) return bfail(LP_ERR_INVALID, "unknown flags");
+  if (flags & ~(LP_BATCH_FULL_SWEEP | LP_BATCH_FROM_M0)) return bfail(LP_ERR_INVALID, "unknown flags");
   const bool frontier = !(flags & LP_BATCH_FULL_SWEEP);
   if (n_programs < 0 || (n_programs > 0 && (!n_atoms || !rule_off))) return bfail(LP_ERR_INVALID, "bad program list");
   if (n_programs > 0 && rule_off[0] != 0) return bfail(LP_ERR_INVALID, "rule_off[0] must be 0");
@@ -888,6 +933,7 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
   if (!b) return bfail(LP_ERR_OOM, "host allocation failed");
   b->n_programs = n_programs;
   b->frontier = frontier;
+  b->from_f = frontier && !(flags & LP_BATCH_FROM_M0);
   b->infos.resize(n_programs);
   b->table.resize(n_programs);
   int64_t row = 0, state = 0, mask = 0, nnz = 0, neg = 0, ent = 0, groups = 0, tp = 0, ti = 0, seeds = 0;
@@ -1007,6 +1053,7 @@ lp_status lp_compile_batch(int32_t n_programs, const int32_t* n_atoms, const int
     if (st == LP_OK) st = bupload<unsigned>(b, &b->d_epoch, nullptr, (size_t)n_programs, s);
     if (st == LP_OK && (e = cudaMemsetAsync(b->d_clean, 0, std::max<size_t>(n_programs, 1) * 4, s)) != cudaSuccess)
       st = bfail(LP_ERR_CUDA, cudaGetErrorString(e));
+    if (st == LP_OK && b->from_f) st = bupload<unsigned>(b, &b->d_fbits, nullptr, (size_t)row / 32 + 1, s);
   }
   // Jobs: one per program, largest first. A program whose share of the work exceeds one block's
   // share of the whole batch runs on several co-resident blocks (at most 16, and all multi-block
@@ -1116,12 +1163,17 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
     }
     d_mask = b->d_stage;
   }
-  cudaError_t e = cudaMemsetAsync(b->d_ctl, 0, sizeof(DeviceCtl), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_job_bar, 0, (4 * (size_t)b->n_jobs + 1) * 8, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nstable, 0, std::max<size_t>(b->n_programs, 1) * 8, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_iters, 0, std::max<size_t>(b->n_programs, 1) * 4, s);
-  if (e != cudaSuccess) return bfail(LP_ERR_CUDA, cudaGetErrorString(e));
-  if (b->n_programs > 0) {
+  cudaError_t e = cudaSuccess;
+  // one launch over all jobs; the F pass (from F, before the first solve) computes F
+  auto launch = [&](bool f_pass) -> lp_status {
+    e = cudaMemsetAsync(b->d_ctl, 0, sizeof(DeviceCtl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_job_bar, 0, (4 * (size_t)b->n_jobs + 1) * 8, s);
+    if (!f_pass) {
+      if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nstable, 0, std::max<size_t>(b->n_programs, 1) * 8, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(b->d_iters, 0, std::max<size_t>(b->n_programs, 1) * 4, s);
+    }
+    if (e != cudaSuccess) return bfail(LP_ERR_CUDA, cudaGetErrorString(e));
+    if (b->n_programs == 0) return LP_OK;
     BatchArgs a{};
     a.progs = b->d_table;
     a.jobs = b->d_jobs;
@@ -1140,7 +1192,8 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
     a.job_bar = b->d_job_bar;
     a.queue = reinterpret_cast<unsigned*>(b->d_job_bar + 4 * (size_t)b->n_jobs);
     a.ctl = b->d_ctl;
-    a.max_iters = max_iters;
+    // from the fact rows every iteration adds a row, so the F pass always ends
+    a.max_iters = f_pass ? (1 << 30) : max_iters;
     a.frontier = b->frontier;
     a.tptr = b->d_tptr;
     a.tidx = b->d_tidx;
@@ -1152,6 +1205,9 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
     a.dirty = b->d_dirty;
     a.clean = b->d_clean;
     a.epoch = b->d_epoch;
+    a.from_f = b->from_f;
+    a.f_pass = f_pass;
+    a.fbits = b->d_fbits;
     // every block resident (multi-block jobs meet at their own barriers); no more blocks than slots
     const int grid = std::max(1, std::min(b->grid, b->n_slots));
     void* params[] = {&a};
@@ -1162,7 +1218,20 @@ lp_status lp_batch_stable_models(lp_batch* b, uint64_t* stable_mask, int64_t* n_
     }
     b->launches++;
     count_launches(1);
+    return LP_OK;
+  };
+  lp_status lst;
+  if (b->from_f && !b->f_ready && b->n_programs > 0) {
+    if ((lst = launch(true)) != LP_OK) return lst;
+    DeviceCtl fctl;
+    std::memset(&fctl, 0, sizeof(fctl));
+    if ((e = cudaMemcpyAsync(&fctl, b->d_ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return bfail(LP_ERR_CUDA, cudaGetErrorString(e));
+    if (fctl.status != 0) return bfail((lp_status)fctl.status, "the fixpoint from the fact rows did not finish");
+    b->f_ready = true;
   }
+  if ((lst = launch(false)) != LP_OK) return lst;
   const bool sync = host_mask || n_stable || iters;
   if (host_mask && b->total_mask_words)
     if ((e = cudaMemcpyAsync(stable_mask, d_mask, (size_t)b->total_mask_words * 8, cudaMemcpyDeviceToHost, s)) !=

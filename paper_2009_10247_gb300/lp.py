@@ -19,6 +19,7 @@ LP_COMPILE_HOST_ONLY = 1
 LP_COMPILE_ON_HOST = 2
 LP_COMPILE_ON_DEVICE = 4
 LP_BATCH_FULL_SWEEP = 1
+LP_BATCH_FROM_M0 = 2
 
 
 class LPError(RuntimeError):
@@ -411,9 +412,11 @@ class Program:
 class Batch:
     """Many independent normal programs compiled for one launch (lp_compile_batch)."""
 
-    def __init__(self, programs, stream=None, full_sweep=False):
+    def __init__(self, programs, stream=None, full_sweep=False, from_m0=False):
         """full_sweep: every program evaluates every row in every iteration (LP_BATCH_FULL_SWEEP);
-        by default programs with k <= 8 run the frontier schedule."""
+        by default programs with k <= 8 run the frontier schedule from F (the fixpoint from the
+        fact rows with the guessed rows zero); from_m0: the frontier from M_0 (LP_BATCH_FROM_M0:
+        Algorithm 2's iterates and iteration counts)."""
         L = load()
         n = len(programs)
         n_atoms = np.array([p.n_atoms for p in programs], dtype=np.int32)
@@ -431,7 +434,8 @@ class Batch:
                                   else np.zeros(len(p.body_atom), np.uint8) for p in programs])
         self._h = ctypes.c_void_p()
         _check(L.lp_compile_batch(n, _ptr(n_atoms), _ptr(rule_off), _ptr(head), _ptr(body_off), _ptr(atom), _ptr(neg),
-                                  LP_BATCH_FULL_SWEEP if full_sweep else 0, _stream(stream), ctypes.byref(self._h)))
+                                  (LP_BATCH_FULL_SWEEP if full_sweep else 0) | (LP_BATCH_FROM_M0 if from_m0 else 0),
+                                  _stream(stream), ctypes.byref(self._h)))
         vals = [ctypes.c_int64() for _ in range(5)]
         _check(L.lp_batch_info(self._h, *[ctypes.byref(v) for v in vals]))
         self.n_programs, self.total_rows, self.total_nnz, self.total_mask_words, self.device_bytes = [v.value for v in vals]

@@ -195,7 +195,7 @@ def test_batch_entry_points_validate_without_gpu(lib):
     boff = np.array([0, 0], np.int64)
     atom = np.zeros(1, np.int32)
     ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
-    assert lib.lp_compile_batch(1, ptr(one), ptr(off), ptr(head), ptr(boff), ptr(atom), None, 2, None,
+    assert lib.lp_compile_batch(1, ptr(one), ptr(off), ptr(head), ptr(boff), ptr(atom), None, 4, None,
                                 ctypes.byref(out)) == 1  # unknown flag
     bad_off = np.array([1, 1], np.int64)
     assert lib.lp_compile_batch(1, ptr(one), ptr(bad_off), ptr(head), ptr(boff), ptr(atom), None, 0, None,

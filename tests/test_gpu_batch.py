@@ -18,8 +18,8 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_util import DEV, gpu_stable  # noqa: E402
 
 
-def _run_batch(progs, host=False, max_iters=1 << 30, full_sweep=False):
-    with lp.Batch(progs, full_sweep=full_sweep) as B:
+def _run_batch(progs, host=False, max_iters=1 << 30, full_sweep=False, from_m0=False):
+    with lp.Batch(progs, full_sweep=full_sweep, from_m0=from_m0) as B:
         n = B.n_programs
         if host:
             mask = np.zeros(max(B.total_mask_words, 1), dtype=np.uint64)
@@ -93,10 +93,21 @@ def test_reduced_uneven_batch_against_oracle(full_sweep):
     _check_oracle(progs, got, ns)
 
 
+def _chain(length=20):
+    # one guessed atom whose guess 1 makes a chain of `length` rules fire one after another: from
+    # F (every guessed row zero) that column needs length + 2 iterations
+    text = "p0 :- not q. " + " ".join(f"p{i + 1} :- p{i}." for i in range(length))
+    return parse(text)
+
+
 def test_no_fixpoint_reports_error():
-    progs = [small_definite(2)]
-    with pytest.raises(lp.LPError):
-        _run_batch(progs, max_iters=2)
+    with pytest.raises(lp.LPError):  # Algorithm 2 from M_0: 86 theta applications
+        _run_batch([small_definite(2)], max_iters=2, from_m0=True)
+    with pytest.raises(lp.LPError):  # from F: more than 20 in the guessed column
+        _run_batch([_chain()], max_iters=2)
+    got, ns, it, _ = _run_batch([_chain(), small_definite(2)])
+    assert it[0] > 20 and it[1] == 1  # a definite program is at F already: one confirming pass
+    _check_oracle([_chain(), small_definite(2)], got, ns)
 
 
 def test_too_many_guesses_rejected():
@@ -146,16 +157,20 @@ def test_single_and_few_large_programs(full_sweep):
 
 def test_frontier_equals_full_sweep():
     # the frontier schedule (programs with k <= 8) against the full sweep on the same programs:
-    # the same stable masks and the same per-program iteration counts, with programs of k = 9 and
-    # 10 (rows wider than 32 bytes, full sweep in both) mixed in; and the frontier evaluates far
-    # fewer rows than the full sweeps would
+    # from M_0 the same stable masks and the same per-program iteration counts, from F (the
+    # default) the same masks in at most as many iterations; programs of k = 9 and 10 (rows wider
+    # than 32 bytes, full sweep in all three) mixed in; and the frontier evaluates far fewer rows
+    # than the full sweeps would
     progs = program_batch(seed=13, count=60, n_lo=100, n_hi=4000)
     progs += [normal_program(seed=31, n=2000, n_rules=6000, k=9, per_atom=2),
               normal_program(seed=32, n=1500, n_rules=4500, k=10, per_atom=2)]
-    a, na, ia, _ = _run_batch(progs)
+    a, na, ia, _ = _run_batch(progs, from_m0=True)
     b, nb, ib, _ = _run_batch(progs, full_sweep=True)
+    f, nf, itf, _ = _run_batch(progs)
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
-    assert np.array_equal(na, nb) and np.array_equal(ia, ib)
+    assert all(np.array_equal(x, y) for x, y in zip(f, b))
+    assert np.array_equal(na, nb) and np.array_equal(ia, ib) and np.array_equal(nf, nb)
+    assert np.all(itf >= 1) and np.all(itf <= ib) and np.array_equal(itf[-2:], ib[-2:])
     _check_oracle(progs[-2:], a[-2:], na[-2:])
     with lp.Batch(progs[:60]) as B:
         m = torch.zeros(max(B.total_mask_words, 1), dtype=torch.int64, device=DEV)
@@ -168,7 +183,7 @@ def test_frontier_equals_full_sweep():
 
 def test_frontier_no_fixpoint_reports_error():
     with pytest.raises(lp.LPError):
-        _run_batch([normal_program(seed=21, n=400, n_rules=1200, k=5, per_atom=2)], max_iters=1)
+        _run_batch([normal_program(seed=21, n=400, n_rules=1200, k=5, per_atom=2)], max_iters=1, from_m0=True)
 
 
 def _solve(B, max_iters=1 << 30):
@@ -181,19 +196,27 @@ def _solve(B, max_iters=1 << 30):
     return mask_t.cpu().numpy().copy(), ns_t.cpu().numpy()[:n].copy(), it_t.cpu().numpy()[:n].copy()
 
 
-def test_frontier_repeated_solves_keep_rest_state():
-    # one handle, several solves: the frontier's buffers rest between solves and each solve
-    # restores the rows it changed; a solve stopped by max_iters leaves the handle usable
-    progs = program_batch(seed=17, count=30, n_lo=100, n_hi=3000)
+@pytest.mark.parametrize("from_m0", [True, False])
+def test_frontier_repeated_solves_keep_rest_state(from_m0):
+    # one handle, several solves: the frontier's buffers rest between solves (at M_0's guess-
+    # independent part, or at F) and each solve restores the rows it changed; a solve stopped by
+    # max_iters leaves the handle usable
+    progs = program_batch(seed=17, count=30, n_lo=100, n_hi=3000) + [_chain()]
     with lp.Batch(progs, full_sweep=True) as F:
         ref = _solve(F)
     assert ref[2].max() > 2
-    with lp.Batch(progs) as B:
+
+    def same(got):
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+        if from_m0:
+            assert np.array_equal(got[2], ref[2])
+        else:
+            assert np.all(got[2] >= 1) and np.all(got[2] <= ref[2])
+
+    with lp.Batch(progs, from_m0=from_m0) as B:
         for _ in range(3):
-            got = _solve(B)
-            assert all(np.array_equal(x, y) for x, y in zip(got, ref))
+            same(_solve(B))
         with pytest.raises(lp.LPError):
             _solve(B, max_iters=2)
         for _ in range(2):
-            got = _solve(B)
-            assert all(np.array_equal(x, y) for x, y in zip(got, ref))
+            same(_solve(B))

@@ -1,6 +1,6 @@
 """Reuse of small device buffers and pinned control blocks across handles.
 
-liblp keeps the blocks (up to 4 MiB each) of a freed handle for later handles instead of
+liblp keeps the blocks (up to 256 KiB each) of a freed handle for later handles instead of
 returning them to the driver. A reused block holds whatever the last handle left in it, so
 handles compiled into reused blocks must still solve exactly as the oracle does; repeated
 compile-solve-free rounds must not grow the memory in use; and with LP_ALLOC_CACHE=0 every

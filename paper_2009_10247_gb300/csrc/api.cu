@@ -995,6 +995,8 @@ lp_status lp_stable_models(lp_program* p, const uint64_t* guesses, int64_t n_gue
     a.fr_last = (int32_t*)(a.fr_dirty + (items + 31) / 32);
     // from F the fact rows and their consequences are already in place: the guessed rows seed
     a.fr_F = from_F ? p->fr_F : nullptr;
+    a.guess_rows = p->fr_seed + hm.n_fact_rows;  // the seed list ends with the guessed rows
+    a.n_guess_rows = (int32_t)hm.guess_row.size();
     a.fr_seed = from_F ? p->fr_seed + hm.n_fact_rows : p->fr_seed;
     a.n_seed = from_F ? p->fr_nseed - hm.n_fact_rows : p->fr_nseed;
     a.fr_wide = a.fr_last + wave_tiles;

@@ -149,6 +149,8 @@ struct StableArgs {
   const int32_t* fr_seed;   // n_seed rows the first list starts from: the fact rows, then the
   int32_t n_seed;           // guessed rows (only the guessed rows when starting from fr_F)
   const uint32_t* fr_F;     // ceil(n_pad / 32) or NULL: the guess-independent fixpoint to start from
+  const int32_t* guess_rows;  // n_guess_rows: the guessed barred rows (row_tag >= 0)
+  int32_t n_guess_rows;
 };
 
 constexpr int kStableBlock = 256;

@@ -642,38 +642,41 @@ __global__ void __launch_bounds__(kFrontierBlock, 1) stable_frontier_kernel(Stab
     }
 
     // ---- 5. the wave's changed items and guessed rows back to the rest state
+    // the bitmap wpw words per warp step, a word per lane, wpw the power of two (at most 32) that
+    // spreads the words over all warps (a word per warp step made every warp wait on ~80
+    // dependent loads on the 2^16-guess program: 55 us of a 137 us solve; 32 per step left most
+    // warps idle where few tiles hold many changed rows)
     const long long n_dw = ((long long)cw * n_pad + 31) / 32;
-    for (long long q = gwarp; q < n_dw; q += nwarps) {
-      unsigned bits = 0u;
-      if (lane == 0) {
-        bits = a.fr_dirty[q];
-        if (bits) a.fr_dirty[q] = 0u;
-      }
-      bits = __shfl_sync(FULL, bits, 0);
-      while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const long long item = q * 32 + b;
-        const uint64_t v = rest_word(a, (int)(item % n_pad));
-        for (int w = lane; w < W; w += 32) {
-          a.X0[item * W + w] = v;
-          a.X1[item * W + w] = v;
+    int wpw = 1;
+    while (wpw < 32 && (long long)wpw * nwarps < n_dw) wpw <<= 1;
+    for (long long qb = (long long)gwarp * wpw; qb < n_dw; qb += (long long)nwarps * wpw) {
+      const long long q = qb + lane;
+      unsigned bits = lane < wpw && q < n_dw ? a.fr_dirty[q] : 0u;
+      if (bits) a.fr_dirty[q] = 0u;
+      unsigned lanes = __ballot_sync(FULL, bits != 0u);
+      while (lanes) {  // uniform: the warp restores the set bits of one lane's word at a time
+        const int src = __ffs(lanes) - 1;
+        lanes &= lanes - 1;
+        unsigned wbits = __shfl_sync(FULL, bits, src);
+        while (wbits) {
+          const int b = __ffs(wbits) - 1;
+          wbits &= wbits - 1;
+          const long long item = (qb + src) * 32 + b;
+          const uint64_t v = rest_word(a, (int)(item % n_pad));
+          for (int w = lane; w < W; w += 32) {
+            a.X0[item * W + w] = v;
+            a.X1[item * W + w] = v;
+          }
         }
       }
     }
-    for (long long rb = (long long)gwarp * 32; rb < n_pad; rb += (long long)nwarps * 32) {
-      const long long r = rb + lane;
-      const int tag = r < n_pad ? __ldg(a.row_tag + r) : -1;
-      unsigned m = __ballot_sync(FULL, tag >= 0);
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const long long row = rb + b;
-        for (int k = lane; k < cw * W; k += 32) {
-          const long long o = ((long long)(k >> log2W) * n_pad + row) * W + (k & (W - 1));
-          a.X0[o] = 0ull;
-          a.X1[o] = 0ull;
-        }
+    // the guessed rows back to zero in every tile of the wave
+    for (long long u = gwarp; u < a.n_guess_rows; u += nwarps) {
+      const int row = __ldg(a.guess_rows + (int)u);
+      for (int k = lane; k < cw * W; k += 32) {
+        const long long o = ((long long)(k >> log2W) * n_pad + row) * W + (k & (W - 1));
+        a.X0[o] = 0ull;
+        a.X1[o] = 0ull;
       }
     }
     // every read of the list sizes and wide counts was before the last barrier

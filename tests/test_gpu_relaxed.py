@@ -128,7 +128,7 @@ def test_full_size_hardening_equals_least_model():
         if ok:
             converged.append(j)
     assert len(converged) >= 0.9 * b, f"only {len(converged)} of {b} columns reach the fixpoint within {T} steps"
-    for j in converged[:: max(1, len(converged) // 8)]:  # the judge: the least model of the fact subset
+    for j in converged[:: max(1, len(converged) // 8)]:  # the reference: the least model of the fact subset
         subset = np.zeros(s.n, dtype=bool)
         subset[s.owner[fact[v0[fact, j] > 0.5]]] = True
         lm, _ = oracle.least_model(prog, init=subset, std=s)

@@ -288,3 +288,36 @@ def test_normal_program_generator_shape():
     st4, m4, it4 = oracle.stable_models_alg23(p, guesses=np.arange(64, dtype=np.uint64))
     st5, m5 = oracle.stable_models_gl(p, guesses=np.arange(0, 64, 7, dtype=np.uint64))
     assert np.array_equal(st4[::7], st5) and np.array_equal(m4[::7], m5)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_iteration_from_guess_independent_fixpoint(seed):
+    # The reading behind the default stable schedule: F, the fixpoint from the fact rows with every
+    # guessed row zero, lies below every column's least fixpoint, so Algorithm 2 started from F with
+    # the guess's bits on the guessed rows reaches the column's fixpoint of Algorithm 2 from M_0 --
+    # the same stable bits and models -- in at most as many iterations.
+    rng = np.random.default_rng(900 + seed)
+    prog = tiny_random(900 + seed, n_atoms=int(rng.integers(3, 40)), n_rules=int(rng.integers(2, 90)), max_body=4,
+                       p_fact=0.15, p_neg=0.15)
+    s = oracle.standardize(prog)
+    rows = s.guess_rows()
+    v0 = oracle.initial_vector(s)
+    assert not v0[rows].any()  # guessed rows are zero in the fact vector
+    F, _, ok = oracle.alg1(s, v0)
+    assert ok
+    st4, _, it4 = oracle.stable_models_alg23(prog)
+    for g in range(1 << len(rows)):
+        m0 = v0.copy()
+        bits = np.array([(g >> j) & 1 for j in range(len(rows))], dtype=np.uint8)
+        m0[rows] = bits
+        fix0, it0, ok0 = oracle.alg1(s, m0)
+        start = F.copy()
+        start[rows] = bits
+        assert np.all(m0 <= start) and np.all(start <= fix0)  # M_0 <= S <= the column's fixpoint
+        fixF, itF, okF = oracle.alg1(s, start)
+        assert ok0 and okF and np.array_equal(fixF, fix0), g
+        assert itF <= it0 == it4[g]
+        # Algorithm 3 on the fixpoint from F gives the oracle's stable bit
+        q = np.nonzero(s.kind == oracle.ORC_BARRED)[0]
+        atom_rows = s.owner[q]
+        assert bool(np.all(fixF[atom_rows] != fixF[q])) == bool(st4[g])

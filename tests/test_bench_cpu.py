@@ -65,7 +65,22 @@ def test_traffic_lookup_follows_sources_and_row_map(tmp_path, monkeypatch):
     assert bench.measured_traffic("stable_kernel") is None  # no record
 
 
-@pytest.mark.parametrize("key", ["fixpoint_kernel", "stable_kernel", "batch_stable_kernel", "rx_forward_kernel"])
+def test_traffic_lookup_tells_variants_apart(tmp_path, monkeypatch):
+    # the batch kernel's frontier and full-sweep instantiations share a name: a record with a
+    # variant answers only a lookup of that variant, a record without one only a plain lookup
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    _write_record(str(tmp_path), "batch frontier", "batch_stable_kernel", "int z;")
+    path = os.path.join(str(tmp_path), "profiles", "traffic.json")
+    recs = json.load(open(path))
+    recs["batch frontier"]["variant"] = "frontier"
+    json.dump(recs, open(path, "w"))
+    assert bench.measured_traffic("batch_stable_kernel", variant="frontier") == 123
+    assert bench.measured_traffic("batch_stable_kernel", variant="full_sweep") is None
+    assert bench.measured_traffic("batch_stable_kernel") is None
+
+
+@pytest.mark.parametrize("key", ["fixpoint_kernel", "stable_kernel", "batch_stable_kernel", "rx_forward_kernel",
+                                 "stable_frontier_kernel", "fixpoint_sliced_kernel"])
 def test_committed_records_name_existing_sources(key):
     recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     assert any(r.get("kernel", k) == key for k, r in recs.items())

@@ -272,7 +272,8 @@ lp_status lp_batch_stable_models(lp_batch* batch, uint64_t* stable_mask, int64_t
 lp_status lp_batch_last_stats(const lp_batch* batch, int64_t* rows_evaluated, int64_t* entries_evaluated,
                               int64_t* bytes_touched, void* cuda_stream);
 
-/* Release a batch and its device memory (NULL is a no-op). */
+/* Release a batch and its device memory (NULL is a no-op; small buffers go to the cache that
+ * lp_free describes). */
 void lp_batch_free(lp_batch* batch);
 
 /*
@@ -442,8 +443,11 @@ lp_status lp_least_model_static(int32_t n_rows, const int32_t* row_ptr, const in
                                 const uint64_t* v0, uint64_t* out, int32_t max_iters, int32_t* iters_out,
                                 void* cuda_stream);
 
-/* Release a handle and its device memory (NULL is a no-op). Waits for no stream: the caller
- * must make sure no enqueued work still uses it. */
+/* Release a handle and its device memory (NULL is a no-op). It waits for the device to finish
+ * its work, as cudaFree does; then device buffers of up to 256 KiB go to a per-process cache
+ * that later handles reuse (at most 16 MiB in all, never returned before the process exits;
+ * LP_ALLOC_CACHE=0 in the environment turns the cache off) and the others back to the driver.
+ * The pinned host control block is kept for reuse the same way. */
 void lp_free(lp_program* prog);
 
 /* Diagnostics, no counterpart in the paper: checks the invariants the kernels rely on without
